@@ -1,0 +1,200 @@
+"""The FP64 oracle against what the paper and the mathematics fix (CPU only)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import spectral
+import synthetic
+import oracle_pins as P
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.mark.parametrize("name", list(P.FAST_PINS))
+def test_fast_pin(orc, name):
+    err = P.FAST_PINS[name](orc)
+    assert err <= P.PIN_LIMITS[name], f"{name}: {err} > {P.PIN_LIMITS[name]}"
+
+
+def test_one_step_general_pressure_law(orc):
+    # gamma != 1 exercises P(rho) = rho^gamma in the pressure term and the initialisation
+    assert P.one_step(orc, gamma=1.4) <= 1e-12
+
+
+def test_fixed_point_is_bitwise(orc):
+    assert P.fixed_point(orc, n=(5, 3)) == 0.0
+
+
+# ---------------------------------------------------------------- Section 5 pins
+
+@pytest.mark.parametrize("base", [(1.0, 0.0, 0.0), (1.0, 1.0, 1.0), (1.3, 0.4, -0.7)])
+@pytest.mark.parametrize("dx", [1e-6, 0.1])
+def test_lemma1_checkerboard_charpoly(base, dx):
+    """Lemma 1: det(zI - E(pi, pi)) = prod_i (z - w_i + 1)^3 (z^2 - w_i(1 - 8 a_i) z + w_i - 1)."""
+    om, al = (1.2, 1.15, 1.3), (0.075, 0.01, 0.2)
+    E = spectral.amplification_matrix((math.pi, math.pi), dx, 8.0, om, al, base)
+    zs = np.array([0.3 + 0.2j, -0.5 + 1j, 1.1, 2.0 - 0.3j, -0.8])
+    det = np.array([np.linalg.det(z * np.eye(15) - E) for z in zs])
+    ref = spectral.checkerboard_charpoly(zs, om, al)
+    assert np.max(np.abs(det - ref) / np.abs(ref)) < 1e-12
+
+
+def test_lemma1_stability_box():
+    """Lemma 1: the checkerboard spectrum is in the unit disk iff w in [0, 2] and a in [0, 1/4]."""
+    def rad(w, a):
+        E = spectral.amplification_matrix((math.pi, math.pi), 1e-3, 8.0, (w,) * 3, (a,) * 3)
+        return np.max(np.abs(np.linalg.eigvals(E)))
+    assert rad(1.15, 0.1) <= 1 + 1e-12
+    assert rad(1.99, 0.25) <= 1 + 1e-9
+    assert rad(1.5, 0.26) > 1 + 1e-6
+    assert rad(2.05, 0.1) > 1 + 1e-6
+    assert rad(1.0, -0.01) > 1 + 1e-6
+
+
+def test_lemma2_determinant_expansion():
+    """Lemma 2: det(z - E(t, t)) = (z^2 - 2z + 1 + 2 S t^2 (z - 1) + 2 t^2/mu^2)(z - 1) z^12 + O(t^3).
+
+    S = a_rho + a_qx + a_qy, relaxation scheme (all omega = 1), dx -> 0.  The
+    printed polynomial lacks the constant "+1" of (z - 1)^2; without it
+    E(0) would have the eigenvalue 2, while E(0) is the projection on the
+    equilibria (eigenvalues 1, 1, 1 and twelve 0).
+    """
+    mu, al, om = 8.0, (0.075, 0.0017, 0.003), (1.0, 1.0, 1.0)
+    s = sum(al)
+
+    def paper(z, t):
+        return (z * z - 2 * z + 1 + 2 * s * t * t * (z - 1) + 2 * t * t / mu ** 2) * (z - 1) * z ** 12
+
+    for z in (0.5 + 0.1j, 1.3 - 0.2j, 0.9):
+        errs = []
+        for t in (2e-2, 1e-2, 5e-3):
+            E = spectral.amplification_matrix((t, t), 1e-6, mu, om, al, (1.0, 0.0, 0.0))
+            errs.append(abs(np.linalg.det(z * np.eye(15) - E) - paper(z, t)))
+        # the remainder is at least third order: halving t divides it by >= 8
+        assert errs[0] / errs[1] > 7.0 and errs[1] / errs[2] > 7.0, errs
+
+
+def test_lemma2_lowfreq_roots():
+    """Lemma 2 roots: z = 1 +- i sqrt(2)/mu t + z2 t^2 on the diagonal (omega = 1).
+
+    The imaginary part is the paper's.  Solving the paper's own determinant to
+    the order it is correct (the constant term 2 (a_qx + a_qy) t^4 / mu^2 is of
+    the same order as the kept ones) gives z2 = -(a_rho + (a_qx + a_qy)/2);
+    the printed -(a_rho + a_qx + a_qy) drops that term.  Along a direction b:
+    z = 1 +- i xi dx / mu - (a_rho + a_qx cos^2 b + a_qy sin^2 b) (xi dx)^2 / 2.
+    """
+    mu, al, om = 8.0, (0.075, 0.0017, 0.003), (1.0, 1.0, 1.0)
+    for t in (1e-2, 5e-3):
+        E = spectral.amplification_matrix((t, t), 1e-6, mu, om, al, (1.0, 0.0, 0.0))
+        ev = np.linalg.eigvals(E)
+        z2 = -(al[0] + 0.5 * (al[1] + al[2]))
+        for sgn in (1, -1):
+            pred = 1 + sgn * 1j * math.sqrt(2) / mu * t + z2 * t * t
+            assert np.min(np.abs(ev - pred)) < 5 * t ** 3
+        # the paper's imaginary part alone, to second order
+        best = ev[np.argmin(np.abs(ev - (1 + 1j * math.sqrt(2) / mu * t)))]
+        assert abs(best.imag - math.sqrt(2) / mu * t) < 5 * t ** 3
+    for b in (0.3, 1.1):
+        xi = 1e-2
+        E = spectral.amplification_matrix((xi * math.cos(b), xi * math.sin(b)), 1e-6, mu, om, al)
+        ev = np.linalg.eigvals(E)
+        z2 = -0.5 * (al[0] + al[1] * math.cos(b) ** 2 + al[2] * math.sin(b) ** 2)
+        for sgn in (1, -1):
+            assert np.min(np.abs(ev - (1 + sgn * 1j * xi / mu + z2 * xi * xi))) < 5 * xi ** 3
+
+
+def test_lemma2_mu_bound_separates_stability():
+    """Low-frequency acoustic modes grow below the mu bound and decay above it."""
+    al, om = (0.05, 0.01, 0.01), (1.0, 1.0, 1.0)
+    bound = (al[0] + 0.5 * (al[1] + al[2])) ** -0.5
+    t = 2e-3
+
+    def acoustic_modulus(mu):
+        E = spectral.amplification_matrix((t, t), 1e-6, mu, om, al)
+        ev = np.linalg.eigvals(E)
+        return np.abs(ev[np.argmin(np.abs(ev - (1 + 1j * math.sqrt(2) / mu * t)))])
+    assert acoustic_modulus(1.1 * bound) < 1.0
+    assert acoustic_modulus(0.9 * bound) > 1.0
+
+
+# ------------------------------------------------------------------ Section 6 pins
+
+def _golden_table1():
+    rows = []
+    with open(os.path.join(GOLDEN, "table1_tgv_convergence.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append(line.split())
+    return rows
+
+
+def test_golden_table1_is_self_consistent():
+    rows = _golden_table1()
+    data = [r for r in rows if r[0] != "average"]
+    avg = [float(v) for v in rows[-1][1:] if v != "-"]
+    for col, printed in zip((3, 5, 7), avg):
+        orders = [float(r[col]) for r in data if r[col] != "-"]
+        assert abs(np.mean(orders) - printed) < 0.01
+        # the dx column is 2 pi / N
+    for r in data:
+        assert abs(float(r[1]) - 2 * math.pi / int(r[0])) < 1e-4
+
+
+@pytest.mark.slow
+def test_tgv_second_order_convergence(orc):
+    """Table 1: second-order convergence of the Taylor-Green vortex (fitted slope >= 1.8).
+
+    Same setting as Table 1 (mu = 8, omega_q = 23/20, the three
+    (omega_rho, alpha_rho) pairs of Eq. params), with nu = 0.01 and t = 0.5.
+    As in Table 1 the pairwise orders oscillate (acoustic waves of speed
+    1/dx leave a resolution-dependent phase at the final time), so the gate is
+    the least-squares slope over N = 32..192.
+    """
+    printed = [float(v) for v in _golden_table1()[-1][1:] if v != "-"]
+    ns = [32, 48, 64, 96, 128, 192]
+    for (w_r, a_r), paper_order in zip(((1.0, 0.05), (1.2, 0.075), (1.5, 0.15)), printed):
+        errs = [P.tgv_error(orc, n, 0.5, omega_rho=w_r, alpha_rho=a_r)[0] for n in ns]
+        slope = np.polyfit(np.log([2 * math.pi / n for n in ns]), np.log(errs), 1)[0]
+        assert slope >= 1.8, (w_r, a_r, errs, slope)
+        assert abs(slope - paper_order) < 0.3, (slope, paper_order)
+
+
+def test_viscosity_relation(orc):
+    """Prop. 1: nu = 2 mu a_q (1/w_q - 1/2); a shear wave decays like exp(-nu k^2 t) + O(dx^2)."""
+    nu, t_final = 0.05, 0.3
+    errs = []
+    for n in (16, 32, 64):
+        u, phi, dx = synthetic.shear_wave(n, 0.5, 1, axis=0)
+        p = oracle.make_params((n, n), dx, nu=nu)
+        nsteps = int(round(t_final / p.dt))
+        _, um, _ = orc.macros(p, orc.run(p, orc.init(p, u, phi), nsteps))
+        amp = np.sum(um[1] * u[1]) / np.sum(u[1] * u[1])
+        errs.append(abs(amp - math.exp(-nu * nsteps * p.dt)))
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, errs
+
+
+def test_invariants_on_uniform_state(orc):
+    n = (6, 5)
+    dx = 0.25
+    p = P._params(n, dx)
+    rho0, q0 = 1.0 + dx * dx * 3.0, np.array([0.4, -0.3])
+    u = np.empty((2, n[1], n[0]))
+    u[0], u[1] = q0[0] / rho0, q0[1] / rho0
+    f = orc.init(p, u, np.full((n[1], n[0]), 3.0))
+    inv = orc.invariants(p, f)
+    N = n[0] * n[1]
+    assert abs(inv[0] - N * rho0) < 1e-12
+    assert np.allclose(inv[1:3], N * q0, rtol=1e-12, atol=1e-12)
+    assert inv[3] == 0.0
+    assert abs(inv[4] - N * 0.5 * (q0 @ q0) / rho0 * dx * dx) < 1e-12
+    assert abs(inv[5] - math.sqrt(q0 @ q0) / rho0) < 1e-12
+    assert inv[6] == 0.0
+    assert abs(inv[7] - N * (rho0 - 1.0)) < 1e-12
+    f[1, 2, 3, 4] = np.nan
+    f[0, 0, 0, 0] = np.inf
+    inv = orc.invariants(p, f)
+    assert inv[6] == 2.0
