@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Throughput of the fused collide-and-stream update of the vectorial D2Q5 scheme.
+
+Workload (one GPU): periodic double shear layer on a 4096^2 lattice, 3 fields x
+5 velocities = 15 populations per node stored in FP32 (deviations from the rest
+equilibrium), nu = 1e-4, mu = 8, omega_rho = 6/5, alpha_rho = 3/40,
+omega_q = 23/20 (Section 6.1 defaults), synthetic seeded input.  One step = one
+lattice update of every node (relaxation + transport).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vlbm|reference]
+
+--impl reference times the FP64 CPU oracle (test infrastructure, as it stands)
+on the same workload on the host cores, each step one full-lattice update,
+bounded in total time.  Under torchrun (N > 1) each rank advances its own
+independent replica of the lattice (no data-path collective); the elapsed time
+is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS & % HBM roofline; time-to-t at stated L2 error vs plain FP32 LBM"
+UNIT = "GLUPS"
+BYTES_PER_NODE = {"fp64": 240, "fp32": 120, "fp16": 60, "bf16": 60}   # 15 populations read + written
+KERNEL = {"fp32": "k_stream_collide_2d_vec<float, false>", "fp64": "k_stream_collide_2d_vec<double, false>",
+          "fp16": "k_stream_collide_2d_vec<__half, false>", "bf16": "k_stream_collide_2d_vec<__nv_bfloat16, false>"}
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["vlbm", "reference"], default="vlbm")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--precision", choices=list(BYTES_PER_NODE), default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--reference-seconds", type=float, default=150.0, help="cap on the reference arm's timed steps")
+    return ap.parse_args()
+
+
+def workload_config(args, extra=None):
+    cfg = {
+        "workload": f"double shear layer {args.n}x{args.n} periodic, D2Q5 vectorial (3 fields x 5 velocities)",
+        "lattice": [args.n, args.n],
+        "populations_per_node": 15,
+        "storage": args.precision,
+        "nu": 1e-4, "mu": 8.0, "omega_rho": 1.2, "alpha_rho": 0.075, "omega_q": 1.15,
+        "init": "u_x = tanh(80(y - pi/2)) (y <= pi) / tanh(80(3pi/2 - y)), u_y = 0.05 sin x, phi = 0",
+        "l2": "working set 2 lattices x {:.2f} GB > 126 MB L2: no flush needed".format(
+            args.n * args.n * BYTES_PER_NODE[args.precision] / 2 / 1e9),
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------- distributed plumbing
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+        return dist
+    return None
+
+
+def max_over_ranks(value, dist, device=None):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.buf = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.buf, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.buf = ""
+
+    def summary(self):
+        if not self.buf:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        rows = [r for r in csv.reader(io.StringIO(self.buf)) if len(r) >= 9]
+        sm = []
+        sm_max = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                sm_max = float(r[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        loaded = [s for s in sm if sm_max and s > 0.3 * sm_max] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": sm_max,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline inputs
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2607_24059_b300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                h.update(fn.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, n, digest):
+    """DRAM bytes per launch from the committed ncu summary, if taken on this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    for e in d.get("entries", []):
+        if e.get("kernel") == kernel and e.get("source_digest") == digest and e.get("n") == n:
+            return float(e["dram_bytes_per_launch"])
+    return None
+
+
+# ---------------------------------------------------------------- CPU oracle baseline
+def oracle_sample(args, seconds):
+    """GLUPS of the FP64 oracle on the same lattice, on the host cores, for ~seconds."""
+    import oracle
+    import synthetic
+    orc = oracle.default()
+    u, phi, dx = synthetic.double_shear_layer(args.n)
+    p = oracle.make_params((args.n, args.n), dx, nu=1e-4)
+    f = orc.init(p, u, phi)
+    t0 = time.perf_counter()
+    f = orc.run(p, f, 1)                      # warm-up step, also sizes the sample
+    t1 = time.perf_counter() - t0
+    m = int(max(1, min(200, seconds / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    f = orc.run(p, f, m)
+    el = time.perf_counter() - t0
+    return {"value": args.n * args.n * m / el / 1e9, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+            "sample": f"{args.n}^2 double shear layer, {m} FP64 oracle steps after 1 warm-up step "
+                      f"(plain C, OpenMP over rows, {orc.num_threads()} threads)", "seconds": el}
+
+
+# ---------------------------------------------------------------- the two arms
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import synthetic
+    orc = oracle.default()
+    u, phi, dx = synthetic.double_shear_layer(args.n)
+    p = oracle.make_params((args.n, args.n), dx, nu=1e-4)
+    f = orc.init(p, u, phi)
+    f = orc.run(p, f, max(1, min(args.warmup, 3)))
+    done = 0
+    t0 = time.perf_counter()
+    while done < args.steps:
+        f = orc.run(p, f, 1)
+        done += 1
+        if time.perf_counter() - t0 > args.reference_seconds:
+            break
+    el = time.perf_counter() - t0
+    value = args.n * args.n * done / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": done,
+        "steps_requested": args.steps, "warmup": max(1, min(args.warmup, 3)), "ms_per_step": el / done * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, {"storage": "fp64 (oracle)"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+                         "sample": f"{done} full-lattice FP64 oracle steps (capped at {args.reference_seconds:.0f} s)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_vlbm(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    import paper_2607_24059_b300 as vlbm
+    import synthetic
+
+    n = args.n
+    u, phi, dx = synthetic.double_shear_layer(n)
+    lat = vlbm.Lattice((n, n), dx, nu=1e-4, precision=args.precision)
+    lat.init(torch.from_numpy(u).cuda())
+    # warm-up: W steps, then prime the CUDA graphs of both buffer parities
+    lat.step(args.warmup)
+    lat.step(64)
+    lat.step(1)
+    lat.step(64)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    # ---- device-resident timing (inputs already in HBM)
+    c0 = lat.launch_count()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        lat.step(args.steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = start.elapsed_time(end) / 1e3
+    launches = lat.launch_count() - c0
+    elapsed_max = max_over_ranks(elapsed, dist, "cuda")
+    nodes = n * n
+    value = world * nodes * args.steps / elapsed_max / 1e9
+    inv = lat.invariants()
+    assert inv[6] == 0, "non-finite populations after the timed steps"
+
+    # roofline of the stream-collide kernel (the only kernel in the timed region)
+    per_launch = elapsed / args.steps
+    bpn = BYTES_PER_NODE[args.precision]
+    achieved = bpn * nodes / per_launch / 1e9
+    peak, peak_kind = measured_peaks()
+    digest = source_digest()
+    traffic = profiled_traffic(KERNEL[args.precision], n, digest)
+
+    # ---- end to end through the C ABI with host buffers
+    u_host = torch.from_numpy(u.astype(np.float32)).pin_memory()
+    u_out = torch.empty_like(u_host).pin_memory()
+    hist = torch.zeros((args.steps, 8), dtype=torch.float64).pin_memory()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    vlbm.vlbm_init(lat.handle, u_host)                       # H2D of the step's input
+    for s in range(args.steps):
+        vlbm.vlbm_step_record(lat.handle, 1, 1, hist[s])     # step + fused invariants, D2H of 64 B
+    vlbm.vlbm_macros(lat.handle, None, u_out, None)          # D2H of the velocity field
+    torch.cuda.synchronize()
+    e2e_el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = world * nodes * args.steps / e2e_el / 1e9
+    assert np.all(np.isfinite(hist.numpy())) and np.all(np.isfinite(u_out.numpy()))
+    ubytes = u_host.numel() * u_host.element_size()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+        "data": "synthetic",
+        "config": workload_config(args, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                         "graph_prime_steps": 129}),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": traffic, "bytes_per_node": bpn,
+                     "kernel": KERNEL[args.precision], "avg_launch_ms": per_launch * 1e3,
+                     "source_digest": digest},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": ubytes / args.steps,
+                "d2h_bytes_per_step": 64 + ubytes / args.steps,
+                "how": "vlbm_init from pinned host u, per step vlbm_step_record (fused invariants, 64 B D2H), "
+                       "vlbm_macros to pinned host u"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(args, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    lat.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_vlbm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

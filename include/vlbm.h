@@ -1,0 +1,196 @@
+/*
+ * vlbm — C ABI of the B300 (sm_103a) implementation of the vectorial lattice
+ * Boltzmann scheme for incompressible Navier-Stokes (Aregba-Driollet,
+ * Bellotti, Natalini, Tenna): each conserved field (rho, q_x, q_y[, q_z])
+ * carries its own D2Q5 (3D: D3Q7) population set, relaxes toward its own
+ * equilibrium (Section 2, Eq. LBM_scheme) under the parabolic scaling
+ * dx^2 / dt = mu (Eq. parabolicScaling), then streams on a periodic
+ * Cartesian lattice with nodes at half-integer positions (i + 1/2) dx.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: VLBM_OK (0) on success, a positive warning code, or a
+ *    negative error code (VLBM_E*).  No exception crosses the ABI; no global
+ *    state; a handle is not thread-safe (one host thread at a time).
+ *  - Caller arrays are contiguous, x fastest: scalar fields (rho, phi) are
+ *    [ny][nx] (3D: [nz][ny][nx]); vector fields (u) are [d][ny][nx]
+ *    (3D: [d][nz][ny][nx]).  Their element type is given by a VLBM_DTYPE_*.
+ *  - Pointers may be device memory or host memory (pinned or pageable): the
+ *    library asks the CUDA driver which one it is.  Host arrays are staged
+ *    through a device buffer that the handle owns, and a call that reads
+ *    back into host memory synchronises the handle's stream before it
+ *    returns.  Device arrays are used in place, in stream order.
+ *  - All GPU work of a handle is enqueued on the stream given at creation
+ *    (or by vlbm_set_stream); NULL means the legacy default stream.
+ *  - The handle owns its population lattices and scratch buffers; the caller
+ *    owns every array it passes.  Nothing is retained after a call returns.
+ *  - The populations held by a handle are the post-relaxation values f*(t);
+ *    their moments equal those of f(t) because relaxation conserves them.
+ */
+#ifndef VLBM_H
+#define VLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define VLBM_OK            0
+#define VLBM_WSTABILITY    1   /* created; mu is below the low-frequency stability bound (Lemma 2) */
+#define VLBM_EINVAL       -1   /* null pointer, bad size, parameter outside its range */
+#define VLBM_ESTABILITY   -2   /* strict mode: mu below the low-frequency bound (Lemma 2) */
+#define VLBM_ENOMEM       -3   /* device or host allocation failed */
+#define VLBM_ECUDA        -4   /* a CUDA call failed; vlbm_last_error() has the message */
+#define VLBM_EDIVERGED    -5   /* a non-finite population was found (check requested) */
+#define VLBM_ETIMEOUT     -6   /* a bounded device wait gave up */
+#define VLBM_EUNSUPPORTED -7   /* valid request this build does not implement */
+
+/* ---- population storage ------------------------------------------------ */
+#define VLBM_FP64          0   /* FP64 storage of deviations from the rest equilibrium, FP64 arithmetic */
+#define VLBM_FP32          1   /* FP32 storage of deviations from the rest equilibrium, FP32 arithmetic */
+#define VLBM_FP16_SHIFTED  2   /* FP16 storage of scaled deviations, FP32 arithmetic */
+#define VLBM_BF16_SHIFTED  3   /* BF16 storage of scaled deviations, FP32 arithmetic */
+
+/* ---- element type of caller arrays ------------------------------------- */
+#define VLBM_DTYPE_F32     0
+#define VLBM_DTYPE_F64     1
+
+/* ---- vlbm_step flags ---------------------------------------------------- */
+#define VLBM_STEP_CHECK_FINITE 1  /* after stepping, scan the lattice; VLBM_EDIVERGED if non-finite */
+#define VLBM_STEP_NO_GRAPH     2  /* launch kernel by kernel instead of replaying a captured CUDA graph */
+
+/* Number of doubles written by vlbm_invariants. */
+#define VLBM_NUM_INVARIANTS 8
+
+typedef struct vlbm_handle vlbm_handle;
+
+/* Scheme parameters (Section 2).  Field index k: 0 = rho, 1 = q_x, 2 = q_y, 3 = q_z. */
+typedef struct {
+    int32_t dim;         /* 2 (D2Q5, 3 fields x 5 velocities) or 3 (D3Q7, 4 fields x 7) */
+    int32_t precision;   /* VLBM_FP64 | VLBM_FP32 | VLBM_FP16_SHIFTED | VLBM_BF16_SHIFTED */
+    int64_t n[3];        /* nodes along x, y, z (n[2] ignored in 2D); each >= 1; periodic */
+    double  dx;          /* space step > 0; the periodic box is n[d] * dx long */
+    double  mu;          /* parabolic scaling dx^2 / dt > 0 (Eq. parabolicScaling) */
+    double  nu;          /* target viscosity >= 0, used for every momentum field with alpha[k] < 0 */
+    double  omega[4];    /* relaxation parameter of field k, in (0, 2) (2 is inviscid, Prop. 1) */
+    double  alpha[4];    /* linear-equilibrium coefficient of field k, in [0, 1/4] (2D, Lemma 1)
+                            or [0, 1/6] (3D); a momentum field with alpha < 0 takes
+                            alpha = nu / (2 mu (1/omega - 1/2)) (Prop. 1) */
+    double  gamma;       /* pressure law P(rho) = rho^gamma, gamma >= 1 (Section 2) */
+    double  rho_bar;     /* reference density > 0 (rest state, Prop. 1) */
+    int32_t strict;      /* nonzero: a mu below the Lemma 2 bound is VLBM_ESTABILITY, not a warning */
+    int32_t reserved;    /* must be 0 */
+} vlbm_params;
+
+/* Quantities derived from vlbm_params by vlbm_params_check. */
+typedef struct {
+    double  dt;                   /* dx^2 / mu */
+    double  alpha[4];             /* resolved alpha per field */
+    double  viscosity[4];         /* 2 mu alpha_k (1/omega_k - 1/2), the diffusion of field k (Prop. 1) */
+    double  mu_min;               /* (alpha_rho + min_k alpha_qk)^(-1/2): low-frequency acoustic bound */
+    int64_t nodes;                /* n[0] n[1] (n[2]) */
+    int32_t populations_per_node; /* 15 (2D) or 28 (3D) */
+    int32_t bytes_per_population; /* 8, 4 or 2 */
+    size_t  lattice_bytes;        /* bytes of one population lattice */
+} vlbm_derived;
+
+/* Fill *p with the parameters of Section 6.1: mu = 8, omega_rho = 6/5,
+ * alpha_rho = 3/40, omega_q = 23/20 with alpha_q from nu (Prop. 1),
+ * gamma = 1, rho_bar = 1, non-strict.  n has dim entries.  Never fails on a
+ * non-null p. */
+void vlbm_params_default(vlbm_params* p, int32_t dim, const int64_t* n, double dx, double nu, int32_t precision);
+
+/* Validate *p and fill *out (may be NULL).  Host only: makes no CUDA call.
+ * Returns VLBM_OK, VLBM_WSTABILITY, VLBM_EINVAL or VLBM_ESTABILITY.
+ * Ranges: omega in (0, 2) (Section 2; 2 excluded by Prop. 1), alpha in
+ * [0, 1/4] (2D) / [0, 1/6] (3D) (Lemma 1), gamma >= 1, dx, mu, rho_bar > 0. */
+int vlbm_params_check(const vlbm_params* p, vlbm_derived* out);
+
+/* Create a handle: validates *p, allocates two population lattices and the
+ * scratch buffers on the current CUDA device, enqueued on `stream`
+ * (a cudaStream_t, NULL for the legacy stream).  The lattice starts zeroed
+ * (the rest state rho = rho_bar, q = 0); call vlbm_init to set a flow.
+ * On failure *out is NULL and nothing is leaked. */
+int vlbm_create(const vlbm_params* p, void* stream, vlbm_handle** out);
+
+/* Release every buffer of h (after its stream's work completes).  NULL is a no-op. */
+void vlbm_destroy(vlbm_handle* h);
+
+/* Move all further work of h onto `stream`. */
+int vlbm_set_stream(vlbm_handle* h, void* stream);
+
+/* Initialise at equilibrium (end of Section 2) from a velocity field u
+ * ([d][..][nx]) and an optional pressure-like potential phi ([..][nx],
+ * NULL means 0): P(rho) = P(rho_bar) + dx^2 rho_bar phi (Prop. 1),
+ * q = rho u, f = f^eq(rho, q).  Resets the step counter to 0. */
+int vlbm_init(vlbm_handle* h, const void* u, const void* phi, int32_t dtype);
+
+/* Advance nsteps >= 0 time steps (relaxation then transport each).  Enqueued
+ * asynchronously unless VLBM_STEP_CHECK_FINITE is set (then it synchronises
+ * and returns VLBM_EDIVERGED if any population is not finite). */
+int vlbm_step(vlbm_handle* h, int64_t nsteps, int32_t flags);
+
+/* Advance nsteps like vlbm_step and record, for every step s (0-based within
+ * the call) with s % every == 0, the invariants of the state that step
+ * produces (time step0 + s + 1: the moments of the transported populations,
+ * which relaxation conserves) into history[(s / every) * 8 + i], in the
+ * layout of vlbm_invariants.  The reduction is fused into the step kernel:
+ * it reads no lattice data beyond what the step reads (row a6 of the hot
+ * path), plus one small final-reduction kernel per record.  history holds
+ * ceil(nsteps / every) records; it may be device memory, pinned host memory
+ * (written asynchronously: valid once the handle's stream has synchronised)
+ * or pageable host memory (the call synchronises before returning).
+ * every >= 1; nsteps = 0 records nothing. */
+int vlbm_step_record(vlbm_handle* h, int64_t nsteps, int64_t every, double* history);
+
+/* Macroscopic fields at the current step: rho, u = q / rho and
+ * phi = (P(rho) - P(rho_bar)) / (dx^2 rho_bar); any pointer may be NULL. */
+int vlbm_macros(vlbm_handle* h, void* rho, void* u, void* phi, int32_t dtype);
+
+/* Reduce the lattice in FP64 into out[8] (host or device pointer):
+ *   { sum rho, sum q_x, sum q_y, sum q_z, E_kin = 1/2 sum |q|^2/rho dx^d,
+ *     max |u|, number of nodes holding a non-finite population,
+ *     sum (rho - rho_bar) }.
+ * Sums run over finite nodes only, in a fixed order (deterministic). */
+int vlbm_invariants(vlbm_handle* h, double* out);
+
+/* Step counter and time t = step * dx^2 / mu.  Either pointer may be NULL. */
+int vlbm_time(const vlbm_handle* h, int64_t* step, double* t);
+
+/* Opaque checkpoint of h: a header (format, sizes, precision, step) followed
+ * by the raw population lattice.  vlbm_state_bytes gives the size;
+ * vlbm_set_state accepts only a checkpoint of an identical configuration
+ * and restores the populations and the step counter bit for bit. */
+size_t vlbm_state_bytes(const vlbm_handle* h);
+int vlbm_get_state(vlbm_handle* h, void* dst, size_t bytes);
+int vlbm_set_state(vlbm_handle* h, const void* src, size_t bytes);
+
+/* Export the populations f*(t) as [k][l][..][nx] (k field, l velocity in the
+ * order rest, +x, -x, +y, -y(, +z, -z)).  deviation = 0: absolute values;
+ * deviation = 1: f - f^eq(rho_bar, 0), the quantity the FP32 and shifted
+ * formats store (exact for those formats when dtype is wide enough). */
+int vlbm_get_populations(vlbm_handle* h, void* dst, int32_t dtype, int32_t deviation);
+
+/* Number of kernel launches this handle has issued (graph replays count
+ * each kernel they contain). */
+int vlbm_launch_count(const vlbm_handle* h, int64_t* count);
+
+/* Tuning and test options.  VLBM_OPT_KERNEL selects the step kernel:
+ * 0 = automatic (vectorised when n_x is a multiple of the vector width,
+ * 16 bytes in 2D and 8 bytes in 3D), 1 = one thread per node (any size),
+ * 2 = vectorised (VLBM_EINVAL when n_x does not allow it).  Both compute the
+ * same arithmetic in the same order, so their results are bitwise equal. */
+#define VLBM_OPT_KERNEL 0
+int vlbm_set_option(vlbm_handle* h, int32_t key, int64_t value);
+
+/* Static text of a status code; message of the last failure of h. */
+const char* vlbm_strerror(int code);
+const char* vlbm_last_error(const vlbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VLBM_H */

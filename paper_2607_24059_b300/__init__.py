@@ -1,0 +1,113 @@
+"""B300-native vectorial lattice Boltzmann scheme for incompressible Navier-Stokes.
+
+The scheme (Aregba-Driollet, Bellotti, Natalini, Tenna, Section 2): every
+conserved field (rho, q_x, q_y[, q_z]) carries its own D2Q5 (3D: D3Q7)
+population set, relaxes toward its own equilibrium with its own omega, and
+streams on a periodic Cartesian lattice, with dt = dx^2 / mu.
+
+The compute path is the C-ABI library libvlbm.so (include/vlbm.h) built from
+hand-written sm_103a CUDA kernels; this package only binds it.  `Lattice` is a
+convenience wrapper over the same calls.
+"""
+from __future__ import annotations
+
+from . import _binding
+from ._binding import *  # noqa: F401,F403  (the C ABI, same names)
+from ._binding import VlbmError, PRECISIONS
+
+__all__ = list(_binding.EXPORTED) + ["Lattice", "VlbmError", "PRECISIONS"]
+
+
+class Lattice:
+    """One periodic lattice on the current CUDA device (a vlbm handle).
+
+    Parameters follow vlbm_params; `n` is (nx, ny) or (nx, ny, nz).  Arrays
+    come back as torch tensors on `device` (default: the current CUDA device).
+    """
+
+    def __init__(self, n, dx, nu, precision="fp32", mu=8.0, omega_rho=1.2, alpha_rho=0.075, omega_q=1.15,
+                 alpha_q=None, gamma=1.0, rho_bar=1.0, strict=False, stream=None):
+        import torch
+        self._torch = torch
+        self.n = tuple(int(v) for v in n)
+        self.dim = len(self.n)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p = _binding.vlbm_params_default(self.dim, self.n, dx, nu, prec)
+        p.mu = mu
+        p.omega[0] = omega_rho
+        p.alpha[0] = alpha_rho
+        for k in range(1, 4):
+            p.omega[k] = omega_q
+            p.alpha[k] = -1.0 if alpha_q is None else alpha_q
+        p.gamma = gamma
+        p.rho_bar = rho_bar
+        p.strict = int(bool(strict))
+        self.params = p
+        _, self.derived = _binding.vlbm_params_check(p)
+        self.handle = _binding.vlbm_create(p, stream)
+        self.grid = tuple(reversed(self.n))
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "handle", None):
+            _binding.vlbm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the scheme
+    def init(self, u, phi=None):
+        _binding.vlbm_init(self.handle, u, phi)
+
+    def step(self, nsteps=1, check=False, graph=True):
+        flags = (_binding.VLBM_STEP_CHECK_FINITE if check else 0) | (0 if graph else _binding.VLBM_STEP_NO_GRAPH)
+        _binding.vlbm_step(self.handle, nsteps, flags)
+
+    def step_record(self, nsteps, every=1, history=None):
+        """Step with the invariants of every `every`-th state reduced in the step kernel."""
+        return _binding.vlbm_step_record(self.handle, nsteps, every, history)
+
+    def macros(self, dtype=None, device="cuda"):
+        """(rho, u, phi) as tensors."""
+        t = self._torch
+        dtype = dtype or t.float64
+        rho = t.empty(self.grid, dtype=dtype, device=device)
+        u = t.empty((self.dim,) + self.grid, dtype=dtype, device=device)
+        phi = t.empty(self.grid, dtype=dtype, device=device)
+        _binding.vlbm_macros(self.handle, rho, u, phi)
+        return rho, u, phi
+
+    def invariants(self):
+        return _binding.vlbm_invariants(self.handle)
+
+    def populations(self, deviation=False, dtype=None, device="cuda"):
+        t = self._torch
+        q = 2 * self.dim + 1
+        out = t.empty((self.dim + 1, q) + self.grid, dtype=dtype or t.float64, device=device)
+        _binding.vlbm_get_populations(self.handle, out, deviation)
+        return out
+
+    def time(self):
+        return _binding.vlbm_time(self.handle)
+
+    def state(self):
+        return _binding.vlbm_get_state(self.handle)
+
+    def load_state(self, blob):
+        _binding.vlbm_set_state(self.handle, blob)
+
+    def set_option(self, key, value):
+        _binding.vlbm_set_option(self.handle, key, value)
+
+    def launch_count(self):
+        return _binding.vlbm_launch_count(self.handle)

@@ -1,0 +1,285 @@
+"""ctypes binding of libvlbm.so: the C ABI of include/vlbm.h, same names.
+
+Argument marshalling only.  Arrays may be torch tensors (CUDA or CPU, pinned
+or not) or numpy arrays; their data pointers go to the library, which finds
+out itself whether they are device or host memory.  Every computation runs in
+the library's CUDA kernels; there is no Python or CPU fallback, and importing
+this module fails if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import warnings
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvlbm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -m paper_2607_24059_b300.build, or __graft_entry__.build())")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+# ---- constants (include/vlbm.h) ------------------------------------------------
+VLBM_OK = 0
+VLBM_WSTABILITY = 1
+VLBM_EINVAL = -1
+VLBM_ESTABILITY = -2
+VLBM_ENOMEM = -3
+VLBM_ECUDA = -4
+VLBM_EDIVERGED = -5
+VLBM_ETIMEOUT = -6
+VLBM_EUNSUPPORTED = -7
+
+VLBM_FP64 = 0
+VLBM_FP32 = 1
+VLBM_FP16_SHIFTED = 2
+VLBM_BF16_SHIFTED = 3
+
+VLBM_DTYPE_F32 = 0
+VLBM_DTYPE_F64 = 1
+
+VLBM_STEP_CHECK_FINITE = 1
+VLBM_STEP_NO_GRAPH = 2
+
+VLBM_NUM_INVARIANTS = 8
+VLBM_OPT_KERNEL = 0
+
+PRECISIONS = {"fp64": VLBM_FP64, "fp32": VLBM_FP32, "fp16": VLBM_FP16_SHIFTED, "bf16": VLBM_BF16_SHIFTED}
+
+EXPORTED = [
+    "vlbm_params_default", "vlbm_params_check", "vlbm_create", "vlbm_destroy", "vlbm_set_stream",
+    "vlbm_init", "vlbm_step", "vlbm_step_record", "vlbm_macros", "vlbm_invariants", "vlbm_time", "vlbm_state_bytes",
+    "vlbm_get_state", "vlbm_set_state", "vlbm_get_populations", "vlbm_launch_count", "vlbm_set_option",
+    "vlbm_strerror", "vlbm_last_error",
+]
+
+
+class vlbm_params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32), ("precision", ctypes.c_int32), ("n", ctypes.c_int64 * 3),
+        ("dx", ctypes.c_double), ("mu", ctypes.c_double), ("nu", ctypes.c_double),
+        ("omega", ctypes.c_double * 4), ("alpha", ctypes.c_double * 4),
+        ("gamma", ctypes.c_double), ("rho_bar", ctypes.c_double),
+        ("strict", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class vlbm_derived(ctypes.Structure):
+    _fields_ = [
+        ("dt", ctypes.c_double), ("alpha", ctypes.c_double * 4), ("viscosity", ctypes.c_double * 4),
+        ("mu_min", ctypes.c_double), ("nodes", ctypes.c_int64), ("populations_per_node", ctypes.c_int32),
+        ("bytes_per_population", ctypes.c_int32), ("lattice_bytes", ctypes.c_size_t),
+    ]
+
+
+_P = ctypes.POINTER(vlbm_params)
+_H = ctypes.c_void_p
+_V = ctypes.c_void_p
+
+lib.vlbm_params_default.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_int32]
+lib.vlbm_params_default.restype = None
+lib.vlbm_params_check.argtypes = [_P, ctypes.POINTER(vlbm_derived)]
+lib.vlbm_create.argtypes = [_P, _V, ctypes.POINTER(_H)]
+lib.vlbm_destroy.argtypes = [_H]
+lib.vlbm_destroy.restype = None
+lib.vlbm_set_stream.argtypes = [_H, _V]
+lib.vlbm_init.argtypes = [_H, _V, _V, ctypes.c_int32]
+lib.vlbm_step.argtypes = [_H, ctypes.c_int64, ctypes.c_int32]
+lib.vlbm_step_record.argtypes = [_H, ctypes.c_int64, ctypes.c_int64, _V]
+lib.vlbm_macros.argtypes = [_H, _V, _V, _V, ctypes.c_int32]
+lib.vlbm_invariants.argtypes = [_H, _V]
+lib.vlbm_time.argtypes = [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+lib.vlbm_state_bytes.argtypes = [_H]
+lib.vlbm_state_bytes.restype = ctypes.c_size_t
+lib.vlbm_get_state.argtypes = [_H, _V, ctypes.c_size_t]
+lib.vlbm_set_state.argtypes = [_H, _V, ctypes.c_size_t]
+lib.vlbm_get_populations.argtypes = [_H, _V, ctypes.c_int32, ctypes.c_int32]
+lib.vlbm_launch_count.argtypes = [_H, ctypes.POINTER(ctypes.c_int64)]
+lib.vlbm_set_option.argtypes = [_H, ctypes.c_int32, ctypes.c_int64]
+lib.vlbm_strerror.argtypes = [ctypes.c_int]
+lib.vlbm_strerror.restype = ctypes.c_char_p
+lib.vlbm_last_error.argtypes = [_H]
+lib.vlbm_last_error.restype = ctypes.c_char_p
+
+
+class VlbmError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        msg = f"{where}: {lib.vlbm_strerror(code).decode()} ({code})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+def _check(code: int, where: str, h=None) -> int:
+    if code < 0:
+        detail = lib.vlbm_last_error(h).decode() if h else ""
+        raise VlbmError(code, where, detail)
+    if code > 0:
+        warnings.warn(f"{where}: {lib.vlbm_strerror(code).decode()}", RuntimeWarning, stacklevel=3)
+    return code
+
+
+# ---- marshalling helpers ----------------------------------------------------------
+def _ptr_dtype(a):
+    """(pointer, VLBM_DTYPE) of a contiguous float32/float64 torch tensor or numpy array."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        if a.dtype == np.float64:
+            return a.ctypes.data, VLBM_DTYPE_F64
+        if a.dtype == np.float32:
+            return a.ctypes.data, VLBM_DTYPE_F32
+        raise TypeError(f"unsupported dtype {a.dtype}")
+    import torch
+    if not isinstance(a, torch.Tensor):
+        raise TypeError(f"expected a torch tensor or numpy array, got {type(a)}")
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if a.dtype == torch.float64:
+        return a.data_ptr(), VLBM_DTYPE_F64
+    if a.dtype == torch.float32:
+        return a.data_ptr(), VLBM_DTYPE_F32
+    raise TypeError(f"unsupported dtype {a.dtype}")
+
+
+def current_stream():
+    """The torch current CUDA stream handle (0 when CUDA is unavailable)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+# ---- the C ABI, same names ------------------------------------------------------------
+def vlbm_params_default(dim, n, dx, nu, precision=VLBM_FP32) -> vlbm_params:
+    p = vlbm_params()
+    arr = (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+    lib.vlbm_params_default(ctypes.byref(p), int(dim), arr, float(dx), float(nu), int(precision))
+    return p
+
+
+def vlbm_params_check(p: vlbm_params):
+    """Returns (status, vlbm_derived); raises on an error status."""
+    d = vlbm_derived()
+    rc = lib.vlbm_params_check(ctypes.byref(p), ctypes.byref(d))
+    _check(rc, "vlbm_params_check")
+    return rc, d
+
+
+def vlbm_create(p: vlbm_params, stream=None):
+    h = _H()
+    s = current_stream() if stream is None else stream
+    rc = lib.vlbm_create(ctypes.byref(p), _V(s), ctypes.byref(h))
+    _check(rc, "vlbm_create")
+    return h
+
+
+def vlbm_destroy(h) -> None:
+    lib.vlbm_destroy(h)
+
+
+def vlbm_set_stream(h, stream) -> None:
+    _check(lib.vlbm_set_stream(h, _V(stream)), "vlbm_set_stream", h)
+
+
+def vlbm_init(h, u, phi=None) -> None:
+    up, dt = _ptr_dtype(u)
+    pp, dt2 = _ptr_dtype(phi)
+    if dt2 is not None and dt2 != dt:
+        raise TypeError("u and phi must have the same dtype")
+    _check(lib.vlbm_init(h, _V(up), _V(pp), dt), "vlbm_init", h)
+
+
+def vlbm_step(h, nsteps: int, flags: int = 0) -> None:
+    _check(lib.vlbm_step(h, int(nsteps), int(flags)), "vlbm_step", h)
+
+
+def vlbm_step_record(h, nsteps: int, every: int, history=None):
+    """Step with fused invariant records; returns `history` (8 float64 per record)."""
+    if history is None:
+        history = np.zeros(((int(nsteps) + int(every) - 1) // int(every), VLBM_NUM_INVARIANTS), dtype=np.float64)
+    p, dt = _ptr_dtype(history)
+    if dt != VLBM_DTYPE_F64:
+        raise TypeError("records are float64")
+    _check(lib.vlbm_step_record(h, int(nsteps), int(every), _V(p)), "vlbm_step_record", h)
+    return history
+
+
+def vlbm_macros(h, rho=None, u=None, phi=None) -> None:
+    dts = {d for d in (_ptr_dtype(a)[1] for a in (rho, u, phi)) if d is not None}
+    if len(dts) != 1:
+        raise TypeError("give at least one output, all of one dtype")
+    _check(lib.vlbm_macros(h, _V(_ptr_dtype(rho)[0]), _V(_ptr_dtype(u)[0]), _V(_ptr_dtype(phi)[0]), dts.pop()),
+           "vlbm_macros", h)
+
+
+def vlbm_invariants(h, out=None):
+    """Fills `out` (8 float64, host or device) or returns a numpy array."""
+    if out is None:
+        out = np.zeros(VLBM_NUM_INVARIANTS, dtype=np.float64)
+    p, dt = _ptr_dtype(out)
+    if dt != VLBM_DTYPE_F64:
+        raise TypeError("invariants are float64")
+    _check(lib.vlbm_invariants(h, _V(p)), "vlbm_invariants", h)
+    return out
+
+
+def vlbm_time(h):
+    s = ctypes.c_int64()
+    t = ctypes.c_double()
+    _check(lib.vlbm_time(h, ctypes.byref(s), ctypes.byref(t)), "vlbm_time", h)
+    return s.value, t.value
+
+
+def vlbm_state_bytes(h) -> int:
+    return int(lib.vlbm_state_bytes(h))
+
+
+def vlbm_get_state(h, dst=None):
+    if dst is None:
+        dst = np.empty(vlbm_state_bytes(h), dtype=np.uint8)
+    ptr = dst.ctypes.data if isinstance(dst, np.ndarray) else dst.data_ptr()
+    nbytes = dst.nbytes if isinstance(dst, np.ndarray) else dst.numel() * dst.element_size()
+    _check(lib.vlbm_get_state(h, _V(ptr), nbytes), "vlbm_get_state", h)
+    return dst
+
+
+def vlbm_set_state(h, src) -> None:
+    ptr = src.ctypes.data if isinstance(src, np.ndarray) else src.data_ptr()
+    nbytes = src.nbytes if isinstance(src, np.ndarray) else src.numel() * src.element_size()
+    _check(lib.vlbm_set_state(h, _V(ptr), nbytes), "vlbm_set_state", h)
+
+
+def vlbm_get_populations(h, dst, deviation: bool = False) -> None:
+    p, dt = _ptr_dtype(dst)
+    _check(lib.vlbm_get_populations(h, _V(p), dt, int(bool(deviation))), "vlbm_get_populations", h)
+
+
+def vlbm_launch_count(h) -> int:
+    c = ctypes.c_int64()
+    _check(lib.vlbm_launch_count(h, ctypes.byref(c)), "vlbm_launch_count", h)
+    return c.value
+
+
+def vlbm_set_option(h, key: int, value: int) -> None:
+    _check(lib.vlbm_set_option(h, int(key), int(value)), "vlbm_set_option", h)
+
+
+def vlbm_strerror(code: int) -> str:
+    return lib.vlbm_strerror(int(code)).decode()
+
+
+def vlbm_last_error(h) -> str:
+    return lib.vlbm_last_error(h).decode()

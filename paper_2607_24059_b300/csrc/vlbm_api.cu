@@ -1,0 +1,780 @@
+// C ABI of the vectorial lattice Boltzmann library (declared in include/vlbm.h).
+// Host-side logic: parameter resolution (Section 2, Prop. 1, Lemmas 1-2),
+// buffer ownership, launch configuration, CUDA-graph replay of step batches,
+// host/device pointer staging and checkpoints.  Every step of the scheme runs
+// in the kernels of vlbm_kernels_2d.cuh / vlbm_kernels_3d.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "vlbm.h"
+#include "vlbm_kernels_2d.cuh"
+#include "vlbm_kernels_3d.cuh"
+
+using namespace vlbm;
+
+namespace {
+
+constexpr int kGraphSteps = 64;               // steps captured per CUDA graph (even: parity is kept)
+constexpr uint64_t kStateMagic = 0x315F4D424C56ull;  // "VLBM_1"
+
+struct StateHeader {
+    uint64_t magic;
+    int32_t dim, precision;
+    int64_t n[3];
+    int64_t step;
+    uint64_t lattice_bytes;
+    double dx, mu;
+    double omega[4], alpha[4];
+};
+
+}  // namespace
+
+struct vlbm_handle {
+    vlbm_params p{};
+    vlbm_derived d{};
+    int device = 0;
+    int sm_count = 148;
+    cudaStream_t stream = nullptr;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* partials = nullptr;
+    int64_t partial_capacity = 0;     // blocks
+    double* inv_dev = nullptr;        // 8 doubles
+    double* inv_host = nullptr;       // 8 doubles, pinned
+    void* staging = nullptr;
+    size_t staging_bytes = 0;
+    double* hist = nullptr;           // device records of vlbm_step_record for host destinations
+    int64_t hist_capacity = 0;        // records
+    int64_t step = 0;
+    int64_t launches = 0;
+    int kernel_variant = 0;           // 0 auto, 1 generic, 2 vectorised
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::string err;
+    Coef<double> kd{};
+    Coef<float> kf{};
+};
+
+// ------------------------------------------------------------------ helpers
+namespace {
+
+template <class C> const Coef<C>& coef(const vlbm_handle* h);
+template <> const Coef<double>& coef<double>(const vlbm_handle* h) { return h->kd; }
+template <> const Coef<float>& coef<float>(const vlbm_handle* h) { return h->kf; }
+
+int fail(vlbm_handle* h, int code, const char* fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return code;
+}
+
+#define VLBM_CUDA(h, call)                                                                        \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? VLBM_ENOMEM : VLBM_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                       \
+    } while (0)
+
+int check_launch(vlbm_handle* h, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(h, VLBM_ECUDA, "%s launch: %s", what, cudaGetErrorString(e));
+    return VLBM_OK;
+}
+
+bool is_device_pointer(const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int elem_bytes(int precision) {
+    switch (precision) {
+        case VLBM_FP64: return 8;
+        case VLBM_FP32: return 4;
+        case VLBM_FP16_SHIFTED:
+        case VLBM_BF16_SHIFTED: return 2;
+        default: return 0;
+    }
+}
+
+template <class C>
+Coef<C> make_coef(const vlbm_params& p, const vlbm_derived& d, const double* scale) {
+    Coef<C> k{};
+    const int F = p.dim + 1;
+    for (int f = 0; f < kMaxFields; ++f) {
+        const double om = f < F ? p.omega[f] : 1.0;
+        const double al = f < F ? d.alpha[f] : 0.0;
+        k.om[f] = (C)om;
+        k.al[f] = (C)al;
+        k.rest[f] = (C)(1.0 - 2.0 * p.dim * al);
+        k.scale[f] = (C)scale[f];
+        k.inv_scale[f] = (C)(1.0 / scale[f]);
+    }
+    k.i2m = (C)(1.0 / (2.0 * p.mu));
+    k.rho_bar = (C)p.rho_bar;
+    k.p_bar = (C)std::pow(p.rho_bar, p.gamma);
+    k.gamma = (C)p.gamma;
+    k.gamma_one = p.gamma == 1.0;
+    return k;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ parameters
+extern "C" void vlbm_params_default(vlbm_params* p, int32_t dim, const int64_t* n, double dx, double nu,
+                                    int32_t precision) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->dim = dim;
+    p->precision = precision;
+    for (int i = 0; i < 3; ++i) p->n[i] = (n && i < dim) ? n[i] : 1;
+    p->dx = dx;
+    p->mu = 8.0;                 // Section 6.1
+    p->nu = nu;
+    p->omega[0] = 6.0 / 5.0;     // Eq. params, middle pair
+    p->alpha[0] = 3.0 / 40.0;
+    for (int k = 1; k < 4; ++k) {
+        p->omega[k] = 23.0 / 20.0;   // Section 6.1.3
+        p->alpha[k] = -1.0;          // from nu (Prop. 1)
+    }
+    p->gamma = 1.0;
+    p->rho_bar = 1.0;
+}
+
+extern "C" int vlbm_params_check(const vlbm_params* p, vlbm_derived* out) {
+    if (!p) return VLBM_EINVAL;
+    if (p->dim != 2 && p->dim != 3) return VLBM_EINVAL;
+    if (p->reserved != 0) return VLBM_EINVAL;
+    if (elem_bytes(p->precision) == 0) return VLBM_EINVAL;
+    for (int i = 0; i < p->dim; ++i)
+        if (p->n[i] < 1 || p->n[i] > (int64_t)1 << 30) return VLBM_EINVAL;
+    if (!(p->dx > 0.0) || !(p->mu > 0.0) || !(p->rho_bar > 0.0) || !(p->gamma >= 1.0) || !(p->nu >= 0.0))
+        return VLBM_EINVAL;
+    if (!std::isfinite(p->dx) || !std::isfinite(p->mu) || !std::isfinite(p->gamma) || !std::isfinite(p->nu))
+        return VLBM_EINVAL;
+    vlbm_derived d{};
+    const int F = p->dim + 1;
+    const double a_max = p->dim == 2 ? 0.25 : 1.0 / 6.0;   // Lemma 1 (3D: rest weight 1 - 6 alpha >= 0)
+    for (int k = 0; k < F; ++k) {
+        const double om = p->omega[k];
+        if (!(om > 0.0 && om < 2.0)) return VLBM_EINVAL;   // (0, 2]; 2 is inviscid (Prop. 1)
+        double al = p->alpha[k];
+        if (k > 0 && al < 0.0) al = p->nu / (2.0 * p->mu * (1.0 / om - 0.5));   // Prop. 1
+        if (!(al >= 0.0 && al <= a_max)) return VLBM_EINVAL;
+        d.alpha[k] = al;
+        d.viscosity[k] = 2.0 * p->mu * al * (1.0 / om - 0.5);
+    }
+    d.dt = p->dx * p->dx / p->mu;
+    double amin = d.alpha[1];
+    for (int k = 2; k < F; ++k) amin = std::min(amin, d.alpha[k]);
+    const double s = d.alpha[0] + amin;
+    d.mu_min = s > 0.0 ? 1.0 / std::sqrt(s) : INFINITY;
+    d.nodes = p->n[0] * p->n[1] * (p->dim == 3 ? p->n[2] : 1);
+    d.populations_per_node = F * (2 * p->dim + 1);
+    d.bytes_per_population = elem_bytes(p->precision);
+    d.lattice_bytes = (size_t)d.nodes * d.populations_per_node * d.bytes_per_population;
+    if (out) *out = d;
+    if (p->mu < d.mu_min) return p->strict ? VLBM_ESTABILITY : VLBM_WSTABILITY;
+    return VLBM_OK;
+}
+
+// ------------------------------------------------------------------ lifecycle
+static int64_t blocks_for(int64_t threads) { return (threads + kThreads - 1) / kThreads; }
+
+// Elements per vector access of the vectorised step kernels: 16-byte vectors in
+// 2D, 8-byte vectors in 3D (28 planes of registers per vector element).
+static int vec_width(const vlbm_handle* h) { return (h->p.dim == 2 ? 16 : 8) / h->d.bytes_per_population; }
+
+static bool use_vec(const vlbm_handle* h) {
+    if (h->kernel_variant == 1) return false;
+    return h->p.n[0] % vec_width(h) == 0 && (h->p.dim == 2 || h->p.dim == 3);
+}
+
+static int64_t step_blocks(const vlbm_handle* h) {
+    const int64_t nx = h->p.n[0];
+    const int64_t rows = h->d.nodes / nx;
+    if (use_vec(h)) {
+        const int64_t wpr = (nx / vec_width(h) + 31) / 32;
+        return (rows * wpr * 32 + kThreads - 1) / kThreads;
+    }
+    return blocks_for(h->d.nodes);
+}
+
+static int64_t inv_blocks(const vlbm_handle* h) {
+    return std::min<int64_t>(blocks_for(h->d.nodes), (int64_t)h->sm_count * 8);
+}
+
+static void free_all(vlbm_handle* h) {
+    for (int i = 0; i < 2; ++i)
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    for (int i = 0; i < 2; ++i)
+        if (h->buf[i]) cudaFree(h->buf[i]);
+    if (h->partials) cudaFree(h->partials);
+    if (h->inv_dev) cudaFree(h->inv_dev);
+    if (h->inv_host) cudaFreeHost(h->inv_host);
+    if (h->staging) cudaFree(h->staging);
+    if (h->hist) cudaFree(h->hist);
+}
+
+static void storage_scales(const vlbm_params& p, const vlbm_derived& d, double* scale);
+
+extern "C" int vlbm_create(const vlbm_params* p, void* stream, vlbm_handle** out) {
+    if (!out) return VLBM_EINVAL;
+    *out = nullptr;
+    vlbm_derived d;
+    const int rc = vlbm_params_check(p, &d);
+    if (rc < 0) return rc;
+    vlbm_handle* h = new (std::nothrow) vlbm_handle();
+    if (!h) return VLBM_ENOMEM;
+    h->p = *p;
+    h->d = d;
+    h->stream = (cudaStream_t)stream;
+    int st = VLBM_OK;
+    do {
+        if (cudaGetDevice(&h->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+            st = fail(h, VLBM_ECUDA, "no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        for (int i = 0; i < 2 && st == VLBM_OK; ++i) {
+            cudaError_t e = cudaMalloc(&h->buf[i], d.lattice_bytes);
+            if (e != cudaSuccess) st = VLBM_ENOMEM;
+        }
+        if (st != VLBM_OK) break;
+        h->partial_capacity = std::max(step_blocks(h), inv_blocks(h));
+        if (cudaMalloc(&h->partials, (size_t)h->partial_capacity * 8 * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&h->inv_dev, 8 * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&h->inv_host, 8 * sizeof(double)) != cudaSuccess) {
+            st = VLBM_ENOMEM;
+            break;
+        }
+        if (cudaMemsetAsync(h->buf[0], 0, d.lattice_bytes, h->stream) != cudaSuccess) {
+            st = VLBM_ECUDA;
+            break;
+        }
+    } while (0);
+    if (st != VLBM_OK) {
+        cudaGetLastError();
+        free_all(h);
+        delete h;
+        return st;
+    }
+    double scale[4];
+    storage_scales(h->p, h->d, scale);
+    h->kd = make_coef<double>(h->p, h->d, scale);
+    h->kf = make_coef<float>(h->p, h->d, scale);
+    *out = h;
+    return rc;   // VLBM_OK or VLBM_WSTABILITY
+}
+
+extern "C" void vlbm_destroy(vlbm_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+extern "C" int vlbm_set_stream(vlbm_handle* h, void* stream) {
+    if (!h) return VLBM_EINVAL;
+    h->stream = (cudaStream_t)stream;
+    return VLBM_OK;
+}
+
+// Storage scales of the shifted half formats: the stored value is g * scale_k,
+// chosen so that the deviations of each field sit near unit magnitude.  The rho
+// field deviates by O(dx^2 phi) (Prop. 1); a momentum field by O(dx |q|).
+static void storage_scales(const vlbm_params& p, const vlbm_derived& d, double* scale) {
+    for (int k = 0; k < 4; ++k) scale[k] = 1.0;
+    if (p.precision != VLBM_FP16_SHIFTED && p.precision != VLBM_BF16_SHIFTED) return;
+    (void)d;
+    scale[0] = 1.0 / (p.dx * p.dx);
+    for (int k = 1; k < 4; ++k) scale[k] = 1.0 / p.dx;
+}
+
+// ------------------------------------------------------------------ staging
+static int ensure_staging(vlbm_handle* h, size_t bytes) {
+    if (h->staging_bytes >= bytes) return VLBM_OK;
+    if (h->staging) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->staging);
+        h->staging = nullptr;
+        h->staging_bytes = 0;
+    }
+    VLBM_CUDA(h, cudaMalloc(&h->staging, bytes));
+    h->staging_bytes = bytes;
+    return VLBM_OK;
+}
+
+// ------------------------------------------------------------------ init / macros
+template <class S, class T>
+static void launch_init(vlbm_handle* h, const T* u, const T* phi) {
+    const int64_t N = h->d.nodes;
+    const double pb = std::pow(h->p.rho_bar, h->p.gamma);
+    const auto& k = coef<typename Storage<S>::C>(h);
+    if (h->p.dim == 2)
+        k_init_2d<S, T><<<blocks_for(N), kThreads, 0, h->stream>>>((S*)h->buf[h->cur], N, u, phi, k, h->p.dx,
+                                                                   h->p.gamma, h->p.rho_bar, pb);
+    else
+        k_init_3d<S, T><<<blocks_for(N), kThreads, 0, h->stream>>>((S*)h->buf[h->cur], N, u, phi, k, h->p.dx,
+                                                                   h->p.gamma, h->p.rho_bar, pb);
+    h->launches++;
+}
+
+template <class S, class T>
+static void launch_macros(vlbm_handle* h, T* rho, T* u, T* phi) {
+    const int64_t N = h->d.nodes;
+    const double pb = std::pow(h->p.rho_bar, h->p.gamma);
+    const auto& k = coef<typename Storage<S>::C>(h);
+    if (h->p.dim == 2)
+        k_macros_2d<S, T><<<blocks_for(N), kThreads, 0, h->stream>>>((const S*)h->buf[h->cur], N, rho, u, phi, k,
+                                                                     h->p.dx, h->p.gamma, h->p.rho_bar, pb);
+    else
+        k_macros_3d<S, T><<<blocks_for(N), kThreads, 0, h->stream>>>((const S*)h->buf[h->cur], N, rho, u, phi, k,
+                                                                     h->p.dx, h->p.gamma, h->p.rho_bar, pb);
+    h->launches++;
+}
+
+#define VLBM_DISPATCH_STORAGE(h, FN, ...)                                    \
+    switch ((h)->p.precision) {                                              \
+        case VLBM_FP64: FN<double>(__VA_ARGS__); break;                      \
+        case VLBM_FP32: FN<float>(__VA_ARGS__); break;                       \
+        case VLBM_FP16_SHIFTED: FN<__half>(__VA_ARGS__); break;              \
+        default: FN<__nv_bfloat16>(__VA_ARGS__); break;                      \
+    }
+
+template <class S>
+static void init_dispatch(vlbm_handle* h, const void* u, const void* phi, int dtype) {
+    if (dtype == VLBM_DTYPE_F64) launch_init<S, double>(h, (const double*)u, (const double*)phi);
+    else launch_init<S, float>(h, (const float*)u, (const float*)phi);
+}
+
+template <class S>
+static void macros_dispatch(vlbm_handle* h, void* rho, void* u, void* phi, int dtype) {
+    if (dtype == VLBM_DTYPE_F64) launch_macros<S, double>(h, (double*)rho, (double*)u, (double*)phi);
+    else launch_macros<S, float>(h, (float*)rho, (float*)u, (float*)phi);
+}
+
+extern "C" int vlbm_init(vlbm_handle* h, const void* u, const void* phi, int32_t dtype) {
+    if (!h || !u || (dtype != VLBM_DTYPE_F32 && dtype != VLBM_DTYPE_F64)) return VLBM_EINVAL;
+    const size_t es = dtype == VLBM_DTYPE_F64 ? 8 : 4;
+    const int64_t N = h->d.nodes;
+    const size_t ub = (size_t)h->p.dim * N * es, pb = phi ? (size_t)N * es : 0;
+    const void* ud = u;
+    const void* pd = phi;
+    const bool u_host = !is_device_pointer(u), p_host = phi && !is_device_pointer(phi);
+    if (u_host || p_host) {
+        int rc = ensure_staging(h, ub + pb);
+        if (rc) return rc;
+        if (u_host) {
+            VLBM_CUDA(h, cudaMemcpyAsync(h->staging, u, ub, cudaMemcpyHostToDevice, h->stream));
+            ud = h->staging;
+        }
+        if (p_host) {
+            VLBM_CUDA(h, cudaMemcpyAsync((char*)h->staging + ub, phi, pb, cudaMemcpyHostToDevice, h->stream));
+            pd = (char*)h->staging + ub;
+        }
+    }
+    VLBM_DISPATCH_STORAGE(h, init_dispatch, h, ud, pd, dtype);
+    int rc = check_launch(h, "init");
+    if (rc) return rc;
+    h->step = 0;
+    if (u_host || p_host) VLBM_CUDA(h, cudaStreamSynchronize(h->stream));   // host arrays may be reused on return
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_macros(vlbm_handle* h, void* rho, void* u, void* phi, int32_t dtype) {
+    if (!h || (dtype != VLBM_DTYPE_F32 && dtype != VLBM_DTYPE_F64)) return VLBM_EINVAL;
+    if (!rho && !u && !phi) return VLBM_OK;
+    const size_t es = dtype == VLBM_DTYPE_F64 ? 8 : 4;
+    const int64_t N = h->d.nodes;
+    const size_t sb = (size_t)N * es, ub = (size_t)h->p.dim * N * es;
+    void* out[3] = {rho, u, phi};
+    const size_t bytes[3] = {sb, ub, sb};
+    void* dev[3] = {rho, u, phi};
+    bool host[3] = {false, false, false};
+    size_t off = 0, offs[3] = {0, 0, 0};
+    for (int i = 0; i < 3; ++i) {
+        if (out[i] && !is_device_pointer(out[i])) {
+            host[i] = true;
+            offs[i] = off;
+            off += bytes[i];
+        }
+    }
+    if (off) {
+        int rc = ensure_staging(h, off);
+        if (rc) return rc;
+        for (int i = 0; i < 3; ++i)
+            if (host[i]) dev[i] = (char*)h->staging + offs[i];
+    }
+    VLBM_DISPATCH_STORAGE(h, macros_dispatch, h, dev[0], dev[1], dev[2], dtype);
+    int rc = check_launch(h, "macros");
+    if (rc) return rc;
+    if (off) {
+        for (int i = 0; i < 3; ++i)
+            if (host[i]) VLBM_CUDA(h, cudaMemcpyAsync(out[i], dev[i], bytes[i], cudaMemcpyDeviceToHost, h->stream));
+        VLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    return VLBM_OK;
+}
+
+// ------------------------------------------------------------------ stepping
+template <class S, bool DIAG>
+static void launch_step_on(vlbm_handle* h, cudaStream_t s, int src, double* partials) {
+    using C = typename Storage<S>::C;
+    const auto& k = coef<C>(h);
+    const S* fin = (const S*)h->buf[src];
+    S* fout = (S*)h->buf[src ^ 1];
+    const int64_t nx = h->p.n[0], ny = h->p.n[1];
+    const int64_t plane = h->d.nodes;
+    const int64_t blocks = step_blocks(h);
+    if (h->p.dim == 2) {
+        if (use_vec(h)) {
+            const int wpr = (int)((nx / vec_width(h) + 31) / 32);
+            k_stream_collide_2d_vec<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, wpr, k,
+                                                                         partials);
+        } else {
+            k_stream_collide_2d_generic<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, k,
+                                                                             partials);
+        }
+    } else {
+        const int64_t nz = h->p.n[2];
+        if (use_vec(h)) {
+            const int wpr = (int)((nx / vec_width(h) + 31) / 32);
+            k_stream_collide_3d_vec<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz, plane,
+                                                                         wpr, k, partials);
+        } else {
+            k_stream_collide_3d_generic<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz,
+                                                                             plane, k, partials);
+        }
+    }
+}
+
+template <class S>
+static void step_plain(vlbm_handle* h, cudaStream_t s, int src) { launch_step_on<S, false>(h, s, src, nullptr); }
+
+template <class S>
+static void step_diag(vlbm_handle* h, cudaStream_t s, int src, double* partials) {
+    launch_step_on<S, true>(h, s, src, partials);
+}
+
+static int launch_one_step(vlbm_handle* h, cudaStream_t s, int src) {
+    VLBM_DISPATCH_STORAGE(h, step_plain, h, s, src);
+    return check_launch(h, "stream-collide");
+}
+
+// Capture kGraphSteps steps starting from buffer `src` on a private stream.
+static int build_graph(vlbm_handle* h, int src) {
+    if (!h->capture_stream) VLBM_CUDA(h, cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+    VLBM_CUDA(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+    int b = src;
+    int rc = VLBM_OK;
+    for (int i = 0; i < kGraphSteps; ++i) {
+        VLBM_DISPATCH_STORAGE(h, step_plain, h, h->capture_stream, b);
+        b ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->capture_stream, &g);
+    if (e != cudaSuccess) return fail(h, VLBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->graph[src], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph[src] = nullptr;
+        rc = fail(h, VLBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    return rc;
+}
+
+static int launch_invariants(vlbm_handle* h, double* out_dev);
+
+extern "C" int vlbm_step(vlbm_handle* h, int64_t nsteps, int32_t flags) {
+    if (!h || nsteps < 0) return VLBM_EINVAL;
+    int64_t left = nsteps;
+    const bool graphs = !(flags & VLBM_STEP_NO_GRAPH);
+    while (left > 0) {
+        if (graphs && left >= kGraphSteps) {
+            if (!h->graph[h->cur]) {
+                int rc = build_graph(h, h->cur);
+                if (rc) return rc;
+            }
+            VLBM_CUDA(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
+            h->launches += kGraphSteps;
+            h->step += kGraphSteps;
+            left -= kGraphSteps;   // kGraphSteps is even: parity unchanged
+        } else {
+            int rc = launch_one_step(h, h->stream, h->cur);
+            if (rc) return rc;
+            h->launches++;
+            h->cur ^= 1;
+            h->step++;
+            left--;
+        }
+    }
+    if (flags & VLBM_STEP_CHECK_FINITE) {
+        int rc = launch_invariants(h, h->inv_dev);
+        if (rc) return rc;
+        VLBM_CUDA(h, cudaMemcpyAsync(h->inv_host, h->inv_dev, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        VLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (h->inv_host[6] != 0.0) return fail(h, VLBM_EDIVERGED, "%.0f non-finite nodes at step %lld", h->inv_host[6],
+                                               (long long)h->step);
+    }
+    return VLBM_OK;
+}
+
+static void launch_final(vlbm_handle* h, int nblocks, double* out_dev);
+
+// Pointer kinds for outputs: device, pinned (page-locked) host, pageable host.
+enum PtrKind { kDevice, kPinned, kPageable };
+
+static PtrKind pointer_kind(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return kPageable;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return kDevice;
+    if (a.type == cudaMemoryTypeHost) return kPinned;
+    return kPageable;
+}
+
+extern "C" int vlbm_step_record(vlbm_handle* h, int64_t nsteps, int64_t every, double* history) {
+    if (!h || nsteps < 0 || every < 1 || (nsteps > 0 && !history)) return VLBM_EINVAL;
+    if (nsteps == 0) return VLBM_OK;
+    const int64_t records = (nsteps + every - 1) / every;
+    const PtrKind kind = pointer_kind(history);
+    double* rec = history;
+    if (kind != kDevice) {
+        if (h->hist_capacity < records) {
+            if (h->hist) {
+                VLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+                cudaFree(h->hist);
+                h->hist = nullptr;
+                h->hist_capacity = 0;
+            }
+            VLBM_CUDA(h, cudaMalloc(&h->hist, (size_t)records * 8 * sizeof(double)));
+            h->hist_capacity = records;
+        }
+        rec = h->hist;
+    }
+    const int blocks = (int)step_blocks(h);
+    for (int64_t s = 0; s < nsteps;) {
+        if (s % every == 0) {
+            VLBM_DISPATCH_STORAGE(h, step_diag, h, h->stream, h->cur, h->partials);
+            int rc = check_launch(h, "stream-collide (diagnostics)");
+            if (rc) return rc;
+            launch_final(h, blocks, rec + (s / every) * 8);
+            rc = check_launch(h, "invariants final");
+            if (rc) return rc;
+            h->launches += 2;
+            h->cur ^= 1;
+            h->step++;
+            ++s;
+        } else {
+            // plain steps up to the next record (graph replay when long enough)
+            const int64_t run = std::min(nsteps - s, every - s % every);
+            int rc = vlbm_step(h, run, 0);
+            if (rc) return rc;
+            s += run;
+        }
+    }
+    if (kind != kDevice) {
+        VLBM_CUDA(h, cudaMemcpyAsync(history, rec, (size_t)records * 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                                     h->stream));
+        if (kind == kPageable) VLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    return VLBM_OK;
+}
+
+// ------------------------------------------------------------------ invariants
+template <class S>
+static void invariants_partials(vlbm_handle* h, int blocks) {
+    using C = typename Storage<S>::C;
+    const auto& k = coef<C>(h);
+    if (h->p.dim == 2)
+        k_invariants_2d<S><<<blocks, kThreads, 0, h->stream>>>((const S*)h->buf[h->cur], h->d.nodes, k, h->partials);
+    else
+        k_invariants_3d<S><<<blocks, kThreads, 0, h->stream>>>((const S*)h->buf[h->cur], h->d.nodes, k, h->partials);
+}
+
+static void launch_final(vlbm_handle* h, int nblocks, double* out_dev) {
+    const double inv_dx = 1.0 / h->p.dx;
+    const double scale_e = h->p.dim == 3 ? h->p.dx : 1.0;
+    k_invariants_final<<<1, 1024, 0, h->stream>>>(h->partials, nblocks, out_dev, (double)h->d.nodes, h->p.rho_bar,
+                                                   inv_dx, scale_e);
+}
+
+static int launch_invariants(vlbm_handle* h, double* out_dev) {
+    const int blocks = (int)inv_blocks(h);
+    VLBM_DISPATCH_STORAGE(h, invariants_partials, h, blocks);
+    int rc = check_launch(h, "invariants");
+    if (rc) return rc;
+    launch_final(h, blocks, out_dev);
+    h->launches += 2;
+    return check_launch(h, "invariants final");
+}
+
+extern "C" int vlbm_invariants(vlbm_handle* h, double* out) {
+    if (!h || !out) return VLBM_EINVAL;
+    if (is_device_pointer(out)) return launch_invariants(h, out);
+    int rc = launch_invariants(h, h->inv_dev);
+    if (rc) return rc;
+    VLBM_CUDA(h, cudaMemcpyAsync(h->inv_host, h->inv_dev, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    VLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    std::memcpy(out, h->inv_host, 8 * sizeof(double));
+    return VLBM_OK;
+}
+
+// ------------------------------------------------------------------ time / state
+extern "C" int vlbm_time(const vlbm_handle* h, int64_t* step, double* t) {
+    if (!h) return VLBM_EINVAL;
+    if (step) *step = h->step;
+    if (t) *t = (double)h->step * h->d.dt;
+    return VLBM_OK;
+}
+
+extern "C" size_t vlbm_state_bytes(const vlbm_handle* h) {
+    return h ? sizeof(StateHeader) + h->d.lattice_bytes : 0;
+}
+
+static StateHeader make_header(const vlbm_handle* h) {
+    StateHeader s{};
+    s.magic = kStateMagic;
+    s.dim = h->p.dim;
+    s.precision = h->p.precision;
+    for (int i = 0; i < 3; ++i) s.n[i] = h->p.n[i];
+    s.step = h->step;
+    s.lattice_bytes = h->d.lattice_bytes;
+    s.dx = h->p.dx;
+    s.mu = h->p.mu;
+    for (int k = 0; k < 4; ++k) {
+        s.omega[k] = h->p.omega[k];
+        s.alpha[k] = h->d.alpha[k];
+    }
+    return s;
+}
+
+extern "C" int vlbm_get_state(vlbm_handle* h, void* dst, size_t bytes) {
+    if (!h || !dst || bytes < vlbm_state_bytes(h)) return VLBM_EINVAL;
+    const StateHeader s = make_header(h);
+    VLBM_CUDA(h, cudaMemcpyAsync(dst, &s, sizeof s, cudaMemcpyDefault, h->stream));
+    VLBM_CUDA(h, cudaMemcpyAsync((char*)dst + sizeof s, h->buf[h->cur], h->d.lattice_bytes, cudaMemcpyDefault,
+                                 h->stream));
+    VLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_set_state(vlbm_handle* h, const void* src, size_t bytes) {
+    if (!h || !src || bytes < vlbm_state_bytes(h)) return VLBM_EINVAL;
+    StateHeader s{};
+    VLBM_CUDA(h, cudaMemcpyAsync(&s, src, sizeof s, cudaMemcpyDefault, h->stream));
+    VLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    const StateHeader mine = make_header(h);
+    if (s.magic != kStateMagic || s.dim != mine.dim || s.precision != mine.precision ||
+        s.lattice_bytes != mine.lattice_bytes || std::memcmp(s.n, mine.n, sizeof s.n) != 0 || s.dx != mine.dx ||
+        s.mu != mine.mu || std::memcmp(s.omega, mine.omega, sizeof s.omega) != 0 ||
+        std::memcmp(s.alpha, mine.alpha, sizeof s.alpha) != 0)
+        return fail(h, VLBM_EINVAL, "checkpoint does not match this handle's configuration");
+    VLBM_CUDA(h, cudaMemcpyAsync(h->buf[h->cur], (const char*)src + sizeof s, h->d.lattice_bytes, cudaMemcpyDefault,
+                                 h->stream));
+    VLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->step = s.step;
+    return VLBM_OK;
+}
+
+template <class S, class T>
+static void launch_export(vlbm_handle* h, T* dst, int deviation) {
+    using C = typename Storage<S>::C;
+    const auto& k = coef<C>(h);
+    const int q = 2 * h->p.dim + 1;
+    const int64_t total = h->d.nodes * h->d.populations_per_node;
+    const double f_rest = (1.0 - 2.0 * h->p.dim * h->d.alpha[0]) * h->p.rho_bar;
+    const double f_move = h->d.alpha[0] * h->p.rho_bar;
+    const double p_half = std::pow(h->p.rho_bar, h->p.gamma) / (2.0 * h->p.mu);
+    k_export<S, T><<<blocks_for(total), kThreads, 0, h->stream>>>((const S*)h->buf[h->cur], total, h->d.nodes, q, dst,
+                                                                  k, f_rest, f_move, p_half, deviation);
+    h->launches++;
+}
+
+template <class S>
+static void export_dispatch(vlbm_handle* h, void* dst, int dtype, int deviation) {
+    if (dtype == VLBM_DTYPE_F64) launch_export<S, double>(h, (double*)dst, deviation);
+    else launch_export<S, float>(h, (float*)dst, deviation);
+}
+
+extern "C" int vlbm_get_populations(vlbm_handle* h, void* dst, int32_t dtype, int32_t deviation) {
+    if (!h || !dst || (dtype != VLBM_DTYPE_F32 && dtype != VLBM_DTYPE_F64)) return VLBM_EINVAL;
+    const size_t bytes = (size_t)h->d.nodes * h->d.populations_per_node * (dtype == VLBM_DTYPE_F64 ? 8 : 4);
+    const bool host = !is_device_pointer(dst);
+    void* d = dst;
+    if (host) {
+        int rc = ensure_staging(h, bytes);
+        if (rc) return rc;
+        d = h->staging;
+    }
+    VLBM_DISPATCH_STORAGE(h, export_dispatch, h, d, dtype, deviation);
+    int rc = check_launch(h, "export");
+    if (rc) return rc;
+    if (host) {
+        VLBM_CUDA(h, cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, h->stream));
+        VLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_launch_count(const vlbm_handle* h, int64_t* count) {
+    if (!h || !count) return VLBM_EINVAL;
+    *count = h->launches;
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_set_option(vlbm_handle* h, int32_t key, int64_t value) {
+    if (!h) return VLBM_EINVAL;
+    switch (key) {
+        case VLBM_OPT_KERNEL:
+            if (value < 0 || value > 2) return VLBM_EINVAL;
+            if (value == 2 && h->p.n[0] % vec_width(h) != 0) return VLBM_EINVAL;
+            h->kernel_variant = (int)value;
+            for (int i = 0; i < 2; ++i)
+                if (h->graph[i]) {
+                    cudaGraphExecDestroy(h->graph[i]);
+                    h->graph[i] = nullptr;
+                }
+            return VLBM_OK;
+        default: return VLBM_EINVAL;
+    }
+}
+
+extern "C" const char* vlbm_strerror(int code) {
+    switch (code) {
+        case VLBM_OK: return "ok";
+        case VLBM_WSTABILITY: return "mu below the low-frequency stability bound (warning)";
+        case VLBM_EINVAL: return "invalid argument";
+        case VLBM_ESTABILITY: return "mu below the low-frequency stability bound";
+        case VLBM_ENOMEM: return "out of memory";
+        case VLBM_ECUDA: return "CUDA error";
+        case VLBM_EDIVERGED: return "non-finite populations";
+        case VLBM_ETIMEOUT: return "device wait timed out";
+        case VLBM_EUNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* vlbm_last_error(const vlbm_handle* h) { return h ? h->err.c_str() : "null handle"; }

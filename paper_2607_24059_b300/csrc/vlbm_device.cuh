@@ -1,0 +1,274 @@
+// Device-side building blocks of the vectorial lattice Boltzmann update
+// (Section 2 of the paper): storage traits, per-field coefficients and the
+// per-node relaxation written on deviations from the rest equilibrium.
+//
+// Deviation variables.  Every format stores g = f - F, where F = f^eq(rho_bar, 0)
+// is the (spatially uniform) rest equilibrium.  F is a fixed point of the
+// relaxation and is invariant under transport, and the relaxation is affine,
+// so the scheme maps g exactly as it maps f:  g* = g + omega_k (g^eq - g) with
+// g^eq = f^eq(rho, q) - F.  The moments become
+//     dr = rho - rho_bar = sum_l g^rho_l,     Q_d = dx q_d = sum_l g^{q_d}_l,
+// and, writing r = 1/rho and i2m = 1/(2 mu), the equilibria of Section 2 read
+//     rho field : rest (1 - 2D a_r) dr,     +-e_d : a_r dr +- i2m Q_d
+//     q_j field : rest (1 - 2D a_j) Q_j,    +-e_d : a_j Q_j +- (i2m Q_j Q_d r + delta_jd dP)
+// with dP = (P(rho) - P(rho_bar)) / (2 mu).  Nothing here depends on dx: it
+// only enters through the moments' scale.  All quantities are O(perturbation),
+// so FP32 keeps full relative precision of the pressure signal even when
+// rho - rho_bar = O(dx^2) (the raw populations of a momentum field carry the
+// constant +-P(rho_bar)/(2 mu), which would swamp it).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace vlbm {
+
+constexpr int kMaxFields = 4;
+
+// ---------------------------------------------------------------- storage traits
+template <class S> struct Storage;
+template <> struct Storage<double> {
+    using C = double;
+    static constexpr bool kScaled = false;
+    static __device__ __forceinline__ double to_c(double v) { return v; }
+    static __device__ __forceinline__ double from_c(double v) { return v; }
+};
+template <> struct Storage<float> {
+    using C = float;
+    static constexpr bool kScaled = false;
+    static __device__ __forceinline__ float to_c(float v) { return v; }
+    static __device__ __forceinline__ float from_c(float v) { return v; }
+};
+template <> struct Storage<__half> {
+    using C = float;
+    static constexpr bool kScaled = true;
+    static __device__ __forceinline__ float to_c(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half from_c(float v) { return __float2half_rn(v); }
+};
+template <> struct Storage<__nv_bfloat16> {
+    using C = float;
+    static constexpr bool kScaled = true;
+    static __device__ __forceinline__ float to_c(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 from_c(float v) { return __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------- coefficients
+// Per-field relaxation and equilibrium coefficients in the compute type C.
+template <class C>
+struct Coef {
+    C om[kMaxFields];      // omega_k
+    C al[kMaxFields];      // alpha_k
+    C rest[kMaxFields];    // 1 - 2D alpha_k
+    C scale[kMaxFields];   // stored = g * scale_k (1 for unscaled formats)
+    C inv_scale[kMaxFields];
+    C i2m;                 // 1 / (2 mu)
+    C rho_bar;
+    C p_bar;               // P(rho_bar) = rho_bar^gamma
+    C gamma;
+    int gamma_one;         // gamma == 1: dP = dr / (2 mu) exactly
+};
+
+// P(rho_bar + dr) - P(rho_bar) without cancellation.
+template <class C>
+__device__ __forceinline__ C pressure_dev(const Coef<C>& k, C dr) {
+    if (k.gamma_one) return dr;
+    return k.p_bar * expm1(k.gamma * log1p(dr / k.rho_bar));
+}
+
+// Equilibrium deviations g^eq of one D2Q5 node, fields (rho, q_x, q_y) x
+// velocities (rest, +x, -x, +y, -y): e[5k + l].
+template <class C>
+__device__ __forceinline__ void equilibrium_d2q5(const Coef<C>& k, C dr, C Qx, C Qy, C (&e)[15]) {
+    const C r = C(1) / (k.rho_bar + dr);
+    const C dP = pressure_dev(k, dr) * k.i2m;
+    const C hx = Qx * k.i2m, hy = Qy * k.i2m;
+    const C xx = Qx * Qx * r * k.i2m;
+    const C xy = Qx * Qy * r * k.i2m;
+    const C yy = Qy * Qy * r * k.i2m;
+    const C ar = k.al[0] * dr;
+    e[0] = k.rest[0] * dr;
+    e[1] = ar + hx;
+    e[2] = ar - hx;
+    e[3] = ar + hy;
+    e[4] = ar - hy;
+    const C ax = k.al[1] * Qx;
+    e[5] = k.rest[1] * Qx;
+    e[6] = ax + (xx + dP);
+    e[7] = ax - (xx + dP);
+    e[8] = ax + xy;
+    e[9] = ax - xy;
+    const C ay = k.al[2] * Qy;
+    e[10] = k.rest[2] * Qy;
+    e[11] = ay + xy;
+    e[12] = ay - xy;
+    e[13] = ay + (yy + dP);
+    e[14] = ay - (yy + dP);
+}
+
+// Moments of one D2Q5 node in the fixed order rest, +x, -x, +y, -y.
+template <class C>
+__device__ __forceinline__ void moments_d2q5(const C (&g)[15], C& dr, C& Qx, C& Qy) {
+    dr = (((g[0] + g[1]) + g[2]) + g[3]) + g[4];
+    Qx = (((g[5] + g[6]) + g[7]) + g[8]) + g[9];
+    Qy = (((g[10] + g[11]) + g[12]) + g[13]) + g[14];
+}
+
+// Relaxation of Eq. LBM_scheme on the deviations of one D2Q5 node, in place.
+template <class C>
+__device__ __forceinline__ void relax_d2q5(const Coef<C>& k, C (&g)[15], C dr, C Qx, C Qy) {
+    C e[15];
+    equilibrium_d2q5(k, dr, Qx, Qy, e);
+#pragma unroll
+    for (int i = 0; i < 15; ++i) g[i] = fma(k.om[i / 5], e[i] - g[i], g[i]);
+}
+
+// Equilibrium deviations of one D3Q7 node, fields (rho, q_x, q_y, q_z) x
+// velocities (rest, +x, -x, +y, -y, +z, -z): e[7k + l].  The paper gives the
+// 2D equilibria and states that 3D follows from the Cartesian structure; this
+// is the direction-by-direction extension (rest weight 1 - 6 alpha).
+template <class C>
+__device__ __forceinline__ void equilibrium_d3q7(const Coef<C>& k, C dr, const C (&Q)[3], C (&e)[28]) {
+    const C r = C(1) / (k.rho_bar + dr);
+    const C dP = pressure_dev(k, dr) * k.i2m;
+    const C ar = k.al[0] * dr;
+    e[0] = k.rest[0] * dr;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const C h = Q[d] * k.i2m;
+        e[1 + 2 * d] = ar + h;
+        e[2 + 2 * d] = ar - h;
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const C a = k.al[j + 1] * Q[j];
+        const C qr = Q[j] * r * k.i2m;
+        e[7 * (j + 1)] = k.rest[j + 1] * Q[j];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const C flux = (j == d) ? (qr * Q[d] + dP) : qr * Q[d];
+            e[7 * (j + 1) + 1 + 2 * d] = a + flux;
+            e[7 * (j + 1) + 2 + 2 * d] = a - flux;
+        }
+    }
+}
+
+template <class C>
+__device__ __forceinline__ void moments_d3q7(const C (&g)[28], C& dr, C (&Q)[3]) {
+    dr = (((((g[0] + g[1]) + g[2]) + g[3]) + g[4]) + g[5]) + g[6];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const C* h = g + 7 * (j + 1);
+        Q[j] = (((((h[0] + h[1]) + h[2]) + h[3]) + h[4]) + h[5]) + h[6];
+    }
+}
+
+template <class C>
+__device__ __forceinline__ void relax_d3q7(const Coef<C>& k, C (&g)[28], C dr, const C (&Q)[3]) {
+    C e[28];
+    equilibrium_d3q7(k, dr, Q, e);
+#pragma unroll
+    for (int i = 0; i < 28; ++i) g[i] = fma(k.om[i / 7], e[i] - g[i], g[i]);
+}
+
+// ---------------------------------------------------------------- vector I/O
+// Aligned vector load/store of V elements of S (V * sizeof(S) in {2,4,8,16} bytes).
+template <int B> struct RawVec;
+template <> struct RawVec<16> { using T = uint4; };
+template <> struct RawVec<8> { using T = uint2; };
+template <> struct RawVec<4> { using T = unsigned int; };
+template <> struct RawVec<2> { using T = unsigned short; };
+
+template <class S, int V>
+__device__ __forceinline__ void vload(S (&e)[V], const S* p) {
+    using R = typename RawVec<V * sizeof(S)>::T;
+    *reinterpret_cast<R*>(&e[0]) = __ldg(reinterpret_cast<const R*>(p));
+}
+
+template <class S, int V>
+__device__ __forceinline__ void vstore(S* p, const S (&e)[V]) {
+    using R = typename RawVec<V * sizeof(S)>::T;
+    *reinterpret_cast<R*>(p) = *reinterpret_cast<const R*>(&e[0]);
+}
+
+// ---------------------------------------------------------------- diagnostics
+// Per-thread FP64 accumulators of the invariants:
+//   a[0] sum dr, a[1..3] sum Q_d, a[4] sum |Q|^2 / (2 rho), a[5] max |Q| / rho,
+//   a[6] non-finite nodes, a[7] unused.
+struct Acc {
+    double a[8];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = 0.0;
+    }
+};
+
+template <class C>
+__device__ __forceinline__ bool all_finite(const C* g, int n) {
+    bool ok = true;
+    for (int i = 0; i < n; ++i) ok = ok && isfinite(g[i]);
+    return ok;
+}
+
+template <class C>
+__device__ __forceinline__ void accumulate_node(Acc& acc, bool finite, C dr, const C* Q, int dim, double rho_bar) {
+    if (!finite) {
+        acc.a[6] += 1.0;
+        return;
+    }
+    const double rho = rho_bar + (double)dr;
+    double q2 = 0.0;
+    acc.a[0] += (double)dr;
+    for (int d = 0; d < dim; ++d) {
+        const double qd = (double)Q[d];
+        acc.a[1 + d] += qd;
+        q2 += qd * qd;
+    }
+    acc.a[4] += 0.5 * q2 / rho;
+    acc.a[5] = fmax(acc.a[5], sqrt(q2) / rho);
+}
+
+// Block-wide reduction of the accumulators (sums, and max for a[5]); the
+// result ends in thread 0's acc.  Fixed shuffle tree and warp order, so the
+// result is deterministic for a given launch shape.
+__device__ __forceinline__ void block_reduce(Acc& acc) {
+    __shared__ double sm[32][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const double o = __shfl_xor_sync(0xffffffffu, acc.a[i], off);
+            acc.a[i] = (i == 5) ? fmax(acc.a[i], o) : acc.a[i] + o;
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sm[warp][i] = acc.a[i];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc.a[i] = lane < nw ? sm[lane][i] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const double o = __shfl_xor_sync(0xffffffffu, acc.a[i], off);
+                acc.a[i] = (i == 5) ? fmax(acc.a[i], o) : acc.a[i] + o;
+            }
+        }
+    }
+}
+
+// Reduce a block's accumulators into partials[blockIdx.x * 8 + i].
+__device__ __forceinline__ void block_reduce_store(Acc& acc, double* __restrict__ partials) {
+    block_reduce(acc);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) partials[(size_t)blockIdx.x * 8 + i] = acc.a[i];
+    }
+}
+
+}  // namespace vlbm

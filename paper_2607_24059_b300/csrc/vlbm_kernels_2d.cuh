@@ -1,0 +1,305 @@
+// D2Q5 vectorial kernels: fused transport + relaxation, initialisation,
+// macroscopic fields, FP64 invariant reduction and population export.
+//
+// Lattice layout in HBM (one lattice per time level, two levels ping-pong):
+//   15 planes p = 5k + l (field k = rho, q_x, q_y; velocity l = rest, +x, -x,
+//   +y, -y), each plane n_y rows of n_x elements, x fastest, no padding.
+//   The buffer holds post-relaxation deviations g*(t) (see vlbm_device.cuh).
+//
+// One time step (pull form of the transport of Section 2):
+//   g(t+dt, x) for velocity c_l is g*(t, x - c_l dx); relax it; store g*(t+dt, x).
+// Each population is read once and written once: 15 reads + 15 writes per node.
+#pragma once
+
+#include "vlbm_device.cuh"
+
+namespace vlbm {
+
+constexpr int kThreads = 256;
+
+template <class S> struct Vec16 {
+    static constexpr int V = 16 / sizeof(S);
+};
+
+template <class S>
+__device__ __forceinline__ void load16(S (&e)[Vec16<S>::V], const S* p) {
+    vload<S, Vec16<S>::V>(e, p);
+}
+
+template <class S>
+__device__ __forceinline__ void store16(S* p, const S (&e)[Vec16<S>::V]) {
+    vstore<S, Vec16<S>::V>(p, e);
+}
+
+// ------------------------------------------------------------------------------
+// Fused stream-collide, vectorised.  Requires n_x % V == 0 (V = 16 B / element).
+// Warp w handles 32 V consecutive nodes of one row; lane L the V nodes starting
+// at x0.  The +x population of node x comes from x - 1: lane L takes its own
+// vector shifted by one element and the last element of lane L-1 by a warp
+// shuffle (lane 0 loads that element from memory, with periodic wrap).  The
+// -x population comes from x + 1, symmetrically.  +y / -y are whole rows
+// y - 1 / y + 1 (periodic), loaded aligned.
+// DIAG: also reduce the invariants of the state being read (time t) into
+// per-block FP64 partials, at no extra HBM traffic.
+template <class S, bool DIAG>
+__global__ void __launch_bounds__(kThreads)
+k_stream_collide_2d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx, int ny, long long plane,
+                        int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+    using C = typename Storage<S>::C;
+    constexpr int V = Vec16<S>::V;
+    const int lane = threadIdx.x & 31;
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    Acc acc;
+    if (DIAG) acc.zero();
+    if (gwarp < (long long)ny * warps_per_row) {   // warp-uniform
+        const int y = (int)(gwarp / warps_per_row);
+        const int x0 = ((int)(gwarp % warps_per_row) * 32 + lane) * V;
+        const bool active = x0 < nx;
+        const long long row = (long long)y * nx;
+        const long long row_m = (long long)(y == 0 ? ny - 1 : y - 1) * nx;
+        const long long row_p = (long long)(y == ny - 1 ? 0 : y + 1) * nx;
+        const int xm = x0 == 0 ? nx - 1 : x0 - 1;        // left neighbour of the lane's first node
+        const int xp = x0 + V >= nx ? 0 : x0 + V;         // right neighbour of the lane's last node
+        const bool fetch_next = active && (lane == 31 || x0 + V >= nx);
+
+        C g[15][V];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const S* base = fin + (long long)(5 * f) * plane;
+            const C isc = Storage<S>::kScaled ? k.inv_scale[f] : C(1);
+            S w[V];
+            // rest: in place
+            if (active) load16(w, base + row + x0); else { for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(C(0)); }
+#pragma unroll
+            for (int i = 0; i < V; ++i) g[5 * f + 0][i] = Storage<S>::to_c(w[i]) * isc;
+            // +x: from x - 1
+            if (active) load16(w, base + plane + row + x0); else { for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(C(0)); }
+            {
+                S prev = __shfl_up_sync(0xffffffffu, w[V - 1], 1);
+                if (lane == 0 && active) prev = base[plane + row + xm];
+                g[5 * f + 1][0] = Storage<S>::to_c(prev) * isc;
+#pragma unroll
+                for (int i = 1; i < V; ++i) g[5 * f + 1][i] = Storage<S>::to_c(w[i - 1]) * isc;
+            }
+            // -x: from x + 1
+            if (active) load16(w, base + 2 * plane + row + x0); else { for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(C(0)); }
+            {
+                S next = __shfl_down_sync(0xffffffffu, w[0], 1);
+                if (fetch_next) next = base[2 * plane + row + xp];
+#pragma unroll
+                for (int i = 0; i < V - 1; ++i) g[5 * f + 2][i] = Storage<S>::to_c(w[i + 1]) * isc;
+                g[5 * f + 2][V - 1] = Storage<S>::to_c(next) * isc;
+            }
+            // +y: from y - 1;  -y: from y + 1
+            if (active) load16(w, base + 3 * plane + row_m + x0); else { for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(C(0)); }
+#pragma unroll
+            for (int i = 0; i < V; ++i) g[5 * f + 3][i] = Storage<S>::to_c(w[i]) * isc;
+            if (active) load16(w, base + 4 * plane + row_p + x0); else { for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(C(0)); }
+#pragma unroll
+            for (int i = 0; i < V; ++i) g[5 * f + 4][i] = Storage<S>::to_c(w[i]) * isc;
+        }
+
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            C gn[15];
+#pragma unroll
+            for (int p = 0; p < 15; ++p) gn[p] = g[p][i];
+            C dr, Qx, Qy;
+            moments_d2q5(gn, dr, Qx, Qy);
+            if (DIAG && active) {
+                const C Q[2] = {Qx, Qy};
+                accumulate_node(acc, all_finite(gn, 15), dr, Q, 2, (double)k.rho_bar);
+            }
+            relax_d2q5(k, gn, dr, Qx, Qy);
+#pragma unroll
+            for (int p = 0; p < 15; ++p) g[p][i] = gn[p];
+        }
+
+        if (active) {
+#pragma unroll
+            for (int p = 0; p < 15; ++p) {
+                const C sc = Storage<S>::kScaled ? k.scale[p / 5] : C(1);
+                S w[V];
+#pragma unroll
+                for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(g[p][i] * sc);
+                store16(fout + (long long)p * plane + row + x0, w);
+            }
+        }
+    }
+    if (DIAG) block_reduce_store(acc, partials);
+}
+
+// ------------------------------------------------------------------------------
+// Fused stream-collide, one thread per node, any n_x (the ragged-size path).
+template <class S, bool DIAG>
+__global__ void __launch_bounds__(kThreads)
+k_stream_collide_2d_generic(const S* __restrict__ fin, S* __restrict__ fout, int nx, int ny, long long plane,
+                            Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+    using C = typename Storage<S>::C;
+    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    Acc acc;
+    if (DIAG) acc.zero();
+    if (node < plane) {
+        const int x = (int)(node % nx), y = (int)(node / nx);
+        const long long row = (long long)y * nx;
+        const long long src[5] = {
+            node,
+            row + (x == 0 ? nx - 1 : x - 1),
+            row + (x == nx - 1 ? 0 : x + 1),
+            (long long)(y == 0 ? ny - 1 : y - 1) * nx + x,
+            (long long)(y == ny - 1 ? 0 : y + 1) * nx + x,
+        };
+        C g[15];
+#pragma unroll
+        for (int p = 0; p < 15; ++p) {
+            const C isc = Storage<S>::kScaled ? k.inv_scale[p / 5] : C(1);
+            g[p] = Storage<S>::to_c(fin[(long long)p * plane + src[p % 5]]) * isc;
+        }
+        C dr, Qx, Qy;
+        moments_d2q5(g, dr, Qx, Qy);
+        if (DIAG) {
+            const C Q[2] = {Qx, Qy};
+            accumulate_node(acc, all_finite(g, 15), dr, Q, 2, (double)k.rho_bar);
+        }
+        relax_d2q5(k, g, dr, Qx, Qy);
+#pragma unroll
+        for (int p = 0; p < 15; ++p) {
+            const C sc = Storage<S>::kScaled ? k.scale[p / 5] : C(1);
+            fout[(long long)p * plane + node] = Storage<S>::from_c(g[p] * sc);
+        }
+    }
+    if (DIAG) block_reduce_store(acc, partials);
+}
+
+// ------------------------------------------------------------------------------
+// Initialisation at equilibrium: P(rho) = P(rho_bar) + dx^2 rho_bar phi,
+// q = rho u, g = f^eq(rho, q) - F.  The density deviation is formed in FP64:
+// gamma = 1 gives dr = dx^2 rho_bar phi exactly; otherwise
+// dr = rho_bar expm1(log1p(dx^2 rho_bar phi / P(rho_bar)) / gamma).
+template <class S, class T>
+__global__ void __launch_bounds__(kThreads)
+k_init_2d(S* __restrict__ f, long long plane, const T* __restrict__ u, const T* __restrict__ phi,
+          Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
+    using C = typename Storage<S>::C;
+    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= plane) return;
+    const double ph = phi ? (double)phi[node] : 0.0;
+    const double lift = dx * dx * rho_bar * ph;
+    const double dr = (gamma == 1.0) ? lift : rho_bar * expm1(log1p(lift / p_bar) / gamma);
+    const double rho = rho_bar + dr;
+    const double Qx = dx * rho * (double)u[node];
+    const double Qy = dx * rho * (double)u[plane + node];
+    C e[15];
+    equilibrium_d2q5(k, (C)dr, (C)Qx, (C)Qy, e);
+#pragma unroll
+    for (int p = 0; p < 15; ++p) {
+        const C sc = Storage<S>::kScaled ? k.scale[p / 5] : C(1);
+        f[(long long)p * plane + node] = Storage<S>::from_c(e[p] * sc);
+    }
+}
+
+// Macroscopic fields of the state (moments of g*(t) = moments of g(t)).
+template <class S, class T>
+__global__ void __launch_bounds__(kThreads)
+k_macros_2d(const S* __restrict__ f, long long plane, T* __restrict__ rho, T* __restrict__ u, T* __restrict__ phi,
+            Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
+    using C = typename Storage<S>::C;
+    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= plane) return;
+    double m[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int fld = 0; fld < 3; ++fld) {
+        const C isc = Storage<S>::kScaled ? k.inv_scale[fld] : C(1);
+        C s = C(0);
+#pragma unroll
+        for (int l = 0; l < 5; ++l) s += Storage<S>::to_c(f[(long long)(5 * fld + l) * plane + node]) * isc;
+        m[fld] = (double)s;
+    }
+    const double r = rho_bar + m[0];
+    if (rho) rho[node] = (T)r;
+    if (u) {
+        u[node] = (T)(m[1] / (dx * r));
+        u[plane + node] = (T)(m[2] / (dx * r));
+    }
+    if (phi) {
+        const double dP = (gamma == 1.0) ? m[0] : p_bar * expm1(gamma * log1p(m[0] / rho_bar));
+        phi[node] = (T)(dP / (dx * dx * rho_bar));
+    }
+}
+
+// Invariant partials over the stored lattice (no transport), grid-stride.
+template <class S>
+__global__ void __launch_bounds__(kThreads)
+k_invariants_2d(const S* __restrict__ f, long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+    using C = typename Storage<S>::C;
+    Acc acc;
+    acc.zero();
+    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < plane;
+         node += (long long)gridDim.x * blockDim.x) {
+        C g[15];
+#pragma unroll
+        for (int p = 0; p < 15; ++p) {
+            const C isc = Storage<S>::kScaled ? k.inv_scale[p / 5] : C(1);
+            g[p] = Storage<S>::to_c(f[(long long)p * plane + node]) * isc;
+        }
+        C dr, Qx, Qy;
+        moments_d2q5(g, dr, Qx, Qy);
+        const C Q[2] = {Qx, Qy};
+        accumulate_node(acc, all_finite(g, 15), dr, Q, 2, (double)k.rho_bar);
+    }
+    block_reduce_store(acc, partials);
+}
+
+// Final reduction of nblocks partials (one block, fixed order) into the
+// invariants { N rho_bar + sum dr, sum Q_d / dx (3), E_kin, max|u|, non-finite
+// nodes, sum dr }.  scale_e = dx^(d-2) turns sum |Q|^2/(2 rho) into
+// 1/2 sum |q|^2/rho dx^d.  Shared by 2D and 3D.
+__global__ void __launch_bounds__(1024)
+k_invariants_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out, double nodes,
+                   double rho_bar, double inv_dx, double scale_e) {
+    Acc acc;
+    acc.zero();
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const double v = partials[(size_t)b * 8 + i];
+            acc.a[i] = (i == 5) ? fmax(acc.a[i], v) : acc.a[i] + v;
+        }
+    }
+    block_reduce(acc);
+    if (threadIdx.x == 0) {
+        out[0] = nodes * rho_bar + acc.a[0];
+        out[1] = acc.a[1] * inv_dx;
+        out[2] = acc.a[2] * inv_dx;
+        out[3] = acc.a[3] * inv_dx;
+        out[4] = acc.a[4] * scale_e;
+        out[5] = acc.a[5] * inv_dx;
+        out[6] = acc.a[6];
+        out[7] = acc.a[0];
+    }
+}
+
+// Export populations in [p][node] order (p = q k + l): the stored deviation
+// g_p, or g_p + F_p with the rest equilibrium F = f^eq(rho_bar, 0):
+// rho field F = (f_rest, f_move, ..., f_move); momentum field j:
+// +p_half on the population along +e_j, -p_half along -e_j, 0 elsewhere.
+// Shared by 2D (q = 5) and 3D (q = 7).
+template <class S, class T>
+__global__ void __launch_bounds__(kThreads)
+k_export(const S* __restrict__ f, long long total, long long plane, int q, T* __restrict__ dst,
+         Coef<typename Storage<S>::C> k, double f_rest, double f_move, double p_half, int deviation) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int p = (int)(i / plane);
+    const int fld = p / q, l = p % q;
+    const double isc = Storage<S>::kScaled ? (double)k.inv_scale[fld] : 1.0;
+    double v = (double)Storage<S>::to_c(f[i]) * isc;
+    if (!deviation) {
+        if (fld == 0) v += (l == 0) ? f_rest : f_move;
+        else if (l == 2 * (fld - 1) + 1) v += p_half;
+        else if (l == 2 * (fld - 1) + 2) v -= p_half;
+    }
+    dst[i] = (T)v;
+}
+
+}  // namespace vlbm

@@ -1,0 +1,348 @@
+"""CUDA path against the FP64 oracle, element by element (needs a B300).
+
+Tolerances:
+  FP64 storage: 1e-12 of max|u| (the CUDA path works on deviations from the rest
+    equilibrium, the oracle on raw populations: rounding orders differ, the
+    difference stays at a few hundred ulps after 1000 steps).
+  FP32 storage: 1e-5 of max|u| after 1000 steps of the 64^2 Taylor-Green vortex
+    (the gate the FP32 form must meet against FP64).
+Inputs are seeded and synthetic (synthetic/), shared by both sides; no expected
+value comes from the CUDA path.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2607_24059_b300 as v  # noqa: E402
+
+
+def resolved(n, dx, nu, omega_rho=1.2, alpha_rho=0.075, omega_q=1.15, gamma=1.0, mu=8.0):
+    """Oracle parameters; alpha_q from the viscosity relation of Prop. 1 (oracle helper)."""
+    return oracle.make_params(n, dx, nu=nu, mu=mu, omega_rho=omega_rho, alpha_rho=alpha_rho, omega_q=omega_q,
+                              gamma=gamma)
+
+
+def gpu_lattice(op: oracle.Params, precision):
+    """A Lattice with exactly the oracle's parameters."""
+    lat = v.Lattice(op.n, op.dx, nu=0.0, precision=precision, mu=op.mu, omega_rho=op.omega[0],
+                    alpha_rho=op.alpha[0], omega_q=op.omega[1], alpha_q=op.alpha[1], gamma=op.gamma,
+                    rho_bar=op.rho_bar)
+    return lat
+
+
+def gpu_run(op, precision, u, phi, nsteps, variant=None, graph=True):
+    lat = gpu_lattice(op, precision)
+    if variant is not None:
+        lat.set_option(v.VLBM_OPT_KERNEL, variant)
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    lat.step(nsteps, graph=graph)
+    rho, uu, ph = lat.macros()
+    torch.cuda.synchronize()
+    out = rho.cpu().numpy(), uu.cpu().numpy(), ph.cpu().numpy()
+    lat.close()
+    return out
+
+
+def orc_run(orc, op, u, phi, nsteps):
+    f = orc.run(op, orc.init(op, u, phi), nsteps)
+    return orc.macros(op, f), f
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def smooth_random_state(n, seed, amp=0.4):
+    """Seeded smooth velocity and potential on an arbitrary (nx, ny) lattice."""
+    rng = np.random.default_rng(seed)
+    nx, ny = n
+    x = (np.arange(nx) + 0.5) / nx * 2 * math.pi
+    y = (np.arange(ny) + 0.5) / ny * 2 * math.pi
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    u = np.zeros((2, ny, nx))
+    for c in range(2):
+        for _ in range(3):
+            kx, ky = rng.integers(0, 3, size=2)
+            ph = rng.uniform(0, 2 * math.pi)
+            u[c] += amp / 3 * np.sin(kx * X + ky * Y + ph)
+    phi = 0.5 * np.cos(X + 2 * Y + rng.uniform(0, 6))
+    return u, phi
+
+
+# ------------------------------------------------------------ Taylor-Green, 64^2, 1000 steps
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_tgv_64_1000_steps(orc, precision, tol):
+    n = 64
+    u, phi, dx = synthetic.taylor_green_2d(n)
+    op = resolved((n, n), dx, nu=0.01)
+    (rho_o, u_o, phi_o), _ = orc_run(orc, op, u, phi, 1000)
+    rho_g, u_g, phi_g = gpu_run(op, precision, u, phi, 1000)
+    err_u = np.max(np.abs(u_g - u_o)) / np.max(np.abs(u_o))
+    assert err_u <= tol, err_u
+    # pressure-like potential: O(dx^2) density signal, still resolved
+    assert rel_err(phi_g, phi_o) <= (1e-9 if precision == "fp64" else 1e-3)
+
+
+# ------------------------------------------------------------ ragged and degenerate sizes
+
+SIZES = [(37, 53), (5, 7), (1, 9), (9, 1), (1, 1), (4, 3), (2, 2), (136, 10), (260, 6), (128, 4)]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_ragged_sizes(orc, n, precision, tol):
+    u, phi = smooth_random_state(n, seed=n[0] * 1000 + n[1])
+    op = resolved(n, 0.05, nu=0.02, omega_rho=1.3, omega_q=1.1)
+    (_, u_o, phi_o), _ = orc_run(orc, op, u, phi, 120)
+    _, u_g, phi_g = gpu_run(op, precision, u, phi, 120)
+    assert np.max(np.abs(u_g - u_o)) <= tol * max(np.max(np.abs(u_o)), 1e-3)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [(64, 48), (128, 20), (8, 3)])
+def test_vector_and_generic_kernels_bitwise(n, precision):
+    u, phi = smooth_random_state(n, seed=3)
+    op = resolved(n, 0.05, nu=0.02)
+    a = gpu_run(op, precision, u, phi, 77, variant=1)
+    b = gpu_run(op, precision, u, phi, 77, variant=2)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_graph_replay_is_bitwise_equal_to_launches():
+    n = (96, 40)
+    u, phi = smooth_random_state(n, seed=9)
+    op = resolved(n, 0.05, nu=0.02)
+    a = gpu_run(op, "fp32", u, phi, 200, graph=True)
+    b = gpu_run(op, "fp32", u, phi, 200, graph=False)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+# ------------------------------------------------------------ populations, init, macros, invariants
+
+def test_init_and_macros_match_oracle(orc):
+    n = (48, 40)
+    u, phi = smooth_random_state(n, seed=21)
+    for gamma in (1.0, 1.4):
+        op = resolved(n, 0.05, nu=0.02, gamma=gamma)
+        (rho_o, u_o, phi_o), _ = orc_run(orc, op, u, phi, 0)
+        rho_g, u_g, phi_g = gpu_run(op, "fp64", u, phi, 0)
+        assert np.max(np.abs(rho_g - rho_o)) < 1e-15
+        assert np.max(np.abs(u_g - u_o)) < 1e-14
+        assert np.max(np.abs(phi_g - phi_o)) < 1e-9
+
+
+@pytest.mark.parametrize("gamma", [1.0, 1.4])
+def test_populations_match_oracle_post_relaxation(orc, gamma):
+    """The handle stores f*(t): compare with the oracle's relaxation of its f(t)."""
+    n = (40, 24)
+    u, phi = smooth_random_state(n, seed=5)
+    op = resolved(n, 0.05, nu=0.02, gamma=gamma)
+    _, f_o = orc_run(orc, op, u, phi, 50)
+    fstar_o = orc.collide(op, f_o)
+    lat = gpu_lattice(op, "fp64")
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    lat.step(50)
+    f_g = lat.populations().cpu().numpy()
+    g_g = lat.populations(deviation=True).cpu().numpy()
+    lat.close()
+    assert np.max(np.abs(f_g - fstar_o)) < 1e-13
+    fbar = orc.init(op, np.zeros((2,) + f_g.shape[2:]), np.zeros(f_g.shape[2:]))
+    assert np.max(np.abs(g_g - (fstar_o - fbar))) < 1e-13
+
+
+def test_invariants_match_oracle(orc):
+    n = (64, 64)
+    u, phi, dx = synthetic.taylor_green_2d(64)
+    u = u + 0.1                                   # nonzero net momentum
+    op = resolved(n, dx, nu=0.01)
+    _, f_o = orc_run(orc, op, u, phi, 100)
+    inv_o = orc.invariants(op, f_o)
+    lat = gpu_lattice(op, "fp64")
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    lat.step(100)
+    inv_g = lat.invariants()
+    assert abs(inv_g[0] - inv_o[0]) <= 1e-13 * inv_o[0]
+    assert np.allclose(inv_g[1:3], inv_o[1:3], rtol=1e-12, atol=1e-10)
+    assert inv_g[3] == 0.0
+    assert abs(inv_g[4] - inv_o[4]) <= 1e-12 * inv_o[4]
+    assert abs(inv_g[5] - inv_o[5]) <= 1e-12 * inv_o[5]
+    assert inv_g[6] == 0.0
+    assert abs(inv_g[7] - inv_o[7]) <= 1e-9 * abs(inv_o[7]) + 1e-12
+    # device-pointer output gives the same numbers
+    out = torch.zeros(8, dtype=torch.float64, device="cuda")
+    v.vlbm_invariants(lat.handle, out)
+    assert np.array_equal(out.cpu().numpy(), inv_g)
+    lat.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fused_records_match_invariants(precision):
+    """vlbm_step_record reduces the invariants inside the step kernel: they must
+    equal a separate vlbm_invariants pass over the state that step produced."""
+    n = (64, 40)
+    u, phi = smooth_random_state(n, seed=23)
+    # the fused pass sums the transported populations, the separate pass the
+    # relaxed ones: equal moments up to the rounding of the relaxation
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    lat = gpu_lattice(resolved(n, 0.05, nu=0.02), precision)
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    for every, nsteps in ((1, 1), (3, 7), (70, 140)):
+        rec = lat.step_record(nsteps, every)
+        ref = lat.invariants()        # the state after the call
+        if (nsteps - 1) % every == 0:  # the last step was recorded
+            last = rec[-1]
+            assert np.allclose(last, ref, rtol=tol, atol=tol * np.max(np.abs(ref)))
+        assert rec.shape == ((nsteps + every - 1) // every, 8)
+    # device destination, and time advanced by every recorded call
+    dev = torch.zeros((2, 8), dtype=torch.float64, device="cuda")
+    lat.step_record(2, 1, dev)
+    ref = lat.invariants()
+    assert np.allclose(dev[1].cpu().numpy(), ref, rtol=tol, atol=tol * np.max(np.abs(ref)))
+    assert lat.time()[0] == 1 + 7 + 140 + 2
+    lat.close()
+
+
+def test_host_and_device_pointers_agree():
+    n = (64, 32)
+    u, phi = smooth_random_state(n, seed=13)
+    op = resolved(n, 0.05, nu=0.02)
+    a = gpu_lattice(op, "fp32")
+    a.init(u, phi)                                          # numpy: host memory
+    a.step(30)
+    rho_h = np.empty((32, 64))
+    u_h = np.empty((2, 32, 64))
+    v.vlbm_macros(a.handle, rho_h, u_h, None)
+    b = gpu_lattice(op, "fp32")
+    b.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    b.step(30)
+    rho_d, u_d, _ = b.macros()
+    assert np.array_equal(rho_h, rho_d.cpu().numpy())
+    assert np.array_equal(u_h, u_d.cpu().numpy())
+    pinned = torch.from_numpy(u).pin_memory()
+    a.init(pinned, torch.from_numpy(phi).pin_memory())
+    a.step(30)
+    rho_p, u_p, _ = a.macros()
+    assert np.array_equal(u_p.cpu().numpy(), u_h)
+    a.close()
+    b.close()
+
+
+# ------------------------------------------------------------ checkpoint / failure detection
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_resume_is_bitwise(precision):
+    n = (64, 40)
+    u, phi = smooth_random_state(n, seed=17)
+    op = resolved(n, 0.05, nu=0.02)
+    lat = gpu_lattice(op, precision)
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    lat.step(40)
+    blob = lat.state()
+    lat.step(90)
+    a = lat.populations(deviation=True).cpu().numpy()
+    lat.step(5)
+    lat.load_state(blob)
+    assert lat.time()[0] == 40
+    lat.step(90)
+    b = lat.populations(deviation=True).cpu().numpy()
+    assert np.array_equal(a, b)
+    other = gpu_lattice(resolved((64, 41), 0.05, nu=0.02), precision)
+    with pytest.raises(v.VlbmError):
+        other.load_state(blob)
+    other.close()
+    lat.close()
+
+
+def test_non_finite_input_is_reported():
+    n = (32, 32)
+    u, phi = smooth_random_state(n, seed=1)
+    u[0, 5, 7] = np.nan
+    lat = gpu_lattice(resolved(n, 0.05, nu=0.02), "fp32")
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    with pytest.raises(v.VlbmError) as e:
+        lat.step(3, check=True)
+    assert e.value.code == v.VLBM_EDIVERGED
+    assert lat.invariants()[6] >= 1
+    lat.close()
+
+
+def test_launch_counter_counts_kernels():
+    n = (64, 64)
+    u, phi = smooth_random_state(n, seed=2)
+    lat = gpu_lattice(resolved(n, 0.05, nu=0.02), "fp32")
+    c0 = lat.launch_count()
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    lat.step(130)
+    assert lat.launch_count() - c0 == 1 + 130
+    lat.close()
+
+
+# ------------------------------------------------------------ D3Q7
+
+@pytest.mark.parametrize("n", [(16, 12, 8), (15, 6, 5), (2, 3, 4), (1, 1, 6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_d3q7_matches_oracle(orc, n, precision, tol):
+    rng = np.random.default_rng(sum(n))
+    grid = tuple(reversed(n))
+    zz, yy, xx = np.meshgrid(*[(np.arange(m) + 0.5) / m * 2 * math.pi for m in grid], indexing="ij")
+    u = np.stack([0.3 * np.sin(xx + yy + rng.uniform()), 0.2 * np.cos(yy - zz), 0.25 * np.sin(zz + 2 * xx)])
+    phi = 0.4 * np.cos(xx + yy + zz)
+    op = oracle.make_params(n, 0.07, nu=0.01, omega_rho=1.2, alpha_rho=0.05, omega_q=1.15)
+    (_, u_o, _), _ = orc_run(orc, op, u, phi, 60)
+    _, u_g, _ = gpu_run(op, precision, u, phi, 60)
+    assert np.max(np.abs(u_g - u_o)) <= tol * np.max(np.abs(u_o))
+
+
+# ------------------------------------------------------------ the benchmark lattice, full size
+
+def test_full_size_4096_sampled_step_and_conservation(orc):
+    """Double shear layer on 4096^2 in FP32, in the launch configuration the
+    benchmark times: one step checked node by node on sampled nodes (pull from
+    the exported state, relax with the oracle), and conservation over 50 steps."""
+    n = 4096
+    u, phi, dx = synthetic.double_shear_layer(n)
+    op = resolved((n, n), dx, nu=1e-4)
+    lat = gpu_lattice(op, "fp32")
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    lat.step(64)
+    inv0 = lat.invariants()
+    g0 = lat.populations(deviation=True, dtype=torch.float32).cpu().numpy()   # exact: FP32 storage
+    lat.step(1)
+    g1 = lat.populations(deviation=True, dtype=torch.float32).cpu().numpy()
+    rng = np.random.default_rng(4096)
+    xs = np.concatenate([rng.integers(0, n, 4000), [0, n - 1, 0, n - 1, 127, 128]])
+    ys = np.concatenate([rng.integers(0, n, 4000), [0, 0, n - 1, n - 1, 5, 4095]])
+    fbar = orc.init(oracle.Params(n=(1, 1), dx=op.dx, mu=op.mu, omega=op.omega, alpha=op.alpha),
+                    np.zeros((2, 1, 1)), np.zeros((1, 1)))[..., 0, 0]           # rest equilibrium (3, 5)
+    src = [(xs, ys), ((xs - 1) % n, ys), ((xs + 1) % n, ys), (xs, (ys - 1) % n), (xs, (ys + 1) % n)]
+    pulled = np.empty((xs.size, 3, 5))
+    for l, (sx, sy) in enumerate(src):
+        pulled[:, :, l] = g0[:, l, sy, sx].T.astype(np.float64)
+    fstar = orc.collide_nodes(op, pulled + fbar[None]) - fbar[None]
+    got = g1[:, :, ys, xs].transpose(2, 0, 1).astype(np.float64)
+    for k in range(3):
+        scale = np.max(np.abs(fstar[:, k, :]))
+        assert np.max(np.abs(got[:, k, :] - fstar[:, k, :])) <= 2e-6 * scale, k
+    lat.step(50)
+    inv1 = lat.invariants()
+    # FP32 storage conserves to rounding: drift of the momentum totals relative
+    # to the total |momentum|, and of the density deviation relative to N dx^2
+    tot_q = np.sum(np.abs(u)) * dx
+    assert abs(inv1[1] - inv0[1]) * dx <= 1e-5 * tot_q
+    assert abs(inv1[2] - inv0[2]) * dx <= 1e-5 * tot_q
+    assert abs(inv1[7] - inv0[7]) <= 1e-5 * n * n * dx * dx
+    assert inv1[6] == 0.0
+    lat.close()
