@@ -192,15 +192,35 @@ __device__ __forceinline__ void vstore(S* p, const S (&e)[V]) {
 }
 
 // ---------------------------------------------------------------- diagnostics
-// Per-thread FP64 accumulators of the invariants:
-//   a[0] sum dr, a[1..3] sum Q_d, a[4] sum |Q|^2 / (2 rho), a[5] max |Q| / rho,
-//   a[6] non-finite nodes, a[7] unused.
+// Invariant accumulators.  B300's FP64 pipe is narrow, so per-node work stays
+// in the compute type: with FP32 compute every sum is carried as an unevaluated
+// float pair (hi, lo) updated by Knuth's TwoSum, which keeps about 48 bits, and
+// FP64 is used only across warps and blocks.  With FP64 compute the pair
+// degenerates to plain FP64 sums.  Slots:
+//   s[0] sum dr, s[1..3] sum Q_d, s[4] sum |Q|^2 / (2 rho); mx = max |Q|^2 / rho^2;
+//   bad = nodes with a non-finite population.
+template <class C>
+__device__ __forceinline__ void two_sum_acc(C& hi, C& lo, C x) {
+    if (sizeof(C) == 8) {          // FP64 compute: plain sums
+        hi += x;
+        return;
+    }
+    const C s = hi + x;
+    const C bb = s - hi;
+    lo += (hi - (s - bb)) + (x - bb);
+    hi = s;
+}
+
+template <class C>
 struct Acc {
-    double a[8];
+    C hi[5], lo[5];
+    C mx, bad;
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) a[i] = 0.0;
+        for (int i = 0; i < 5; ++i) hi[i] = lo[i] = C(0);
+        mx = bad = C(0);
     }
+    __device__ __forceinline__ void add(int i, C x) { two_sum_acc(hi[i], lo[i], x); }
 };
 
 template <class C>
@@ -211,63 +231,74 @@ __device__ __forceinline__ bool all_finite(const C* g, int n) {
 }
 
 template <class C>
-__device__ __forceinline__ void accumulate_node(Acc& acc, bool finite, C dr, const C* Q, int dim, double rho_bar) {
+__device__ __forceinline__ void accumulate_node(Acc<C>& acc, bool finite, C dr, const C* Q, int dim, C rho_bar) {
     if (!finite) {
-        acc.a[6] += 1.0;
+        acc.bad += C(1);
         return;
     }
-    const double rho = rho_bar + (double)dr;
-    double q2 = 0.0;
-    acc.a[0] += (double)dr;
+    const C r = C(1) / (rho_bar + dr);
+    C q2 = C(0);
+    acc.add(0, dr);
     for (int d = 0; d < dim; ++d) {
-        const double qd = (double)Q[d];
-        acc.a[1 + d] += qd;
-        q2 += qd * qd;
+        acc.add(1 + d, Q[d]);
+        q2 += Q[d] * Q[d];
     }
-    acc.a[4] += 0.5 * q2 / rho;
-    acc.a[5] = fmax(acc.a[5], sqrt(q2) / rho);
+    acc.add(4, C(0.5) * q2 * r);
+    acc.mx = fmax(acc.mx, q2 * r * r);
 }
 
-// Block-wide reduction of the accumulators (sums, and max for a[5]); the
-// result ends in thread 0's acc.  Fixed shuffle tree and warp order, so the
-// result is deterministic for a given launch shape.
-__device__ __forceinline__ void block_reduce(Acc& acc) {
-    __shared__ double sm[32][8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Warp tree on the pairs: (h1, l1) + (h2, l2) by TwoSum of the heads.
+template <class C>
+__device__ __forceinline__ void warp_reduce(Acc<C>& acc) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const double o = __shfl_xor_sync(0xffffffffu, acc.a[i], off);
-            acc.a[i] = (i == 5) ? fmax(acc.a[i], o) : acc.a[i] + o;
+        for (int i = 0; i < 5; ++i) {
+            const C oh = __shfl_xor_sync(0xffffffffu, acc.hi[i], off);
+            const C ol = __shfl_xor_sync(0xffffffffu, acc.lo[i], off);
+            C h = acc.hi[i], l = acc.lo[i] + ol;
+            two_sum_acc(h, l, oh);
+            acc.hi[i] = h;
+            acc.lo[i] = l;
         }
+        acc.mx = fmax(acc.mx, __shfl_xor_sync(0xffffffffu, acc.mx, off));
+        acc.bad += __shfl_xor_sync(0xffffffffu, acc.bad, off);
     }
+}
+
+// Reduce a block's accumulators into partials[blockIdx.x * 8 + i] (FP64):
+// { sum dr, sum Q_x, sum Q_y, sum Q_z, sum |Q|^2/(2 rho), max |Q|/rho, bad, 0 }.
+// Fixed shuffle tree and warp order: deterministic for a given launch shape.
+template <class C>
+__device__ __forceinline__ void block_reduce_store(Acc<C>& acc, double* __restrict__ partials) {
+    __shared__ double sm[32][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    warp_reduce(acc);
     if (lane == 0) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) sm[warp][i] = acc.a[i];
+        for (int i = 0; i < 5; ++i) sm[warp][i] = (double)acc.hi[i] + (double)acc.lo[i];
+        sm[warp][5] = sqrt((double)acc.mx);
+        sm[warp][6] = (double)acc.bad;
+        sm[warp][7] = 0.0;
     }
     __syncthreads();
     if (warp == 0) {
         const int nw = (blockDim.x + 31) >> 5;
+        double v[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc.a[i] = lane < nw ? sm[lane][i] : 0.0;
+        for (int i = 0; i < 8; ++i) v[i] = lane < nw ? sm[lane][i] : 0.0;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const double o = __shfl_xor_sync(0xffffffffu, acc.a[i], off);
-                acc.a[i] = (i == 5) ? fmax(acc.a[i], o) : acc.a[i] + o;
+                const double o = __shfl_xor_sync(0xffffffffu, v[i], off);
+                v[i] = (i == 5) ? fmax(v[i], o) : v[i] + o;
             }
         }
-    }
-}
-
-// Reduce a block's accumulators into partials[blockIdx.x * 8 + i].
-__device__ __forceinline__ void block_reduce_store(Acc& acc, double* __restrict__ partials) {
-    block_reduce(acc);
-    if (threadIdx.x == 0) {
+        if (lane == 0) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) partials[(size_t)blockIdx.x * 8 + i] = acc.a[i];
+            for (int i = 0; i < 8; ++i) partials[(size_t)blockIdx.x * 8 + i] = v[i];
+        }
     }
 }
 

@@ -49,7 +49,7 @@ k_stream_collide_2d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx,
     constexpr int V = Vec16<S>::V;
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    Acc acc;
+    Acc<C> acc;
     if (DIAG) acc.zero();
     if (gwarp < (long long)ny * warps_per_row) {   // warp-uniform
         const int y = (int)(gwarp / warps_per_row);
@@ -108,7 +108,7 @@ k_stream_collide_2d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx,
             moments_d2q5(gn, dr, Qx, Qy);
             if (DIAG && active) {
                 const C Q[2] = {Qx, Qy};
-                accumulate_node(acc, all_finite(gn, 15), dr, Q, 2, (double)k.rho_bar);
+                accumulate_node(acc, all_finite(gn, 15), dr, Q, 2, k.rho_bar);
             }
             relax_d2q5(k, gn, dr, Qx, Qy);
 #pragma unroll
@@ -137,7 +137,7 @@ k_stream_collide_2d_generic(const S* __restrict__ fin, S* __restrict__ fout, int
                             Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
     using C = typename Storage<S>::C;
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    Acc acc;
+    Acc<C> acc;
     if (DIAG) acc.zero();
     if (node < plane) {
         const int x = (int)(node % nx), y = (int)(node / nx);
@@ -159,7 +159,7 @@ k_stream_collide_2d_generic(const S* __restrict__ fin, S* __restrict__ fout, int
         moments_d2q5(g, dr, Qx, Qy);
         if (DIAG) {
             const C Q[2] = {Qx, Qy};
-            accumulate_node(acc, all_finite(g, 15), dr, Q, 2, (double)k.rho_bar);
+            accumulate_node(acc, all_finite(g, 15), dr, Q, 2, k.rho_bar);
         }
         relax_d2q5(k, g, dr, Qx, Qy);
 #pragma unroll
@@ -232,7 +232,7 @@ template <class S>
 __global__ void __launch_bounds__(kThreads)
 k_invariants_2d(const S* __restrict__ f, long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
     using C = typename Storage<S>::C;
-    Acc acc;
+    Acc<C> acc;
     acc.zero();
     for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < plane;
          node += (long long)gridDim.x * blockDim.x) {
@@ -245,37 +245,46 @@ k_invariants_2d(const S* __restrict__ f, long long plane, Coef<typename Storage<
         C dr, Qx, Qy;
         moments_d2q5(g, dr, Qx, Qy);
         const C Q[2] = {Qx, Qy};
-        accumulate_node(acc, all_finite(g, 15), dr, Q, 2, (double)k.rho_bar);
+        accumulate_node(acc, all_finite(g, 15), dr, Q, 2, k.rho_bar);
     }
     block_reduce_store(acc, partials);
 }
 
-// Final reduction of nblocks partials (one block, fixed order) into the
-// invariants { N rho_bar + sum dr, sum Q_d / dx (3), E_kin, max|u|, non-finite
-// nodes, sum dr }.  scale_e = dx^(d-2) turns sum |Q|^2/(2 rho) into
-// 1/2 sum |q|^2/rho dx^d.  Shared by 2D and 3D.
+// Final reduction of nblocks partials (one block of 1024 threads, fixed order)
+// into the invariants { N rho_bar + sum dr, sum Q_d / dx (3), E_kin, max|u|,
+// non-finite nodes, sum dr }.  Thread t owns slot t % 8 of blocks t / 8,
+// t / 8 + 128, ...: consecutive threads read consecutive doubles.
+// scale_e = dx^(d-2) turns sum |Q|^2/(2 rho) into 1/2 sum |q|^2/rho dx^d.
+// Shared by 2D and 3D.
 __global__ void __launch_bounds__(1024)
 k_invariants_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out, double nodes,
                    double rho_bar, double inv_dx, double scale_e) {
-    Acc acc;
-    acc.zero();
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const double v = partials[(size_t)b * 8 + i];
-            acc.a[i] = (i == 5) ? fmax(acc.a[i], v) : acc.a[i] + v;
-        }
+    __shared__ double sh[1024];
+    const int t = threadIdx.x, slot = t & 7;
+    const bool is_max = slot == 5;
+    double a = 0.0;
+    for (int b = t >> 3; b < nblocks; b += 128) {
+        const double v = partials[(size_t)b * 8 + slot];
+        a = is_max ? fmax(a, v) : a + v;
     }
-    block_reduce(acc);
-    if (threadIdx.x == 0) {
-        out[0] = nodes * rho_bar + acc.a[0];
-        out[1] = acc.a[1] * inv_dx;
-        out[2] = acc.a[2] * inv_dx;
-        out[3] = acc.a[3] * inv_dx;
-        out[4] = acc.a[4] * scale_e;
-        out[5] = acc.a[5] * inv_dx;
-        out[6] = acc.a[6];
-        out[7] = acc.a[0];
+    sh[t] = a;
+    __syncthreads();
+    for (int stride = 64; stride > 0; stride >>= 1) {
+        if ((t >> 3) < stride) {
+            const double o = sh[t + stride * 8];
+            sh[t] = is_max ? fmax(sh[t], o) : sh[t] + o;
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        out[0] = nodes * rho_bar + sh[0];
+        out[1] = sh[1] * inv_dx;
+        out[2] = sh[2] * inv_dx;
+        out[3] = sh[3] * inv_dx;
+        out[4] = sh[4] * scale_e;
+        out[5] = sh[5] * inv_dx;
+        out[6] = sh[6];
+        out[7] = sh[0];
     }
 }
 

@@ -24,7 +24,7 @@ k_stream_collide_3d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx,
     constexpr int V = Vec8<S>::V;
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    Acc acc;
+    Acc<C> acc;
     if (DIAG) acc.zero();
     if (gwarp < (long long)ny * nz * warps_per_row) {
         const long long r = gwarp / warps_per_row;        // row index (z * ny + y)
@@ -79,7 +79,7 @@ k_stream_collide_3d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx,
             for (int p = 0; p < 28; ++p) gn[p] = g[p][i];
             C dr, Q[3];
             moments_d3q7(gn, dr, Q);
-            if (DIAG && active) accumulate_node(acc, all_finite(gn, 28), dr, Q, 3, (double)k.rho_bar);
+            if (DIAG && active) accumulate_node(acc, all_finite(gn, 28), dr, Q, 3, k.rho_bar);
             relax_d3q7(k, gn, dr, Q);
 #pragma unroll
             for (int p = 0; p < 28; ++p) g[p][i] = gn[p];
@@ -106,7 +106,7 @@ k_stream_collide_3d_generic(const S* __restrict__ fin, S* __restrict__ fout, int
                             long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
     using C = typename Storage<S>::C;
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    Acc acc;
+    Acc<C> acc;
     if (DIAG) acc.zero();
     if (node < plane) {
         const int x = (int)(node % nx);
@@ -130,7 +130,7 @@ k_stream_collide_3d_generic(const S* __restrict__ fin, S* __restrict__ fout, int
         }
         C dr, Q[3];
         moments_d3q7(g, dr, Q);
-        if (DIAG) accumulate_node(acc, all_finite(g, 28), dr, Q, 3, (double)k.rho_bar);
+        if (DIAG) accumulate_node(acc, all_finite(g, 28), dr, Q, 3, k.rho_bar);
         relax_d3q7(k, g, dr, Q);
 #pragma unroll
         for (int p = 0; p < 28; ++p) {
@@ -194,7 +194,7 @@ template <class S>
 __global__ void __launch_bounds__(kThreads)
 k_invariants_3d(const S* __restrict__ f, long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
     using C = typename Storage<S>::C;
-    Acc acc;
+    Acc<C> acc;
     acc.zero();
     for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < plane;
          node += (long long)gridDim.x * blockDim.x) {
@@ -206,7 +206,7 @@ k_invariants_3d(const S* __restrict__ f, long long plane, Coef<typename Storage<
         }
         C dr, Q[3];
         moments_d3q7(g, dr, Q);
-        accumulate_node(acc, all_finite(g, 28), dr, Q, 3, (double)k.rho_bar);
+        accumulate_node(acc, all_finite(g, 28), dr, Q, 3, k.rho_bar);
     }
     block_reduce_store(acc, partials);
 }
