@@ -193,14 +193,15 @@ def oracle_sample(args, seconds):
     u, phi, dx = synthetic.double_shear_layer(args.n)
     p = oracle.make_params((args.n, args.n), dx, nu=1e-4)
     f = orc.init(p, u, phi)
-    f = orc.run(p, f, 1)                      # warm-up step (first touch of the work lattice)
+    f = orc.run(p, f, 2)                      # warm-up (first touch of the work lattice, thread start)
+    m = 0
     t0 = time.perf_counter()
-    f = orc.run(p, f, 1)                      # sizes the sample
-    t1 = time.perf_counter() - t0
-    m = int(max(1, min(200, seconds / max(t1, 1e-6))))
-    t0 = time.perf_counter()
-    f = orc.run(p, f, m)
-    el = time.perf_counter() - t0
+    while True:                               # whole steps until the time budget is used
+        f = orc.run(p, f, 1)
+        m += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or m >= 500:
+            break
     return {"value": args.n * args.n * m / el / 1e9, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
             "sample": f"{args.n}^2 double shear layer, {m} FP64 oracle steps after 2 warm-up steps "
                       f"(plain C, OpenMP over rows, {orc.num_threads()} threads)", "seconds": el}

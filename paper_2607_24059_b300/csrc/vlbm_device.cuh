@@ -223,10 +223,13 @@ struct Acc {
     __device__ __forceinline__ void add(int i, C x) { two_sum_acc(hi[i], lo[i], x); }
 };
 
+// A node holds a non-finite population exactly when one of its field sums is
+// non-finite (NaN and inf propagate through the sum; inf - inf is NaN), so the
+// test runs on the D + 1 moments instead of every population.
 template <class C>
-__device__ __forceinline__ bool all_finite(const C* g, int n) {
-    bool ok = true;
-    for (int i = 0; i < n; ++i) ok = ok && isfinite(g[i]);
+__device__ __forceinline__ bool moments_finite(C dr, const C* Q, int dim) {
+    bool ok = isfinite(dr);
+    for (int d = 0; d < dim; ++d) ok = ok && isfinite(Q[d]);
     return ok;
 }
 
@@ -277,7 +280,7 @@ __device__ __forceinline__ void block_reduce_store(Acc<C>& acc, double* __restri
     if (lane == 0) {
 #pragma unroll
         for (int i = 0; i < 5; ++i) sm[warp][i] = (double)acc.hi[i] + (double)acc.lo[i];
-        sm[warp][5] = sqrt((double)acc.mx);
+        sm[warp][5] = (double)sqrt(acc.mx);
         sm[warp][6] = (double)acc.bad;
         sm[warp][7] = 0.0;
     }

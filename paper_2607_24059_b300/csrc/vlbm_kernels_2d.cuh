@@ -108,7 +108,7 @@ k_stream_collide_2d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx,
             moments_d2q5(gn, dr, Qx, Qy);
             if (DIAG && active) {
                 const C Q[2] = {Qx, Qy};
-                accumulate_node(acc, all_finite(gn, 15), dr, Q, 2, k.rho_bar);
+                accumulate_node(acc, moments_finite(dr, Q, 2), dr, Q, 2, k.rho_bar);
             }
             relax_d2q5(k, gn, dr, Qx, Qy);
 #pragma unroll
@@ -159,7 +159,7 @@ k_stream_collide_2d_generic(const S* __restrict__ fin, S* __restrict__ fout, int
         moments_d2q5(g, dr, Qx, Qy);
         if (DIAG) {
             const C Q[2] = {Qx, Qy};
-            accumulate_node(acc, all_finite(g, 15), dr, Q, 2, k.rho_bar);
+            accumulate_node(acc, moments_finite(dr, Q, 2), dr, Q, 2, k.rho_bar);
         }
         relax_d2q5(k, g, dr, Qx, Qy);
 #pragma unroll
@@ -245,7 +245,7 @@ k_invariants_2d(const S* __restrict__ f, long long plane, Coef<typename Storage<
         C dr, Qx, Qy;
         moments_d2q5(g, dr, Qx, Qy);
         const C Q[2] = {Qx, Qy};
-        accumulate_node(acc, all_finite(g, 15), dr, Q, 2, k.rho_bar);
+        accumulate_node(acc, moments_finite(dr, Q, 2), dr, Q, 2, k.rho_bar);
     }
     block_reduce_store(acc, partials);
 }
@@ -263,6 +263,7 @@ k_invariants_final(const double* __restrict__ partials, int nblocks, double* __r
     const int t = threadIdx.x, slot = t & 7;
     const bool is_max = slot == 5;
     double a = 0.0;
+#pragma unroll 16
     for (int b = t >> 3; b < nblocks; b += 128) {
         const double v = partials[(size_t)b * 8 + slot];
         a = is_max ? fmax(a, v) : a + v;

@@ -79,7 +79,7 @@ k_stream_collide_3d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx,
             for (int p = 0; p < 28; ++p) gn[p] = g[p][i];
             C dr, Q[3];
             moments_d3q7(gn, dr, Q);
-            if (DIAG && active) accumulate_node(acc, all_finite(gn, 28), dr, Q, 3, k.rho_bar);
+            if (DIAG && active) accumulate_node(acc, moments_finite(dr, Q, 3), dr, Q, 3, k.rho_bar);
             relax_d3q7(k, gn, dr, Q);
 #pragma unroll
             for (int p = 0; p < 28; ++p) g[p][i] = gn[p];
@@ -130,7 +130,7 @@ k_stream_collide_3d_generic(const S* __restrict__ fin, S* __restrict__ fout, int
         }
         C dr, Q[3];
         moments_d3q7(g, dr, Q);
-        if (DIAG) accumulate_node(acc, all_finite(g, 28), dr, Q, 3, k.rho_bar);
+        if (DIAG) accumulate_node(acc, moments_finite(dr, Q, 3), dr, Q, 3, k.rho_bar);
         relax_d3q7(k, g, dr, Q);
 #pragma unroll
         for (int p = 0; p < 28; ++p) {
@@ -206,7 +206,7 @@ k_invariants_3d(const S* __restrict__ f, long long plane, Coef<typename Storage<
         }
         C dr, Q[3];
         moments_d3q7(g, dr, Q);
-        accumulate_node(acc, all_finite(g, 28), dr, Q, 3, k.rho_bar);
+        accumulate_node(acc, moments_finite(dr, Q, 3), dr, Q, 3, k.rho_bar);
     }
     block_reduce_store(acc, partials);
 }
