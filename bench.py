@@ -193,11 +193,12 @@ def oracle_sample(args, seconds):
     u, phi, dx = synthetic.double_shear_layer(args.n)
     p = oracle.make_params((args.n, args.n), dx, nu=1e-4)
     f = orc.init(p, u, phi)
-    f = orc.run(p, f, 2)                      # warm-up (first touch of the work lattice, thread start)
+    work = np.empty_like(f)
+    orc.run_inplace(p, f, work, 2)            # warm-up (first touch of the work lattice, thread start)
     m = 0
     t0 = time.perf_counter()
     while True:                               # whole steps until the time budget is used
-        f = orc.run(p, f, 1)
+        orc.run_inplace(p, f, work, 1)
         m += 1
         el = time.perf_counter() - t0
         if el >= seconds or m >= 500:
@@ -218,11 +219,12 @@ def run_reference(args):
     u, phi, dx = synthetic.double_shear_layer(args.n)
     p = oracle.make_params((args.n, args.n), dx, nu=1e-4)
     f = orc.init(p, u, phi)
-    f = orc.run(p, f, max(1, min(args.warmup, 3)))
+    work = np.empty_like(f)
+    orc.run_inplace(p, f, work, max(1, min(args.warmup, 3)))
     done = 0
     t0 = time.perf_counter()
     while done < args.steps:
-        f = orc.run(p, f, 1)
+        orc.run_inplace(p, f, work, 1)
         done += 1
         if time.perf_counter() - t0 > args.reference_seconds:
             break

@@ -186,6 +186,29 @@ int vlbm_launch_count(const vlbm_handle* h, int64_t* count);
 #define VLBM_OPT_KERNEL 0
 int vlbm_set_option(vlbm_handle* h, int32_t key, int64_t value);
 
+/* The reduction of vlbm_invariants for callers that cannot allocate device
+ * memory: code running inside a pool or arena that owns all device memory,
+ * in a real-time loop that may not take the allocator's locks or its implicit
+ * synchronisation, or near the memory limit.  The paper has no counterpart;
+ * it is an integration aid.  It needs no handle and allocates nothing: the
+ * per-block partial sums live in a static device array of about 512 KiB that
+ * each GPU loading the library keeps until the process exits.
+ *   p       parameters of the lattice (checked like vlbm_params_check)
+ *   lattice device pointer to one population lattice in a handle's storage
+ *           layout: the vlbm_derived.lattice_bytes that follow the checkpoint
+ *           header in a vlbm_get_state blob (the caller may keep that copy in
+ *           its own device memory)
+ *   out     8 doubles in the layout of vlbm_invariants; device memory, or host
+ *           memory (then the call synchronises `stream` before returning)
+ *   stream  cudaStream_t, NULL for the legacy stream
+ * At most 8192 x 8192 = 67,108,864 nodes; larger lattices, a host-memory
+ * lattice or bad parameters give VLBM_EINVAL.  The first call on a device
+ * looks up the static array's device address (cudaGetSymbolAddress): make
+ * that first call before any stream capture.  All calls share the array, and
+ * each writes every slot it later reads; calls whose kernels overlap on the
+ * GPU (two streams or two host threads) race on it and must be serialised. */
+int vlbm_invariants_noalloc(const vlbm_params* p, const void* lattice, double* out, void* stream);
+
 /* Static text of a status code; message of the last failure of h. */
 const char* vlbm_strerror(int code);
 const char* vlbm_last_error(const vlbm_handle* h);

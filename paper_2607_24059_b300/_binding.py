@@ -55,7 +55,7 @@ EXPORTED = [
     "vlbm_params_default", "vlbm_params_check", "vlbm_create", "vlbm_destroy", "vlbm_set_stream",
     "vlbm_init", "vlbm_step", "vlbm_step_record", "vlbm_macros", "vlbm_invariants", "vlbm_time", "vlbm_state_bytes",
     "vlbm_get_state", "vlbm_set_state", "vlbm_get_populations", "vlbm_launch_count", "vlbm_set_option",
-    "vlbm_strerror", "vlbm_last_error",
+    "vlbm_strerror", "vlbm_last_error", "vlbm_invariants_noalloc",
 ]
 
 
@@ -102,6 +102,7 @@ lib.vlbm_set_state.argtypes = [_H, _V, ctypes.c_size_t]
 lib.vlbm_get_populations.argtypes = [_H, _V, ctypes.c_int32, ctypes.c_int32]
 lib.vlbm_launch_count.argtypes = [_H, ctypes.POINTER(ctypes.c_int64)]
 lib.vlbm_set_option.argtypes = [_H, ctypes.c_int32, ctypes.c_int64]
+lib.vlbm_invariants_noalloc.argtypes = [_P, _V, _V, _V]
 lib.vlbm_strerror.argtypes = [ctypes.c_int]
 lib.vlbm_strerror.restype = ctypes.c_char_p
 lib.vlbm_last_error.argtypes = [_H]
@@ -275,6 +276,20 @@ def vlbm_launch_count(h) -> int:
 
 def vlbm_set_option(h, key: int, value: int) -> None:
     _check(lib.vlbm_set_option(h, int(key), int(value)), "vlbm_set_option", h)
+
+
+def vlbm_invariants_noalloc(p: vlbm_params, lattice, out, stream=None) -> None:
+    """Invariants of a caller-owned device lattice; the library allocates nothing.
+
+    lattice: CUDA tensor (or raw device address) holding one population lattice
+    in a handle's storage layout; out: 8 float64, device or host.
+    """
+    lp = lattice if isinstance(lattice, int) else lattice.data_ptr()
+    op, dt = _ptr_dtype(out)
+    if dt != VLBM_DTYPE_F64:
+        raise TypeError("invariants are float64")
+    s = current_stream() if stream is None else stream
+    _check(lib.vlbm_invariants_noalloc(ctypes.byref(p), _V(lp), _V(op), _V(s)), "vlbm_invariants_noalloc")
 
 
 def vlbm_strerror(code: int) -> str:

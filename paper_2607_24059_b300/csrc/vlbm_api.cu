@@ -235,7 +235,11 @@ static void free_all(vlbm_handle* h) {
     if (h->hist) cudaFree(h->hist);
 }
 
-static void storage_scales(const vlbm_params& p, const vlbm_derived& d, double* scale);
+void vlbm_storage_scales(const vlbm_params& p, double* scale);
+static void storage_scales(const vlbm_params& p, const vlbm_derived& d, double* scale) {
+    (void)d;
+    vlbm_storage_scales(p, scale);
+}
 
 extern "C" int vlbm_create(const vlbm_params* p, void* stream, vlbm_handle** out) {
     if (!out) return VLBM_EINVAL;
@@ -302,10 +306,10 @@ extern "C" int vlbm_set_stream(vlbm_handle* h, void* stream) {
 // Storage scales of the shifted half formats: the stored value is g * scale_k,
 // chosen so that the deviations of each field sit near unit magnitude.  The rho
 // field deviates by O(dx^2 phi) (Prop. 1); a momentum field by O(dx |q|).
-static void storage_scales(const vlbm_params& p, const vlbm_derived& d, double* scale) {
+// (library-internal; hidden from the exported symbol table)
+__attribute__((visibility("hidden"))) void vlbm_storage_scales(const vlbm_params& p, double* scale) {
     for (int k = 0; k < 4; ++k) scale[k] = 1.0;
     if (p.precision != VLBM_FP16_SHIFTED && p.precision != VLBM_BF16_SHIFTED) return;
-    (void)d;
     scale[0] = 1.0 / (p.dx * p.dx);
     for (int k = 1; k < 4; ++k) scale[k] = 1.0 / p.dx;
 }

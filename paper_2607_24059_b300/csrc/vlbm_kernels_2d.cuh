@@ -256,7 +256,7 @@ k_invariants_2d(const S* __restrict__ f, long long plane, Coef<typename Storage<
 // t / 8 + 128, ...: consecutive threads read consecutive doubles.
 // scale_e = dx^(d-2) turns sum |Q|^2/(2 rho) into 1/2 sum |q|^2/rho dx^d.
 // Shared by 2D and 3D.
-__global__ void __launch_bounds__(1024)
+static __global__ void __launch_bounds__(1024)
 k_invariants_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out, double nodes,
                    double rho_bar, double inv_dx, double scale_e) {
     __shared__ double sh[1024];
