@@ -36,9 +36,23 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GLUPS & % HBM roofline; time-to-t at stated L2 error vs plain FP32 LBM"
 UNIT = "GLUPS"
-BYTES_PER_NODE = {"fp64": 240, "fp32": 120, "fp16": 60, "bf16": 60}   # 15 populations read + written
-KERNEL = {"fp32": "k_stream_collide_2d_vec<float, false>", "fp64": "k_stream_collide_2d_vec<double, false>",
-          "fp16": "k_stream_collide_2d_vec<__half, false>", "bf16": "k_stream_collide_2d_vec<__nv_bfloat16, false>"}
+ELEM_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+CTYPE = {"fp64": "double", "fp32": "float", "fp16": "__half", "bf16": "__nv_bfloat16"}
+WORKLOADS = {
+    # name: (dim, populations per node, default side, nu)
+    "dsl2d": (2, 15, 4096, 1e-4),
+    "tgv3d": (3, 28, 256, 1.0 / 1600.0),
+}
+
+
+def bytes_per_node(args):
+    """Algorithmic bytes of one node update: every population read once and written once."""
+    return 2 * WORKLOADS[args.workload][1] * ELEM_BYTES[args.precision]
+
+
+def kernel_name(args):
+    dim = WORKLOADS[args.workload][0]
+    return f"k_stream_collide_{dim}d_vec<{CTYPE[args.precision]}, false>"
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -50,24 +64,49 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["vlbm", "reference"], default="vlbm")
-    ap.add_argument("--n", type=int, default=4096)
-    ap.add_argument("--precision", choices=list(BYTES_PER_NODE), default="fp32")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="dsl2d")
+    ap.add_argument("--n", type=int, default=None, help="lattice side (default: 4096 in 2D, 256 in 3D)")
+    ap.add_argument("--precision", choices=list(ELEM_BYTES), default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--reference-seconds", type=float, default=150.0, help="cap on the reference arm's timed steps")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.n is None:
+        args.n = WORKLOADS[args.workload][2]
+    return args
+
+
+def nodes_of(args):
+    return args.n ** WORKLOADS[args.workload][0]
+
+
+def make_input(args):
+    """(u, phi, dx, n-tuple) of the workload; seeded and synthetic."""
+    import synthetic
+    if args.workload == "dsl2d":
+        u, phi, dx = synthetic.double_shear_layer(args.n)
+        return u, phi, dx, (args.n, args.n)
+    u, phi, dx = synthetic.taylor_green_3d(args.n)
+    return u, phi, dx, (args.n,) * 3
 
 
 def workload_config(args, extra=None):
+    dim, ppn, _, nu = WORKLOADS[args.workload]
+    if args.workload == "dsl2d":
+        name = f"double shear layer {args.n}x{args.n} periodic, D2Q5 vectorial (3 fields x 5 velocities)"
+        init = "u_x = tanh(80(y - pi/2)) (y <= pi) / tanh(80(3pi/2 - y)), u_y = 0.05 sin x, phi = 0"
+    else:
+        name = f"Taylor-Green vortex {args.n}^3 periodic, D3Q7 vectorial (4 fields x 7 velocities)"
+        init = "u = (sin x cos y cos z, -cos x sin y cos z, 0), phi = (cos 2x + cos 2y)(cos 2z + 2)/16"
     cfg = {
-        "workload": f"double shear layer {args.n}x{args.n} periodic, D2Q5 vectorial (3 fields x 5 velocities)",
-        "lattice": [args.n, args.n],
-        "populations_per_node": 15,
+        "workload": name,
+        "lattice": [args.n] * dim,
+        "populations_per_node": ppn,
         "storage": args.precision,
-        "nu": 1e-4, "mu": 8.0, "omega_rho": 1.2, "alpha_rho": 0.075, "omega_q": 1.15,
-        "init": "u_x = tanh(80(y - pi/2)) (y <= pi) / tanh(80(3pi/2 - y)), u_y = 0.05 sin x, phi = 0",
+        "nu": nu, "mu": 8.0, "omega_rho": 1.2, "alpha_rho": 0.075, "omega_q": 1.15,
+        "init": init,
         "l2": "working set 2 lattices x {:.2f} GB > 126 MB L2: no flush needed".format(
-            args.n * args.n * BYTES_PER_NODE[args.precision] / 2 / 1e9),
+            nodes_of(args) * bytes_per_node(args) / 2 / 1e9),
     }
     if extra:
         cfg.update(extra)
@@ -190,8 +229,8 @@ def oracle_sample(args, seconds):
     import oracle
     import synthetic
     orc = oracle.default()
-    u, phi, dx = synthetic.double_shear_layer(args.n)
-    p = oracle.make_params((args.n, args.n), dx, nu=1e-4)
+    u, phi, dx, n = make_input(args)
+    p = oracle.make_params(n, dx, nu=WORKLOADS[args.workload][3])
     f = orc.init(p, u, phi)
     work = np.empty_like(f)
     orc.run_inplace(p, f, work, 2)            # warm-up (first touch of the work lattice, thread start)
@@ -203,8 +242,8 @@ def oracle_sample(args, seconds):
         el = time.perf_counter() - t0
         if el >= seconds or m >= 500:
             break
-    return {"value": args.n * args.n * m / el / 1e9, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
-            "sample": f"{args.n}^2 double shear layer, {m} FP64 oracle steps after 2 warm-up steps "
+    return {"value": nodes_of(args) * m / el / 1e9, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+            "sample": f"{args.workload} {args.n}^{WORKLOADS[args.workload][0]}, {m} FP64 oracle steps after 2 warm-up steps "
                       f"(plain C, OpenMP over rows, {orc.num_threads()} threads)", "seconds": el}
 
 
@@ -216,8 +255,8 @@ def run_reference(args):
     import oracle
     import synthetic
     orc = oracle.default()
-    u, phi, dx = synthetic.double_shear_layer(args.n)
-    p = oracle.make_params((args.n, args.n), dx, nu=1e-4)
+    u, phi, dx, n = make_input(args)
+    p = oracle.make_params(n, dx, nu=WORKLOADS[args.workload][3])
     f = orc.init(p, u, phi)
     work = np.empty_like(f)
     orc.run_inplace(p, f, work, max(1, min(args.warmup, 3)))
@@ -229,7 +268,7 @@ def run_reference(args):
         if time.perf_counter() - t0 > args.reference_seconds:
             break
     el = time.perf_counter() - t0
-    value = args.n * args.n * done / el / 1e9
+    value = nodes_of(args) * done / el / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": done,
         "steps_requested": args.steps, "warmup": max(1, min(args.warmup, 3)), "ms_per_step": el / done * 1e3,
@@ -251,10 +290,9 @@ def run_vlbm(args):
     import paper_2607_24059_b300 as vlbm
     import synthetic
 
-    n = args.n
-    u, phi, dx = synthetic.double_shear_layer(n)
-    lat = vlbm.Lattice((n, n), dx, nu=1e-4, precision=args.precision)
-    lat.init(torch.from_numpy(u).cuda())
+    u, phi, dx, shape = make_input(args)
+    lat = vlbm.Lattice(shape, dx, nu=WORKLOADS[args.workload][3], precision=args.precision)
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
     # warm-up: W steps, then prime the CUDA graphs of both buffer parities
     lat.step(args.warmup)
     lat.step(64)
@@ -279,28 +317,29 @@ def run_vlbm(args):
     elapsed = start.elapsed_time(end) / 1e3
     launches = lat.launch_count() - c0
     elapsed_max = max_over_ranks(elapsed, dist, "cuda")
-    nodes = n * n
+    nodes = nodes_of(args)
     value = world * nodes * args.steps / elapsed_max / 1e9
     inv = lat.invariants()
     assert inv[6] == 0, "non-finite populations after the timed steps"
 
     # roofline of the stream-collide kernel (the only kernel in the timed region)
     per_launch = elapsed / args.steps
-    bpn = BYTES_PER_NODE[args.precision]
+    bpn = bytes_per_node(args)
     achieved = bpn * nodes / per_launch / 1e9
     peak, peak_kind = measured_peaks()
     digest = source_digest()
-    traffic = profiled_traffic(KERNEL[args.precision], n, digest)
+    traffic = profiled_traffic(kernel_name(args), args.n, digest)
 
     # ---- end to end through the C ABI with host buffers
     u_host = torch.from_numpy(u.astype(np.float32)).pin_memory()
+    phi_host = torch.from_numpy(phi.astype(np.float32)).pin_memory()
     u_out = torch.empty_like(u_host).pin_memory()
     hist = torch.zeros((args.steps, 8), dtype=torch.float64).pin_memory()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    vlbm.vlbm_init(lat.handle, u_host)                       # H2D of the step's input
+    vlbm.vlbm_init(lat.handle, u_host, phi_host)             # H2D of the step's input
     for s in range(args.steps):
         vlbm.vlbm_step_record(lat.handle, 1, 1, hist[s])     # step + fused invariants, D2H of 64 B
     vlbm.vlbm_macros(lat.handle, None, u_out, None)          # D2H of the velocity field
@@ -309,6 +348,7 @@ def run_vlbm(args):
     e2e_value = world * nodes * args.steps / e2e_el / 1e9
     assert np.all(np.isfinite(hist.numpy())) and np.all(np.isfinite(u_out.numpy()))
     ubytes = u_host.numel() * u_host.element_size()
+    pbytes = phi_host.numel() * phi_host.element_size()
 
     if rank != 0:
         if dist:
@@ -318,18 +358,18 @@ def run_vlbm(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64"}.get(args.precision, args.precision + "-storage/f32"),
         "data": "synthetic",
         "config": workload_config(args, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                                          "graph_prime_steps": 129}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic, "bytes_per_node": bpn,
-                     "kernel": KERNEL[args.precision], "avg_launch_ms": per_launch * 1e3,
+                     "kernel": kernel_name(args), "avg_launch_ms": per_launch * 1e3,
                      "source_digest": digest},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": ubytes / args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (ubytes + pbytes) / args.steps,
                 "d2h_bytes_per_step": 64 + ubytes / args.steps,
-                "how": "vlbm_init from pinned host u, per step vlbm_step_record (fused invariants, 64 B D2H), "
-                       "vlbm_macros to pinned host u"},
+                "how": "vlbm_init from pinned host u and phi, per step vlbm_step_record (fused invariants, 64 B "
+                       "D2H), vlbm_macros to pinned host u"},
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }

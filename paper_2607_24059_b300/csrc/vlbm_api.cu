@@ -22,6 +22,7 @@ using namespace vlbm;
 namespace {
 
 constexpr int kGraphSteps = 64;               // steps captured per CUDA graph (even: parity is kept)
+constexpr int kStageBlocks = 128;             // first-stage blocks when many partial rows are reduced
 constexpr uint64_t kStateMagic = 0x315F4D424C56ull;  // "VLBM_1"
 
 struct StateHeader {
@@ -46,6 +47,7 @@ struct vlbm_handle {
     int cur = 0;
     double* partials = nullptr;
     int64_t partial_capacity = 0;     // blocks
+    double* stage = nullptr;          // kStageBlocks rows of the two-stage final reduction
     double* inv_dev = nullptr;        // 8 doubles
     double* inv_host = nullptr;       // 8 doubles, pinned
     void* staging = nullptr;
@@ -229,6 +231,7 @@ static void free_all(vlbm_handle* h) {
     for (int i = 0; i < 2; ++i)
         if (h->buf[i]) cudaFree(h->buf[i]);
     if (h->partials) cudaFree(h->partials);
+    if (h->stage) cudaFree(h->stage);
     if (h->inv_dev) cudaFree(h->inv_dev);
     if (h->inv_host) cudaFreeHost(h->inv_host);
     if (h->staging) cudaFree(h->staging);
@@ -266,6 +269,7 @@ extern "C" int vlbm_create(const vlbm_params* p, void* stream, vlbm_handle** out
         if (st != VLBM_OK) break;
         h->partial_capacity = std::max(step_blocks(h), inv_blocks(h));
         if (cudaMalloc(&h->partials, (size_t)h->partial_capacity * 8 * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&h->stage, (size_t)kStageBlocks * 8 * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&h->inv_dev, 8 * sizeof(double)) != cudaSuccess ||
             cudaMallocHost(&h->inv_host, 8 * sizeof(double)) != cudaSuccess) {
             st = VLBM_ENOMEM;
@@ -621,7 +625,14 @@ static void invariants_partials(vlbm_handle* h, int blocks) {
 static void launch_final(vlbm_handle* h, int nblocks, double* out_dev) {
     const double inv_dx = 1.0 / h->p.dx;
     const double scale_e = h->p.dim == 3 ? h->p.dx : 1.0;
-    k_invariants_final<<<1, 1024, 0, h->stream>>>(h->partials, nblocks, out_dev, (double)h->d.nodes, h->p.rho_bar,
+    const double* rows = h->partials;
+    if (nblocks > 2 * kStageBlocks) {     // two stages: spread the FP64 additions over many SMs
+        k_invariants_stage<<<kStageBlocks, 256, 0, h->stream>>>(h->partials, nblocks, h->stage);
+        h->launches++;
+        rows = h->stage;
+        nblocks = kStageBlocks;
+    }
+    k_invariants_final<<<1, 1024, 0, h->stream>>>(rows, nblocks, out_dev, (double)h->d.nodes, h->p.rho_bar,
                                                    inv_dx, scale_e);
 }
 
@@ -631,7 +642,7 @@ static int launch_invariants(vlbm_handle* h, double* out_dev) {
     int rc = check_launch(h, "invariants");
     if (rc) return rc;
     launch_final(h, blocks, out_dev);
-    h->launches += 2;
+    h->launches += 2;      // partials + final (a first stage, when used, counts itself)
     return check_launch(h, "invariants final");
 }
 

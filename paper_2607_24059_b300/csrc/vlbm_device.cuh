@@ -271,36 +271,42 @@ __device__ __forceinline__ void warp_reduce(Acc<C>& acc) {
 
 // Reduce a block's accumulators into partials[blockIdx.x * 8 + i] (FP64):
 // { sum dr, sum Q_x, sum Q_y, sum Q_z, sum |Q|^2/(2 rho), max |Q|/rho, bad, 0 }.
-// Fixed shuffle tree and warp order: deterministic for a given launch shape.
+// Warp trees, then one tree over the warps' results, all in the compute type
+// (float pairs for FP32); thread 0 alone converts to FP64.  Fixed shuffle
+// trees and warp order: deterministic for a given launch shape.
 template <class C>
 __device__ __forceinline__ void block_reduce_store(Acc<C>& acc, double* __restrict__ partials) {
-    __shared__ double sm[32][8];
+    __shared__ C sh_hi[32][5], sh_lo[32][5], sh_mx[32], sh_bad[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     warp_reduce(acc);
     if (lane == 0) {
 #pragma unroll
-        for (int i = 0; i < 5; ++i) sm[warp][i] = (double)acc.hi[i] + (double)acc.lo[i];
-        sm[warp][5] = (double)sqrt(acc.mx);
-        sm[warp][6] = (double)acc.bad;
-        sm[warp][7] = 0.0;
+        for (int i = 0; i < 5; ++i) {
+            sh_hi[warp][i] = acc.hi[i];
+            sh_lo[warp][i] = acc.lo[i];
+        }
+        sh_mx[warp] = acc.mx;
+        sh_bad[warp] = acc.bad;
     }
     __syncthreads();
     if (warp == 0) {
         const int nw = (blockDim.x + 31) >> 5;
-        double v[8];
+        const bool in = lane < nw;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = lane < nw ? sm[lane][i] : 0.0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const double o = __shfl_xor_sync(0xffffffffu, v[i], off);
-                v[i] = (i == 5) ? fmax(v[i], o) : v[i] + o;
-            }
+        for (int i = 0; i < 5; ++i) {
+            acc.hi[i] = in ? sh_hi[lane][i] : C(0);
+            acc.lo[i] = in ? sh_lo[lane][i] : C(0);
         }
+        acc.mx = in ? sh_mx[lane] : C(0);
+        acc.bad = in ? sh_bad[lane] : C(0);
+        warp_reduce(acc);
         if (lane == 0) {
+            double* o = partials + (size_t)blockIdx.x * 8;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) partials[(size_t)blockIdx.x * 8 + i] = v[i];
+            for (int i = 0; i < 5; ++i) o[i] = (double)acc.hi[i] + (double)acc.lo[i];
+            o[5] = (double)sqrt(acc.mx);
+            o[6] = (double)acc.bad;
+            o[7] = 0.0;
         }
     }
 }

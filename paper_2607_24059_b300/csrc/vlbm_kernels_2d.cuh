@@ -250,6 +250,32 @@ k_invariants_2d(const S* __restrict__ f, long long plane, Coef<typename Storage<
     block_reduce_store(acc, partials);
 }
 
+// First stage of the reduction of many partial rows: block b folds rows
+// b, b + gridDim.x, ... (fixed order) into stage[b * 8 + slot].  Spreads the
+// FP64 additions over many SMs (B300's FP64 rate per SM is low); the final
+// kernel then folds gridDim.x rows.  Thread t owns slot t % 8.
+static __global__ void __launch_bounds__(256)
+k_invariants_stage(const double* __restrict__ partials, int nblocks, double* __restrict__ stage) {
+    __shared__ double sh[256];
+    const int t = threadIdx.x, slot = t & 7;
+    const bool is_max = slot == 5;
+    double a = 0.0;
+    for (int b = blockIdx.x + (t >> 3) * gridDim.x; b < nblocks; b += 32 * gridDim.x) {
+        const double v = partials[(size_t)b * 8 + slot];
+        a = is_max ? fmax(a, v) : a + v;
+    }
+    sh[t] = a;
+    __syncthreads();
+    for (int stride = 16; stride > 0; stride >>= 1) {
+        if ((t >> 3) < stride) {
+            const double o = sh[t + stride * 8];
+            sh[t] = is_max ? fmax(sh[t], o) : sh[t] + o;
+        }
+        __syncthreads();
+    }
+    if (t < 8) stage[(size_t)blockIdx.x * 8 + t] = sh[t];
+}
+
 // Final reduction of nblocks partials (one block of 1024 threads, fixed order)
 // into the invariants { N rho_bar + sum dr, sum Q_d / dx (3), E_kin, max|u|,
 // non-finite nodes, sum dr }.  Thread t owns slot t % 8 of blocks t / 8,
