@@ -179,8 +179,9 @@ int vlbm_get_populations(vlbm_handle* h, void* dst, int32_t dtype, int32_t devia
 int vlbm_launch_count(const vlbm_handle* h, int64_t* count);
 
 /* Tuning and test options.  VLBM_OPT_KERNEL selects the step kernel:
- * 0 = automatic (vectorised when n_x is a multiple of the vector width,
- * 16 bytes in 2D and 8 bytes in 3D), 1 = one thread per node (any size),
+ * 0 = automatic (vectorised when n_x is a multiple of the nodes per lane:
+ * 2D 4 (FP32, 16-bit formats) or 2 (FP64); 3D 2 or 1 (FP64)), 1 = one thread
+ * per node (any size),
  * 2 = vectorised (VLBM_EINVAL when n_x does not allow it).  Both compute the
  * same arithmetic in the same order, so their results are bitwise equal. */
 #define VLBM_OPT_KERNEL 0

@@ -201,9 +201,12 @@ extern "C" int vlbm_params_check(const vlbm_params* p, vlbm_derived* out) {
 // ------------------------------------------------------------------ lifecycle
 static int64_t blocks_for(int64_t threads) { return (threads + kThreads - 1) / kThreads; }
 
-// Elements per vector access of the vectorised step kernels: 16-byte vectors in
-// 2D, 8-byte vectors in 3D (28 planes of registers per vector element).
-static int vec_width(const vlbm_handle* h) { return (h->p.dim == 2 ? 16 : 8) / h->d.bytes_per_population; }
+// Nodes per lane of the vectorised step kernels (Vec16 / Vec8 in the kernel
+// headers): 2D min(4, 16 B / element), 3D min(2, 8 B / element).
+static int vec_width(const vlbm_handle* h) {
+    const int b = h->d.bytes_per_population;
+    return h->p.dim == 2 ? std::min(4, 16 / b) : std::min(2, 8 / b);
+}
 
 static bool use_vec(const vlbm_handle* h) {
     if (h->kernel_variant == 1) return false;

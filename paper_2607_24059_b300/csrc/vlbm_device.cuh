@@ -106,21 +106,41 @@ __device__ __forceinline__ void equilibrium_d2q5(const Coef<C>& k, C dr, C Qx, C
     e[14] = ay - (yy + dP);
 }
 
-// Moments of one D2Q5 node in the fixed order rest, +x, -x, +y, -y.
+// Sum of the moving populations of one field, in opposite pairs: the +-flux
+// parts of each pair cancel before they meet the other terms.
+template <class C>
+__device__ __forceinline__ C moving_sum_d2q5(const C* g) {
+    return (g[1] + g[2]) + (g[3] + g[4]);
+}
+
+// Moments of one D2Q5 node: m_k = g_rest + (moving sum).  The rest population
+// of a momentum field carries almost all of Q; adding the small moving sum to
+// it last rounds once.
 template <class C>
 __device__ __forceinline__ void moments_d2q5(const C (&g)[15], C& dr, C& Qx, C& Qy) {
-    dr = (((g[0] + g[1]) + g[2]) + g[3]) + g[4];
-    Qx = (((g[5] + g[6]) + g[7]) + g[8]) + g[9];
-    Qy = (((g[10] + g[11]) + g[12]) + g[13]) + g[14];
+    dr = g[0] + moving_sum_d2q5(g);
+    Qx = g[5] + moving_sum_d2q5(g + 5);
+    Qy = g[10] + moving_sum_d2q5(g + 10);
 }
 
 // Relaxation of Eq. LBM_scheme on the deviations of one D2Q5 node, in place.
+// For the rest population the increment e_0 - g_0 = rest m - g_0 is formed as
+// rest s - (1 - rest) g_0 with s the moving sum (same value, since m = g_0 + s):
+// it is small, while rest m and g_0 are both of the size of m, and their
+// difference would keep only the rounding of rest m.  At FP32 that rounding is
+// systematic for a slowly varying field and grows linearly with the steps.
 template <class C>
 __device__ __forceinline__ void relax_d2q5(const Coef<C>& k, C (&g)[15], C dr, C Qx, C Qy) {
     C e[15];
     equilibrium_d2q5(k, dr, Qx, Qy, e);
 #pragma unroll
-    for (int i = 0; i < 15; ++i) g[i] = fma(k.om[i / 5], e[i] - g[i], g[i]);
+    for (int f = 0; f < 3; ++f) {
+        C* h = g + 5 * f;
+        const C d0 = k.rest[f] * moving_sum_d2q5(h) - (C(1) - k.rest[f]) * h[0];
+        h[0] = fma(k.om[f], d0, h[0]);
+#pragma unroll
+        for (int l = 1; l < 5; ++l) h[l] = fma(k.om[f], e[5 * f + l] - h[l], h[l]);
+    }
 }
 
 // Equilibrium deviations of one D3Q7 node, fields (rho, q_x, q_y, q_z) x
@@ -154,21 +174,31 @@ __device__ __forceinline__ void equilibrium_d3q7(const Coef<C>& k, C dr, const C
 }
 
 template <class C>
-__device__ __forceinline__ void moments_d3q7(const C (&g)[28], C& dr, C (&Q)[3]) {
-    dr = (((((g[0] + g[1]) + g[2]) + g[3]) + g[4]) + g[5]) + g[6];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const C* h = g + 7 * (j + 1);
-        Q[j] = (((((h[0] + h[1]) + h[2]) + h[3]) + h[4]) + h[5]) + h[6];
-    }
+__device__ __forceinline__ C moving_sum_d3q7(const C* g) {
+    return ((g[1] + g[2]) + (g[3] + g[4])) + (g[5] + g[6]);
 }
 
+// Moments of one D3Q7 node (rest population last, as in 2D).
+template <class C>
+__device__ __forceinline__ void moments_d3q7(const C (&g)[28], C& dr, C (&Q)[3]) {
+    dr = g[0] + moving_sum_d3q7(g);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Q[j] = g[7 * (j + 1)] + moving_sum_d3q7(g + 7 * (j + 1));
+}
+
+// Relaxation of one D3Q7 node; rest-population increment formed as in relax_d2q5.
 template <class C>
 __device__ __forceinline__ void relax_d3q7(const Coef<C>& k, C (&g)[28], C dr, const C (&Q)[3]) {
     C e[28];
     equilibrium_d3q7(k, dr, Q, e);
 #pragma unroll
-    for (int i = 0; i < 28; ++i) g[i] = fma(k.om[i / 7], e[i] - g[i], g[i]);
+    for (int f = 0; f < 4; ++f) {
+        C* h = g + 7 * f;
+        const C d0 = k.rest[f] * moving_sum_d3q7(h) - (C(1) - k.rest[f]) * h[0];
+        h[0] = fma(k.om[f], d0, h[0]);
+#pragma unroll
+        for (int l = 1; l < 7; ++l) h[l] = fma(k.om[f], e[7 * f + l] - h[l], h[l]);
+    }
 }
 
 // ---------------------------------------------------------------- vector I/O

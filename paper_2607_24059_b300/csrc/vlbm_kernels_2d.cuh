@@ -17,8 +17,11 @@ namespace vlbm {
 
 constexpr int kThreads = 256;
 
+// Nodes per lane of the vectorised 2D kernel: 16-byte vectors for FP32 (4) and
+// FP64 (2); 8-byte vectors (4 nodes) for the 16-bit formats, so that every
+// format keeps at most 15 x 4 values in registers.
 template <class S> struct Vec16 {
-    static constexpr int V = 16 / sizeof(S);
+    static constexpr int V = (16 / sizeof(S)) < 4 ? (16 / sizeof(S)) : 4;
 };
 
 template <class S>
@@ -32,7 +35,7 @@ __device__ __forceinline__ void store16(S* p, const S (&e)[Vec16<S>::V]) {
 }
 
 // ------------------------------------------------------------------------------
-// Fused stream-collide, vectorised.  Requires n_x % V == 0 (V = 16 B / element).
+// Fused stream-collide, vectorised.  Requires n_x % V == 0 (V nodes per lane, Vec16).
 // Warp w handles 32 V consecutive nodes of one row; lane L the V nodes starting
 // at x0.  The +x population of node x comes from x - 1: lane L takes its own
 // vector shifted by one element and the last element of lane L-1 by a warp

@@ -8,9 +8,10 @@
 
 namespace vlbm {
 
-// 8-byte vectors: 28 planes x V values stay in registers (V = 2 for FP32).
+// Nodes per lane in 3D: at most 2 (28 planes x V values stay in registers):
+// 8-byte vectors for FP32, 4-byte for the 16-bit formats, one FP64 per lane.
 template <class S> struct Vec8 {
-    static constexpr int V = 8 / sizeof(S);
+    static constexpr int V = (8 / sizeof(S)) < 2 ? (8 / sizeof(S)) : 2;
 };
 
 // Fused stream-collide, vectorised along x (n_x % V == 0).  Warp w handles
