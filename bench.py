@@ -36,8 +36,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GLUPS & % HBM roofline; time-to-t at stated L2 error vs plain FP32 LBM"
 UNIT = "GLUPS"
-ELEM_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
-CTYPE = {"fp64": "double", "fp32": "float", "fp16": "__half", "bf16": "__nv_bfloat16"}
+ELEM_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2, "fp16split": 2, "bf16split": 2}
+CTYPE = {"fp64": "double", "fp32": "float", "fp16": "__half", "bf16": "__nv_bfloat16", "fp16split": "__half",
+         "bf16split": "__nv_bfloat16"}
 WORKLOADS = {
     # name: (dim, populations per node, default side, nu)
     "dsl2d": (2, 15, 4096, 1e-4),
@@ -45,14 +46,26 @@ WORKLOADS = {
 }
 
 
+def split(args):
+    return args.precision.endswith("split")
+
+
 def bytes_per_node(args):
-    """Algorithmic bytes of one node update: every population read once and written once."""
-    return 2 * WORKLOADS[args.workload][1] * ELEM_BYTES[args.precision]
+    """Algorithmic bytes of one node update: every stored value read once and written once
+    (split layouts: one FP32 moment per field and 16-bit non-equilibrium parts of the moving
+    populations)."""
+    dim, ppn = WORKLOADS[args.workload][:2]
+    if split(args):
+        fields = dim + 1
+        return 2 * (fields * 4 + (ppn - fields) * 2)
+    return 2 * ppn * ELEM_BYTES[args.precision]
 
 
 def kernel_name(args):
     dim = WORKLOADS[args.workload][0]
-    return f"k_stream_collide_{dim}d_vec<{CTYPE[args.precision]}, false>"
+    if split(args):
+        return f"k_split_step_{dim}d_vec<{CTYPE[args.precision]}, false>"
+    return f"k_stream_collide_{dim}d_vec<{CTYPE[args.precision]}, false, false>"
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")

@@ -53,6 +53,8 @@ extern "C" {
 #define VLBM_FP32          1   /* FP32 storage of deviations from the rest equilibrium, FP32 arithmetic */
 #define VLBM_FP16_SHIFTED  2   /* FP16 storage of scaled deviations, FP32 arithmetic */
 #define VLBM_BF16_SHIFTED  3   /* BF16 storage of scaled deviations, FP32 arithmetic */
+#define VLBM_FP16_SPLIT    4   /* rest populations FP32, moving populations FP16 (scaled deviations), FP32 arithmetic */
+#define VLBM_BF16_SPLIT    5   /* rest populations FP32, moving populations BF16 (scaled deviations), FP32 arithmetic */
 
 /* ---- element type of caller arrays ------------------------------------- */
 #define VLBM_DTYPE_F32     0
@@ -70,7 +72,8 @@ typedef struct vlbm_handle vlbm_handle;
 /* Scheme parameters (Section 2).  Field index k: 0 = rho, 1 = q_x, 2 = q_y, 3 = q_z. */
 typedef struct {
     int32_t dim;         /* 2 (D2Q5, 3 fields x 5 velocities) or 3 (D3Q7, 4 fields x 7) */
-    int32_t precision;   /* VLBM_FP64 | VLBM_FP32 | VLBM_FP16_SHIFTED | VLBM_BF16_SHIFTED */
+    int32_t precision;   /* VLBM_FP64 | VLBM_FP32 | VLBM_FP16_SHIFTED | VLBM_BF16_SHIFTED |
+                            VLBM_FP16_SPLIT | VLBM_BF16_SPLIT */
     int64_t n[3];        /* nodes along x, y, z (n[2] ignored in 2D); each >= 1; periodic */
     double  dx;          /* space step > 0; the periodic box is n[d] * dx long */
     double  mu;          /* parabolic scaling dx^2 / dt > 0 (Eq. parabolicScaling) */
@@ -93,7 +96,7 @@ typedef struct {
     double  mu_min;               /* (alpha_rho + min_k alpha_qk)^(-1/2): low-frequency acoustic bound */
     int64_t nodes;                /* n[0] n[1] (n[2]) */
     int32_t populations_per_node; /* 15 (2D) or 28 (3D) */
-    int32_t bytes_per_population; /* 8, 4 or 2 */
+    int32_t bytes_per_population; /* 8, 4 or 2 (mixed layouts: 2 for the moving populations, 4 for the rest) */
     size_t  lattice_bytes;        /* bytes of one population lattice */
 } vlbm_derived;
 

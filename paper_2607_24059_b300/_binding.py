@@ -39,6 +39,8 @@ VLBM_FP64 = 0
 VLBM_FP32 = 1
 VLBM_FP16_SHIFTED = 2
 VLBM_BF16_SHIFTED = 3
+VLBM_FP16_SPLIT = 4
+VLBM_BF16_SPLIT = 5
 
 VLBM_DTYPE_F32 = 0
 VLBM_DTYPE_F64 = 1
@@ -49,7 +51,8 @@ VLBM_STEP_NO_GRAPH = 2
 VLBM_NUM_INVARIANTS = 8
 VLBM_OPT_KERNEL = 0
 
-PRECISIONS = {"fp64": VLBM_FP64, "fp32": VLBM_FP32, "fp16": VLBM_FP16_SHIFTED, "bf16": VLBM_BF16_SHIFTED}
+PRECISIONS = {"fp64": VLBM_FP64, "fp32": VLBM_FP32, "fp16": VLBM_FP16_SHIFTED, "bf16": VLBM_BF16_SHIFTED,
+              "fp16split": VLBM_FP16_SPLIT, "bf16split": VLBM_BF16_SPLIT}
 
 EXPORTED = [
     "vlbm_params_default", "vlbm_params_check", "vlbm_create", "vlbm_destroy", "vlbm_set_stream",

@@ -16,6 +16,7 @@
 #include "vlbm.h"
 #include "vlbm_kernels_2d.cuh"
 #include "vlbm_kernels_3d.cuh"
+#include "vlbm_split.cuh"
 
 using namespace vlbm;
 
@@ -107,15 +108,21 @@ bool is_device_pointer(const void* ptr) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Bytes of a moving population (all populations, except in the mixed layouts
+// whose rest populations are FP32).
 int elem_bytes(int precision) {
     switch (precision) {
         case VLBM_FP64: return 8;
         case VLBM_FP32: return 4;
         case VLBM_FP16_SHIFTED:
-        case VLBM_BF16_SHIFTED: return 2;
+        case VLBM_BF16_SHIFTED:
+        case VLBM_FP16_SPLIT:
+        case VLBM_BF16_SPLIT: return 2;
         default: return 0;
     }
 }
+
+bool is_split(int precision) { return precision == VLBM_FP16_SPLIT || precision == VLBM_BF16_SPLIT; }
 
 template <class C>
 Coef<C> make_coef(const vlbm_params& p, const vlbm_derived& d, const double* scale) {
@@ -192,7 +199,7 @@ extern "C" int vlbm_params_check(const vlbm_params* p, vlbm_derived* out) {
     d.nodes = p->n[0] * p->n[1] * (p->dim == 3 ? p->n[2] : 1);
     d.populations_per_node = F * (2 * p->dim + 1);
     d.bytes_per_population = elem_bytes(p->precision);
-    d.lattice_bytes = (size_t)d.nodes * d.populations_per_node * d.bytes_per_population;
+    d.lattice_bytes = (size_t)layout_bytes(d.bytes_per_population, is_split(p->precision), 2 * p->dim + 1, d.nodes);
     if (out) *out = d;
     if (p->mu < d.mu_min) return p->strict ? VLBM_ESTABILITY : VLBM_WSTABILITY;
     return VLBM_OK;
@@ -204,6 +211,7 @@ static int64_t blocks_for(int64_t threads) { return (threads + kThreads - 1) / k
 // Nodes per lane of the vectorised step kernels (Vec16 / Vec8 in the kernel
 // headers): 2D min(4, 16 B / element), 3D min(2, 8 B / element).
 static int vec_width(const vlbm_handle* h) {
+    if (is_split(h->p.precision)) return h->p.dim == 2 ? kSplitV2 : kSplitV3;
     const int b = h->d.bytes_per_population;
     return h->p.dim == 2 ? std::min(4, 16 / b) : std::min(2, 8 / b);
 }
@@ -316,9 +324,11 @@ extern "C" int vlbm_set_stream(vlbm_handle* h, void* stream) {
 // (library-internal; hidden from the exported symbol table)
 __attribute__((visibility("hidden"))) void vlbm_storage_scales(const vlbm_params& p, double* scale) {
     for (int k = 0; k < 4; ++k) scale[k] = 1.0;
-    if (p.precision != VLBM_FP16_SHIFTED && p.precision != VLBM_BF16_SHIFTED) return;
+    if (elem_bytes(p.precision) != 2) return;
     scale[0] = 1.0 / (p.dx * p.dx);
-    for (int k = 1; k < 4; ++k) scale[k] = 1.0 / p.dx;
+    // shifted populations of a momentum field are O(dx |q|); the split layout's
+    // non-equilibrium parts are O(dx^2) in every field
+    for (int k = 1; k < 4; ++k) scale[k] = is_split(p.precision) ? 1.0 / (p.dx * p.dx) : 1.0 / p.dx;
 }
 
 // ------------------------------------------------------------------ staging
@@ -336,52 +346,55 @@ static int ensure_staging(vlbm_handle* h, size_t bytes) {
 }
 
 // ------------------------------------------------------------------ init / macros
-template <class S, class T>
+template <class S, bool M, class T>
 static void launch_init(vlbm_handle* h, const T* u, const T* phi) {
     const int64_t N = h->d.nodes;
     const double pb = std::pow(h->p.rho_bar, h->p.gamma);
     const auto& k = coef<typename Storage<S>::C>(h);
     if (h->p.dim == 2)
-        k_init_2d<S, T><<<blocks_for(N), kThreads, 0, h->stream>>>((S*)h->buf[h->cur], N, u, phi, k, h->p.dx,
+        k_init_2d<S, M, T><<<blocks_for(N), kThreads, 0, h->stream>>>((char*)h->buf[h->cur], N, u, phi, k, h->p.dx,
                                                                    h->p.gamma, h->p.rho_bar, pb);
     else
-        k_init_3d<S, T><<<blocks_for(N), kThreads, 0, h->stream>>>((S*)h->buf[h->cur], N, u, phi, k, h->p.dx,
+        k_init_3d<S, M, T><<<blocks_for(N), kThreads, 0, h->stream>>>((char*)h->buf[h->cur], N, u, phi, k, h->p.dx,
                                                                    h->p.gamma, h->p.rho_bar, pb);
     h->launches++;
 }
 
-template <class S, class T>
+template <class S, bool M, class T>
 static void launch_macros(vlbm_handle* h, T* rho, T* u, T* phi) {
     const int64_t N = h->d.nodes;
     const double pb = std::pow(h->p.rho_bar, h->p.gamma);
     const auto& k = coef<typename Storage<S>::C>(h);
     if (h->p.dim == 2)
-        k_macros_2d<S, T><<<blocks_for(N), kThreads, 0, h->stream>>>((const S*)h->buf[h->cur], N, rho, u, phi, k,
+        k_macros_2d<S, M, T><<<blocks_for(N), kThreads, 0, h->stream>>>((const char*)h->buf[h->cur], N, rho, u, phi, k,
                                                                      h->p.dx, h->p.gamma, h->p.rho_bar, pb);
     else
-        k_macros_3d<S, T><<<blocks_for(N), kThreads, 0, h->stream>>>((const S*)h->buf[h->cur], N, rho, u, phi, k,
+        k_macros_3d<S, M, T><<<blocks_for(N), kThreads, 0, h->stream>>>((const char*)h->buf[h->cur], N, rho, u, phi, k,
                                                                      h->p.dx, h->p.gamma, h->p.rho_bar, pb);
     h->launches++;
 }
 
-#define VLBM_DISPATCH_STORAGE(h, FN, ...)                                    \
-    switch ((h)->p.precision) {                                              \
-        case VLBM_FP64: FN<double>(__VA_ARGS__); break;                      \
-        case VLBM_FP32: FN<float>(__VA_ARGS__); break;                       \
-        case VLBM_FP16_SHIFTED: FN<__half>(__VA_ARGS__); break;              \
-        default: FN<__nv_bfloat16>(__VA_ARGS__); break;                      \
+// Instantiate FN<storage, mixed layout> for the handle's precision.
+#define VLBM_DISPATCH_STORAGE(h, FN, ...)                                      \
+    switch ((h)->p.precision) {                                                \
+        case VLBM_FP64: FN<double, false>(__VA_ARGS__); break;                 \
+        case VLBM_FP32: FN<float, false>(__VA_ARGS__); break;                  \
+        case VLBM_FP16_SHIFTED: FN<__half, false>(__VA_ARGS__); break;         \
+        case VLBM_BF16_SHIFTED: FN<__nv_bfloat16, false>(__VA_ARGS__); break;  \
+        case VLBM_FP16_SPLIT: FN<__half, true>(__VA_ARGS__); break;            \
+        default: FN<__nv_bfloat16, true>(__VA_ARGS__); break;                  \
     }
 
-template <class S>
+template <class S, bool M>
 static void init_dispatch(vlbm_handle* h, const void* u, const void* phi, int dtype) {
-    if (dtype == VLBM_DTYPE_F64) launch_init<S, double>(h, (const double*)u, (const double*)phi);
-    else launch_init<S, float>(h, (const float*)u, (const float*)phi);
+    if (dtype == VLBM_DTYPE_F64) launch_init<S, M, double>(h, (const double*)u, (const double*)phi);
+    else launch_init<S, M, float>(h, (const float*)u, (const float*)phi);
 }
 
-template <class S>
+template <class S, bool M>
 static void macros_dispatch(vlbm_handle* h, void* rho, void* u, void* phi, int dtype) {
-    if (dtype == VLBM_DTYPE_F64) launch_macros<S, double>(h, (double*)rho, (double*)u, (double*)phi);
-    else launch_macros<S, float>(h, (float*)rho, (float*)u, (float*)phi);
+    if (dtype == VLBM_DTYPE_F64) launch_macros<S, M, double>(h, (double*)rho, (double*)u, (double*)phi);
+    else launch_macros<S, M, float>(h, (float*)rho, (float*)u, (float*)phi);
 }
 
 extern "C" int vlbm_init(vlbm_handle* h, const void* u, const void* phi, int32_t dtype) {
@@ -448,43 +461,57 @@ extern "C" int vlbm_macros(vlbm_handle* h, void* rho, void* u, void* phi, int32_
 }
 
 // ------------------------------------------------------------------ stepping
-template <class S, bool DIAG>
+template <class S, bool M, bool DIAG>
 static void launch_step_on(vlbm_handle* h, cudaStream_t s, int src, double* partials) {
     using C = typename Storage<S>::C;
     const auto& k = coef<C>(h);
-    const S* fin = (const S*)h->buf[src];
-    S* fout = (S*)h->buf[src ^ 1];
+    const char* fin = (const char*)h->buf[src];
+    char* fout = (char*)h->buf[src ^ 1];
     const int64_t nx = h->p.n[0], ny = h->p.n[1];
     const int64_t plane = h->d.nodes;
     const int64_t blocks = step_blocks(h);
-    if (h->p.dim == 2) {
-        if (use_vec(h)) {
-            const int wpr = (int)((nx / vec_width(h) + 31) / 32);
-            k_stream_collide_2d_vec<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, wpr, k,
+    const int64_t nz = h->p.n[2];
+    const bool vec = use_vec(h);
+    const int wpr = (int)((nx / vec_width(h) + 31) / 32);
+    if constexpr (M) {
+        if (h->p.dim == 2) {
+            if (vec)
+                k_split_step_2d_vec<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, wpr, k,
                                                                          partials);
-        } else {
-            k_stream_collide_2d_generic<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, k,
+            else
+                k_split_step_2d_generic<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, k,
                                                                              partials);
-        }
-    } else {
-        const int64_t nz = h->p.n[2];
-        if (use_vec(h)) {
-            const int wpr = (int)((nx / vec_width(h) + 31) / 32);
-            k_stream_collide_3d_vec<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz, plane,
-                                                                         wpr, k, partials);
         } else {
-            k_stream_collide_3d_generic<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz,
+            if (vec)
+                k_split_step_3d_vec<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz, plane,
+                                                                         wpr, k, partials);
+            else
+                k_split_step_3d_generic<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz,
                                                                              plane, k, partials);
         }
+    } else if (h->p.dim == 2) {
+        if (vec)
+            k_stream_collide_2d_vec<S, M, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, wpr,
+                                                                            k, partials);
+        else
+            k_stream_collide_2d_generic<S, M, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, k,
+                                                                                partials);
+    } else {
+        if (vec)
+            k_stream_collide_3d_vec<S, M, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz,
+                                                                            plane, wpr, k, partials);
+        else
+            k_stream_collide_3d_generic<S, M, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz,
+                                                                                plane, k, partials);
     }
 }
 
-template <class S>
-static void step_plain(vlbm_handle* h, cudaStream_t s, int src) { launch_step_on<S, false>(h, s, src, nullptr); }
+template <class S, bool M>
+static void step_plain(vlbm_handle* h, cudaStream_t s, int src) { launch_step_on<S, M, false>(h, s, src, nullptr); }
 
-template <class S>
+template <class S, bool M>
 static void step_diag(vlbm_handle* h, cudaStream_t s, int src, double* partials) {
-    launch_step_on<S, true>(h, s, src, partials);
+    launch_step_on<S, M, true>(h, s, src, partials);
 }
 
 static int launch_one_step(vlbm_handle* h, cudaStream_t s, int src) {
@@ -615,14 +642,16 @@ extern "C" int vlbm_step_record(vlbm_handle* h, int64_t nsteps, int64_t every, d
 }
 
 // ------------------------------------------------------------------ invariants
-template <class S>
+template <class S, bool M>
 static void invariants_partials(vlbm_handle* h, int blocks) {
     using C = typename Storage<S>::C;
     const auto& k = coef<C>(h);
     if (h->p.dim == 2)
-        k_invariants_2d<S><<<blocks, kThreads, 0, h->stream>>>((const S*)h->buf[h->cur], h->d.nodes, k, h->partials);
+        k_invariants_2d<S, M><<<blocks, kThreads, 0, h->stream>>>((const char*)h->buf[h->cur], h->d.nodes, k,
+                                                                   h->partials);
     else
-        k_invariants_3d<S><<<blocks, kThreads, 0, h->stream>>>((const S*)h->buf[h->cur], h->d.nodes, k, h->partials);
+        k_invariants_3d<S, M><<<blocks, kThreads, 0, h->stream>>>((const char*)h->buf[h->cur], h->d.nodes, k,
+                                                                   h->partials);
 }
 
 static void launch_final(vlbm_handle* h, int nblocks, double* out_dev) {
@@ -717,7 +746,7 @@ extern "C" int vlbm_set_state(vlbm_handle* h, const void* src, size_t bytes) {
     return VLBM_OK;
 }
 
-template <class S, class T>
+template <class S, bool M, class T>
 static void launch_export(vlbm_handle* h, T* dst, int deviation) {
     using C = typename Storage<S>::C;
     const auto& k = coef<C>(h);
@@ -726,15 +755,19 @@ static void launch_export(vlbm_handle* h, T* dst, int deviation) {
     const double f_rest = (1.0 - 2.0 * h->p.dim * h->d.alpha[0]) * h->p.rho_bar;
     const double f_move = h->d.alpha[0] * h->p.rho_bar;
     const double p_half = std::pow(h->p.rho_bar, h->p.gamma) / (2.0 * h->p.mu);
-    k_export<S, T><<<blocks_for(total), kThreads, 0, h->stream>>>((const S*)h->buf[h->cur], total, h->d.nodes, q, dst,
-                                                                  k, f_rest, f_move, p_half, deviation);
+    if (q == 5)
+        k_export<S, M, 5, T><<<blocks_for(total), kThreads, 0, h->stream>>>(
+            (const char*)h->buf[h->cur], total, h->d.nodes, dst, k, f_rest, f_move, p_half, deviation);
+    else
+        k_export<S, M, 7, T><<<blocks_for(total), kThreads, 0, h->stream>>>(
+            (const char*)h->buf[h->cur], total, h->d.nodes, dst, k, f_rest, f_move, p_half, deviation);
     h->launches++;
 }
 
-template <class S>
+template <class S, bool M>
 static void export_dispatch(vlbm_handle* h, void* dst, int dtype, int deviation) {
-    if (dtype == VLBM_DTYPE_F64) launch_export<S, double>(h, (double*)dst, deviation);
-    else launch_export<S, float>(h, (float*)dst, deviation);
+    if (dtype == VLBM_DTYPE_F64) launch_export<S, M, double>(h, (double*)dst, deviation);
+    else launch_export<S, M, float>(h, (float*)dst, deviation);
 }
 
 extern "C" int vlbm_get_populations(vlbm_handle* h, void* dst, int32_t dtype, int32_t deviation) {

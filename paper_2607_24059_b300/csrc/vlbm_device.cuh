@@ -22,6 +22,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace vlbm {
 
 constexpr int kMaxFields = 4;
@@ -53,6 +55,37 @@ template <> struct Storage<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 from_c(float v) { return __float2bfloat16_rn(v); }
 };
 
+// ---------------------------------------------------------------- lattice layout
+// Plane addressing of one population lattice of F = (Q + 1) / 2 fields x Q
+// velocities over N nodes (a plane holds one population of every node, x fastest).
+//   uniform (SPLIT = false): F * Q planes of S, plane k * Q + l.
+//   mixed   (SPLIT = true):  the F rest planes (l = 0) in FP32, then the
+//                            F * (Q - 1) moving planes of S, plane k * (Q - 1) + l - 1.
+// The mixed layout keeps the population that carries each field's conserved
+// moment at FP32 resolution while the moving ones use a 16-bit format.
+template <class S, bool SPLIT, int Q>
+struct Layout {
+    static constexpr int F = (Q + 1) / 2;
+    using R = typename std::conditional<SPLIT, float, S>::type;   // rest-plane storage
+    char* base;
+    long long N;
+    __device__ __forceinline__ R* rest(int k) const {
+        return SPLIT ? reinterpret_cast<R*>(base) + (long long)k * N
+                     : reinterpret_cast<R*>(base) + (long long)k * Q * N;
+    }
+    __device__ __forceinline__ S* mov(int k, int l) const {
+        return SPLIT ? reinterpret_cast<S*>(reinterpret_cast<float*>(base) + (long long)F * N) +
+                           ((long long)k * (Q - 1) + (l - 1)) * N
+                     : reinterpret_cast<S*>(base) + ((long long)k * Q + l) * N;
+    }
+};
+
+// Bytes of one lattice in a layout (host side mirror of Layout).
+inline long long layout_bytes(int elem_bytes, bool mixed, int q, long long nodes) {
+    const int f = (q + 1) / 2;
+    return mixed ? nodes * (f * 4LL + (long long)f * (q - 1) * elem_bytes) : nodes * f * q * (long long)elem_bytes;
+}
+
 // ---------------------------------------------------------------- coefficients
 // Per-field relaxation and equilibrium coefficients in the compute type C.
 template <class C>
@@ -69,6 +102,25 @@ struct Coef {
     int gamma_one;         // gamma == 1: dP = dr / (2 mu) exactly
 };
 
+// Factors from stored values to deviations (load) and back (store).  Rest planes
+// of the mixed layout are FP32 and unscaled.
+template <class S, bool SPLIT, class C>
+__device__ __forceinline__ C rest_load_scale(const Coef<C>& k, int f) {
+    return (Storage<S>::kScaled && !SPLIT) ? k.inv_scale[f] : C(1);
+}
+template <class S, bool SPLIT, class C>
+__device__ __forceinline__ C rest_store_scale(const Coef<C>& k, int f) {
+    return (Storage<S>::kScaled && !SPLIT) ? k.scale[f] : C(1);
+}
+template <class S, class C>
+__device__ __forceinline__ C mov_load_scale(const Coef<C>& k, int f) {
+    return Storage<S>::kScaled ? k.inv_scale[f] : C(1);
+}
+template <class S, class C>
+__device__ __forceinline__ C mov_store_scale(const Coef<C>& k, int f) {
+    return Storage<S>::kScaled ? k.scale[f] : C(1);
+}
+
 // P(rho_bar + dr) - P(rho_bar) without cancellation.
 template <class C>
 __device__ __forceinline__ C pressure_dev(const Coef<C>& k, C dr) {
@@ -76,11 +128,16 @@ __device__ __forceinline__ C pressure_dev(const Coef<C>& k, C dr) {
     return k.p_bar * expm1(k.gamma * log1p(dr / k.rho_bar));
 }
 
+// Correctly rounded reciprocal: the same value as 1 / x, without the general
+// division sequence.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+
 // Equilibrium deviations g^eq of one D2Q5 node, fields (rho, q_x, q_y) x
 // velocities (rest, +x, -x, +y, -y): e[5k + l].
 template <class C>
 __device__ __forceinline__ void equilibrium_d2q5(const Coef<C>& k, C dr, C Qx, C Qy, C (&e)[15]) {
-    const C r = C(1) / (k.rho_bar + dr);
+    const C r = recip(k.rho_bar + dr);
     const C dP = pressure_dev(k, dr) * k.i2m;
     const C hx = Qx * k.i2m, hy = Qy * k.i2m;
     const C xx = Qx * Qx * r * k.i2m;
@@ -149,7 +206,7 @@ __device__ __forceinline__ void relax_d2q5(const Coef<C>& k, C (&g)[15], C dr, C
 // is the direction-by-direction extension (rest weight 1 - 6 alpha).
 template <class C>
 __device__ __forceinline__ void equilibrium_d3q7(const Coef<C>& k, C dr, const C (&Q)[3], C (&e)[28]) {
-    const C r = C(1) / (k.rho_bar + dr);
+    const C r = recip(k.rho_bar + dr);
     const C dP = pressure_dev(k, dr) * k.i2m;
     const C ar = k.al[0] * dr;
     e[0] = k.rest[0] * dr;
@@ -269,7 +326,7 @@ __device__ __forceinline__ void accumulate_node(Acc<C>& acc, bool finite, C dr, 
         acc.bad += C(1);
         return;
     }
-    const C r = C(1) / (rho_bar + dr);
+    const C r = recip(rho_bar + dr);
     C q2 = C(0);
     acc.add(0, dr);
     for (int d = 0; d < dim; ++d) {

@@ -2,9 +2,12 @@
 // macroscopic fields, FP64 invariant reduction and population export.
 //
 // Lattice layout in HBM (one lattice per time level, two levels ping-pong):
-//   15 planes p = 5k + l (field k = rho, q_x, q_y; velocity l = rest, +x, -x,
-//   +y, -y), each plane n_y rows of n_x elements, x fastest, no padding.
-//   The buffer holds post-relaxation deviations g*(t) (see vlbm_device.cuh).
+//   15 planes (field k = rho, q_x, q_y; velocity l = rest, +x, -x, +y, -y),
+//   each plane n_y rows of n_x elements, x fastest, no padding, addressed
+//   through Layout<S, SPLIT, 5> (vlbm_device.cuh).  Uniform layouts hold the
+//   post-relaxation deviations g*(t) (see vlbm_device.cuh); the split layout
+//   holds FP32 moments and 16-bit non-equilibrium parts (vlbm_split.cuh), and
+//   its step kernels live there.
 //
 // One time step (pull form of the transport of Section 2):
 //   g(t+dt, x) for velocity c_l is g*(t, x - c_l dx); relax it; store g*(t+dt, x).
@@ -24,32 +27,35 @@ template <class S> struct Vec16 {
     static constexpr int V = (16 / sizeof(S)) < 4 ? (16 / sizeof(S)) : 4;
 };
 
-template <class S>
-__device__ __forceinline__ void load16(S (&e)[Vec16<S>::V], const S* p) {
-    vload<S, Vec16<S>::V>(e, p);
-}
-
-template <class S>
-__device__ __forceinline__ void store16(S* p, const S (&e)[Vec16<S>::V]) {
-    vstore<S, Vec16<S>::V>(p, e);
+template <class T, int V>
+__device__ __forceinline__ void load_or_zero(T (&w)[V], const T* p, bool active) {
+    if (active) {
+        vload<T, V>(w, p);
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) w[i] = Storage<T>::from_c(typename Storage<T>::C(0));
+    }
 }
 
 // ------------------------------------------------------------------------------
-// Fused stream-collide, vectorised.  Requires n_x % V == 0 (V nodes per lane, Vec16).
+// Fused stream-collide, vectorised.  Requires n_x % V == 0 (V nodes per lane).
 // Warp w handles 32 V consecutive nodes of one row; lane L the V nodes starting
 // at x0.  The +x population of node x comes from x - 1: lane L takes its own
 // vector shifted by one element and the last element of lane L-1 by a warp
 // shuffle (lane 0 loads that element from memory, with periodic wrap).  The
 // -x population comes from x + 1, symmetrically.  +y / -y are whole rows
 // y - 1 / y + 1 (periodic), loaded aligned.
-// DIAG: also reduce the invariants of the state being read (time t) into
-// per-block FP64 partials, at no extra HBM traffic.
-template <class S, bool DIAG>
+// DIAG: also reduce the invariants of the transported state (time t + dt)
+// into per-block FP64 partials, at no extra HBM traffic.
+template <class S, bool SPLIT, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
-k_stream_collide_2d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx, int ny, long long plane,
+k_stream_collide_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
                         int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
     using C = typename Storage<S>::C;
+    using L = Layout<S, SPLIT, 5>;
+    using R = typename L::R;
     constexpr int V = Vec16<S>::V;
+    const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     Acc<C> acc;
@@ -68,36 +74,40 @@ k_stream_collide_2d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx,
         C g[15][V];
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            const S* base = fin + (long long)(5 * f) * plane;
-            const C isc = Storage<S>::kScaled ? k.inv_scale[f] : C(1);
-            S w[V];
-            // rest: in place
-            if (active) load16(w, base + row + x0); else { for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(C(0)); }
+            const C risc = rest_load_scale<S, SPLIT>(k, f);
+            const C isc = mov_load_scale<S>(k, f);
+            {   // rest: in place
+                R w[V];
+                load_or_zero<R, V>(w, fin.rest(f) + row + x0, active);
 #pragma unroll
-            for (int i = 0; i < V; ++i) g[5 * f + 0][i] = Storage<S>::to_c(w[i]) * isc;
+                for (int i = 0; i < V; ++i) g[5 * f + 0][i] = Storage<R>::to_c(w[i]) * risc;
+            }
+            S w[V];
             // +x: from x - 1
-            if (active) load16(w, base + plane + row + x0); else { for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(C(0)); }
+            const S* px = fin.mov(f, 1);
+            load_or_zero<S, V>(w, px + row + x0, active);
             {
                 S prev = __shfl_up_sync(0xffffffffu, w[V - 1], 1);
-                if (lane == 0 && active) prev = base[plane + row + xm];
+                if (lane == 0 && active) prev = px[row + xm];
                 g[5 * f + 1][0] = Storage<S>::to_c(prev) * isc;
 #pragma unroll
                 for (int i = 1; i < V; ++i) g[5 * f + 1][i] = Storage<S>::to_c(w[i - 1]) * isc;
             }
             // -x: from x + 1
-            if (active) load16(w, base + 2 * plane + row + x0); else { for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(C(0)); }
+            const S* mx = fin.mov(f, 2);
+            load_or_zero<S, V>(w, mx + row + x0, active);
             {
                 S next = __shfl_down_sync(0xffffffffu, w[0], 1);
-                if (fetch_next) next = base[2 * plane + row + xp];
+                if (fetch_next) next = mx[row + xp];
 #pragma unroll
                 for (int i = 0; i < V - 1; ++i) g[5 * f + 2][i] = Storage<S>::to_c(w[i + 1]) * isc;
                 g[5 * f + 2][V - 1] = Storage<S>::to_c(next) * isc;
             }
             // +y: from y - 1;  -y: from y + 1
-            if (active) load16(w, base + 3 * plane + row_m + x0); else { for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(C(0)); }
+            load_or_zero<S, V>(w, fin.mov(f, 3) + row_m + x0, active);
 #pragma unroll
             for (int i = 0; i < V; ++i) g[5 * f + 3][i] = Storage<S>::to_c(w[i]) * isc;
-            if (active) load16(w, base + 4 * plane + row_p + x0); else { for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(C(0)); }
+            load_or_zero<S, V>(w, fin.mov(f, 4) + row_p + x0, active);
 #pragma unroll
             for (int i = 0; i < V; ++i) g[5 * f + 4][i] = Storage<S>::to_c(w[i]) * isc;
         }
@@ -120,25 +130,54 @@ k_stream_collide_2d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx,
 
         if (active) {
 #pragma unroll
-            for (int p = 0; p < 15; ++p) {
-                const C sc = Storage<S>::kScaled ? k.scale[p / 5] : C(1);
-                S w[V];
+            for (int f = 0; f < 3; ++f) {
+                {
+                    const C rsc = rest_store_scale<S, SPLIT>(k, f);
+                    R w[V];
 #pragma unroll
-                for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(g[p][i] * sc);
-                store16(fout + (long long)p * plane + row + x0, w);
+                    for (int i = 0; i < V; ++i) w[i] = Storage<R>::from_c(g[5 * f][i] * rsc);
+                    vstore<R, V>(fout.rest(f) + row + x0, w);
+                }
+                const C sc = mov_store_scale<S>(k, f);
+#pragma unroll
+                for (int l = 1; l < 5; ++l) {
+                    S w[V];
+#pragma unroll
+                    for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(g[5 * f + l][i] * sc);
+                    vstore<S, V>(fout.mov(f, l) + row + x0, w);
+                }
             }
         }
     }
     if (DIAG) block_reduce_store(acc, partials);
 }
 
+// Load / store one population of one node through the layout (scaled to deviations).
+template <class S, bool SPLIT, int Q>
+__device__ __forceinline__ typename Storage<S>::C load_pop(const Layout<S, SPLIT, Q>& L, int f, int l, long long node,
+                                                           const Coef<typename Storage<S>::C>& k) {
+    using R = typename Layout<S, SPLIT, Q>::R;
+    if (l == 0) return Storage<R>::to_c(L.rest(f)[node]) * rest_load_scale<S, SPLIT>(k, f);
+    return Storage<S>::to_c(L.mov(f, l)[node]) * mov_load_scale<S>(k, f);
+}
+
+template <class S, bool SPLIT, int Q>
+__device__ __forceinline__ void store_pop(const Layout<S, SPLIT, Q>& L, int f, int l, long long node,
+                                          typename Storage<S>::C v, const Coef<typename Storage<S>::C>& k) {
+    using R = typename Layout<S, SPLIT, Q>::R;
+    if (l == 0) L.rest(f)[node] = Storage<R>::from_c(v * rest_store_scale<S, SPLIT>(k, f));
+    else L.mov(f, l)[node] = Storage<S>::from_c(v * mov_store_scale<S>(k, f));
+}
+
 // ------------------------------------------------------------------------------
 // Fused stream-collide, one thread per node, any n_x (the ragged-size path).
-template <class S, bool DIAG>
+template <class S, bool SPLIT, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
-k_stream_collide_2d_generic(const S* __restrict__ fin, S* __restrict__ fout, int nx, int ny, long long plane,
-                            Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+k_stream_collide_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny,
+                            long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
     using C = typename Storage<S>::C;
+    using L = Layout<S, SPLIT, 5>;
+    const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     Acc<C> acc;
     if (DIAG) acc.zero();
@@ -154,10 +193,7 @@ k_stream_collide_2d_generic(const S* __restrict__ fin, S* __restrict__ fout, int
         };
         C g[15];
 #pragma unroll
-        for (int p = 0; p < 15; ++p) {
-            const C isc = Storage<S>::kScaled ? k.inv_scale[p / 5] : C(1);
-            g[p] = Storage<S>::to_c(fin[(long long)p * plane + src[p % 5]]) * isc;
-        }
+        for (int p = 0; p < 15; ++p) g[p] = load_pop(fin, p / 5, p % 5, src[p % 5], k);
         C dr, Qx, Qy;
         moments_d2q5(g, dr, Qx, Qy);
         if (DIAG) {
@@ -166,10 +202,7 @@ k_stream_collide_2d_generic(const S* __restrict__ fin, S* __restrict__ fout, int
         }
         relax_d2q5(k, g, dr, Qx, Qy);
 #pragma unroll
-        for (int p = 0; p < 15; ++p) {
-            const C sc = Storage<S>::kScaled ? k.scale[p / 5] : C(1);
-            fout[(long long)p * plane + node] = Storage<S>::from_c(g[p] * sc);
-        }
+        for (int p = 0; p < 15; ++p) store_pop(fout, p / 5, p % 5, node, g[p], k);
     }
     if (DIAG) block_reduce_store(acc, partials);
 }
@@ -179,11 +212,12 @@ k_stream_collide_2d_generic(const S* __restrict__ fin, S* __restrict__ fout, int
 // q = rho u, g = f^eq(rho, q) - F.  The density deviation is formed in FP64:
 // gamma = 1 gives dr = dx^2 rho_bar phi exactly; otherwise
 // dr = rho_bar expm1(log1p(dx^2 rho_bar phi / P(rho_bar)) / gamma).
-template <class S, class T>
+template <class S, bool SPLIT, class T>
 __global__ void __launch_bounds__(kThreads)
-k_init_2d(S* __restrict__ f, long long plane, const T* __restrict__ u, const T* __restrict__ phi,
+k_init_2d(char* __restrict__ f_b, long long plane, const T* __restrict__ u, const T* __restrict__ phi,
           Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
     using C = typename Storage<S>::C;
+    const Layout<S, SPLIT, 5> f{f_b, plane};
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= plane) return;
     const double ph = phi ? (double)phi[node] : 0.0;
@@ -192,31 +226,40 @@ k_init_2d(S* __restrict__ f, long long plane, const T* __restrict__ u, const T* 
     const double rho = rho_bar + dr;
     const double Qx = dx * rho * (double)u[node];
     const double Qy = dx * rho * (double)u[plane + node];
-    C e[15];
-    equilibrium_d2q5(k, (C)dr, (C)Qx, (C)Qy, e);
+    if constexpr (SPLIT) {   // moments, and no departure from equilibrium
+        f.rest(0)[node] = (float)dr;
+        f.rest(1)[node] = (float)Qx;
+        f.rest(2)[node] = (float)Qy;
 #pragma unroll
-    for (int p = 0; p < 15; ++p) {
-        const C sc = Storage<S>::kScaled ? k.scale[p / 5] : C(1);
-        f[(long long)p * plane + node] = Storage<S>::from_c(e[p] * sc);
+        for (int p = 0; p < 15; ++p)
+            if (p % 5) f.mov(p / 5, p % 5)[node] = Storage<S>::from_c(C(0));
+    } else {
+        C e[15];
+        equilibrium_d2q5(k, (C)dr, (C)Qx, (C)Qy, e);
+#pragma unroll
+        for (int p = 0; p < 15; ++p) store_pop(f, p / 5, p % 5, node, e[p], k);
     }
 }
 
-// Macroscopic fields of the state (moments of g*(t) = moments of g(t)).
-template <class S, class T>
+// Macroscopic fields of the state (moments of g*(t) = moments of g(t)), in FP64.
+template <class S, bool SPLIT, class T>
 __global__ void __launch_bounds__(kThreads)
-k_macros_2d(const S* __restrict__ f, long long plane, T* __restrict__ rho, T* __restrict__ u, T* __restrict__ phi,
+k_macros_2d(const char* __restrict__ f_b, long long plane, T* __restrict__ rho, T* __restrict__ u, T* __restrict__ phi,
             Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
-    using C = typename Storage<S>::C;
+    const Layout<S, SPLIT, 5> f{const_cast<char*>(f_b), plane};
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= plane) return;
-    double m[3] = {0.0, 0.0, 0.0};
+    double m[3];
 #pragma unroll
     for (int fld = 0; fld < 3; ++fld) {
-        const C isc = Storage<S>::kScaled ? k.inv_scale[fld] : C(1);
-        C s = C(0);
+        if constexpr (SPLIT) {
+            m[fld] = (double)f.rest(fld)[node];
+        } else {
+            double mv = 0.0;
 #pragma unroll
-        for (int l = 0; l < 5; ++l) s += Storage<S>::to_c(f[(long long)(5 * fld + l) * plane + node]) * isc;
-        m[fld] = (double)s;
+            for (int l = 1; l < 5; ++l) mv += (double)load_pop(f, fld, l, node, k);
+            m[fld] = (double)load_pop(f, fld, 0, node, k) + mv;
+        }
     }
     const double r = rho_bar + m[0];
     if (rho) rho[node] = (T)r;
@@ -231,22 +274,27 @@ k_macros_2d(const S* __restrict__ f, long long plane, T* __restrict__ rho, T* __
 }
 
 // Invariant partials over the stored lattice (no transport), grid-stride.
-template <class S>
+template <class S, bool SPLIT>
 __global__ void __launch_bounds__(kThreads)
-k_invariants_2d(const S* __restrict__ f, long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+k_invariants_2d(const char* __restrict__ f_b, long long plane, Coef<typename Storage<S>::C> k,
+                double* __restrict__ partials) {
     using C = typename Storage<S>::C;
+    const Layout<S, SPLIT, 5> f{const_cast<char*>(f_b), plane};
     Acc<C> acc;
     acc.zero();
     for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < plane;
          node += (long long)gridDim.x * blockDim.x) {
-        C g[15];
-#pragma unroll
-        for (int p = 0; p < 15; ++p) {
-            const C isc = Storage<S>::kScaled ? k.inv_scale[p / 5] : C(1);
-            g[p] = Storage<S>::to_c(f[(long long)p * plane + node]) * isc;
-        }
         C dr, Qx, Qy;
-        moments_d2q5(g, dr, Qx, Qy);
+        if constexpr (SPLIT) {
+            dr = (C)f.rest(0)[node];
+            Qx = (C)f.rest(1)[node];
+            Qy = (C)f.rest(2)[node];
+        } else {
+            C g[15];
+#pragma unroll
+            for (int p = 0; p < 15; ++p) g[p] = load_pop(f, p / 5, p % 5, node, k);
+            moments_d2q5(g, dr, Qx, Qy);
+        }
         const C Q[2] = {Qx, Qy};
         accumulate_node(acc, moments_finite(dr, Q, 2), dr, Q, 2, k.rho_bar);
     }
@@ -322,17 +370,42 @@ k_invariants_final(const double* __restrict__ partials, int nblocks, double* __r
 // g_p, or g_p + F_p with the rest equilibrium F = f^eq(rho_bar, 0):
 // rho field F = (f_rest, f_move, ..., f_move); momentum field j:
 // +p_half on the population along +e_j, -p_half along -e_j, 0 elsewhere.
-// Shared by 2D (q = 5) and 3D (q = 7).
-template <class S, class T>
+// Shared by 2D (Q = 5) and 3D (Q = 7).
+template <class S, bool SPLIT, int Q, class T>
 __global__ void __launch_bounds__(kThreads)
-k_export(const S* __restrict__ f, long long total, long long plane, int q, T* __restrict__ dst,
+k_export(const char* __restrict__ f_b, long long total, long long plane, T* __restrict__ dst,
          Coef<typename Storage<S>::C> k, double f_rest, double f_move, double p_half, int deviation) {
+    const Layout<S, SPLIT, Q> f{const_cast<char*>(f_b), plane};
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
     const int p = (int)(i / plane);
-    const int fld = p / q, l = p % q;
-    const double isc = Storage<S>::kScaled ? (double)k.inv_scale[fld] : 1.0;
-    double v = (double)Storage<S>::to_c(f[i]) * isc;
+    const long long node = i - (long long)p * plane;
+    const int fld = p / Q, l = p % Q;
+    double v;
+    if constexpr (SPLIT) {   // g* = e(m) + n, rest: e_0(m) - sum of n
+        using C = typename Storage<S>::C;
+        C e[4 * 7];
+        if constexpr (Q == 5) {
+            C ev[15];
+            equilibrium_d2q5(k, (C)f.rest(0)[node], (C)f.rest(1)[node], (C)f.rest(2)[node], ev);
+            for (int i = 0; i < 15; ++i) e[i] = ev[i];
+        } else {
+            C ev[28];
+            const C qv[3] = {(C)f.rest(1)[node], (C)f.rest(2)[node], (C)f.rest(3)[node]};
+            equilibrium_d3q7(k, (C)f.rest(0)[node], qv, ev);
+            for (int i = 0; i < 28; ++i) e[i] = ev[i];
+        }
+        const C isc = mov_load_scale<S>(k, fld);
+        if (l == 0) {
+            double sn = 0.0;
+            for (int j = 1; j < Q; ++j) sn += (double)(Storage<S>::to_c(f.mov(fld, j)[node]) * isc);
+            v = (double)e[fld * Q] - sn;
+        } else {
+            v = (double)e[fld * Q + l] + (double)(Storage<S>::to_c(f.mov(fld, l)[node]) * isc);
+        }
+    } else {
+        v = (double)load_pop(f, fld, l, node, k);
+    }
     if (!deviation) {
         if (fld == 0) v += (l == 0) ? f_rest : f_move;
         else if (l == 2 * (fld - 1) + 1) v += p_half;

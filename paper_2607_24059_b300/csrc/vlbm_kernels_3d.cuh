@@ -1,7 +1,8 @@
 // D3Q7 vectorial kernels (4 fields x 7 velocities = 28 populations per node):
 // fused transport + relaxation, initialisation, macroscopic fields and the
-// FP64 invariant partials.  Layout: 28 planes p = 7k + l, each plane
-// n_z x n_y x n_x, x fastest; velocities rest, +x, -x, +y, -y, +z, -z.
+// FP64 invariant partials.  Layout: 28 planes addressed through
+// Layout<S, SPLIT, 7>, each plane n_z x n_y x n_x, x fastest; velocities rest,
+// +x, -x, +y, -y, +z, -z.
 #pragma once
 
 #include "vlbm_kernels_2d.cuh"
@@ -17,12 +18,16 @@ template <class S> struct Vec8 {
 // Fused stream-collide, vectorised along x (n_x % V == 0).  Warp w handles
 // 32 V consecutive nodes of one (y, z) row.  x-shifts by warp shuffle as in
 // 2D; +-y are rows y -+ 1 of the same z slab, +-z the same row of slab z -+ 1.
-template <class S, bool DIAG>
+template <class S, bool SPLIT, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
-k_stream_collide_3d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx, int ny, int nz, long long plane,
-                        int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
+                        long long plane, int warps_per_row, Coef<typename Storage<S>::C> k,
+                        double* __restrict__ partials) {
     using C = typename Storage<S>::C;
+    using L = Layout<S, SPLIT, 7>;
+    using R = typename L::R;
     constexpr int V = Vec8<S>::V;
+    const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     Acc<C> acc;
@@ -44,25 +49,28 @@ k_stream_collide_3d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx,
         C g[28][V];
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            const S* base = fin + (long long)(7 * f) * plane;
-            const C isc = Storage<S>::kScaled ? k.inv_scale[f] : C(1);
+            const C risc = rest_load_scale<S, SPLIT>(k, f);
+            const C isc = mov_load_scale<S>(k, f);
+            {
+                R w[V];
+                load_or_zero<R, V>(w, fin.rest(f) + row + x0, active);
 #pragma unroll
-            for (int l = 0; l < 7; ++l) {
+                for (int i = 0; i < V; ++i) g[7 * f][i] = Storage<R>::to_c(w[i]) * risc;
+            }
+#pragma unroll
+            for (int l = 1; l < 7; ++l) {
+                const S* pl = fin.mov(f, l);
                 S w[V];
-                if (active) vload<S, V>(w, base + l * plane + src_row[l] + x0);
-                else {
-#pragma unroll
-                    for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(C(0));
-                }
+                load_or_zero<S, V>(w, pl + src_row[l] + x0, active);
                 if (l == 1) {           // +x: from x - 1
                     S prev = __shfl_up_sync(0xffffffffu, w[V - 1], 1);
-                    if (lane == 0 && active) prev = base[plane + row + xm];
+                    if (lane == 0 && active) prev = pl[row + xm];
                     g[7 * f + 1][0] = Storage<S>::to_c(prev) * isc;
 #pragma unroll
                     for (int i = 1; i < V; ++i) g[7 * f + 1][i] = Storage<S>::to_c(w[i - 1]) * isc;
                 } else if (l == 2) {    // -x: from x + 1
                     S next = __shfl_down_sync(0xffffffffu, w[0], 1);
-                    if (fetch_next) next = base[2 * plane + row + xp];
+                    if (fetch_next) next = pl[row + xp];
 #pragma unroll
                     for (int i = 0; i < V - 1; ++i) g[7 * f + 2][i] = Storage<S>::to_c(w[i + 1]) * isc;
                     g[7 * f + 2][V - 1] = Storage<S>::to_c(next) * isc;
@@ -88,12 +96,22 @@ k_stream_collide_3d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx,
 
         if (active) {
 #pragma unroll
-            for (int p = 0; p < 28; ++p) {
-                const C sc = Storage<S>::kScaled ? k.scale[p / 7] : C(1);
-                S w[V];
+            for (int f = 0; f < 4; ++f) {
+                {
+                    const C rsc = rest_store_scale<S, SPLIT>(k, f);
+                    R w[V];
 #pragma unroll
-                for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(g[p][i] * sc);
-                vstore<S, V>(fout + (long long)p * plane + row + x0, w);
+                    for (int i = 0; i < V; ++i) w[i] = Storage<R>::from_c(g[7 * f][i] * rsc);
+                    vstore<R, V>(fout.rest(f) + row + x0, w);
+                }
+                const C sc = mov_store_scale<S>(k, f);
+#pragma unroll
+                for (int l = 1; l < 7; ++l) {
+                    S w[V];
+#pragma unroll
+                    for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(g[7 * f + l][i] * sc);
+                    vstore<S, V>(fout.mov(f, l) + row + x0, w);
+                }
             }
         }
     }
@@ -101,11 +119,13 @@ k_stream_collide_3d_vec(const S* __restrict__ fin, S* __restrict__ fout, int nx,
 }
 
 // One thread per node, any size.
-template <class S, bool DIAG>
+template <class S, bool SPLIT, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
-k_stream_collide_3d_generic(const S* __restrict__ fin, S* __restrict__ fout, int nx, int ny, int nz,
+k_stream_collide_3d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
                             long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
     using C = typename Storage<S>::C;
+    using L = Layout<S, SPLIT, 7>;
+    const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     Acc<C> acc;
     if (DIAG) acc.zero();
@@ -125,28 +145,23 @@ k_stream_collide_3d_generic(const S* __restrict__ fin, S* __restrict__ fout, int
                                   ((long long)zp * ny + y) * nx + x};
         C g[28];
 #pragma unroll
-        for (int p = 0; p < 28; ++p) {
-            const C isc = Storage<S>::kScaled ? k.inv_scale[p / 7] : C(1);
-            g[p] = Storage<S>::to_c(fin[(long long)p * plane + src[p % 7]]) * isc;
-        }
+        for (int p = 0; p < 28; ++p) g[p] = load_pop(fin, p / 7, p % 7, src[p % 7], k);
         C dr, Q[3];
         moments_d3q7(g, dr, Q);
         if (DIAG) accumulate_node(acc, moments_finite(dr, Q, 3), dr, Q, 3, k.rho_bar);
         relax_d3q7(k, g, dr, Q);
 #pragma unroll
-        for (int p = 0; p < 28; ++p) {
-            const C sc = Storage<S>::kScaled ? k.scale[p / 7] : C(1);
-            fout[(long long)p * plane + node] = Storage<S>::from_c(g[p] * sc);
-        }
+        for (int p = 0; p < 28; ++p) store_pop(fout, p / 7, p % 7, node, g[p], k);
     }
     if (DIAG) block_reduce_store(acc, partials);
 }
 
-template <class S, class T>
+template <class S, bool SPLIT, class T>
 __global__ void __launch_bounds__(kThreads)
-k_init_3d(S* __restrict__ f, long long plane, const T* __restrict__ u, const T* __restrict__ phi,
+k_init_3d(char* __restrict__ f_b, long long plane, const T* __restrict__ u, const T* __restrict__ phi,
           Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
     using C = typename Storage<S>::C;
+    const Layout<S, SPLIT, 7> f{f_b, plane};
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= plane) return;
     const double ph = phi ? (double)phi[node] : 0.0;
@@ -156,30 +171,39 @@ k_init_3d(S* __restrict__ f, long long plane, const T* __restrict__ u, const T* 
     C Q[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) Q[d] = (C)(dx * rho * (double)u[d * plane + node]);
-    C e[28];
-    equilibrium_d3q7(k, (C)dr, Q, e);
+    if constexpr (SPLIT) {   // moments, and no departure from equilibrium
+        f.rest(0)[node] = (float)dr;
 #pragma unroll
-    for (int p = 0; p < 28; ++p) {
-        const C sc = Storage<S>::kScaled ? k.scale[p / 7] : C(1);
-        f[(long long)p * plane + node] = Storage<S>::from_c(e[p] * sc);
+        for (int d = 0; d < 3; ++d) f.rest(d + 1)[node] = (float)Q[d];
+#pragma unroll
+        for (int p = 0; p < 28; ++p)
+            if (p % 7) f.mov(p / 7, p % 7)[node] = Storage<S>::from_c(C(0));
+    } else {
+        C e[28];
+        equilibrium_d3q7(k, (C)dr, Q, e);
+#pragma unroll
+        for (int p = 0; p < 28; ++p) store_pop(f, p / 7, p % 7, node, e[p], k);
     }
 }
 
-template <class S, class T>
+template <class S, bool SPLIT, class T>
 __global__ void __launch_bounds__(kThreads)
-k_macros_3d(const S* __restrict__ f, long long plane, T* __restrict__ rho, T* __restrict__ u, T* __restrict__ phi,
+k_macros_3d(const char* __restrict__ f_b, long long plane, T* __restrict__ rho, T* __restrict__ u, T* __restrict__ phi,
             Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
-    using C = typename Storage<S>::C;
+    const Layout<S, SPLIT, 7> f{const_cast<char*>(f_b), plane};
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= plane) return;
     double m[4];
 #pragma unroll
     for (int fld = 0; fld < 4; ++fld) {
-        const C isc = Storage<S>::kScaled ? k.inv_scale[fld] : C(1);
-        C s = C(0);
+        if constexpr (SPLIT) {
+            m[fld] = (double)f.rest(fld)[node];
+        } else {
+            double mv = 0.0;
 #pragma unroll
-        for (int l = 0; l < 7; ++l) s += Storage<S>::to_c(f[(long long)(7 * fld + l) * plane + node]) * isc;
-        m[fld] = (double)s;
+            for (int l = 1; l < 7; ++l) mv += (double)load_pop(f, fld, l, node, k);
+            m[fld] = (double)load_pop(f, fld, 0, node, k) + mv;
+        }
     }
     const double r = rho_bar + m[0];
     if (rho) rho[node] = (T)r;
@@ -191,22 +215,27 @@ k_macros_3d(const S* __restrict__ f, long long plane, T* __restrict__ rho, T* __
     }
 }
 
-template <class S>
+template <class S, bool SPLIT>
 __global__ void __launch_bounds__(kThreads)
-k_invariants_3d(const S* __restrict__ f, long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+k_invariants_3d(const char* __restrict__ f_b, long long plane, Coef<typename Storage<S>::C> k,
+                double* __restrict__ partials) {
     using C = typename Storage<S>::C;
+    const Layout<S, SPLIT, 7> f{const_cast<char*>(f_b), plane};
     Acc<C> acc;
     acc.zero();
     for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < plane;
          node += (long long)gridDim.x * blockDim.x) {
-        C g[28];
-#pragma unroll
-        for (int p = 0; p < 28; ++p) {
-            const C isc = Storage<S>::kScaled ? k.inv_scale[p / 7] : C(1);
-            g[p] = Storage<S>::to_c(f[(long long)p * plane + node]) * isc;
-        }
         C dr, Q[3];
-        moments_d3q7(g, dr, Q);
+        if constexpr (SPLIT) {
+            dr = (C)f.rest(0)[node];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) Q[d] = (C)f.rest(d + 1)[node];
+        } else {
+            C g[28];
+#pragma unroll
+            for (int p = 0; p < 28; ++p) g[p] = load_pop(f, p / 7, p % 7, node, k);
+            moments_d3q7(g, dr, Q);
+        }
         accumulate_node(acc, moments_finite(dr, Q, 3), dr, Q, 3, k.rho_bar);
     }
     block_reduce_store(acc, partials);

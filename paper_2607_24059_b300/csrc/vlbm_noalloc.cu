@@ -76,15 +76,15 @@ Coef<C> reduction_coef(const vlbm_params& p) {
     return k;
 }
 
-template <class S>
+template <class S, bool M>
 void launch_partials(const vlbm_params& p, const void* lattice, long long nodes, int blocks, double* partials,
                      cudaStream_t s) {
     using C = typename Storage<S>::C;
     const Coef<C> k = reduction_coef<C>(p);
     if (p.dim == 2)
-        k_invariants_2d<S><<<blocks, kThreads, 0, s>>>((const S*)lattice, nodes, k, partials);
+        k_invariants_2d<S, M><<<blocks, kThreads, 0, s>>>((const char*)lattice, nodes, k, partials);
     else
-        k_invariants_3d<S><<<blocks, kThreads, 0, s>>>((const S*)lattice, nodes, k, partials);
+        k_invariants_3d<S, M><<<blocks, kThreads, 0, s>>>((const char*)lattice, nodes, k, partials);
 }
 
 }  // namespace
@@ -110,10 +110,14 @@ extern "C" int vlbm_invariants_noalloc(const vlbm_params* p, const void* lattice
     cudaGetLastError();
     cudaStream_t s = (cudaStream_t)stream;
     switch (p->precision) {
-        case VLBM_FP64: launch_partials<double>(*p, lattice, nodes, (int)blocks, partials, s); break;
-        case VLBM_FP32: launch_partials<float>(*p, lattice, nodes, (int)blocks, partials, s); break;
-        case VLBM_FP16_SHIFTED: launch_partials<__half>(*p, lattice, nodes, (int)blocks, partials, s); break;
-        default: launch_partials<__nv_bfloat16>(*p, lattice, nodes, (int)blocks, partials, s); break;
+        case VLBM_FP64: launch_partials<double, false>(*p, lattice, nodes, (int)blocks, partials, s); break;
+        case VLBM_FP32: launch_partials<float, false>(*p, lattice, nodes, (int)blocks, partials, s); break;
+        case VLBM_FP16_SHIFTED: launch_partials<__half, false>(*p, lattice, nodes, (int)blocks, partials, s); break;
+        case VLBM_BF16_SHIFTED:
+            launch_partials<__nv_bfloat16, false>(*p, lattice, nodes, (int)blocks, partials, s);
+            break;
+        case VLBM_FP16_SPLIT: launch_partials<__half, true>(*p, lattice, nodes, (int)blocks, partials, s); break;
+        default: launch_partials<__nv_bfloat16, true>(*p, lattice, nodes, (int)blocks, partials, s); break;
     }
     // the row after the partials holds the result when `out` is host memory
     double* result = out_on_device ? out : partials + (size_t)kNoAllocMaxBlocks * 8;

@@ -109,7 +109,7 @@ def test_ragged_sizes(orc, n, precision, tol):
     assert np.max(np.abs(u_g - u_o)) <= tol * max(np.max(np.abs(u_o)), 1e-3)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16", "bf16", "fp16split", "bf16split"])
 @pytest.mark.parametrize("n", [(64, 48), (128, 20), (8, 3)])
 def test_vector_and_generic_kernels_bitwise(n, precision):
     u, phi = smooth_random_state(n, seed=3)
@@ -117,7 +117,12 @@ def test_vector_and_generic_kernels_bitwise(n, precision):
     a = gpu_run(op, precision, u, phi, 77, variant=1)
     b = gpu_run(op, precision, u, phi, 77, variant=2)
     for x, y in zip(a, b):
-        assert np.array_equal(x, y)
+        if precision.endswith("split"):
+            # the split kernels inline the same arithmetic into different code, where
+            # the compiler may contract a different multiply-add pair into an FMA
+            assert np.max(np.abs(x - y)) <= 1e-6 * max(np.max(np.abs(y)), 1e-30)
+        else:
+            assert np.array_equal(x, y)
 
 
 def test_graph_replay_is_bitwise_equal_to_launches():
@@ -244,7 +249,7 @@ def test_host_and_device_pointers_agree():
 
 # ------------------------------------------------------------ checkpoint / failure detection
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16", "fp16split"])
 def test_checkpoint_resume_is_bitwise(precision):
     n = (64, 40)
     u, phi = smooth_random_state(n, seed=17)
@@ -292,10 +297,57 @@ def test_launch_counter_counts_kernels():
     lat.close()
 
 
+# ------------------------------------------------------------ reduced-precision storage
+
+def l2_rel(a, b):
+    return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
+
+# Gates: the split layouts (FP32 moments, 16-bit non-equilibrium parts) must
+# hold L2 <= 1e-3 of the velocity against the oracle.  The pure 16-bit layouts
+# lose every per-step change smaller than half an ulp of the stored value (about
+# 2.4e-4 relative for FP16, 2e-3 for BF16): a slowly evolving flow stops
+# evolving, so their error is bounded by the change the flow makes over the run
+# (2.4 % for 1000 steps of this Taylor-Green vortex); stated here as 5e-2.
+@pytest.mark.parametrize("precision,gate", [("fp16split", 1e-3), ("bf16split", 1e-3), ("fp16", 5e-2), ("bf16", 5e-2)])
+def test_reduced_precision_tgv_64_1000_steps(orc, precision, gate):
+    n = 64
+    u, phi, dx = synthetic.taylor_green_2d(n)
+    op = resolved((n, n), dx, nu=0.01)
+    (_, u_o, _), _ = orc_run(orc, op, u, phi, 1000)
+    _, u_g, _ = gpu_run(op, precision, u, phi, 1000)
+    err = l2_rel(u_g, u_o)
+    print(f"TGV 64^2 1000 steps {precision}: L2 {err:.3e}")
+    assert err <= gate, err
+
+
+@pytest.mark.parametrize("precision,gate", [("fp16split", 1e-3), ("bf16split", 1e-3), ("fp16", 5e-2), ("bf16", 5e-2)])
+def test_reduced_precision_shear_layer_256(orc, precision, gate):
+    n = 256
+    u, phi, dx = synthetic.double_shear_layer(n)
+    op = resolved((n, n), dx, nu=1e-4)
+    (_, u_o, _), _ = orc_run(orc, op, u, phi, 1000)
+    _, u_g, _ = gpu_run(op, precision, u, phi, 1000)
+    err = l2_rel(u_g, u_o)
+    print(f"shear layer 256^2 1000 steps {precision}: L2 {err:.3e}")
+    assert err <= gate, err
+
+
+@pytest.mark.parametrize("n", [(37, 53), (136, 10), (1, 9)])
+@pytest.mark.parametrize("precision", ["fp16split", "bf16split", "fp16", "bf16"])
+def test_reduced_precision_ragged(orc, n, precision):
+    u, phi = smooth_random_state(n, seed=n[0] + 7 * n[1])
+    op = resolved(n, 0.05, nu=0.02, omega_rho=1.3, omega_q=1.1)
+    (_, u_o, _), _ = orc_run(orc, op, u, phi, 60)
+    _, u_g, _ = gpu_run(op, precision, u, phi, 60)
+    tol = 1e-4 if precision.endswith("split") else 5e-2
+    assert np.max(np.abs(u_g - u_o)) <= tol * max(np.max(np.abs(u_o)), 1e-3)
+
+
 # ------------------------------------------------------------ D3Q7
 
 @pytest.mark.parametrize("n", [(16, 12, 8), (15, 6, 5), (2, 3, 4), (1, 1, 6)])
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("fp16split", 2e-3)])
 def test_d3q7_matches_oracle(orc, n, precision, tol):
     rng = np.random.default_rng(sum(n))
     grid = tuple(reversed(n))
