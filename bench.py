@@ -64,7 +64,9 @@ def bytes_per_node(args):
 def kernel_name(args):
     dim = WORKLOADS[args.workload][0]
     if split(args):
-        return f"k_split_step_{dim}d_vec<{CTYPE[args.precision]}, false>"
+        lanes = (args.split_lanes or 4) if dim == 2 else None
+        mid = f", {lanes}" if lanes else ""
+        return f"k_split_step_{dim}d_vec<{CTYPE[args.precision]}{mid}, false>"
     return f"k_stream_collide_{dim}d_vec<{CTYPE[args.precision]}, false, false>"
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -80,6 +82,8 @@ def parse_args():
     ap.add_argument("--workload", choices=list(WORKLOADS), default="dsl2d")
     ap.add_argument("--n", type=int, default=None, help="lattice side (default: 4096 in 2D, 256 in 3D)")
     ap.add_argument("--precision", choices=list(ELEM_BYTES), default="fp32")
+    ap.add_argument("--split-lanes", type=int, choices=[2, 4], default=None,
+                    help="nodes per lane of the 2D split kernels (tuning)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--reference-seconds", type=float, default=150.0, help="cap on the reference arm's timed steps")
@@ -305,6 +309,8 @@ def run_vlbm(args):
 
     u, phi, dx, shape = make_input(args)
     lat = vlbm.Lattice(shape, dx, nu=WORKLOADS[args.workload][3], precision=args.precision)
+    if args.split_lanes:
+        lat.set_option(vlbm.VLBM_OPT_SPLIT_LANES, args.split_lanes)
     lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
     # warm-up: W steps, then prime the CUDA graphs of both buffer parities
     lat.step(args.warmup)

@@ -188,6 +188,9 @@ int vlbm_launch_count(const vlbm_handle* h, int64_t* count);
  * 2 = vectorised (VLBM_EINVAL when n_x does not allow it).  Both compute the
  * same arithmetic in the same order, so their results are bitwise equal. */
 #define VLBM_OPT_KERNEL 0
+/* VLBM_OPT_SPLIT_LANES: nodes per lane (2 or 4, default 4) of the vectorised 2D
+ * kernel of the split formats; a tuning knob, same results up to FMA contraction. */
+#define VLBM_OPT_SPLIT_LANES 1
 int vlbm_set_option(vlbm_handle* h, int32_t key, int64_t value);
 
 /* The reduction of vlbm_invariants for callers that cannot allocate device

@@ -58,6 +58,7 @@ struct vlbm_handle {
     int64_t step = 0;
     int64_t launches = 0;
     int kernel_variant = 0;           // 0 auto, 1 generic, 2 vectorised
+    int split_lanes = kSplitV2;       // nodes per lane of the 2D split kernel (2 or 4)
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::string err;
@@ -211,7 +212,7 @@ static int64_t blocks_for(int64_t threads) { return (threads + kThreads - 1) / k
 // Nodes per lane of the vectorised step kernels (Vec16 / Vec8 in the kernel
 // headers): 2D min(4, 16 B / element), 3D min(2, 8 B / element).
 static int vec_width(const vlbm_handle* h) {
-    if (is_split(h->p.precision)) return h->p.dim == 2 ? kSplitV2 : kSplitV3;
+    if (is_split(h->p.precision)) return h->p.dim == 2 ? h->split_lanes : kSplitV3;
     const int b = h->d.bytes_per_population;
     return h->p.dim == 2 ? std::min(4, 16 / b) : std::min(2, 8 / b);
 }
@@ -278,7 +279,11 @@ extern "C" int vlbm_create(const vlbm_params* p, void* stream, vlbm_handle** out
             if (e != cudaSuccess) st = VLBM_ENOMEM;
         }
         if (st != VLBM_OK) break;
-        h->partial_capacity = std::max(step_blocks(h), inv_blocks(h));
+        // any step variant may be selected later (VLBM_OPT_*): size for the largest
+        // grid, one thread per node or one lane per node (vector width 1)
+        const int64_t rows = d.nodes / p->n[0];
+        const int64_t widest = (rows * ((p->n[0] + 31) / 32) * 32 + kThreads - 1) / kThreads;
+        h->partial_capacity = std::max({blocks_for(d.nodes), widest, inv_blocks(h)});
         if (cudaMalloc(&h->partials, (size_t)h->partial_capacity * 8 * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&h->stage, (size_t)kStageBlocks * 8 * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&h->inv_dev, 8 * sizeof(double)) != cudaSuccess ||
@@ -475,9 +480,12 @@ static void launch_step_on(vlbm_handle* h, cudaStream_t s, int src, double* part
     const int wpr = (int)((nx / vec_width(h) + 31) / 32);
     if constexpr (M) {
         if (h->p.dim == 2) {
-            if (vec)
-                k_split_step_2d_vec<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, wpr, k,
-                                                                         partials);
+            if (vec && h->split_lanes == 2)
+                k_split_step_2d_vec<S, 2, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, wpr,
+                                                                            k, partials);
+            else if (vec)
+                k_split_step_2d_vec<S, 4, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, wpr,
+                                                                            k, partials);
             else
                 k_split_step_2d_generic<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, k,
                                                                              partials);
@@ -803,6 +811,16 @@ extern "C" int vlbm_set_option(vlbm_handle* h, int32_t key, int64_t value) {
             if (value < 0 || value > 2) return VLBM_EINVAL;
             if (value == 2 && h->p.n[0] % vec_width(h) != 0) return VLBM_EINVAL;
             h->kernel_variant = (int)value;
+            for (int i = 0; i < 2; ++i)
+                if (h->graph[i]) {
+                    cudaGraphExecDestroy(h->graph[i]);
+                    h->graph[i] = nullptr;
+                }
+            return VLBM_OK;
+        case VLBM_OPT_SPLIT_LANES:
+            if (value != 2 && value != 4) return VLBM_EINVAL;
+            if (h->p.dim == 2 && h->p.n[0] % value != 0 && h->kernel_variant == 2) return VLBM_EINVAL;
+            h->split_lanes = (int)value;
             for (int i = 0; i < 2; ++i)
                 if (h->graph[i]) {
                     cudaGraphExecDestroy(h->graph[i]);

@@ -111,13 +111,16 @@ __device__ __forceinline__ void pulled_d2q5(const Coef<C>& k, const C (&ms)[3], 
     for (int f = 0; f < 3; ++f) B[f][L - 1] = e[f] + n[f];
 }
 
-template <class S, bool DIAG>
+// Vectorised 2D split step with V nodes per lane.  All loads of a lane are
+// issued first (its moments, the moment rows y -+ 1, the six own-row and six
+// pulled rows of non-equilibrium parts, and the warp-edge halo values), then
+// the arithmetic runs: the kernel is limited by how many bytes are in flight.
+template <class S, int V, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
 k_split_step_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
                     int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
     using C = typename Storage<S>::C;
     using L = Layout<S, true, 5>;
-    constexpr int V = kSplitV2;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -135,85 +138,95 @@ k_split_step_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, i
         const bool left_edge = lane == 0 && active;
         const bool right_edge = active && (lane == 31 || x0 + V >= nx);
 
+        // ---- load phase
+        float mo[3][V], mym[3][V], myp[3][V];
+        S n_px[3][V], n_mx[3][V], n_py_pull[3][V], n_my_pull[3][V], n_py_own[3][V], n_my_own[3][V];
+        float hm_l[3], hm_r[3];
+        S hn_l[3], hn_r[3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            load_or_zero<float, V>(mo[f], fin.rest(f) + row + x0, active);
+            load_or_zero<float, V>(mym[f], fin.rest(f) + row_m + x0, active);
+            load_or_zero<float, V>(myp[f], fin.rest(f) + row_p + x0, active);
+            load_or_zero<S, V>(n_px[f], fin.mov(f, 1) + row + x0, active);
+            load_or_zero<S, V>(n_mx[f], fin.mov(f, 2) + row + x0, active);
+            load_or_zero<S, V>(n_py_pull[f], fin.mov(f, 3) + row_m + x0, active);
+            load_or_zero<S, V>(n_my_pull[f], fin.mov(f, 4) + row_p + x0, active);
+            load_or_zero<S, V>(n_py_own[f], fin.mov(f, 3) + row + x0, active);
+            load_or_zero<S, V>(n_my_own[f], fin.mov(f, 4) + row + x0, active);
+            hm_l[f] = hm_r[f] = 0.0f;
+            hn_l[f] = hn_r[f] = Storage<S>::from_c(C(0));
+            if (left_edge) {
+                hm_l[f] = fin.rest(f)[row + xm];
+                hn_l[f] = fin.mov(f, 1)[row + xm];
+            }
+            if (right_edge) {
+                hm_r[f] = fin.rest(f)[row + xp];
+                hn_r[f] = fin.mov(f, 2)[row + xp];
+            }
+        }
+
+        // ---- arithmetic
         C m[3][V], nown[3][V], B[3][4][V];
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            load_vec_c<float, V>(m[f], fin.rest(f) + row + x0, active, C(1));
-#pragma unroll
-            for (int i = 0; i < V; ++i) nown[f][i] = C(0);
-        }
-        // +x (l = 1) and -x (l = 2): sources x -+ 1, moments and n shifted across lanes
-#pragma unroll
-        for (int l = 1; l <= 2; ++l) {
-            C ms[3][V], np[3][V];
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                const float* mp = fin.rest(f);
-                const S* npl = fin.mov(f, l);
-                const C isc = mov_load_scale<S>(k, f);
-                C own[V];
-                load_vec_c<S, V>(own, npl + row + x0, active, isc);
-#pragma unroll
-                for (int i = 0; i < V; ++i) nown[f][i] += own[i];
-                if (l == 1) {
-                    C em = C(0), en = C(0);
-                    if (left_edge) {
-                        em = (C)mp[row + xm];
-                        en = Storage<S>::to_c(npl[row + xm]) * isc;
-                    }
-                    shift_from_left<C, V>(ms[f], m[f], left_edge, em);
-                    shift_from_left<C, V>(np[f], own, left_edge, en);
-                } else {
-                    C em = C(0), en = C(0);
-                    if (right_edge) {
-                        em = (C)mp[row + xp];
-                        en = Storage<S>::to_c(npl[row + xp]) * isc;
-                    }
-                    shift_from_right<C, V>(ms[f], m[f], right_edge, em);
-                    shift_from_right<C, V>(np[f], own, right_edge, en);
-                }
-            }
+            const C isc = mov_load_scale<S>(k, f);
+            C a[V], b[V];
 #pragma unroll
             for (int i = 0; i < V; ++i) {
-                const C msi[3] = {ms[0][i], ms[1][i], ms[2][i]}, npi[3] = {np[0][i], np[1][i], np[2][i]};
-                C Bi[3][4];
-                if (l == 1) pulled_d2q5<C, 1>(k, msi, npi, Bi);
-                else if (l == 2) pulled_d2q5<C, 2>(k, msi, npi, Bi);
-                else if (l == 3) pulled_d2q5<C, 3>(k, msi, npi, Bi);
-                else pulled_d2q5<C, 4>(k, msi, npi, Bi);
-#pragma unroll
-                for (int f = 0; f < 3; ++f) B[f][l - 1][i] = Bi[f][l - 1];
+                m[f][i] = (C)mo[f][i];
+                a[i] = Storage<S>::to_c(n_px[f][i]) * isc;
+                b[i] = Storage<S>::to_c(n_mx[f][i]) * isc;
+                nown[f][i] = (a[i] + b[i]) + (Storage<S>::to_c(n_py_own[f][i]) * isc +
+                                              Storage<S>::to_c(n_my_own[f][i]) * isc);
             }
-        }
-        // +y (l = 3) from row y - 1, -y (l = 4) from row y + 1
+            // pulled non-equilibrium parts, stashed in B until the equilibria are added
+            C sh[V];
+            shift_from_left<C, V>(sh, a, left_edge, Storage<S>::to_c(hn_l[f]) * isc);
 #pragma unroll
-        for (int l = 3; l <= 4; ++l) {
-            const long long src = l == 3 ? row_m : row_p;
-            C ms[3][V], np[3][V];
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                const C isc = mov_load_scale<S>(k, f);
-                load_vec_c<float, V>(ms[f], fin.rest(f) + src + x0, active, C(1));
-                load_vec_c<S, V>(np[f], fin.mov(f, l) + src + x0, active, isc);
-                C own[V];
-                load_vec_c<S, V>(own, fin.mov(f, l) + row + x0, active, isc);
-#pragma unroll
-                for (int i = 0; i < V; ++i) nown[f][i] += own[i];
-            }
+            for (int i = 0; i < V; ++i) B[f][0][i] = sh[i];
+            shift_from_right<C, V>(sh, b, right_edge, Storage<S>::to_c(hn_r[f]) * isc);
 #pragma unroll
             for (int i = 0; i < V; ++i) {
-                const C msi[3] = {ms[0][i], ms[1][i], ms[2][i]}, npi[3] = {np[0][i], np[1][i], np[2][i]};
-                C Bi[3][4];
-                if (l == 1) pulled_d2q5<C, 1>(k, msi, npi, Bi);
-                else if (l == 2) pulled_d2q5<C, 2>(k, msi, npi, Bi);
-                else if (l == 3) pulled_d2q5<C, 3>(k, msi, npi, Bi);
-                else pulled_d2q5<C, 4>(k, msi, npi, Bi);
-#pragma unroll
-                for (int f = 0; f < 3; ++f) B[f][l - 1][i] = Bi[f][l - 1];
+                B[f][1][i] = sh[i];
+                B[f][2][i] = Storage<S>::to_c(n_py_pull[f][i]) * isc;
+                B[f][3][i] = Storage<S>::to_c(n_my_pull[f][i]) * isc;
             }
+        }
+        // source moments of the x neighbours by warp shuffle
+        C mxl[3][V], mxr[3][V];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            shift_from_left<C, V>(mxl[f], m[f], left_edge, (C)hm_l[f]);
+            shift_from_right<C, V>(mxr[f], m[f], right_edge, (C)hm_r[f]);
         }
 #pragma unroll
         for (int i = 0; i < V; ++i) {
+            C e[3];
+            {
+                const C ms[3] = {mxl[0][i], mxl[1][i], mxl[2][i]};
+                equilibrium_dir<C, 3, 1>(k, ms, e);
+#pragma unroll
+                for (int f = 0; f < 3; ++f) B[f][0][i] += e[f];
+            }
+            {
+                const C ms[3] = {mxr[0][i], mxr[1][i], mxr[2][i]};
+                equilibrium_dir<C, 3, 2>(k, ms, e);
+#pragma unroll
+                for (int f = 0; f < 3; ++f) B[f][1][i] += e[f];
+            }
+            {
+                const C ms[3] = {(C)mym[0][i], (C)mym[1][i], (C)mym[2][i]};
+                equilibrium_dir<C, 3, 3>(k, ms, e);
+#pragma unroll
+                for (int f = 0; f < 3; ++f) B[f][2][i] += e[f];
+            }
+            {
+                const C ms[3] = {(C)myp[0][i], (C)myp[1][i], (C)myp[2][i]};
+                equilibrium_dir<C, 3, 4>(k, ms, e);
+#pragma unroll
+                for (int f = 0; f < 3; ++f) B[f][3][i] += e[f];
+            }
             C mi[3] = {m[0][i], m[1][i], m[2][i]};
             C Bi[3][4];
             const C ni[3] = {nown[0][i], nown[1][i], nown[2][i]};
