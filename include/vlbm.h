@@ -216,6 +216,49 @@ int vlbm_set_option(vlbm_handle* h, int32_t key, int64_t value);
  * GPU (two streams or two host threads) race on it and must be serialised. */
 int vlbm_invariants_noalloc(const vlbm_params* p, const void* lattice, double* out, void* stream);
 
+/* ---- batched problems ----------------------------------------------------
+ * Many independent periodic 2D problems advanced together: each has its own
+ * vlbm_params (size, dx, viscosity, relaxation; dt = dx^2 / mu of its own),
+ * all share one precision, and n[0] of each must be a multiple of 4.  A
+ * vlbm_batch_step advances every problem by one of its own time steps with
+ * one persistent kernel launch over a work list of (problem, row, segment)
+ * items; runs of steps replay a captured CUDA graph.  The arithmetic is that
+ * of a single handle.  Not an operation of the paper: a way to run many of
+ * its problems at once. */
+typedef struct vlbm_batch vlbm_batch;
+
+/* problems: `count` parameter sets (dim 2, same precision).  Allocates two
+ * levels of all lattices (each 256-byte aligned) on the current device,
+ * zeroed (rest state).  On failure *out is NULL. */
+int vlbm_batch_create(const vlbm_params* problems, int32_t count, void* stream, vlbm_batch** out);
+void vlbm_batch_destroy(vlbm_batch* b);
+
+/* Initialise problem `problem` at equilibrium from u ([2][ny][nx]) and phi
+ * ([ny][nx] or NULL), as vlbm_init; host or device pointers. */
+int vlbm_batch_init(vlbm_batch* b, int32_t problem, const void* u, const void* phi, int32_t dtype);
+
+/* Advance every problem by nsteps of its own time step (asynchronous). */
+int vlbm_batch_step(vlbm_batch* b, int64_t nsteps, int32_t flags);
+
+/* Macroscopic fields / invariants of one problem, as vlbm_macros / vlbm_invariants. */
+int vlbm_batch_macros(vlbm_batch* b, int32_t problem, void* rho, void* u, void* phi, int32_t dtype);
+int vlbm_batch_invariants(vlbm_batch* b, int32_t problem, double* out);
+
+/* Launch shape of the step kernel: threads per block (128 or 256), blocks per
+ * SM (1..16) and, for the split formats, nodes per lane (2 or 4). */
+int vlbm_batch_set_config(vlbm_batch* b, int32_t threads, int32_t blocks_per_sm, int32_t lanes);
+
+/* Time every candidate launch shape on `repeats` dry-run steps (they read the
+ * current level and write the other without committing it, so the state is
+ * unchanged), keep the fastest, and return it in config_out[3] =
+ * {threads, blocks_per_sm, lanes} and its time per step in *best_ms (either
+ * may be NULL).  Synchronises the batch's stream. */
+int vlbm_batch_autotune(vlbm_batch* b, int32_t repeats, int32_t* config_out, double* best_ms);
+
+/* Total nodes, steps taken and kernel launches issued; any pointer may be NULL. */
+int vlbm_batch_info(const vlbm_batch* b, int64_t* nodes_total, int64_t* step, int64_t* launches);
+const char* vlbm_batch_last_error(const vlbm_batch* b);
+
 /* Static text of a status code; message of the last failure of h. */
 const char* vlbm_strerror(int code);
 const char* vlbm_last_error(const vlbm_handle* h);

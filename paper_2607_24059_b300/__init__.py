@@ -15,7 +15,7 @@ from . import _binding
 from ._binding import *  # noqa: F401,F403  (the C ABI, same names)
 from ._binding import VlbmError, PRECISIONS
 
-__all__ = list(_binding.EXPORTED) + ["Lattice", "VlbmError", "PRECISIONS"]
+__all__ = list(_binding.EXPORTED) + ["Lattice", "Batch", "VlbmError", "PRECISIONS"]
 
 
 class Lattice:
@@ -111,3 +111,65 @@ class Lattice:
 
     def launch_count(self):
         return _binding.vlbm_launch_count(self.handle)
+
+
+class Batch:
+    """Many independent periodic 2D problems advanced together (a vlbm_batch).
+
+    problems: sequence of dicts with keys n=(nx, ny), dx, nu and optionally
+    mu, omega_rho, alpha_rho, omega_q, alpha_q, gamma, rho_bar.
+    """
+
+    def __init__(self, problems, precision="fp16split", stream=None):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        plist = []
+        for q in problems:
+            n = tuple(int(v) for v in q["n"])
+            p = _binding.vlbm_params_default(2, n, q["dx"], q["nu"], prec)
+            p.mu = q.get("mu", 8.0)
+            p.omega[0] = q.get("omega_rho", 1.2)
+            p.alpha[0] = q.get("alpha_rho", 0.075)
+            for k in range(1, 4):
+                p.omega[k] = q.get("omega_q", 1.15)
+                p.alpha[k] = q.get("alpha_q", -1.0) if q.get("alpha_q") is not None else -1.0
+            p.gamma = q.get("gamma", 1.0)
+            p.rho_bar = q.get("rho_bar", 1.0)
+            plist.append(p)
+        self.params = plist
+        self.shapes = [tuple(reversed(tuple(int(v) for v in q["n"]))) for q in problems]
+        self.handle = _binding.vlbm_batch_create(plist, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _binding.vlbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, problem, u, phi=None):
+        _binding.vlbm_batch_init(self.handle, problem, u, phi)
+
+    def step(self, nsteps=1, graph=True):
+        _binding.vlbm_batch_step(self.handle, nsteps, 0 if graph else _binding.VLBM_STEP_NO_GRAPH)
+
+    def velocity(self, problem, dtype=None, device="cuda"):
+        import torch
+        u = torch.empty((2,) + self.shapes[problem], dtype=dtype or torch.float64, device=device)
+        _binding.vlbm_batch_macros(self.handle, problem, None, u, None)
+        return u
+
+    def invariants(self, problem):
+        return _binding.vlbm_batch_invariants(self.handle, problem)
+
+    def autotune(self, repeats=5):
+        return _binding.vlbm_batch_autotune(self.handle, repeats)
+
+    def set_config(self, threads, blocks_per_sm, lanes=4):
+        _binding.vlbm_batch_set_config(self.handle, threads, blocks_per_sm, lanes)
+
+    def info(self):
+        return _binding.vlbm_batch_info(self.handle)

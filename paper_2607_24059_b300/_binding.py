@@ -60,6 +60,9 @@ EXPORTED = [
     "vlbm_init", "vlbm_step", "vlbm_step_record", "vlbm_macros", "vlbm_invariants", "vlbm_time", "vlbm_state_bytes",
     "vlbm_get_state", "vlbm_set_state", "vlbm_get_populations", "vlbm_launch_count", "vlbm_set_option",
     "vlbm_strerror", "vlbm_last_error", "vlbm_invariants_noalloc",
+    "vlbm_batch_create", "vlbm_batch_destroy", "vlbm_batch_init", "vlbm_batch_step", "vlbm_batch_macros",
+    "vlbm_batch_invariants", "vlbm_batch_set_config", "vlbm_batch_autotune", "vlbm_batch_info",
+    "vlbm_batch_last_error",
 ]
 
 
@@ -107,6 +110,19 @@ lib.vlbm_get_populations.argtypes = [_H, _V, ctypes.c_int32, ctypes.c_int32]
 lib.vlbm_launch_count.argtypes = [_H, ctypes.POINTER(ctypes.c_int64)]
 lib.vlbm_set_option.argtypes = [_H, ctypes.c_int32, ctypes.c_int64]
 lib.vlbm_invariants_noalloc.argtypes = [_P, _V, _V, _V]
+lib.vlbm_batch_create.argtypes = [_P, ctypes.c_int32, _V, ctypes.POINTER(_H)]
+lib.vlbm_batch_destroy.argtypes = [_H]
+lib.vlbm_batch_destroy.restype = None
+lib.vlbm_batch_init.argtypes = [_H, ctypes.c_int32, _V, _V, ctypes.c_int32]
+lib.vlbm_batch_step.argtypes = [_H, ctypes.c_int64, ctypes.c_int32]
+lib.vlbm_batch_macros.argtypes = [_H, ctypes.c_int32, _V, _V, _V, ctypes.c_int32]
+lib.vlbm_batch_invariants.argtypes = [_H, ctypes.c_int32, _V]
+lib.vlbm_batch_set_config.argtypes = [_H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+lib.vlbm_batch_autotune.argtypes = [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
+lib.vlbm_batch_info.argtypes = [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                ctypes.POINTER(ctypes.c_int64)]
+lib.vlbm_batch_last_error.argtypes = [_H]
+lib.vlbm_batch_last_error.restype = ctypes.c_char_p
 lib.vlbm_strerror.argtypes = [ctypes.c_int]
 lib.vlbm_strerror.restype = ctypes.c_char_p
 lib.vlbm_last_error.argtypes = [_H]
@@ -294,6 +310,74 @@ def vlbm_invariants_noalloc(p: vlbm_params, lattice, out, stream=None) -> None:
         raise TypeError("invariants are float64")
     s = current_stream() if stream is None else stream
     _check(lib.vlbm_invariants_noalloc(ctypes.byref(p), _V(lp), _V(op), _V(s)), "vlbm_invariants_noalloc")
+
+
+# ---- batched problems
+def _bcheck(code, where, b):
+    if code < 0:
+        raise VlbmError(code, where, lib.vlbm_batch_last_error(b).decode() if b else "")
+    return code
+
+
+def vlbm_batch_create(problems, stream=None):
+    """problems: sequence of vlbm_params (dim 2, one precision)."""
+    arr = (vlbm_params * len(problems))(*problems)
+    b = _H()
+    s = current_stream() if stream is None else stream
+    _bcheck(lib.vlbm_batch_create(arr, len(problems), _V(s), ctypes.byref(b)), "vlbm_batch_create", None)
+    return b
+
+
+def vlbm_batch_destroy(b) -> None:
+    lib.vlbm_batch_destroy(b)
+
+
+def vlbm_batch_init(b, problem: int, u, phi=None) -> None:
+    up, dt = _ptr_dtype(u)
+    pp, _ = _ptr_dtype(phi)
+    _bcheck(lib.vlbm_batch_init(b, int(problem), _V(up), _V(pp), dt), "vlbm_batch_init", b)
+
+
+def vlbm_batch_step(b, nsteps: int, flags: int = 0) -> None:
+    _bcheck(lib.vlbm_batch_step(b, int(nsteps), int(flags)), "vlbm_batch_step", b)
+
+
+def vlbm_batch_macros(b, problem: int, rho=None, u=None, phi=None) -> None:
+    dts = {d for d in (_ptr_dtype(a)[1] for a in (rho, u, phi)) if d is not None}
+    if len(dts) != 1:
+        raise TypeError("give at least one output, all of one dtype")
+    _bcheck(lib.vlbm_batch_macros(b, int(problem), _V(_ptr_dtype(rho)[0]), _V(_ptr_dtype(u)[0]),
+                                  _V(_ptr_dtype(phi)[0]), dts.pop()), "vlbm_batch_macros", b)
+
+
+def vlbm_batch_invariants(b, problem: int, out=None):
+    if out is None:
+        out = np.zeros(VLBM_NUM_INVARIANTS, dtype=np.float64)
+    p, _ = _ptr_dtype(out)
+    _bcheck(lib.vlbm_batch_invariants(b, int(problem), _V(p)), "vlbm_batch_invariants", b)
+    return out
+
+
+def vlbm_batch_set_config(b, threads: int, blocks_per_sm: int, lanes: int = 4) -> None:
+    _bcheck(lib.vlbm_batch_set_config(b, threads, blocks_per_sm, lanes), "vlbm_batch_set_config", b)
+
+
+def vlbm_batch_autotune(b, repeats: int = 5):
+    """Returns ((threads, blocks_per_sm, lanes), ms_per_step)."""
+    cfg = (ctypes.c_int32 * 3)()
+    ms = ctypes.c_double()
+    _bcheck(lib.vlbm_batch_autotune(b, int(repeats), cfg, ctypes.byref(ms)), "vlbm_batch_autotune", b)
+    return tuple(cfg), ms.value
+
+
+def vlbm_batch_info(b):
+    n, s, l = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _bcheck(lib.vlbm_batch_info(b, ctypes.byref(n), ctypes.byref(s), ctypes.byref(l)), "vlbm_batch_info", b)
+    return n.value, s.value, l.value
+
+
+def vlbm_batch_last_error(b) -> str:
+    return lib.vlbm_batch_last_error(b).decode()
 
 
 def vlbm_strerror(code: int) -> str:

@@ -17,6 +17,7 @@
 #include "vlbm_kernels_2d.cuh"
 #include "vlbm_kernels_3d.cuh"
 #include "vlbm_split.cuh"
+#include "vlbm_host.hpp"
 
 using namespace vlbm;
 
@@ -107,43 +108,6 @@ bool is_device_pointer(const void* ptr) {
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-// Bytes of a moving population (all populations, except in the mixed layouts
-// whose rest populations are FP32).
-int elem_bytes(int precision) {
-    switch (precision) {
-        case VLBM_FP64: return 8;
-        case VLBM_FP32: return 4;
-        case VLBM_FP16_SHIFTED:
-        case VLBM_BF16_SHIFTED:
-        case VLBM_FP16_SPLIT:
-        case VLBM_BF16_SPLIT: return 2;
-        default: return 0;
-    }
-}
-
-bool is_split(int precision) { return precision == VLBM_FP16_SPLIT || precision == VLBM_BF16_SPLIT; }
-
-template <class C>
-Coef<C> make_coef(const vlbm_params& p, const vlbm_derived& d, const double* scale) {
-    Coef<C> k{};
-    const int F = p.dim + 1;
-    for (int f = 0; f < kMaxFields; ++f) {
-        const double om = f < F ? p.omega[f] : 1.0;
-        const double al = f < F ? d.alpha[f] : 0.0;
-        k.om[f] = (C)om;
-        k.al[f] = (C)al;
-        k.rest[f] = (C)(1.0 - 2.0 * p.dim * al);
-        k.scale[f] = (C)scale[f];
-        k.inv_scale[f] = (C)(1.0 / scale[f]);
-    }
-    k.i2m = (C)(1.0 / (2.0 * p.mu));
-    k.rho_bar = (C)p.rho_bar;
-    k.p_bar = (C)std::pow(p.rho_bar, p.gamma);
-    k.gamma = (C)p.gamma;
-    k.gamma_one = p.gamma == 1.0;
-    return k;
 }
 
 }  // namespace
@@ -250,7 +214,6 @@ static void free_all(vlbm_handle* h) {
     if (h->hist) cudaFree(h->hist);
 }
 
-void vlbm_storage_scales(const vlbm_params& p, double* scale);
 static void storage_scales(const vlbm_params& p, const vlbm_derived& d, double* scale) {
     (void)d;
     vlbm_storage_scales(p, scale);
@@ -321,19 +284,6 @@ extern "C" int vlbm_set_stream(vlbm_handle* h, void* stream) {
     if (!h) return VLBM_EINVAL;
     h->stream = (cudaStream_t)stream;
     return VLBM_OK;
-}
-
-// Storage scales of the shifted half formats: the stored value is g * scale_k,
-// chosen so that the deviations of each field sit near unit magnitude.  The rho
-// field deviates by O(dx^2 phi) (Prop. 1); a momentum field by O(dx |q|).
-// (library-internal; hidden from the exported symbol table)
-__attribute__((visibility("hidden"))) void vlbm_storage_scales(const vlbm_params& p, double* scale) {
-    for (int k = 0; k < 4; ++k) scale[k] = 1.0;
-    if (elem_bytes(p.precision) != 2) return;
-    scale[0] = 1.0 / (p.dx * p.dx);
-    // shifted populations of a momentum field are O(dx |q|); the split layout's
-    // non-equilibrium parts are O(dx^2) in every field
-    for (int k = 1; k < 4; ++k) scale[k] = is_split(p.precision) ? 1.0 / (p.dx * p.dx) : 1.0 / p.dx;
 }
 
 // ------------------------------------------------------------------ staging

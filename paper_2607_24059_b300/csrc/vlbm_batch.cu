@@ -1,0 +1,550 @@
+// Batched execution: many independent periodic 2D problems (each with its own
+// size, dx, viscosity and time step dx^2/mu) advanced together, one persistent
+// launch per time step over a work list of (problem, row, row segment) items,
+// the launches of a run replayed from a captured CUDA graph.
+//
+// Every problem keeps the storage of a single handle (same kernels, same
+// arithmetic: the per-warp step bodies of vlbm_kernels_2d.cuh / vlbm_split.cuh),
+// at its own offset in one allocation per time level.  A step of the batch is a
+// step of every problem; kernel boundaries order the steps, so no kernel waits
+// on another.  Work items are numbered problem by problem, row by row, and
+// every warp of the grid takes an equal contiguous range of them.  The launch shape (threads per block, blocks per SM, nodes per
+// lane of the split kernels) is chosen by vlbm_batch_autotune, which times each
+// candidate on dry-run steps that read the current level and write the other
+// one without committing it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vlbm.h"
+#include "vlbm_host.hpp"
+#include "vlbm_split.cuh"
+
+using namespace vlbm;
+
+namespace {
+
+constexpr int kBatchGraphSteps = 32;   // steps per captured graph (even)
+constexpr int kMaxBatchThreads = 256;
+
+// One problem as the step kernel sees it.
+template <class C>
+struct BatchProblem {
+    long long offset;        // bytes from the level base
+    long long plane;         // nodes
+    long long item0;         // first work item of this problem
+    int nx, ny, wpr;         // sizes, warps (row segments) per row
+    int pad;
+    Coef<C> k;
+};
+
+// Problem owning work item `item`: last p with item0[p] <= item (binary search).
+template <class C>
+__device__ __forceinline__ int find_problem(const BatchProblem<C>* __restrict__ probs, int count, long long item) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (probs[mid].item0 <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One time step of every problem.  Warp w takes the contiguous item range
+// [w per, (w + 1) per): one search for its first problem, then the problem
+// index only moves forward.
+template <class S, bool SPLIT, int V>
+__global__ void __launch_bounds__(kMaxBatchThreads)
+k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
+                const BatchProblem<typename Storage<S>::C>* __restrict__ probs, int count, long long items) {
+    using C = typename Storage<S>::C;
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long per = (items + nwarps - 1) / nwarps;
+    const long long begin = warp * per;
+    const long long end = begin + per < items ? begin + per : items;
+    Acc<C> unused;
+    int p = begin < items ? find_problem(probs, count, begin) : 0;
+    for (long long item = begin; item < end; ++item) {   // warp-uniform
+        while (p + 1 < count && probs[p + 1].item0 <= item) ++p;
+        const BatchProblem<C>& P = probs[p];
+        const long long local = item - P.item0;
+        const int y = (int)(local / P.wpr), seg = (int)(local % P.wpr);
+        const Layout<S, SPLIT, 5> fin{const_cast<char*>(in_base) + P.offset, P.plane};
+        const Layout<S, SPLIT, 5> fout{out_base + P.offset, P.plane};
+        const Coef<C>& k = P.k;   // read through L1, not copied into registers
+        if constexpr (SPLIT)
+            warp_split_step_2d<S, V, false>(fin, fout, P.nx, P.ny, y, seg, lane, k, unused);
+        else
+            warp_stream_collide_2d<S, false, false>(fin, fout, P.nx, P.ny, y, seg, lane, k, unused);
+    }
+}
+
+}  // namespace
+
+struct vlbm_batch {
+    std::vector<vlbm_params> p;
+    std::vector<vlbm_derived> d;
+    std::vector<long long> offset;
+    int precision = VLBM_FP32;
+    int count = 0;
+    int sm_count = 148;
+    cudaStream_t stream = nullptr;
+    char* level[2] = {nullptr, nullptr};
+    size_t level_bytes = 0;
+    int cur = 0;
+    void* table = nullptr;          // BatchProblem<C>[count] on the device
+    long long items = 0;
+    int threads = 256, blocks_per_sm = 4, lanes = 4;
+    double* partials = nullptr;
+    int partial_blocks = 0;
+    double* inv_dev = nullptr;
+    double* inv_host = nullptr;
+    void* staging = nullptr;
+    size_t staging_bytes = 0;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t step = 0, launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int bfail(vlbm_batch* b, int code, const char* what, cudaError_t e) {
+    if (b) b->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return code;
+}
+
+#define VLBM_BCUDA(b, call)                                                                              \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) return bfail((b), e_ == cudaErrorMemoryAllocation ? VLBM_ENOMEM : VLBM_ECUDA, \
+                                            #call, e_);                                                  \
+    } while (0)
+
+// Nodes per lane of the step kernel for the batch's precision and config.
+int batch_lanes(const vlbm_batch* b) {
+    if (is_split(b->precision)) return b->lanes;
+    switch (b->precision) {
+        case VLBM_FP64: return Vec16<double>::V;
+        case VLBM_FP32: return Vec16<float>::V;
+        default: return Vec16<__half>::V;
+    }
+}
+
+template <class C>
+int upload_table(vlbm_batch* b) {
+    const int V = batch_lanes(b);
+    std::vector<BatchProblem<C>> t(b->count);
+    long long item = 0;
+    for (int i = 0; i < b->count; ++i) {
+        double scale[4];
+        vlbm_storage_scales(b->p[i], scale);
+        t[i].offset = b->offset[i];
+        t[i].plane = b->d[i].nodes;
+        t[i].nx = (int)b->p[i].n[0];
+        t[i].ny = (int)b->p[i].n[1];
+        t[i].wpr = (int)((b->p[i].n[0] / V + 31) / 32);
+        t[i].pad = 0;
+        t[i].item0 = item;
+        t[i].k = make_coef<C>(b->p[i], b->d[i], scale);
+        item += (long long)t[i].ny * t[i].wpr;
+    }
+    b->items = item;
+    if (!b->table) VLBM_BCUDA(b, cudaMalloc(&b->table, sizeof(BatchProblem<C>) * b->count));
+    VLBM_BCUDA(b, cudaMemcpyAsync(b->table, t.data(), sizeof(BatchProblem<C>) * b->count, cudaMemcpyHostToDevice,
+                                  b->stream));
+    VLBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+    return VLBM_OK;
+}
+
+int rebuild_table(vlbm_batch* b) {
+    return b->precision == VLBM_FP64 ? upload_table<double>(b) : upload_table<float>(b);
+}
+
+void drop_graphs(vlbm_batch* b) {
+    for (int i = 0; i < 2; ++i)
+        if (b->graph[i]) {
+            cudaGraphExecDestroy(b->graph[i]);
+            b->graph[i] = nullptr;
+        }
+}
+
+template <class S, bool SPLIT, int V>
+void launch_batch(vlbm_batch* b, cudaStream_t s, int src) {
+    using C = typename Storage<S>::C;
+    k_batch_step_2d<S, SPLIT, V><<<b->sm_count * b->blocks_per_sm, b->threads, 0, s>>>(
+        b->level[src], b->level[src ^ 1], (const BatchProblem<C>*)b->table, b->count, b->items);
+}
+
+void launch_batch_step(vlbm_batch* b, cudaStream_t s, int src) {
+    switch (b->precision) {
+        case VLBM_FP64: launch_batch<double, false, Vec16<double>::V>(b, s, src); break;
+        case VLBM_FP32: launch_batch<float, false, Vec16<float>::V>(b, s, src); break;
+        case VLBM_FP16_SHIFTED: launch_batch<__half, false, Vec16<__half>::V>(b, s, src); break;
+        case VLBM_BF16_SHIFTED: launch_batch<__nv_bfloat16, false, Vec16<__nv_bfloat16>::V>(b, s, src); break;
+        case VLBM_FP16_SPLIT:
+            if (b->lanes == 2) launch_batch<__half, true, 2>(b, s, src);
+            else launch_batch<__half, true, 4>(b, s, src);
+            break;
+        default:
+            if (b->lanes == 2) launch_batch<__nv_bfloat16, true, 2>(b, s, src);
+            else launch_batch<__nv_bfloat16, true, 4>(b, s, src);
+            break;
+    }
+}
+
+bool device_pointer(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int ensure_bstaging(vlbm_batch* b, size_t bytes) {
+    if (b->staging_bytes >= bytes) return VLBM_OK;
+    if (b->staging) {
+        cudaStreamSynchronize(b->stream);
+        cudaFree(b->staging);
+        b->staging = nullptr;
+        b->staging_bytes = 0;
+    }
+    VLBM_BCUDA(b, cudaMalloc(&b->staging, bytes));
+    b->staging_bytes = bytes;
+    return VLBM_OK;
+}
+
+void free_batch(vlbm_batch* b) {
+    drop_graphs(b);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    for (int i = 0; i < 2; ++i)
+        if (b->level[i]) cudaFree(b->level[i]);
+    if (b->table) cudaFree(b->table);
+    if (b->partials) cudaFree(b->partials);
+    if (b->inv_dev) cudaFree(b->inv_dev);
+    if (b->inv_host) cudaFreeHost(b->inv_host);
+    if (b->staging) cudaFree(b->staging);
+}
+
+// Per-problem kernels reuse the single-lattice ones on the problem's slice.
+template <class S, bool SPLIT, class T>
+void launch_problem_init(vlbm_batch* b, int i, const T* u, const T* phi) {
+    using C = typename Storage<S>::C;
+    double scale[4];
+    vlbm_storage_scales(b->p[i], scale);
+    const Coef<C> k = make_coef<C>(b->p[i], b->d[i], scale);
+    const long long N = b->d[i].nodes;
+    k_init_2d<S, SPLIT, T><<<(N + kThreads - 1) / kThreads, kThreads, 0, b->stream>>>(
+        b->level[b->cur] + b->offset[i], N, u, phi, k, b->p[i].dx, b->p[i].gamma, b->p[i].rho_bar,
+        std::pow(b->p[i].rho_bar, b->p[i].gamma));
+}
+
+template <class S, bool SPLIT, class T>
+void launch_problem_macros(vlbm_batch* b, int i, T* rho, T* u, T* phi) {
+    using C = typename Storage<S>::C;
+    double scale[4];
+    vlbm_storage_scales(b->p[i], scale);
+    const Coef<C> k = make_coef<C>(b->p[i], b->d[i], scale);
+    const long long N = b->d[i].nodes;
+    k_macros_2d<S, SPLIT, T><<<(N + kThreads - 1) / kThreads, kThreads, 0, b->stream>>>(
+        b->level[b->cur] + b->offset[i], N, rho, u, phi, k, b->p[i].dx, b->p[i].gamma, b->p[i].rho_bar,
+        std::pow(b->p[i].rho_bar, b->p[i].gamma));
+}
+
+template <class S, bool SPLIT>
+void launch_problem_invariants(vlbm_batch* b, int i) {
+    using C = typename Storage<S>::C;
+    double scale[4];
+    vlbm_storage_scales(b->p[i], scale);
+    const Coef<C> k = make_coef<C>(b->p[i], b->d[i], scale);
+    k_invariants_2d<S, SPLIT><<<b->partial_blocks, kThreads, 0, b->stream>>>(b->level[b->cur] + b->offset[i],
+                                                                             b->d[i].nodes, k, b->partials);
+    k_invariants_final<<<1, 1024, 0, b->stream>>>(b->partials, b->partial_blocks, b->inv_dev, (double)b->d[i].nodes,
+                                                   b->p[i].rho_bar, 1.0 / b->p[i].dx, 1.0);
+}
+
+#define VLBM_BATCH_DISPATCH(b, FN, ...)                                            \
+    switch ((b)->precision) {                                                      \
+        case VLBM_FP64: FN<double, false>(__VA_ARGS__); break;                     \
+        case VLBM_FP32: FN<float, false>(__VA_ARGS__); break;                      \
+        case VLBM_FP16_SHIFTED: FN<__half, false>(__VA_ARGS__); break;             \
+        case VLBM_BF16_SHIFTED: FN<__nv_bfloat16, false>(__VA_ARGS__); break;      \
+        case VLBM_FP16_SPLIT: FN<__half, true>(__VA_ARGS__); break;                \
+        default: FN<__nv_bfloat16, true>(__VA_ARGS__); break;                      \
+    }
+
+template <class S, bool SPLIT>
+void init_any(vlbm_batch* b, int i, const void* u, const void* phi, int dtype) {
+    if (dtype == VLBM_DTYPE_F64) launch_problem_init<S, SPLIT, double>(b, i, (const double*)u, (const double*)phi);
+    else launch_problem_init<S, SPLIT, float>(b, i, (const float*)u, (const float*)phi);
+}
+
+template <class S, bool SPLIT>
+void macros_any(vlbm_batch* b, int i, void* rho, void* u, void* phi, int dtype) {
+    if (dtype == VLBM_DTYPE_F64) launch_problem_macros<S, SPLIT, double>(b, i, (double*)rho, (double*)u, (double*)phi);
+    else launch_problem_macros<S, SPLIT, float>(b, i, (float*)rho, (float*)u, (float*)phi);
+}
+
+int build_batch_graph(vlbm_batch* b, int src) {
+    if (!b->capture_stream) VLBM_BCUDA(b, cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking));
+    VLBM_BCUDA(b, cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal));
+    int l = src;
+    for (int i = 0; i < kBatchGraphSteps; ++i) {
+        launch_batch_step(b, b->capture_stream, l);
+        l ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    VLBM_BCUDA(b, cudaStreamEndCapture(b->capture_stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&b->graph[src], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph[src] = nullptr;
+        return bfail(b, VLBM_ECUDA, "graph instantiate", e);
+    }
+    return VLBM_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" int vlbm_batch_create(const vlbm_params* problems, int32_t count, void* stream, vlbm_batch** out) {
+    if (!out || !problems || count < 1) return VLBM_EINVAL;
+    *out = nullptr;
+    const int prec = problems[0].precision;
+    std::vector<vlbm_derived> d(count);
+    for (int i = 0; i < count; ++i) {
+        const vlbm_params& q = problems[i];
+        if (q.dim != 2 || q.precision != prec || q.n[0] % 4 != 0) return VLBM_EINVAL;
+        if (q.n[0] > (1 << 24) || q.n[1] > (1 << 24)) return VLBM_EINVAL;
+        if (vlbm_params_check(&q, &d[i]) < 0) return VLBM_EINVAL;
+    }
+    vlbm_batch* b = new (std::nothrow) vlbm_batch();
+    if (!b) return VLBM_ENOMEM;
+    b->p.assign(problems, problems + count);
+    b->d = d;
+    b->precision = prec;
+    b->count = count;
+    b->stream = (cudaStream_t)stream;
+    size_t off = 0, largest = 0;
+    for (int i = 0; i < count; ++i) {
+        b->offset.push_back((long long)off);
+        off += (d[i].lattice_bytes + 255) & ~(size_t)255;
+        largest = std::max(largest, (size_t)d[i].nodes);
+    }
+    b->level_bytes = off;
+    int dev = 0;
+    int st = VLBM_OK;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        st = VLBM_ECUDA;
+    for (int i = 0; i < 2 && st == VLBM_OK; ++i)
+        if (cudaMalloc((void**)&b->level[i], off) != cudaSuccess) st = VLBM_ENOMEM;
+    b->partial_blocks = (int)std::min<long long>(((long long)largest + kThreads - 1) / kThreads, b->sm_count * 8LL);
+    if (st == VLBM_OK &&
+        (cudaMalloc(&b->partials, (size_t)b->partial_blocks * 8 * sizeof(double)) != cudaSuccess ||
+         cudaMalloc(&b->inv_dev, 8 * sizeof(double)) != cudaSuccess ||
+         cudaMallocHost(&b->inv_host, 8 * sizeof(double)) != cudaSuccess))
+        st = VLBM_ENOMEM;
+    if (st == VLBM_OK && cudaMemsetAsync(b->level[0], 0, off, b->stream) != cudaSuccess) st = VLBM_ECUDA;
+    if (st == VLBM_OK) st = rebuild_table(b);
+    if (st != VLBM_OK) {
+        cudaGetLastError();
+        free_batch(b);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return VLBM_OK;
+}
+
+extern "C" void vlbm_batch_destroy(vlbm_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    delete b;
+}
+
+extern "C" int vlbm_batch_init(vlbm_batch* b, int32_t problem, const void* u, const void* phi, int32_t dtype) {
+    if (!b || !u || problem < 0 || problem >= b->count || (dtype != VLBM_DTYPE_F32 && dtype != VLBM_DTYPE_F64))
+        return VLBM_EINVAL;
+    const size_t es = dtype == VLBM_DTYPE_F64 ? 8 : 4;
+    const long long N = b->d[problem].nodes;
+    const size_t ub = 2 * N * es, pb = phi ? N * es : 0;
+    const void* ud = u;
+    const void* pd = phi;
+    const bool host = !device_pointer(u) || (phi && !device_pointer(phi));
+    if (host) {
+        int rc = ensure_bstaging(b, ub + pb);
+        if (rc) return rc;
+        VLBM_BCUDA(b, cudaMemcpyAsync(b->staging, u, ub, cudaMemcpyDefault, b->stream));
+        ud = b->staging;
+        if (phi) {
+            VLBM_BCUDA(b, cudaMemcpyAsync((char*)b->staging + ub, phi, pb, cudaMemcpyDefault, b->stream));
+            pd = (char*)b->staging + ub;
+        }
+    }
+    VLBM_BATCH_DISPATCH(b, init_any, b, problem, ud, pd, dtype);
+    VLBM_BCUDA(b, cudaGetLastError());
+    b->launches++;
+    if (host) VLBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_batch_step(vlbm_batch* b, int64_t nsteps, int32_t flags) {
+    if (!b || nsteps < 0) return VLBM_EINVAL;
+    const bool graphs = !(flags & VLBM_STEP_NO_GRAPH);
+    int64_t left = nsteps;
+    while (left > 0) {
+        if (graphs && left >= kBatchGraphSteps) {
+            if (!b->graph[b->cur]) {
+                int rc = build_batch_graph(b, b->cur);
+                if (rc) return rc;
+            }
+            VLBM_BCUDA(b, cudaGraphLaunch(b->graph[b->cur], b->stream));
+            b->launches += kBatchGraphSteps;
+            b->step += kBatchGraphSteps;
+            left -= kBatchGraphSteps;
+        } else {
+            launch_batch_step(b, b->stream, b->cur);
+            VLBM_BCUDA(b, cudaGetLastError());
+            b->launches++;
+            b->cur ^= 1;
+            b->step++;
+            left--;
+        }
+    }
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_batch_macros(vlbm_batch* b, int32_t problem, void* rho, void* u, void* phi, int32_t dtype) {
+    if (!b || problem < 0 || problem >= b->count || (dtype != VLBM_DTYPE_F32 && dtype != VLBM_DTYPE_F64))
+        return VLBM_EINVAL;
+    if (!rho && !u && !phi) return VLBM_OK;
+    const size_t es = dtype == VLBM_DTYPE_F64 ? 8 : 4;
+    const long long N = b->d[problem].nodes;
+    void* out[3] = {rho, u, phi};
+    const size_t bytes[3] = {N * es, 2 * N * es, N * es};
+    void* dev[3] = {rho, u, phi};
+    bool host[3] = {false, false, false};
+    size_t off = 0, offs[3] = {0, 0, 0};
+    for (int i = 0; i < 3; ++i)
+        if (out[i] && !device_pointer(out[i])) {
+            host[i] = true;
+            offs[i] = off;
+            off += bytes[i];
+        }
+    if (off) {
+        int rc = ensure_bstaging(b, off);
+        if (rc) return rc;
+        for (int i = 0; i < 3; ++i)
+            if (host[i]) dev[i] = (char*)b->staging + offs[i];
+    }
+    VLBM_BATCH_DISPATCH(b, macros_any, b, problem, dev[0], dev[1], dev[2], dtype);
+    VLBM_BCUDA(b, cudaGetLastError());
+    b->launches++;
+    if (off) {
+        for (int i = 0; i < 3; ++i)
+            if (host[i]) VLBM_BCUDA(b, cudaMemcpyAsync(out[i], dev[i], bytes[i], cudaMemcpyDeviceToHost, b->stream));
+        VLBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+    }
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_batch_invariants(vlbm_batch* b, int32_t problem, double* out) {
+    if (!b || !out || problem < 0 || problem >= b->count) return VLBM_EINVAL;
+    VLBM_BATCH_DISPATCH(b, launch_problem_invariants, b, problem);
+    VLBM_BCUDA(b, cudaGetLastError());
+    b->launches += 2;
+    if (device_pointer(out)) {
+        VLBM_BCUDA(b, cudaMemcpyAsync(out, b->inv_dev, 8 * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
+        return VLBM_OK;
+    }
+    VLBM_BCUDA(b, cudaMemcpyAsync(b->inv_host, b->inv_dev, 8 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    VLBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+    std::memcpy(out, b->inv_host, 8 * sizeof(double));
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_batch_set_config(vlbm_batch* b, int32_t threads, int32_t blocks_per_sm, int32_t lanes) {
+    if (!b || (threads != 128 && threads != 256) || blocks_per_sm < 1 || blocks_per_sm > 16) return VLBM_EINVAL;
+    if (is_split(b->precision) && lanes != 2 && lanes != 4) return VLBM_EINVAL;
+    const bool relayout = is_split(b->precision) && lanes != b->lanes;
+    b->threads = threads;
+    b->blocks_per_sm = blocks_per_sm;
+    if (is_split(b->precision)) b->lanes = lanes;
+    drop_graphs(b);
+    return relayout ? rebuild_table(b) : VLBM_OK;
+}
+
+extern "C" int vlbm_batch_autotune(vlbm_batch* b, int32_t repeats, int32_t* config_out, double* best_ms) {
+    if (!b || repeats < 1) return VLBM_EINVAL;
+    const int thread_opts[2] = {128, 256};
+    const int bps_opts[5] = {1, 2, 4, 8, 16};
+    const int lane_opts[2] = {2, 4};
+    const int nl = is_split(b->precision) ? 2 : 1;
+    cudaEvent_t e0, e1;
+    VLBM_BCUDA(b, cudaEventCreate(&e0));
+    VLBM_BCUDA(b, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bt = b->threads, bb = b->blocks_per_sm, bl = b->lanes;
+    int rc = VLBM_OK;
+    for (int li = 0; li < nl && rc == VLBM_OK; ++li)
+        for (int ti = 0; ti < 2 && rc == VLBM_OK; ++ti)
+            for (int bi = 0; bi < 5 && rc == VLBM_OK; ++bi) {
+                rc = vlbm_batch_set_config(b, thread_opts[ti], bps_opts[bi], nl > 1 ? lane_opts[li] : b->lanes);
+                if (rc) break;
+                // dry runs: read the current level, write the other, do not commit
+                launch_batch_step(b, b->stream, b->cur);
+                cudaEventRecord(e0, b->stream);
+                for (int r = 0; r < repeats; ++r) launch_batch_step(b, b->stream, b->cur);
+                cudaEventRecord(e1, b->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+                    rc = VLBM_ECUDA;
+                    break;
+                }
+                b->launches += repeats + 1;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= repeats;
+                if (ms < best) {
+                    best = ms;
+                    bt = b->threads;
+                    bb = b->blocks_per_sm;
+                    bl = b->lanes;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    rc = vlbm_batch_set_config(b, bt, bb, bl);
+    if (rc) return rc;
+    if (config_out) {
+        config_out[0] = bt;
+        config_out[1] = bb;
+        config_out[2] = bl;
+    }
+    if (best_ms) *best_ms = best;
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_batch_info(const vlbm_batch* b, int64_t* nodes_total, int64_t* step, int64_t* launches) {
+    if (!b) return VLBM_EINVAL;
+    if (nodes_total) {
+        int64_t n = 0;
+        for (const auto& d : b->d) n += d.nodes;
+        *nodes_total = n;
+    }
+    if (step) *step = b->step;
+    if (launches) *launches = b->launches;
+    return VLBM_OK;
+}
+
+extern "C" const char* vlbm_batch_last_error(const vlbm_batch* b) { return b ? b->err.c_str() : "null batch"; }

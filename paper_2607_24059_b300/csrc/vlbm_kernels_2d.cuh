@@ -47,22 +47,20 @@ __device__ __forceinline__ void load_or_zero(T (&w)[V], const T* p, bool active)
 // y - 1 / y + 1 (periodic), loaded aligned.
 // DIAG: also reduce the invariants of the transported state (time t + dt)
 // into per-block FP64 partials, at no extra HBM traffic.
+// One warp's share of a step: V * 32 consecutive nodes of row y starting at
+// segment seg.  Called with every lane of the warp (shuffles); lanes past the
+// row end load nothing and store nothing.
 template <class S, bool SPLIT, bool DIAG>
-__global__ void __launch_bounds__(kThreads)
-k_stream_collide_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
-                        int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+__device__ __forceinline__ void warp_stream_collide_2d(const Layout<S, SPLIT, 5>& fin, const Layout<S, SPLIT, 5>& fout,
+                                                       int nx, int ny, int y, int seg, int lane,
+                                                       const Coef<typename Storage<S>::C>& k,
+                                                       Acc<typename Storage<S>::C>& acc) {
     using C = typename Storage<S>::C;
     using L = Layout<S, SPLIT, 5>;
     using R = typename L::R;
     constexpr int V = Vec16<S>::V;
-    const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
-    const int lane = threadIdx.x & 31;
-    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    Acc<C> acc;
-    if (DIAG) acc.zero();
-    if (gwarp < (long long)ny * warps_per_row) {   // warp-uniform
-        const int y = (int)(gwarp / warps_per_row);
-        const int x0 = ((int)(gwarp % warps_per_row) * 32 + lane) * V;
+    {
+        const int x0 = (seg * 32 + lane) * V;
         const bool active = x0 < nx;
         const long long row = (long long)y * nx;
         const long long row_m = (long long)(y == 0 ? ny - 1 : y - 1) * nx;
@@ -149,6 +147,22 @@ k_stream_collide_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
             }
         }
     }
+}
+
+template <class S, bool SPLIT, bool DIAG>
+__global__ void __launch_bounds__(kThreads)
+k_stream_collide_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
+                        int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+    using C = typename Storage<S>::C;
+    using L = Layout<S, SPLIT, 5>;
+    const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
+    const int lane = threadIdx.x & 31;
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    Acc<C> acc;
+    if (DIAG) acc.zero();
+    if (gwarp < (long long)ny * warps_per_row)   // warp-uniform
+        warp_stream_collide_2d<S, SPLIT, DIAG>(fin, fout, nx, ny, (int)(gwarp / warps_per_row),
+                                               (int)(gwarp % warps_per_row), lane, k, acc);
     if (DIAG) block_reduce_store(acc, partials);
 }
 

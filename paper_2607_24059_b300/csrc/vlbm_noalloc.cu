@@ -28,11 +28,10 @@
 
 #include "vlbm.h"
 #include "vlbm_kernels_2d.cuh"
+#include "vlbm_host.hpp"
 #include "vlbm_kernels_3d.cuh"
 
 using namespace vlbm;
-
-void vlbm_storage_scales(const vlbm_params& p, double* scale);
 
 namespace {
 

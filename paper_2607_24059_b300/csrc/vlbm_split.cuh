@@ -116,19 +116,13 @@ __device__ __forceinline__ void pulled_d2q5(const Coef<C>& k, const C (&ms)[3], 
 // pulled rows of non-equilibrium parts, and the warp-edge halo values), then
 // the arithmetic runs: the kernel is limited by how many bytes are in flight.
 template <class S, int V, bool DIAG>
-__global__ void __launch_bounds__(kThreads)
-k_split_step_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
-                    int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+__device__ __forceinline__ void warp_split_step_2d(const Layout<S, true, 5>& fin, const Layout<S, true, 5>& fout,
+                                                   int nx, int ny, int y, int seg, int lane,
+                                                   const Coef<typename Storage<S>::C>& k,
+                                                   Acc<typename Storage<S>::C>& acc) {
     using C = typename Storage<S>::C;
-    using L = Layout<S, true, 5>;
-    const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
-    const int lane = threadIdx.x & 31;
-    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    Acc<C> acc;
-    if (DIAG) acc.zero();
-    if (gwarp < (long long)ny * warps_per_row) {   // warp-uniform
-        const int y = (int)(gwarp / warps_per_row);
-        const int x0 = ((int)(gwarp % warps_per_row) * 32 + lane) * V;
+    {
+        const int x0 = (seg * 32 + lane) * V;
         const bool active = x0 < nx;
         const long long row = (long long)y * nx;
         const long long row_m = (long long)(y == 0 ? ny - 1 : y - 1) * nx;
@@ -264,6 +258,22 @@ k_split_step_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, i
             }
         }
     }
+}
+
+template <class S, int V, bool DIAG>
+__global__ void __launch_bounds__(kThreads)
+k_split_step_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
+                    int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+    using C = typename Storage<S>::C;
+    using L = Layout<S, true, 5>;
+    const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
+    const int lane = threadIdx.x & 31;
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    Acc<C> acc;
+    if (DIAG) acc.zero();
+    if (gwarp < (long long)ny * warps_per_row)   // warp-uniform
+        warp_split_step_2d<S, V, DIAG>(fin, fout, nx, ny, (int)(gwarp / warps_per_row), (int)(gwarp % warps_per_row),
+                                       lane, k, acc);
     if (DIAG) block_reduce_store(acc, partials);
 }
 
