@@ -436,3 +436,34 @@ def test_full_size_4096_sampled_step_and_conservation(orc):
     assert abs(inv1[7] - inv0[7]) <= 1e-5 * n * n * dx * dx
     assert inv1[6] == 0.0
     lat.close()
+
+
+# ------------------------------------------------------------ 3D energy history (fused records)
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-6)])
+def test_d3q7_energy_history_matches_oracle(orc, precision, tol):
+    """Kinetic-energy history of a 3D Taylor-Green vortex reduced inside the step
+    kernel (every 4 steps) against the oracle's invariants after the same steps;
+    the dissipation -dE/dt from centred differences of both histories agrees."""
+    n = 16
+    u, phi, dx = synthetic.taylor_green_3d(n)
+    op = oracle.make_params((n, n, n), dx, nu=1.0 / 1600.0 * 40)
+    lat = gpu_lattice(op, precision)
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    every, nsteps = 4, 48
+    rec = lat.step_record(nsteps, every)
+    lat.close()
+    f = orc.init(op, u, phi)
+    e_orc = []
+    for s in range(nsteps):
+        f = orc.run(op, f, 1)
+        if s % every == 0:
+            e_orc.append(orc.invariants(op, f)[4])
+    e_orc = np.array(e_orc)
+    e_gpu = rec[:, 4]
+    assert np.max(np.abs(e_gpu - e_orc)) <= tol * np.max(e_orc)
+    dt = op.dt * every
+    diss_o = -(e_orc[2:] - e_orc[:-2]) / (2 * dt)
+    diss_g = -(e_gpu[2:] - e_gpu[:-2]) / (2 * dt)
+    assert np.all(diss_o > 0)
+    assert np.max(np.abs(diss_g - diss_o)) <= (1e-9 if precision == "fp64" else 2e-2) * np.max(diss_o)
