@@ -7,8 +7,7 @@
 // arithmetic: the per-warp step bodies of vlbm_kernels_2d.cuh / vlbm_split.cuh),
 // at its own offset in one allocation per time level.  A step of the batch is a
 // step of every problem; kernel boundaries order the steps, so no kernel waits
-// on another.  Work items are numbered problem by problem, row by row, and
-// every warp of the grid takes an equal contiguous range of them.  The launch shape (threads per block, blocks per SM, nodes per
+// on another.  Work items are numbered problem by problem, row by row.  The launch shape (threads per block, blocks per SM, nodes per
 // lane of the split kernels) is chosen by vlbm_batch_autotune, which times each
 // candidate on dry-run steps that read the current level and write the other
 // one without committing it.
@@ -43,35 +42,25 @@ struct BatchProblem {
     Coef<C> k;
 };
 
-// Problem owning work item `item`: last p with item0[p] <= item (binary search).
-template <class C>
-__device__ __forceinline__ int find_problem(const BatchProblem<C>* __restrict__ probs, int count, long long item) {
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (probs[mid].item0 <= item) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
+// One time step of every problem.  Warps take items in the strided order
+// item = warp, warp + nwarps, ...: at any moment the grid works on a contiguous
+// band of rows, so the rows y -+ 1 one warp reads were just read by another and
+// come from L2.  The owning problem comes from the chunk table (problem of item
+// 64 c) and at most a few forward steps.
+constexpr int kChunkShift = 6;
 
-// One time step of every problem.  Warp w takes the contiguous item range
-// [w per, (w + 1) per): one search for its first problem, then the problem
-// index only moves forward.
 template <class S, bool SPLIT, int V>
 __global__ void __launch_bounds__(kMaxBatchThreads)
 k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
-                const BatchProblem<typename Storage<S>::C>* __restrict__ probs, int count, long long items) {
+                const BatchProblem<typename Storage<S>::C>* __restrict__ probs, const int* __restrict__ chunk_problem,
+                int count, long long items) {
     using C = typename Storage<S>::C;
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long per = (items + nwarps - 1) / nwarps;
-    const long long begin = warp * per;
-    const long long end = begin + per < items ? begin + per : items;
     Acc<C> unused;
-    int p = begin < items ? find_problem(probs, count, begin) : 0;
-    for (long long item = begin; item < end; ++item) {   // warp-uniform
+    for (long long item = warp; item < items; item += nwarps) {   // warp-uniform
+        int p = __ldg(chunk_problem + (item >> kChunkShift));
         while (p + 1 < count && probs[p + 1].item0 <= item) ++p;
         const BatchProblem<C>& P = probs[p];
         const long long local = item - P.item0;
@@ -100,6 +89,7 @@ struct vlbm_batch {
     size_t level_bytes = 0;
     int cur = 0;
     void* table = nullptr;          // BatchProblem<C>[count] on the device
+    int* chunks = nullptr;          // problem of item 64 c, c = 0 .. items / 64
     long long items = 0;
     int threads = 256, blocks_per_sm = 4, lanes = 4;
     double* partials = nullptr;
@@ -157,8 +147,22 @@ int upload_table(vlbm_batch* b) {
         item += (long long)t[i].ny * t[i].wpr;
     }
     b->items = item;
+    std::vector<int> chunk((size_t)((item >> kChunkShift) + 1), 0);
+    for (int i = 0, c = 0; c < (int)chunk.size(); ++c) {
+        const long long first = (long long)c << kChunkShift;
+        while (i + 1 < b->count && t[i + 1].item0 <= first) ++i;
+        chunk[c] = i;
+    }
     if (!b->table) VLBM_BCUDA(b, cudaMalloc(&b->table, sizeof(BatchProblem<C>) * b->count));
+    if (b->chunks) {
+        VLBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+        cudaFree(b->chunks);
+        b->chunks = nullptr;
+    }
+    VLBM_BCUDA(b, cudaMalloc(&b->chunks, sizeof(int) * chunk.size()));
     VLBM_BCUDA(b, cudaMemcpyAsync(b->table, t.data(), sizeof(BatchProblem<C>) * b->count, cudaMemcpyHostToDevice,
+                                  b->stream));
+    VLBM_BCUDA(b, cudaMemcpyAsync(b->chunks, chunk.data(), sizeof(int) * chunk.size(), cudaMemcpyHostToDevice,
                                   b->stream));
     VLBM_BCUDA(b, cudaStreamSynchronize(b->stream));
     return VLBM_OK;
@@ -180,7 +184,7 @@ template <class S, bool SPLIT, int V>
 void launch_batch(vlbm_batch* b, cudaStream_t s, int src) {
     using C = typename Storage<S>::C;
     k_batch_step_2d<S, SPLIT, V><<<b->sm_count * b->blocks_per_sm, b->threads, 0, s>>>(
-        b->level[src], b->level[src ^ 1], (const BatchProblem<C>*)b->table, b->count, b->items);
+        b->level[src], b->level[src ^ 1], (const BatchProblem<C>*)b->table, b->chunks, b->count, b->items);
 }
 
 void launch_batch_step(vlbm_batch* b, cudaStream_t s, int src) {
@@ -228,6 +232,7 @@ void free_batch(vlbm_batch* b) {
     for (int i = 0; i < 2; ++i)
         if (b->level[i]) cudaFree(b->level[i]);
     if (b->table) cudaFree(b->table);
+    if (b->chunks) cudaFree(b->chunks);
     if (b->partials) cudaFree(b->partials);
     if (b->inv_dev) cudaFree(b->inv_dev);
     if (b->inv_host) cudaFreeHost(b->inv_host);

@@ -86,7 +86,7 @@ __device__ __forceinline__ void warp_stream_collide_2d(const Layout<S, SPLIT, 5>
             load_or_zero<S, V>(w, px + row + x0, active);
             {
                 S prev = __shfl_up_sync(0xffffffffu, w[V - 1], 1);
-                if (lane == 0 && active) prev = px[row + xm];
+                if (lane == 0 && active) prev = __ldg(px + row + xm);
                 g[5 * f + 1][0] = Storage<S>::to_c(prev) * isc;
 #pragma unroll
                 for (int i = 1; i < V; ++i) g[5 * f + 1][i] = Storage<S>::to_c(w[i - 1]) * isc;
@@ -96,7 +96,7 @@ __device__ __forceinline__ void warp_stream_collide_2d(const Layout<S, SPLIT, 5>
             load_or_zero<S, V>(w, mx + row + x0, active);
             {
                 S next = __shfl_down_sync(0xffffffffu, w[0], 1);
-                if (fetch_next) next = mx[row + xp];
+                if (fetch_next) next = __ldg(mx + row + xp);
 #pragma unroll
                 for (int i = 0; i < V - 1; ++i) g[5 * f + 2][i] = Storage<S>::to_c(w[i + 1]) * isc;
                 g[5 * f + 2][V - 1] = Storage<S>::to_c(next) * isc;

@@ -64,13 +64,13 @@ k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
                 load_or_zero<S, V>(w, pl + src_row[l] + x0, active);
                 if (l == 1) {           // +x: from x - 1
                     S prev = __shfl_up_sync(0xffffffffu, w[V - 1], 1);
-                    if (lane == 0 && active) prev = pl[row + xm];
+                    if (lane == 0 && active) prev = __ldg(pl + row + xm);
                     g[7 * f + 1][0] = Storage<S>::to_c(prev) * isc;
 #pragma unroll
                     for (int i = 1; i < V; ++i) g[7 * f + 1][i] = Storage<S>::to_c(w[i - 1]) * isc;
                 } else if (l == 2) {    // -x: from x + 1
                     S next = __shfl_down_sync(0xffffffffu, w[0], 1);
-                    if (fetch_next) next = pl[row + xp];
+                    if (fetch_next) next = __ldg(pl + row + xp);
 #pragma unroll
                     for (int i = 0; i < V - 1; ++i) g[7 * f + 2][i] = Storage<S>::to_c(w[i + 1]) * isc;
                     g[7 * f + 2][V - 1] = Storage<S>::to_c(next) * isc;

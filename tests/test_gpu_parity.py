@@ -440,7 +440,7 @@ def test_full_size_4096_sampled_step_and_conservation(orc):
 
 # ------------------------------------------------------------ 3D energy history (fused records)
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_d3q7_energy_history_matches_oracle(orc, precision, tol):
     """Kinetic-energy history of a 3D Taylor-Green vortex reduced inside the step
     kernel (every 4 steps) against the oracle's invariants after the same steps;
