@@ -259,6 +259,16 @@ int vlbm_batch_autotune(vlbm_batch* b, int32_t repeats, int32_t* config_out, dou
 int vlbm_batch_info(const vlbm_batch* b, int64_t* nodes_total, int64_t* step, int64_t* launches);
 const char* vlbm_batch_last_error(const vlbm_batch* b);
 
+/* ---- tensor-core building block of the surrogate ---------------------------
+ * D = A B^T on the fifth-generation tensor cores (tcgen05, BF16 operands,
+ * FP32 accumulation in tensor memory): A [M][K] and B [N][K] row-major BF16
+ * device arrays, D [M][N] row-major FP32 device array.  M % 128 == 0,
+ * 16 <= N <= 256 with N % 16 == 0, K % 64 == 0.  *err_dev (device int) is set
+ * to 1 if a bounded wait for the tensor core gave up.  Asynchronous on stream.
+ * Not an operation of the paper: the GEMM the learned surrogate is built on. */
+int vlbm_tc_gemm_bf16(const void* A, const void* B, float* D, int64_t M, int64_t N, int64_t K, int32_t* err_dev,
+                      void* stream);
+
 /* Static text of a status code; message of the last failure of h. */
 const char* vlbm_strerror(int code);
 const char* vlbm_last_error(const vlbm_handle* h);

@@ -62,7 +62,7 @@ EXPORTED = [
     "vlbm_strerror", "vlbm_last_error", "vlbm_invariants_noalloc",
     "vlbm_batch_create", "vlbm_batch_destroy", "vlbm_batch_init", "vlbm_batch_step", "vlbm_batch_macros",
     "vlbm_batch_invariants", "vlbm_batch_set_config", "vlbm_batch_autotune", "vlbm_batch_info",
-    "vlbm_batch_last_error",
+    "vlbm_batch_last_error", "vlbm_tc_gemm_bf16",
 ]
 
 
@@ -123,6 +123,7 @@ lib.vlbm_batch_info.argtypes = [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINT
                                 ctypes.POINTER(ctypes.c_int64)]
 lib.vlbm_batch_last_error.argtypes = [_H]
 lib.vlbm_batch_last_error.restype = ctypes.c_char_p
+lib.vlbm_tc_gemm_bf16.argtypes = [_V, _V, _V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _V, _V]
 lib.vlbm_strerror.argtypes = [ctypes.c_int]
 lib.vlbm_strerror.restype = ctypes.c_char_p
 lib.vlbm_last_error.argtypes = [_H]
@@ -378,6 +379,16 @@ def vlbm_batch_info(b):
 
 def vlbm_batch_last_error(b) -> str:
     return lib.vlbm_batch_last_error(b).decode()
+
+
+def vlbm_tc_gemm_bf16(A, B, D, err, stream=None) -> None:
+    """D = A B^T on tcgen05 tensor cores; CUDA tensors: A (M, K) bf16, B (N, K) bf16, D (M, N) fp32,
+    err: one int32 set to 1 if a wait for the tensor core gave up."""
+    M, K = A.shape
+    N = B.shape[0]
+    s = current_stream() if stream is None else stream
+    _check(lib.vlbm_tc_gemm_bf16(_V(A.data_ptr()), _V(B.data_ptr()), _V(D.data_ptr()), M, N, K,
+                                 _V(err.data_ptr()), _V(s)), "vlbm_tc_gemm_bf16")
 
 
 def vlbm_strerror(code: int) -> str:
