@@ -269,6 +269,63 @@ const char* vlbm_batch_last_error(const vlbm_batch* b);
 int vlbm_tc_gemm_bf16(const void* A, const void* B, float* D, int64_t M, int64_t N, int64_t K, int32_t* err_dev,
                       void* stream);
 
+/* 3x3 convolution with periodic padding on the tensor cores (implicit GEMM):
+ *   Y[b][y][x][co] = act(bias[co] + sum_{dy,dx,ci} W[co][3(dy+1)+(dx+1)][ci] X[b][y+dy][x+dx][ci])
+ * with indices wrapped periodically.  X [B][H][W][cin] and Y, Z [B][H][W][cout]
+ * are BF16 NHWC device arrays, W [cout][9][cin] BF16, bias [cout] FP32.
+ * act = 1 applies GELU (erf form) and, when Z is not NULL, also stores the
+ * pre-activation in Z; act = 0 stores the affine result.  (cin, cout) in
+ * {16, 64} x {16, 64}.  *err_dev is set to 1 if a wait for the tensor core
+ * gave up.  Asynchronous on stream. */
+int vlbm_sur_conv3x3(const void* X, const void* W, const float* bias, void* Y, void* Z, int64_t B, int64_t H,
+                     int64_t Wd, int32_t cin, int32_t cout, int32_t act, int32_t* err_dev, void* stream);
+
+/* Weight and bias gradients of vlbm_sur_conv3x3, accumulated (+=) into
+ *   G[co][3(dy+1)+(dx+1)][ci] += sum_{b,y,x} X[b][y+dy][x+dx][ci] dZ[b][y][x][co]
+ *   Gb[co]                   += sum_{b,y,x} dZ[b][y][x][co]
+ * (periodic indices) on the tensor cores.  X [B][H][W][cin], dZ [B][H][W][cout]
+ * BF16 NHWC device arrays; G [cout][9][cin] and Gb [cout] FP32 device arrays
+ * that the caller zeroes first.  (cin, cout) in {(16,64), (64,64), (64,16)};
+ * B H W < 2^31.  Asynchronous on stream; *err_dev as above. */
+int vlbm_sur_conv3x3_wgrad(const void* X, const void* dZ, float* G, float* Gb, int64_t B, int64_t H, int64_t Wd,
+                           int32_t cin, int32_t cout, int32_t* err_dev, void* stream);
+
+/* ---- learned surrogate (Section 6 of the paper) ----------------------------
+ * A five-layer fully convolutional network with periodic 3x3 kernels,
+ * 64 hidden channels and GELU, that maps a velocity field u [B][2][H][W]
+ * (FP32, device) to an increment du of the same shape; the caller advances
+ * u(t + T) = u(t) + S du with its own step T and scale S.  Weights are BF16
+ * copies of FP32 master parameters, activations BF16, every product
+ * accumulated in FP32 on the tensor cores.  Training minimises the mean
+ * squared error against target increments with Adam (beta1 = 0.9,
+ * beta2 = 0.999, eps = 1e-8).  The handle owns all its device memory
+ * (parameters, Adam moments and activations for max_batch fields) and works
+ * on the stream given at creation. */
+typedef struct vlbm_sur vlbm_sur;
+
+/* Seeded initialisation (uniform, scaled by the fan-in).  Synchronises. */
+int vlbm_sur_create(int32_t H, int32_t W, int32_t max_batch, uint64_t seed, void* stream, vlbm_sur** out);
+void vlbm_sur_destroy(vlbm_sur* s);
+/* Number of FP32 parameters: per layer the weights [cout][9][cin] then the
+ * bias [cout], layers in order, with (cin, cout) = (16,64), (64,64), (64,64),
+ * (64,64), (64,16); input channels 2..15 of the first layer and output
+ * channels 2..15 of the last are padding and stay zero. */
+int64_t vlbm_sur_num_params(const vlbm_sur* s);
+/* du = net(u) for 1 <= batch <= max_batch fields; device pointers; asynchronous. */
+int vlbm_sur_forward(vlbm_sur* s, const float* u, float* du, int32_t batch);
+/* One Adam step on the mean squared error of net(u) against target (both
+ * [batch][2][H][W] FP32 device arrays) with learning rate lr.  When loss is
+ * not NULL the loss before the update is written there (host float) and the
+ * call synchronises; otherwise it is asynchronous. */
+int vlbm_sur_train_step(vlbm_sur* s, const float* u, const float* target, int32_t batch, float lr, float* loss);
+/* Copy the FP32 parameters (or the gradients of the last train step) to dst;
+ * set_params also resets Adam's moments.  Any pointer kind; synchronise. */
+int vlbm_sur_get_params(vlbm_sur* s, float* dst);
+int vlbm_sur_get_grads(vlbm_sur* s, float* dst);
+int vlbm_sur_set_params(vlbm_sur* s, const float* src);
+/* VLBM_ETIMEOUT if a wait for the tensor core gave up since creation; synchronises. */
+int vlbm_sur_status(vlbm_sur* s);
+
 /* Static text of a status code; message of the last failure of h. */
 const char* vlbm_strerror(int code);
 const char* vlbm_last_error(const vlbm_handle* h);

@@ -15,7 +15,7 @@ from . import _binding
 from ._binding import *  # noqa: F401,F403  (the C ABI, same names)
 from ._binding import VlbmError, PRECISIONS
 
-__all__ = list(_binding.EXPORTED) + ["Lattice", "Batch", "VlbmError", "PRECISIONS"]
+__all__ = list(_binding.EXPORTED) + ["Lattice", "Batch", "Surrogate", "VlbmError", "PRECISIONS"]
 
 
 class Lattice:
@@ -173,3 +173,79 @@ class Batch:
 
     def info(self):
         return _binding.vlbm_batch_info(self.handle)
+
+
+class Surrogate:
+    """The learned surrogate of Section 6 (a vlbm_sur): five periodic 3x3 convolutions with
+    64 hidden channels and GELU, BF16 weights and activations, FP32 accumulation, trained with Adam.
+
+    forward(u) maps velocity fields u (B, 2, H, W) FP32 on the device to increments du of the
+    same shape; train_step(u, target, lr) takes one Adam step on the mean squared error.
+    """
+
+    LAYERS = ((16, 64), (64, 64), (64, 64), (64, 64), (64, 16))
+
+    def __init__(self, H, W, max_batch, seed=0, stream=None):
+        self.H, self.W, self.max_batch = int(H), int(W), int(max_batch)
+        self.handle = _binding.vlbm_sur_create(self.H, self.W, self.max_batch, int(seed), stream)
+        self.num_params = _binding.vlbm_sur_num_params(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _binding.vlbm_sur_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_fields(self, u):
+        if u.dtype.itemsize != 4 or not u.is_cuda or not u.is_contiguous() or u.dim() != 4 \
+                or tuple(u.shape[1:]) != (2, self.H, self.W) or not 1 <= u.shape[0] <= self.max_batch:
+            raise ValueError(f"expected contiguous float32 CUDA fields (B<= {self.max_batch}, 2, {self.H}, {self.W})")
+
+    def forward(self, u, out=None):
+        import torch
+        self._check_fields(u)
+        du = torch.empty_like(u) if out is None else out
+        _binding.vlbm_sur_forward(self.handle, u, du, u.shape[0])
+        return du
+
+    def train_step(self, u, target, lr, want_loss=True):
+        self._check_fields(u)
+        self._check_fields(target)
+        return _binding.vlbm_sur_train_step(self.handle, u, target, u.shape[0], float(lr), want_loss)
+
+    def params(self, device="cuda"):
+        import torch
+        p = torch.empty(self.num_params, dtype=torch.float32, device=device)
+        _binding.vlbm_sur_get_params(self.handle, p)
+        return p
+
+    def grads(self, device="cuda"):
+        import torch
+        g = torch.empty(self.num_params, dtype=torch.float32, device=device)
+        _binding.vlbm_sur_get_grads(self.handle, g)
+        return g
+
+    def load_params(self, p):
+        import torch
+        p = p.to(torch.float32).contiguous()
+        if p.numel() != self.num_params:
+            raise ValueError(f"expected {self.num_params} parameters")
+        _binding.vlbm_sur_set_params(self.handle, p)
+
+    def status(self):
+        _binding.vlbm_sur_status(self.handle)
+
+    @classmethod
+    def split_params(cls, p):
+        """Views (W (cout, 9, cin), bias (cout,)) per layer of a flat parameter vector."""
+        out, off = [], 0
+        for cin, cout in cls.LAYERS:
+            nw = cout * 9 * cin
+            out.append((p[off:off + nw].view(cout, 9, cin), p[off + nw:off + nw + cout]))
+            off += nw + cout
+        return out

@@ -62,7 +62,9 @@ EXPORTED = [
     "vlbm_strerror", "vlbm_last_error", "vlbm_invariants_noalloc",
     "vlbm_batch_create", "vlbm_batch_destroy", "vlbm_batch_init", "vlbm_batch_step", "vlbm_batch_macros",
     "vlbm_batch_invariants", "vlbm_batch_set_config", "vlbm_batch_autotune", "vlbm_batch_info",
-    "vlbm_batch_last_error", "vlbm_tc_gemm_bf16",
+    "vlbm_batch_last_error", "vlbm_tc_gemm_bf16", "vlbm_sur_conv3x3", "vlbm_sur_conv3x3_wgrad",
+    "vlbm_sur_create", "vlbm_sur_destroy", "vlbm_sur_num_params", "vlbm_sur_forward", "vlbm_sur_train_step",
+    "vlbm_sur_get_params", "vlbm_sur_get_grads", "vlbm_sur_set_params", "vlbm_sur_status",
 ]
 
 
@@ -124,6 +126,22 @@ lib.vlbm_batch_info.argtypes = [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINT
 lib.vlbm_batch_last_error.argtypes = [_H]
 lib.vlbm_batch_last_error.restype = ctypes.c_char_p
 lib.vlbm_tc_gemm_bf16.argtypes = [_V, _V, _V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _V, _V]
+lib.vlbm_sur_conv3x3.argtypes = [_V, _V, _V, _V, _V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                 ctypes.c_int32, ctypes.c_int32, _V, _V]
+lib.vlbm_sur_conv3x3_wgrad.argtypes = [_V, _V, _V, _V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_int32, _V, _V]
+lib.vlbm_sur_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _V,
+                                ctypes.POINTER(_H)]
+lib.vlbm_sur_destroy.argtypes = [_H]
+lib.vlbm_sur_destroy.restype = None
+lib.vlbm_sur_num_params.argtypes = [_H]
+lib.vlbm_sur_num_params.restype = ctypes.c_int64
+lib.vlbm_sur_forward.argtypes = [_H, _V, _V, ctypes.c_int32]
+lib.vlbm_sur_train_step.argtypes = [_H, _V, _V, ctypes.c_int32, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]
+lib.vlbm_sur_get_params.argtypes = [_H, _V]
+lib.vlbm_sur_get_grads.argtypes = [_H, _V]
+lib.vlbm_sur_set_params.argtypes = [_H, _V]
+lib.vlbm_sur_status.argtypes = [_H]
 lib.vlbm_strerror.argtypes = [ctypes.c_int]
 lib.vlbm_strerror.restype = ctypes.c_char_p
 lib.vlbm_last_error.argtypes = [_H]
@@ -389,6 +407,69 @@ def vlbm_tc_gemm_bf16(A, B, D, err, stream=None) -> None:
     s = current_stream() if stream is None else stream
     _check(lib.vlbm_tc_gemm_bf16(_V(A.data_ptr()), _V(B.data_ptr()), _V(D.data_ptr()), M, N, K,
                                  _V(err.data_ptr()), _V(s)), "vlbm_tc_gemm_bf16")
+
+
+def vlbm_sur_conv3x3(X, W, bias, Y, err, act=True, Z=None, stream=None) -> None:
+    """Periodic 3x3 convolution on tcgen05: X (B, H, W, cin) bf16, W (cout, 9, cin) bf16, bias (cout,) fp32,
+    Y (and Z) (B, H, W, cout) bf16, err one int32 on the device."""
+    B, H, Wd, cin = X.shape
+    cout = W.shape[0]
+    s = current_stream() if stream is None else stream
+    _check(lib.vlbm_sur_conv3x3(_V(X.data_ptr()), _V(W.data_ptr()), _V(bias.data_ptr()), _V(Y.data_ptr()),
+                                _V(Z.data_ptr() if Z is not None else None), B, H, Wd, cin, cout, int(bool(act)),
+                                _V(err.data_ptr()), _V(s)), "vlbm_sur_conv3x3")
+
+
+def vlbm_sur_conv3x3_wgrad(X, dZ, G, Gb, err, stream=None) -> None:
+    """Accumulate weight (G (cout, 9, cin) fp32) and bias (Gb (cout,) fp32) gradients of vlbm_sur_conv3x3
+    from X (B, H, W, cin) bf16 and dZ (B, H, W, cout) bf16."""
+    B, H, Wd, cin = X.shape
+    cout = dZ.shape[3]
+    s = current_stream() if stream is None else stream
+    _check(lib.vlbm_sur_conv3x3_wgrad(_V(X.data_ptr()), _V(dZ.data_ptr()), _V(G.data_ptr()), _V(Gb.data_ptr()),
+                                      B, H, Wd, cin, cout, _V(err.data_ptr()), _V(s)), "vlbm_sur_conv3x3_wgrad")
+
+
+def vlbm_sur_create(H: int, W: int, max_batch: int, seed: int, stream=None):
+    h = _H()
+    s = current_stream() if stream is None else stream
+    _check(lib.vlbm_sur_create(H, W, max_batch, seed, _V(s), ctypes.byref(h)), "vlbm_sur_create")
+    return h
+
+
+def vlbm_sur_destroy(h) -> None:
+    lib.vlbm_sur_destroy(h)
+
+
+def vlbm_sur_num_params(h) -> int:
+    return int(lib.vlbm_sur_num_params(h))
+
+
+def vlbm_sur_forward(h, u, du, batch: int) -> None:
+    _check(lib.vlbm_sur_forward(h, _V(u.data_ptr()), _V(du.data_ptr()), batch), "vlbm_sur_forward")
+
+
+def vlbm_sur_train_step(h, u, target, batch: int, lr: float, want_loss: bool = True):
+    loss = ctypes.c_float(0.0)
+    _check(lib.vlbm_sur_train_step(h, _V(u.data_ptr()), _V(target.data_ptr()), batch, lr,
+                                   ctypes.byref(loss) if want_loss else None), "vlbm_sur_train_step")
+    return float(loss.value) if want_loss else None
+
+
+def vlbm_sur_get_params(h, dst) -> None:
+    _check(lib.vlbm_sur_get_params(h, _V(dst.data_ptr())), "vlbm_sur_get_params")
+
+
+def vlbm_sur_get_grads(h, dst) -> None:
+    _check(lib.vlbm_sur_get_grads(h, _V(dst.data_ptr())), "vlbm_sur_get_grads")
+
+
+def vlbm_sur_set_params(h, src) -> None:
+    _check(lib.vlbm_sur_set_params(h, _V(src.data_ptr())), "vlbm_sur_set_params")
+
+
+def vlbm_sur_status(h) -> None:
+    _check(lib.vlbm_sur_status(h), "vlbm_sur_status")
 
 
 def vlbm_strerror(code: int) -> str:

@@ -4,7 +4,10 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
+#include <new>
+#include <vector>
 
 #include "vlbm.h"
 #include "vlbm_tc.cuh"
@@ -94,6 +97,358 @@ k_tc_gemm_bf16(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restr
     if (warp == 0) tc::tmem_dealloc(taddr, ncols);
 }
 
+// ---------------------------------------------------------------------------
+// 3x3 convolution with periodic padding as an implicit GEMM on tcgen05.
+// Activations are NHWC BF16, weights [COUT][9][CIN] BF16 with tap = 3 (dy + 1)
+// + (dx + 1).  A CTA computes 128 consecutive output pixels (flattened
+// b, y, x) for every output channel: M = 128 pixels, N = COUT, K = 9 CIN.  The
+// weight tile (COUT x 9 CIN) is staged once; for each tap the 128 source pixels'
+// CIN channels are staged and CIN / 16 MMAs accumulate into tensor memory.  The
+// epilogue adds the bias, optionally stores the pre-activation Z, applies GELU
+// when ACT and stores Y.
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+constexpr int align1k(int b) { return (b + 1023) & ~1023; }
+
+template <int CIN, int COUT>
+constexpr int conv_smem_bytes() { return align1k(COUT * 9 * CIN * 2) + 128 * CIN * 2; }
+
+template <int CIN, int COUT, bool ACT, bool STORE_Z>
+__global__ void __launch_bounds__(kTcThreads)
+k_conv3x3(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ bias,
+          __nv_bfloat16* __restrict__ Y, __nv_bfloat16* __restrict__ Z, int B, int H, int Wd, int* __restrict__ err) {
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 256, "tile shape");
+    constexpr int KT = 9 * CIN;
+    constexpr uint32_t NCOL = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : (COUT <= 128 ? 128 : 256));
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sB = smem;
+    uint8_t* sA = smem + align1k(COUT * KT * 2);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_taddr;
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    if (warp == 0) {
+        tc::tmem_alloc(&s_taddr, NCOL);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) tc::mbar_init(&bar, 1);
+    for (int i = tid; i < COUT * (KT / 8); i += kTcThreads) {
+        const int row = i / (KT / 8), kb = i % (KT / 8);
+        *reinterpret_cast<uint4*>(sB + tc::kmajor_offset(row, kb * 8, KT)) =
+            *reinterpret_cast<const uint4*>(Wt + (long long)row * KT + kb * 8);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = s_taddr;
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
+
+    const long long npix = (long long)B * H * Wd;
+    const long long pix = (long long)blockIdx.x * 128 + tid;
+    const bool valid = pix < npix;
+    const int x = (int)(pix % Wd);
+    const long long by = pix / Wd;
+    const int y = (int)(by % H);
+    const long long b = by / H;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int tap = 0; tap < 9 && ok; ++tap) {
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const int ys = y + dy < 0 ? H - 1 : (y + dy >= H ? 0 : y + dy);
+        const int xs = x + dx < 0 ? Wd - 1 : (x + dx >= Wd ? 0 : x + dx);
+        const __nv_bfloat16* src = X + ((b * H + ys) * Wd + xs) * CIN;
+#pragma unroll
+        for (int kb = 0; kb < CIN / 8; ++kb) {
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (valid) v = *reinterpret_cast<const uint4*>(src + kb * 8);
+            *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(tid, kb * 8, CIN)) = v;
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
+#pragma unroll
+            for (int s = 0; s < CIN / 16; ++s) {
+                const uint64_t da = tc::smem_desc(a0 + s * 256, 128, CIN * 16);
+                const uint64_t db = tc::smem_desc(b0 + ((tap * CIN + 16 * s) / 8) * 128, 128, KT * 16);
+                tc::mma_bf16(taddr, da, db, idesc, (tap > 0 || s > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&bar);
+        }
+        if (!tc::mbar_wait(&bar, phase, kWaitPolls)) {
+            ok = false;
+            atomicExch(err, 1);
+        }
+        phase ^= 1;
+        __syncthreads();
+    }
+    if (ok) {
+        tc::fence_after_sync();
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll
+        for (int c = 0; c < COUT; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + lane_base + (uint32_t)c, v);
+            if (valid) {
+                __align__(16) __nv_bfloat16 zo[16], yo[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float z = v[j] + bias[c + j];
+                    zo[j] = __float2bfloat16_rn(z);
+                    yo[j] = __float2bfloat16_rn(ACT ? gelu(z) : z);
+                }
+                uint4* yd = reinterpret_cast<uint4*>(Y + pix * COUT + c);
+                yd[0] = reinterpret_cast<const uint4*>(yo)[0];
+                yd[1] = reinterpret_cast<const uint4*>(yo)[1];
+                if (STORE_Z) {
+                    uint4* zd = reinterpret_cast<uint4*>(Z + pix * COUT + c);
+                    zd[0] = reinterpret_cast<const uint4*>(zo)[0];
+                    zd[1] = reinterpret_cast<const uint4*>(zo)[1];
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, NCOL);
+}
+
+template <int CIN, int COUT, bool ACT, bool STORE_Z>
+int launch_conv(const void* X, const void* W, const float* bias, void* Y, void* Z, long long B, long long H,
+                long long Wd, int* err, cudaStream_t s) {
+    constexpr int smem = conv_smem_bytes<CIN, COUT>();
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(k_conv3x3<CIN, COUT, ACT, STORE_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem) != cudaSuccess)
+            return VLBM_ECUDA;
+        configured = true;
+    }
+    const long long npix = B * H * Wd;
+    k_conv3x3<CIN, COUT, ACT, STORE_Z><<<(unsigned)((npix + 127) / 128), kTcThreads, smem, s>>>(
+        (const __nv_bfloat16*)X, (const __nv_bfloat16*)W, bias, (__nv_bfloat16*)Y, (__nv_bfloat16*)Z, (int)B, (int)H,
+        (int)Wd, err);
+    return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
+}
+
+template <int CIN, int COUT>
+int launch_conv_act(const void* X, const void* W, const float* bias, void* Y, void* Z, long long B, long long H,
+                    long long Wd, int act, int* err, cudaStream_t s) {
+    if (act && Z) return launch_conv<CIN, COUT, true, true>(X, W, bias, Y, Z, B, H, Wd, err, s);
+    if (act) return launch_conv<CIN, COUT, true, false>(X, W, bias, Y, nullptr, B, H, Wd, err, s);
+    return launch_conv<CIN, COUT, false, false>(X, W, bias, Y, nullptr, B, H, Wd, err, s);
+}
+
+// ---------------------------------------------------------------------------
+// Weight and bias gradients of a periodic 3x3 convolution, on tcgen05:
+//   G[co][tap * CIN + ci] += sum_p X[p + tap][ci] dZ[p][co],   Gb[co] += sum_p dZ[p][co]
+// as a GEMM with M = rows (tap, ci) plus one row of ones (which yields the bias
+// gradient), N = COUT and K = pixels.  blockIdx.y picks a 128-row tile,
+// blockIdx.x a range of pixels (split K); partial results are added to G / Gb
+// with FP32 atomics.  Staging transposes pixel-major activations into the
+// K-major layout (each thread: one pixel, 8-channel groups).
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kTcThreads)
+k_conv3x3_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dZ, float* __restrict__ G,
+                float* __restrict__ Gb, int B, int H, int Wd, int pix_per_cta, int* __restrict__ err) {
+    constexpr int KT = 9 * CIN;
+    constexpr uint32_t NCOL = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);
+    __shared__ __align__(1024) uint8_t sA[128 * 64 * 2];
+    __shared__ __align__(1024) uint8_t sB[COUT * 64 * 2];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_taddr;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        tc::tmem_alloc(&s_taddr, NCOL);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) tc::mbar_init(&bar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = s_taddr;
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
+    const long long npix = (long long)B * H * Wd;
+    const long long p_begin = (long long)blockIdx.x * pix_per_cta;
+    const long long p_end = p_begin + pix_per_cta < npix ? p_begin + pix_per_cta : npix;
+    const int row0 = blockIdx.y * 128;
+    const int k = tid & 63, half = tid >> 6;
+    uint32_t phase = 0;
+    bool ok = true;
+    int round = 0;
+    for (long long c0 = p_begin; c0 < p_end && ok; c0 += 64, ++round) {
+        const long long p = c0 + k;
+        const bool valid = p < p_end;
+        const int x = (int)(p % Wd);
+        const long long by = p / Wd;
+        const int y = (int)(by % H);
+        const long long b = by / H;
+        // A: rows half * 64 .. half * 64 + 63 of this tile, column k
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const int lr = half * 64 + 8 * g;          // local row of the group
+            const int r = row0 + lr;                   // global row (tap, ci) or the ones row
+            __align__(16) __nv_bfloat16 e[8];
+            if (valid && r < KT) {
+                const int tap = r / CIN, ci0 = r % CIN;
+                const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+                const int ys = y + dy < 0 ? H - 1 : (y + dy >= H ? 0 : y + dy);
+                const int xs = x + dx < 0 ? Wd - 1 : (x + dx >= Wd ? 0 : x + dx);
+                *reinterpret_cast<uint4*>(e) =
+                    *reinterpret_cast<const uint4*>(X + ((b * H + ys) * Wd + xs) * CIN + ci0);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) e[j] = __float2bfloat16_rn((valid && r + j == KT) ? 1.0f : 0.0f);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<__nv_bfloat16*>(sA + tc::kmajor_offset(lr + j, k, 64)) = e[j];
+        }
+        // B: output channels half * COUT/2 .., column k
+#pragma unroll
+        for (int g = 0; g < COUT / 16; ++g) {
+            const int co = half * (COUT / 2) + 8 * g;
+            __align__(16) __nv_bfloat16 e[8];
+            if (valid) *reinterpret_cast<uint4*>(e) = *reinterpret_cast<const uint4*>(dZ + p * COUT + co);
+            else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) e[j] = __float2bfloat16_rn(0.0f);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(co + j, k, 64)) = e[j];
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const uint64_t da = tc::smem_desc(a0 + s * 256, 128, 64 * 16);
+                const uint64_t db = tc::smem_desc(b0 + s * 256, 128, 64 * 16);
+                tc::mma_bf16(taddr, da, db, idesc, (round > 0 || s > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&bar);
+        }
+        if (!tc::mbar_wait(&bar, phase, kWaitPolls)) {
+            ok = false;
+            atomicExch(err, 1);
+        }
+        phase ^= 1;
+        __syncthreads();
+    }
+    if (ok && round > 0) {
+        tc::fence_after_sync();
+        const int r = row0 + warp * 32 + (tid & 31);
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll
+        for (int c = 0; c < COUT; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + lane_base + (uint32_t)c, v);
+            if (r < KT) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) atomicAdd(G + (long long)(c + j) * KT + r, v[j]);
+            } else if (r == KT) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) atomicAdd(Gb + c + j, v[j]);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, NCOL);
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise kernels of the surrogate's training step.
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * __expf(-0.5f * z * z);
+}
+
+// u [B][2][H][W] FP32 -> X [B][H][W][16] BF16 (channels 2..15 zero)
+__global__ void k_pack_input(const float* __restrict__ u, __nv_bfloat16* __restrict__ X, long long plane, long long npix) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const long long b = p / plane, q = p - b * plane;
+    __align__(16) __nv_bfloat16 e[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) e[c] = __float2bfloat16_rn(0.0f);
+    e[0] = __float2bfloat16_rn(u[(b * 2 + 0) * plane + q]);
+    e[1] = __float2bfloat16_rn(u[(b * 2 + 1) * plane + q]);
+    reinterpret_cast<uint4*>(X + p * 16)[0] = reinterpret_cast<const uint4*>(e)[0];
+    reinterpret_cast<uint4*>(X + p * 16)[1] = reinterpret_cast<const uint4*>(e)[1];
+}
+
+// Y [B][H][W][16] BF16 (channels 0, 1) -> du [B][2][H][W] FP32
+__global__ void k_unpack_output(const __nv_bfloat16* __restrict__ Y, float* __restrict__ du, long long plane,
+                                long long npix) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const long long b = p / plane, q = p - b * plane;
+    du[(b * 2 + 0) * plane + q] = __bfloat162float(Y[p * 16 + 0]);
+    du[(b * 2 + 1) * plane + q] = __bfloat162float(Y[p * 16 + 1]);
+}
+
+// Mean-squared loss of output channels 0, 1 against t [B][2][H][W]; dY (16 ch) and sum of squares.
+__global__ void k_mse_grad(const __nv_bfloat16* __restrict__ Y, const float* __restrict__ t,
+                           __nv_bfloat16* __restrict__ dY, double* __restrict__ sse, long long plane, long long npix,
+                           float inv_count) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float local = 0.0f;
+    if (p < npix) {
+        const long long b = p / plane, q = p - b * plane;
+        __align__(16) __nv_bfloat16 e[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) e[c] = __float2bfloat16_rn(0.0f);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float d = __bfloat162float(Y[p * 16 + c]) - t[(b * 2 + c) * plane + q];
+            local += d * d;
+            e[c] = __float2bfloat16_rn(2.0f * d * inv_count);
+        }
+        reinterpret_cast<uint4*>(dY + p * 16)[0] = reinterpret_cast<const uint4*>(e)[0];
+        reinterpret_cast<uint4*>(dY + p * 16)[1] = reinterpret_cast<const uint4*>(e)[1];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(sse, (double)local);
+}
+
+// dZ = dY * GELU'(Z), BF16, n elements
+__global__ void k_gelu_back(const __nv_bfloat16* __restrict__ dY, const __nv_bfloat16* __restrict__ Z,
+                            __nv_bfloat16* __restrict__ dZ, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dZ[i] = __float2bfloat16_rn(__bfloat162float(dY[i]) * gelu_grad(__bfloat162float(Z[i])));
+}
+
+// Adam on FP32 master parameters; refreshes the BF16 weights W [cout][9][cin],
+// their flipped transpose Wt [cin][9][cout] (tap -> 8 - tap) used for the data
+// gradient, and the FP32 bias.  Parameter vector per layer: W then bias.
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v, const float* __restrict__ g,
+                       long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+}
+
+__global__ void k_refresh_weights(const float* __restrict__ w, __nv_bfloat16* __restrict__ W,
+                                  __nv_bfloat16* __restrict__ Wflip, int cin, int cout) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = cout * 9 * cin;
+    if (i >= n) return;
+    const int co = i / (9 * cin), rem = i % (9 * cin), tap = rem / cin, ci = rem % cin;
+    const __nv_bfloat16 h = __float2bfloat16_rn(w[i]);
+    W[i] = h;
+    Wflip[((long long)ci * 9 + (8 - tap)) * cout + co] = h;
+}
+
 }  // namespace
 
 extern "C" int vlbm_tc_gemm_bf16(const void* A, const void* B, float* D, int64_t M, int64_t N, int64_t K,
@@ -104,3 +459,303 @@ extern "C" int vlbm_tc_gemm_bf16(const void* A, const void* B, float* D, int64_t
         (const __nv_bfloat16*)A, (const __nv_bfloat16*)B, D, (int)N, (int)K, err_dev);
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
 }
+
+extern "C" int vlbm_sur_conv3x3(const void* X, const void* W, const float* bias, void* Y, void* Z, int64_t B,
+                                int64_t H, int64_t Wd, int32_t cin, int32_t cout, int32_t act, int32_t* err_dev,
+                                void* stream) {
+    if (!X || !W || !bias || !Y || !err_dev || B < 1 || H < 1 || Wd < 1) return VLBM_EINVAL;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (cin == 16 && cout == 64) return launch_conv_act<16, 64>(X, W, bias, Y, Z, B, H, Wd, act, err_dev, s);
+    if (cin == 64 && cout == 64) return launch_conv_act<64, 64>(X, W, bias, Y, Z, B, H, Wd, act, err_dev, s);
+    if (cin == 64 && cout == 16) return launch_conv_act<64, 16>(X, W, bias, Y, Z, B, H, Wd, act, err_dev, s);
+    if (cin == 16 && cout == 16) return launch_conv_act<16, 16>(X, W, bias, Y, Z, B, H, Wd, act, err_dev, s);
+    return VLBM_EUNSUPPORTED;
+}
+
+// ===========================================================================
+// The surrogate network: five periodic 3x3 convolutions, 2 -> 64 -> 64 -> 64
+// -> 64 -> 2 channels (stored padded to 16 at both ends), GELU after the first
+// four, BF16 weights and activations, FP32 accumulation, FP32 master weights
+// trained with Adam.  Its input is a velocity field u [B][2][H][W]; its output
+// is an increment du of the same shape (the caller scales and adds it).
+namespace {
+
+constexpr int kLayers = 5;
+constexpr int kCin[kLayers] = {16, 64, 64, 64, 64};
+constexpr int kCout[kLayers] = {64, 64, 64, 64, 16};
+constexpr int kPixPerWgradCta = 4096;
+
+uint64_t splitmix64(uint64_t& s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <int CIN, int COUT>
+int launch_wgrad(const void* X, const void* dZ, float* G, float* Gb, long long B, long long H, long long W, int* err,
+                 cudaStream_t s) {
+    const long long npix = B * H * W;
+    const dim3 grid((unsigned)((npix + kPixPerWgradCta - 1) / kPixPerWgradCta), (unsigned)((9 * CIN + 1 + 127) / 128));
+    k_conv3x3_wgrad<CIN, COUT><<<grid, kTcThreads, 0, s>>>((const __nv_bfloat16*)X, (const __nv_bfloat16*)dZ, G, Gb,
+                                                           (int)B, (int)H, (int)W, kPixPerWgradCta, err);
+    return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
+}
+
+int conv_any(int cin, int cout, const void* X, const void* W, const float* bias, void* Y, void* Z, long long B,
+             long long H, long long Wd, int act, int* err, cudaStream_t s) {
+    return vlbm_sur_conv3x3(X, W, bias, Y, Z, B, H, Wd, cin, cout, act, err, s);
+}
+
+int wgrad_any(int cin, int cout, const void* X, const void* dZ, float* G, float* Gb, long long B, long long H,
+              long long W, int* err, cudaStream_t s) {
+    if (cin == 16 && cout == 64) return launch_wgrad<16, 64>(X, dZ, G, Gb, B, H, W, err, s);
+    if (cin == 64 && cout == 64) return launch_wgrad<64, 64>(X, dZ, G, Gb, B, H, W, err, s);
+    if (cin == 64 && cout == 16) return launch_wgrad<64, 16>(X, dZ, G, Gb, B, H, W, err, s);
+    return VLBM_EUNSUPPORTED;
+}
+
+}  // namespace
+
+struct vlbm_sur {
+    int H = 0, W = 0, maxB = 0;
+    cudaStream_t stream = nullptr;
+    long long off_w[kLayers] = {}, off_b[kLayers] = {}, nparams = 0;
+    float* params = nullptr;
+    float* grads = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    long long adam_t = 0;
+    __nv_bfloat16* Wb[kLayers] = {};
+    __nv_bfloat16* Wflip[kLayers] = {};
+    __nv_bfloat16* X0 = nullptr;
+    __nv_bfloat16* Y[kLayers] = {};
+    __nv_bfloat16* Z[kLayers - 1] = {};
+    __nv_bfloat16* dA = nullptr;
+    __nv_bfloat16* dB = nullptr;
+    float* zero_bias = nullptr;
+    double* sse = nullptr;
+    int* err = nullptr;
+};
+
+namespace {
+
+void free_sur(vlbm_sur* s) {
+    void* ptrs[] = {s->params, s->grads, s->adam_m, s->adam_v, s->X0, s->dA, s->dB, s->zero_bias, s->sse, s->err};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int l = 0; l < kLayers; ++l) {
+        if (s->Wb[l]) cudaFree(s->Wb[l]);
+        if (s->Wflip[l]) cudaFree(s->Wflip[l]);
+        if (s->Y[l]) cudaFree(s->Y[l]);
+        if (l < kLayers - 1 && s->Z[l]) cudaFree(s->Z[l]);
+    }
+}
+
+int refresh_all(vlbm_sur* s) {
+    for (int l = 0; l < kLayers; ++l) {
+        const int n = kCout[l] * 9 * kCin[l];
+        k_refresh_weights<<<(n + 255) / 256, 256, 0, s->stream>>>(s->params + s->off_w[l], s->Wb[l], s->Wflip[l],
+                                                                  kCin[l], kCout[l]);
+    }
+    return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
+}
+
+int check_err(vlbm_sur* s) {
+    int e = 0;
+    if (cudaMemcpyAsync(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return VLBM_ECUDA;
+    return e ? VLBM_ETIMEOUT : VLBM_OK;
+}
+
+// Forward pass of `batch` fields; keeps the pre-activations when `train`.
+int sur_forward(vlbm_sur* s, const float* u, int batch, bool train) {
+    const long long plane = (long long)s->H * s->W, npix = plane * batch;
+    k_pack_input<<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(u, s->X0, plane, npix);
+    const void* x = s->X0;
+    for (int l = 0; l < kLayers; ++l) {
+        const bool act = l < kLayers - 1;
+        int rc = conv_any(kCin[l], kCout[l], x, s->Wb[l], s->params + s->off_b[l], s->Y[l],
+                          (act && train) ? s->Z[l] : nullptr, batch, s->H, s->W, act ? 1 : 0, s->err, s->stream);
+        if (rc) return rc;
+        x = s->Y[l];
+    }
+    return VLBM_OK;
+}
+
+}  // namespace
+
+extern "C" int vlbm_sur_conv3x3_wgrad(const void* X, const void* dZ, float* G, float* Gb, int64_t B, int64_t H,
+                                      int64_t Wd, int32_t cin, int32_t cout, int32_t* err_dev, void* stream) {
+    if (!X || !dZ || !G || !Gb || !err_dev || B < 1 || H < 1 || Wd < 1) return VLBM_EINVAL;
+    if ((unsigned long long)(B * H * Wd) >= (1ull << 31)) return VLBM_EINVAL;
+    return wgrad_any(cin, cout, X, dZ, G, Gb, B, H, Wd, err_dev, (cudaStream_t)stream);
+}
+
+extern "C" int vlbm_sur_create(int32_t H, int32_t W, int32_t max_batch, uint64_t seed, void* stream, vlbm_sur** out) {
+    if (!out || H < 1 || W < 1 || max_batch < 1) return VLBM_EINVAL;
+    *out = nullptr;
+    vlbm_sur* s = new (std::nothrow) vlbm_sur();
+    if (!s) return VLBM_ENOMEM;
+    s->H = H;
+    s->W = W;
+    s->maxB = max_batch;
+    s->stream = (cudaStream_t)stream;
+    long long off = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        s->off_w[l] = off;
+        off += (long long)kCout[l] * 9 * kCin[l];
+        s->off_b[l] = off;
+        off += kCout[l];
+    }
+    s->nparams = off;
+    const long long npix = (long long)H * W * max_batch;
+    bool okm = true;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (okm && cudaMalloc(p, bytes) != cudaSuccess) okm = false;
+    };
+    alloc((void**)&s->params, off * 4);
+    alloc((void**)&s->grads, off * 4);
+    alloc((void**)&s->adam_m, off * 4);
+    alloc((void**)&s->adam_v, off * 4);
+    alloc((void**)&s->X0, npix * 16 * 2);
+    alloc((void**)&s->dA, npix * 64 * 2);
+    alloc((void**)&s->dB, npix * 64 * 2);
+    alloc((void**)&s->zero_bias, 64 * 4);
+    alloc((void**)&s->sse, sizeof(double));
+    alloc((void**)&s->err, sizeof(int));
+    for (int l = 0; l < kLayers; ++l) {
+        alloc((void**)&s->Wb[l], (size_t)kCout[l] * 9 * kCin[l] * 2);
+        alloc((void**)&s->Wflip[l], (size_t)kCout[l] * 9 * kCin[l] * 2);
+        alloc((void**)&s->Y[l], npix * kCout[l] * 2);
+        if (l < kLayers - 1) alloc((void**)&s->Z[l], npix * kCout[l] * 2);
+    }
+    if (!okm) {
+        cudaGetLastError();
+        free_sur(s);
+        delete s;
+        return VLBM_ENOMEM;
+    }
+    // seeded initialisation: uniform(-a, a), a = sqrt(6 / fan_in) over the real input
+    // channels; the padded input channels of layer 1 and outputs of layer 5 are 0,
+    // and layer 5 starts at a tenth of that scale so that the first increments are small
+    std::vector<float> h(off, 0.0f);
+    uint64_t st = seed;
+    for (int l = 0; l < kLayers; ++l) {
+        const int real_in = l == 0 ? 2 : kCin[l], real_out = l == kLayers - 1 ? 2 : kCout[l];
+        const float a = std::sqrt(6.0f / (9.0f * real_in)) * (l == kLayers - 1 ? 0.1f : 1.0f);
+        for (int co = 0; co < kCout[l]; ++co)
+            for (int t = 0; t < 9; ++t)
+                for (int ci = 0; ci < kCin[l]; ++ci) {
+                    const float r = (float)((splitmix64(st) >> 11) * (1.0 / 9007199254740992.0)) * 2.0f - 1.0f;
+                    h[s->off_w[l] + ((long long)co * 9 + t) * kCin[l] + ci] = (co < real_out && ci < real_in) ? a * r : 0.0f;
+                }
+    }
+    int rc = VLBM_OK;
+    if (cudaMemcpyAsync(s->params, h.data(), off * 4, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->adam_m, 0, off * 4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->adam_v, 0, off * 4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->zero_bias, 0, 64 * 4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->err, 0, sizeof(int), s->stream) != cudaSuccess)
+        rc = VLBM_ECUDA;
+    if (!rc) rc = refresh_all(s);
+    if (!rc && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = VLBM_ECUDA;
+    if (rc) {
+        free_sur(s);
+        delete s;
+        return rc;
+    }
+    *out = s;
+    return VLBM_OK;
+}
+
+extern "C" void vlbm_sur_destroy(vlbm_sur* s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    free_sur(s);
+    delete s;
+}
+
+extern "C" int64_t vlbm_sur_num_params(const vlbm_sur* s) { return s ? s->nparams : 0; }
+
+extern "C" int vlbm_sur_forward(vlbm_sur* s, const float* u, float* du, int32_t batch) {
+    if (!s || !u || !du || batch < 1 || batch > s->maxB) return VLBM_EINVAL;
+    int rc = sur_forward(s, u, batch, false);
+    if (rc) return rc;
+    const long long plane = (long long)s->H * s->W, npix = plane * batch;
+    k_unpack_output<<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(s->Y[kLayers - 1], du, plane, npix);
+    return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
+}
+
+extern "C" int vlbm_sur_train_step(vlbm_sur* s, const float* u, const float* target, int32_t batch, float lr,
+                                   float* loss) {
+    if (!s || !u || !target || batch < 1 || batch > s->maxB) return VLBM_EINVAL;
+    const long long plane = (long long)s->H * s->W, npix = plane * batch;
+    int rc = sur_forward(s, u, batch, true);
+    if (rc) return rc;
+    if (cudaMemsetAsync(s->sse, 0, sizeof(double), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->grads, 0, s->nparams * 4, s->stream) != cudaSuccess)
+        return VLBM_ECUDA;
+    const unsigned eb = (unsigned)((npix + 255) / 256);
+    k_mse_grad<<<eb, 256, 0, s->stream>>>(s->Y[kLayers - 1], target, s->dA, s->sse, plane, npix,
+                                          1.0f / (float)(2 * npix));
+    // backward, last layer first: dA holds dZ of layer l (its pre-activation gradient)
+    for (int l = kLayers - 1; l >= 0; --l) {
+        const void* xin = l == 0 ? (const void*)s->X0 : (const void*)s->Y[l - 1];
+        rc = wgrad_any(kCin[l], kCout[l], xin, s->dA, s->grads + s->off_w[l], s->grads + s->off_b[l], batch, s->H,
+                       s->W, s->err, s->stream);
+        if (rc) return rc;
+        if (l == 0) break;
+        // dY of layer l-1 = conv(dZ_l, flipped transposed W_l); then dZ_{l-1} = dY * GELU'(Z_{l-1})
+        rc = conv_any(kCout[l], kCin[l], s->dA, s->Wflip[l], s->zero_bias, s->dB, nullptr, batch, s->H, s->W, 0,
+                      s->err, s->stream);
+        if (rc) return rc;
+        const long long n = npix * kCin[l];
+        k_gelu_back<<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>(s->dB, s->Z[l - 1], s->dA, n);
+    }
+    s->adam_t++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f / (1.0f - std::pow(b1, (float)s->adam_t));
+    const float c2 = 1.0f / (1.0f - std::pow(b2, (float)s->adam_t));
+    k_adam<<<(unsigned)((s->nparams + 255) / 256), 256, 0, s->stream>>>(s->params, s->adam_m, s->adam_v, s->grads,
+                                                                         s->nparams, lr, b1, b2, 1e-8f, c1, c2);
+    rc = refresh_all(s);
+    if (rc) return rc;
+    if (loss) {
+        double h = 0.0;
+        if (cudaMemcpyAsync(&h, s->sse, sizeof(double), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+            return VLBM_ECUDA;
+        rc = check_err(s);
+        if (rc) return rc;
+        *loss = (float)(h / (double)(2 * npix));
+    }
+    return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
+}
+
+static int copy_vec(vlbm_sur* s, void* dst, const void* src, long long n) {
+    if (cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyDefault, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return VLBM_ECUDA;
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_sur_get_params(vlbm_sur* s, float* dst) {
+    return (!s || !dst) ? VLBM_EINVAL : copy_vec(s, dst, s->params, s->nparams);
+}
+extern "C" int vlbm_sur_get_grads(vlbm_sur* s, float* dst) {
+    return (!s || !dst) ? VLBM_EINVAL : copy_vec(s, dst, s->grads, s->nparams);
+}
+extern "C" int vlbm_sur_set_params(vlbm_sur* s, const float* src) {
+    if (!s || !src) return VLBM_EINVAL;
+    int rc = copy_vec(s, s->params, src, s->nparams);
+    if (rc) return rc;
+    s->adam_t = 0;
+    if (cudaMemsetAsync(s->adam_m, 0, s->nparams * 4, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->adam_v, 0, s->nparams * 4, s->stream) != cudaSuccess)
+        return VLBM_ECUDA;
+    rc = refresh_all(s);
+    if (rc) return rc;
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
+}
+extern "C" int vlbm_sur_status(vlbm_sur* s) { return s ? check_err(s) : VLBM_EINVAL; }

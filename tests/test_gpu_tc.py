@@ -24,3 +24,176 @@ def test_tc_gemm_matches_matmul(M, N, K):
     scale = (A.double().abs() @ B.double().abs().T).max().item()
     assert torch.isfinite(D).all()
     assert (D.double() - ref).abs().max().item() <= 1e-6 * scale
+
+
+def torch_conv_periodic(X, W, bias, act):
+    """Reference: X (B, H, W, cin) bf16 NHWC, W (cout, 9, cin) -> FP32 NHWC via conv2d with circular padding."""
+    import torch.nn.functional as F
+    cout, _, cin = W.shape
+    w = W.float().reshape(cout, 3, 3, cin).permute(0, 3, 1, 2)          # (cout, cin, kh, kw)
+    x = X.float().permute(0, 3, 1, 2)
+    z = F.conv2d(F.pad(x, (1, 1, 1, 1), mode="circular"), w) + bias.view(1, -1, 1, 1)
+    y = F.gelu(z) if act else z
+    return y.permute(0, 2, 3, 1), z.permute(0, 2, 3, 1)
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 64), (64, 64), (64, 16), (16, 16)])
+@pytest.mark.parametrize("shape", [(2, 16, 32), (1, 8, 24), (3, 5, 7)])
+def test_conv3x3_periodic_matches_torch(cin, cout, shape):
+    B, H, Wd = shape
+    g = torch.Generator(device="cuda").manual_seed(cin * 7 + cout + H)
+    X = torch.randn(B, H, Wd, cin, device="cuda", generator=g).to(torch.bfloat16)
+    W = (torch.randn(cout, 9, cin, device="cuda", generator=g) * 0.1).to(torch.bfloat16)
+    bias = torch.randn(cout, device="cuda", generator=g)
+    for act in (True, False):
+        Y = torch.empty(B, H, Wd, cout, device="cuda", dtype=torch.bfloat16)
+        Z = torch.empty_like(Y) if act else None
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        v.vlbm_sur_conv3x3(X, W, bias, Y, err, act=act, Z=Z)
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        ry, rz = torch_conv_periodic(X, W, bias, act)
+        tol = 1e-2 * ry.abs().max().item()            # one BF16 rounding of the output
+        assert (Y.float() - ry).abs().max().item() <= tol
+        if act:
+            assert (Z.float() - rz).abs().max().item() <= 1e-2 * rz.abs().max().item()
+
+
+def ref_wgrad(X, dZ):
+    """FP64 CPU weight and bias gradients of the periodic conv: G[co][tap][ci] = sum_p dZ[p][co] X[p + tap][ci]."""
+    x, dz = X.double().cpu(), dZ.double().cpu()
+    cin, cout = x.shape[3], dz.shape[3]
+    G = torch.zeros(cout, 9, cin, dtype=torch.float64)
+    for tap in range(9):
+        dy, dx = tap // 3 - 1, tap % 3 - 1
+        xs = torch.roll(x, shifts=(-dy, -dx), dims=(1, 2))          # xs[y][x] = x[y + dy][x + dx]
+        G[:, tap, :] = dz.reshape(-1, cout).T @ xs.reshape(-1, cin)
+    return G, dz.reshape(-1, cout).sum(0)
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 64), (64, 64), (64, 16)])
+@pytest.mark.parametrize("shape", [(2, 16, 32), (3, 40, 72), (1, 5, 7)])
+def test_conv3x3_wgrad_matches_fp64(cin, cout, shape):
+    B, H, Wd = shape
+    g = torch.Generator(device="cuda").manual_seed(cin + cout * 3 + H * Wd)
+    X = torch.randn(B, H, Wd, cin, device="cuda", generator=g).to(torch.bfloat16)
+    dZ = torch.randn(B, H, Wd, cout, device="cuda", generator=g).to(torch.bfloat16)
+    G = torch.zeros(cout, 9, cin, device="cuda")
+    Gb = torch.zeros(cout, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    v.vlbm_sur_conv3x3_wgrad(X, dZ, G, Gb, err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    rG, rGb = ref_wgrad(X, dZ)
+    scale = float(B * H * Wd) * 16.0                                # bound of sum |dZ||X| for these draws
+    assert (G.double().cpu() - rG).abs().max().item() <= 1e-6 * scale
+    assert (Gb.double().cpu() - rGb).abs().max().item() <= 1e-6 * scale
+
+
+def ste_bf16(t):
+    """Round to BF16 in the forward pass, identity in the backward pass."""
+    return t + (t.to(torch.bfloat16).float() - t).detach()
+
+
+def torch_surrogate(params, u):
+    """FP32 reference of the surrogate network with the kernels' BF16 roundings of weights and activations."""
+    import torch.nn.functional as F
+    B, _, H, W = u.shape
+    x = torch.zeros(B, 16, H, W, device=u.device)
+    x = torch.cat([u, x[:, 2:]], dim=1)
+    x = ste_bf16(x)
+    layers = v.Surrogate.split_params(params)
+    for l, (Wl, bl) in enumerate(layers):
+        cout, _, cin = Wl.shape
+        w = ste_bf16(Wl).reshape(cout, 3, 3, cin).permute(0, 3, 1, 2)
+        z = F.conv2d(F.pad(x, (1, 1, 1, 1), mode="circular"), w) + bl.view(1, -1, 1, 1)
+        x = ste_bf16(F.gelu(z) if l < len(layers) - 1 else z)
+    return x[:, :2]
+
+
+def smooth_fields(B, H, W, seed):
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    u = torch.randn(B, 2, H, W, device="cuda", generator=g)
+    for _ in range(3):                                               # a few box filters: smooth random flow
+        u = (u + u.roll(1, 2) + u.roll(-1, 2) + u.roll(1, 3) + u.roll(-1, 3)) / 5.0
+    return (u / u.abs().max()).contiguous()
+
+
+def laplacian(u):
+    return u.roll(1, 2) + u.roll(-1, 2) + u.roll(1, 3) + u.roll(-1, 3) - 4 * u
+
+
+@pytest.fixture
+def no_tf32():
+    old = torch.backends.cudnn.allow_tf32, torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cudnn.allow_tf32 = False
+    torch.backends.cuda.matmul.allow_tf32 = False
+    yield
+    torch.backends.cudnn.allow_tf32, torch.backends.cuda.matmul.allow_tf32 = old
+
+
+@pytest.mark.parametrize("shape", [(2, 32, 48), (1, 20, 12)])
+def test_surrogate_forward_matches_torch(shape, no_tf32):
+    B, H, W = shape
+    net = v.Surrogate(H, W, max_batch=B, seed=7)
+    # larger last layer than the initialisation so that the output is not tiny
+    p = net.params()
+    layers = v.Surrogate.split_params(p)
+    layers[4][0].mul_(10.0)
+    layers[4][0][2:].zero_()
+    net.load_params(p)
+    u = smooth_fields(B, H, W, seed=H)
+    du = net.forward(u)
+    net.status()
+    ref = torch_surrogate(p, u)
+    assert torch.isfinite(du).all()
+    assert (du - ref).abs().max().item() <= 2e-2 * ref.abs().max().item()
+    net.close()
+
+
+def test_surrogate_gradients_match_autograd(no_tf32):
+    B, H, W = 2, 24, 32
+    net = v.Surrogate(H, W, max_batch=B, seed=3)
+    p0 = net.params()
+    u = smooth_fields(B, H, W, seed=1)
+    target = (0.05 * laplacian(u)).contiguous()
+    loss = net.train_step(u, target, lr=0.0)
+    grads = net.grads()
+    w = p0.clone().requires_grad_(True)
+    out = torch_surrogate(w, u)
+    ref_loss = ((out - target) ** 2).mean()
+    ref_loss.backward()
+    assert abs(loss - ref_loss.item()) <= 1e-2 * ref_loss.item()
+    for l, ((gk, bk), (gr, br)) in enumerate(zip(v.Surrogate.split_params(grads), v.Surrogate.split_params(w.grad))):
+        for a, b in ((gk, gr), (bk, br)):
+            nb = b.norm().item()
+            if nb == 0.0:
+                assert a.abs().max().item() == 0.0
+                continue
+            assert (a - b).norm().item() <= 5e-2 * nb, f"layer {l}"
+    # padding stays exactly zero: layer 1 inputs 2..15, layer 5 outputs 2..15
+    g = v.Surrogate.split_params(grads)
+    assert g[0][0][:, :, 2:].abs().max().item() == 0.0
+    assert g[4][0][2:].abs().max().item() == 0.0 and g[4][1][2:].abs().max().item() == 0.0
+    net.close()
+
+
+def test_surrogate_training_reduces_loss():
+    B, H, W = 4, 32, 32
+    net = v.Surrogate(H, W, max_batch=B, seed=11)
+    u = smooth_fields(B, H, W, seed=5)
+    target = (0.05 * laplacian(u)).contiguous()
+    losses = [net.train_step(u, target, lr=2e-3) for _ in range(150)]
+    net.status()
+    assert all(map(lambda x: x == x, losses))
+    assert losses[-1] < 0.1 * losses[0]
+    p = net.params()
+    layers = v.Surrogate.split_params(p)
+    assert layers[0][0][:, :, 2:].abs().max().item() == 0.0
+    assert layers[4][0][2:].abs().max().item() == 0.0
+    # parameters round-trip through load_params
+    net2 = v.Surrogate(H, W, max_batch=B, seed=99)
+    net2.load_params(p)
+    assert torch.equal(net2.forward(u), net.forward(u))
+    net.close()
+    net2.close()
