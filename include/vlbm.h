@@ -290,33 +290,59 @@ int vlbm_sur_conv3x3(const void* X, const void* W, const float* bias, void* Y, v
 int vlbm_sur_conv3x3_wgrad(const void* X, const void* dZ, float* G, float* Gb, int64_t B, int64_t H, int64_t Wd,
                            int32_t cin, int32_t cout, int32_t* err_dev, void* stream);
 
-/* ---- learned surrogate (Section 6 of the paper) ----------------------------
- * A five-layer fully convolutional network with periodic 3x3 kernels,
- * 64 hidden channels and GELU, that maps a velocity field u [B][2][H][W]
- * (FP32, device) to an increment du of the same shape; the caller advances
- * u(t + T) = u(t) + S du with its own step T and scale S.  Weights are BF16
- * copies of FP32 master parameters, activations BF16, every product
+/* ---- learned surrogate (an extension: the paper has no counterpart) ---------
+ * A five-layer fully convolutional network with periodic 3x3 kernels, 64
+ * hidden channels and GELU, mapping a coarse state u [B][C][H][W] (FP32,
+ * device; C = channels, e.g. u_x, u_y and the pressure potential phi) to an
+ * increment of the same shape.  The input is multiplied per channel by
+ * in_scale before the network, its output by out_scale after it, so that
+ * vlbm_sur_advance computes u + out_scale * net(in_scale * u).  Weights are
+ * BF16 copies of FP32 master parameters, activations BF16, every product
  * accumulated in FP32 on the tensor cores.  Training minimises the mean
- * squared error against target increments with Adam (beta1 = 0.9,
- * beta2 = 0.999, eps = 1e-8).  The handle owns all its device memory
- * (parameters, Adam moments and activations for max_batch fields) and works
- * on the stream given at creation. */
+ * squared error of net(in_scale * u) against a target increment already
+ * divided by out_scale, with Adam (beta1 = 0.9, beta2 = 0.999, eps = 1e-8).
+ * The handle owns all its device memory (parameters, Adam moments and
+ * activations for max_batch states) and works on the stream given at creation. */
 typedef struct vlbm_sur vlbm_sur;
 
-/* Seeded initialisation (uniform, scaled by the fan-in).  Synchronises. */
-int vlbm_sur_create(int32_t H, int32_t W, int32_t max_batch, uint64_t seed, void* stream, vlbm_sur** out);
+/* Derived input channel: the periodic central-difference divergence of
+ * channels 0, 1 (unit spacing), taken in FP32 before the input is rounded to
+ * BF16.  It becomes input channel `channels`. */
+#define VLBM_SUR_FEATURE_DIV 1
+
+/* 1 <= channels, channels + derived features <= 16, H W max_batch < 2^31.
+ * features: 0 or VLBM_SUR_FEATURE_DIV (needs channels >= 2).  Seeded
+ * initialisation (uniform, scaled by the fan-in), scales 1.  Synchronises. */
+int vlbm_sur_create(int32_t H, int32_t W, int32_t channels, int32_t features, int32_t max_batch, uint64_t seed,
+                    void* stream, vlbm_sur** out);
 void vlbm_sur_destroy(vlbm_sur* s);
+/* Per-channel input factors (host array of channels + derived features floats,
+ * the derived ones last) and output factors (host array of `channels`
+ * floats); NULL = all 1. */
+int vlbm_sur_set_scaling(vlbm_sur* s, const float* in_scale, const float* out_scale);
+/* Gaussian noise added to the network's inputs in vlbm_sur_train_step only
+ * (after the input factors, so in units of the scaled inputs): standard
+ * deviation sigma[c] per input channel (host array of channels + derived
+ * features floats, >= 0; NULL = none), drawn from a counter-based generator
+ * seeded by `seed`, a fresh draw for every step, pixel and channel.
+ * Synchronises. */
+int vlbm_sur_set_train_noise(vlbm_sur* s, const float* sigma, uint64_t seed);
 /* Number of FP32 parameters: per layer the weights [cout][9][cin] then the
  * bias [cout], layers in order, with (cin, cout) = (16,64), (64,64), (64,64),
- * (64,64), (64,16); input channels 2..15 of the first layer and output
- * channels 2..15 of the last are padding and stay zero. */
+ * (64,64), (64,16); input channels beyond channels + derived features of the
+ * first layer and output channels >= `channels` of the last are padding and
+ * stay zero. */
 int64_t vlbm_sur_num_params(const vlbm_sur* s);
-/* du = net(u) for 1 <= batch <= max_batch fields; device pointers; asynchronous. */
+/* du = net(in_scale * u) (no output scaling) for 1 <= batch <= max_batch
+ * states; device pointers; asynchronous. */
 int vlbm_sur_forward(vlbm_sur* s, const float* u, float* du, int32_t batch);
-/* One Adam step on the mean squared error of net(u) against target (both
- * [batch][2][H][W] FP32 device arrays) with learning rate lr.  When loss is
- * not NULL the loss before the update is written there (host float) and the
- * call synchronises; otherwise it is asynchronous. */
+/* One surrogate step: u_next = u + out_scale * net(in_scale * u); u_next may
+ * alias u.  Asynchronous. */
+int vlbm_sur_advance(vlbm_sur* s, const float* u, float* u_next, int32_t batch);
+/* One Adam step on the mean squared error of net(in_scale * u) against target
+ * (both [batch][C][H][W] FP32 device arrays) with learning rate lr.  When
+ * loss is not NULL the loss before the update is written there (host float)
+ * and the call synchronises; otherwise it is asynchronous. */
 int vlbm_sur_train_step(vlbm_sur* s, const float* u, const float* target, int32_t batch, float lr, float* loss);
 /* Copy the FP32 parameters (or the gradients of the last train step) to dst;
  * set_params also resets Adam's moments.  Any pointer kind; synchronise. */
@@ -325,6 +351,29 @@ int vlbm_sur_get_grads(vlbm_sur* s, float* dst);
 int vlbm_sur_set_params(vlbm_sur* s, const float* src);
 /* VLBM_ETIMEOUT if a wait for the tensor core gave up since creation; synchronises. */
 int vlbm_sur_status(vlbm_sur* s);
+
+/* ---- field utilities of the surrogate's data path (not operations of the paper)
+ * Average pooling of in [B][C][H factor][W factor] to out [B][C][H][W], FP32
+ * device arrays (the coarse-graining of fine lattice fields). */
+int vlbm_field_pool(const float* in, float* out, int64_t B, int64_t C, int64_t H, int64_t W, int32_t factor,
+                    void* stream);
+/* Training pairs from a store of consecutive states snaps [n][C][H][W]:
+ * u[b] = snaps[idx[b]], target[b][c] = (snaps[idx[b]+1][c] - snaps[idx[b]][c]) * inv_scale[c],
+ * idx a device int64 array of batch entries with idx[b] + 1 < n (not
+ * checked), inv_scale a host array of C floats. */
+int vlbm_sur_gather_pairs(const float* snaps, const int64_t* idx, float* u, float* target, int32_t channels,
+                          int64_t H, int64_t W, int32_t batch, const float* inv_scale, void* stream);
+/* Per-state statistics of the velocity channels 0, 1 of u [batch][channels][H][W]
+ * (periodic, unit spacing, central differences) into out [batch][3] FP64
+ * device array: kinetic energy sum |u|^2 / 2, sum of squared divergence, sum
+ * of |grad u|^2.  The surrogate's rollout check reads these.  Asynchronous. */
+int vlbm_field_stats(const float* u, double* out, int32_t batch, int32_t channels, int64_t H, int64_t W,
+                     void* stream);
+/* Per-field error sums over the first n FP32 values of nfields fields that
+ * lie ld values apart (device arrays a, b): out[f][0] = sum (a - b)^2,
+ * out[f][1] = sum b^2, FP64 device array out [nfields][2].  Asynchronous. */
+int vlbm_field_diff_norms(const float* a, const float* b, double* out, int32_t nfields, int64_t n, int64_t ld,
+                          void* stream);
 
 /* Static text of a status code; message of the last failure of h. */
 const char* vlbm_strerror(int code);

@@ -176,18 +176,24 @@ class Batch:
 
 
 class Surrogate:
-    """The learned surrogate of Section 6 (a vlbm_sur): five periodic 3x3 convolutions with
-    64 hidden channels and GELU, BF16 weights and activations, FP32 accumulation, trained with Adam.
+    """The learned surrogate (a vlbm_sur; an extension the paper has no counterpart for): five
+    periodic 3x3 convolutions with 64 hidden channels and GELU, BF16 weights and activations, FP32
+    accumulation, trained with Adam.
 
-    forward(u) maps velocity fields u (B, 2, H, W) FP32 on the device to increments du of the
-    same shape; train_step(u, target, lr) takes one Adam step on the mean squared error.
+    States are (B, channels, H, W) FP32 CUDA tensors.  With divergence_input the network also
+    reads in_scale[channels] times the divergence of channels 0, 1.  forward(u) = net(in_scale u);
+    advance(u) = u + out_scale net(in_scale u); train_step(u, target, lr) takes one Adam step on
+    the mean squared error of net(in_scale u) against target (an increment divided by out_scale).
     """
 
     LAYERS = ((16, 64), (64, 64), (64, 64), (64, 64), (64, 16))
 
-    def __init__(self, H, W, max_batch, seed=0, stream=None):
-        self.H, self.W, self.max_batch = int(H), int(W), int(max_batch)
-        self.handle = _binding.vlbm_sur_create(self.H, self.W, self.max_batch, int(seed), stream)
+    def __init__(self, H, W, max_batch, channels=2, divergence_input=False, seed=0, stream=None):
+        self.H, self.W, self.max_batch, self.channels = int(H), int(W), int(max_batch), int(channels)
+        features = _binding.VLBM_SUR_FEATURE_DIV if divergence_input else 0
+        self.inputs = self.channels + (1 if divergence_input else 0)
+        self.handle = _binding.vlbm_sur_create(self.H, self.W, self.channels, features, self.max_batch, int(seed),
+                                               stream)
         self.num_params = _binding.vlbm_sur_num_params(self.handle)
 
     def close(self):
@@ -201,10 +207,18 @@ class Surrogate:
         except Exception:
             pass
 
+    def set_scaling(self, in_scale=None, out_scale=None):
+        _binding.vlbm_sur_set_scaling(self.handle, in_scale, out_scale)
+
+    def set_train_noise(self, sigma=None, seed=0):
+        """Gaussian noise (std per input channel, in scaled-input units) added to training inputs."""
+        _binding.vlbm_sur_set_train_noise(self.handle, sigma, seed)
+
     def _check_fields(self, u):
         if u.dtype.itemsize != 4 or not u.is_cuda or not u.is_contiguous() or u.dim() != 4 \
-                or tuple(u.shape[1:]) != (2, self.H, self.W) or not 1 <= u.shape[0] <= self.max_batch:
-            raise ValueError(f"expected contiguous float32 CUDA fields (B<= {self.max_batch}, 2, {self.H}, {self.W})")
+                or tuple(u.shape[1:]) != (self.channels, self.H, self.W) or not 1 <= u.shape[0] <= self.max_batch:
+            raise ValueError(f"expected contiguous float32 CUDA states (B <= {self.max_batch}, {self.channels}, "
+                             f"{self.H}, {self.W})")
 
     def forward(self, u, out=None):
         import torch
@@ -212,6 +226,14 @@ class Surrogate:
         du = torch.empty_like(u) if out is None else out
         _binding.vlbm_sur_forward(self.handle, u, du, u.shape[0])
         return du
+
+    def advance(self, u, out=None):
+        """u + out_scale * net(in_scale * u) (out may be u itself)."""
+        import torch
+        self._check_fields(u)
+        nxt = torch.empty_like(u) if out is None else out
+        _binding.vlbm_sur_advance(self.handle, u, nxt, u.shape[0])
+        return nxt
 
     def train_step(self, u, target, lr, want_loss=True):
         self._check_fields(u)

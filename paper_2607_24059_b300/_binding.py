@@ -64,7 +64,9 @@ EXPORTED = [
     "vlbm_batch_invariants", "vlbm_batch_set_config", "vlbm_batch_autotune", "vlbm_batch_info",
     "vlbm_batch_last_error", "vlbm_tc_gemm_bf16", "vlbm_sur_conv3x3", "vlbm_sur_conv3x3_wgrad",
     "vlbm_sur_create", "vlbm_sur_destroy", "vlbm_sur_num_params", "vlbm_sur_forward", "vlbm_sur_train_step",
-    "vlbm_sur_get_params", "vlbm_sur_get_grads", "vlbm_sur_set_params", "vlbm_sur_status",
+    "vlbm_sur_get_params", "vlbm_sur_get_grads", "vlbm_sur_set_params", "vlbm_sur_status", "vlbm_sur_advance",
+    "vlbm_sur_set_scaling", "vlbm_sur_set_train_noise",
+    "vlbm_field_pool", "vlbm_sur_gather_pairs", "vlbm_field_stats", "vlbm_field_diff_norms",
 ]
 
 
@@ -130,8 +132,10 @@ lib.vlbm_sur_conv3x3.argtypes = [_V, _V, _V, _V, _V, ctypes.c_int64, ctypes.c_in
                                  ctypes.c_int32, ctypes.c_int32, _V, _V]
 lib.vlbm_sur_conv3x3_wgrad.argtypes = [_V, _V, _V, _V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                        ctypes.c_int32, _V, _V]
-lib.vlbm_sur_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _V,
-                                ctypes.POINTER(_H)]
+lib.vlbm_sur_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                ctypes.c_uint64, _V, ctypes.POINTER(_H)]
+lib.vlbm_sur_set_scaling.argtypes = [_H, _V, _V]
+lib.vlbm_sur_set_train_noise.argtypes = [_H, _V, ctypes.c_uint64]
 lib.vlbm_sur_destroy.argtypes = [_H]
 lib.vlbm_sur_destroy.restype = None
 lib.vlbm_sur_num_params.argtypes = [_H]
@@ -142,6 +146,13 @@ lib.vlbm_sur_get_params.argtypes = [_H, _V]
 lib.vlbm_sur_get_grads.argtypes = [_H, _V]
 lib.vlbm_sur_set_params.argtypes = [_H, _V]
 lib.vlbm_sur_status.argtypes = [_H]
+lib.vlbm_sur_advance.argtypes = [_H, _V, _V, ctypes.c_int32]
+lib.vlbm_field_pool.argtypes = [_V, _V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                _V]
+lib.vlbm_sur_gather_pairs.argtypes = [_V, _V, _V, _V, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                      _V, _V]
+lib.vlbm_field_stats.argtypes = [_V, _V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _V]
+lib.vlbm_field_diff_norms.argtypes = [_V, _V, _V, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _V]
 lib.vlbm_strerror.argtypes = [ctypes.c_int]
 lib.vlbm_strerror.restype = ctypes.c_char_p
 lib.vlbm_last_error.argtypes = [_H]
@@ -430,15 +441,35 @@ def vlbm_sur_conv3x3_wgrad(X, dZ, G, Gb, err, stream=None) -> None:
                                       B, H, Wd, cin, cout, _V(err.data_ptr()), _V(s)), "vlbm_sur_conv3x3_wgrad")
 
 
-def vlbm_sur_create(H: int, W: int, max_batch: int, seed: int, stream=None):
+VLBM_SUR_FEATURE_DIV = 1
+
+
+def vlbm_sur_create(H: int, W: int, channels: int, features: int, max_batch: int, seed: int, stream=None):
     h = _H()
     s = current_stream() if stream is None else stream
-    _check(lib.vlbm_sur_create(H, W, max_batch, seed, _V(s), ctypes.byref(h)), "vlbm_sur_create")
+    _check(lib.vlbm_sur_create(H, W, channels, features, max_batch, seed, _V(s), ctypes.byref(h)), "vlbm_sur_create")
     return h
+
+
+def _float_array(vals):
+    if vals is None:
+        return None
+    vals = [float(x) for x in vals]
+    return (ctypes.c_float * len(vals))(*vals)
+
+
+def vlbm_sur_set_scaling(h, in_scale=None, out_scale=None) -> None:
+    """Per-channel input and output factors (sequences of floats; None = 1)."""
+    _check(lib.vlbm_sur_set_scaling(h, _float_array(in_scale), _float_array(out_scale)), "vlbm_sur_set_scaling")
 
 
 def vlbm_sur_destroy(h) -> None:
     lib.vlbm_sur_destroy(h)
+
+
+def vlbm_sur_set_train_noise(h, sigma=None, seed: int = 0) -> None:
+    """Per-input-channel standard deviation of the training-input noise (None = off)."""
+    _check(lib.vlbm_sur_set_train_noise(h, _float_array(sigma), int(seed)), "vlbm_sur_set_train_noise")
 
 
 def vlbm_sur_num_params(h) -> int:
@@ -470,6 +501,49 @@ def vlbm_sur_set_params(h, src) -> None:
 
 def vlbm_sur_status(h) -> None:
     _check(lib.vlbm_sur_status(h), "vlbm_sur_status")
+
+
+def vlbm_sur_advance(h, u, u_next, batch: int) -> None:
+    _check(lib.vlbm_sur_advance(h, _V(u.data_ptr()), _V(u_next.data_ptr()), batch), "vlbm_sur_advance")
+
+
+def vlbm_field_pool(x, out, factor: int, stream=None) -> None:
+    """Average-pool x (B, C, H f, W f) fp32 into out (B, C, H, W) fp32 on the device."""
+    B, C, H, W = out.shape
+    s = current_stream() if stream is None else stream
+    _check(lib.vlbm_field_pool(_V(x.data_ptr()), _V(out.data_ptr()), B, C, H, W, factor, _V(s)), "vlbm_field_pool")
+
+
+def vlbm_sur_gather_pairs(snaps, idx, u, target, inv_scale, stream=None) -> None:
+    """u[b] = snaps[idx[b]], target[b][c] = (snaps[idx[b]+1][c] - snaps[idx[b]][c]) * inv_scale[c]
+    (device arrays; inv_scale a sequence of C floats or one float for every channel)."""
+    B, C, H, W = u.shape
+    if isinstance(inv_scale, (int, float)):
+        inv_scale = [inv_scale] * C
+    if len(inv_scale) != C:
+        raise ValueError("one inverse scale per channel")
+    s = current_stream() if stream is None else stream
+    _check(lib.vlbm_sur_gather_pairs(_V(snaps.data_ptr()), _V(idx.data_ptr()), _V(u.data_ptr()),
+                                     _V(target.data_ptr()), C, H, W, B, _float_array(inv_scale), _V(s)),
+           "vlbm_sur_gather_pairs")
+
+
+def vlbm_field_stats(u, out, stream=None) -> None:
+    """out (B, 3) fp64 = per-state energy, squared divergence and squared gradient sums of the
+    velocity channels 0, 1 of u (B, C, H, W)."""
+    B, C, H, W = u.shape
+    s = current_stream() if stream is None else stream
+    _check(lib.vlbm_field_stats(_V(u.data_ptr()), _V(out.data_ptr()), B, C, H, W, _V(s)), "vlbm_field_stats")
+
+
+def vlbm_field_diff_norms(a, b, out, n=None, stream=None) -> None:
+    """out (F, 2) fp64 = per-field sum (a - b)^2 and sum b^2 over the first n values (default: all)
+    of each field of a, b (F, ...) fp32 on the device."""
+    F = a.shape[0]
+    ld = a.numel() // F
+    s = current_stream() if stream is None else stream
+    _check(lib.vlbm_field_diff_norms(_V(a.data_ptr()), _V(b.data_ptr()), _V(out.data_ptr()), F,
+                                     ld if n is None else int(n), ld, _V(s)), "vlbm_field_diff_norms")
 
 
 def vlbm_strerror(code: int) -> str:

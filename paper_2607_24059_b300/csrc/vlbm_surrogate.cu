@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <new>
@@ -367,34 +368,176 @@ __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * __expf(-0.5f * z * z);
 }
 
-// u [B][2][H][W] FP32 -> X [B][H][W][16] BF16 (channels 2..15 zero)
-__global__ void k_pack_input(const float* __restrict__ u, __nv_bfloat16* __restrict__ X, long long plane, long long npix) {
+// Per-channel factors passed by value (channels <= 16).
+struct ChanScale {
+    float v[16];
+};
+
+// u [B][C][H][W] FP32 -> X [B][H][W][16] BF16, channel c scaled by in.v[c]; when DIV, channel C
+// holds in.v[C] times the periodic central-difference divergence of channels 0, 1 (unit spacing),
+// taken in FP32 before the rounding to BF16 (it is ~1e-3 of the velocity, below BF16's resolution
+// of the velocity itself).  Remaining channels are zero.
+// Training noise: a standard normal draw per (step, pixel, channel) from a counter-based
+// generator (the splitmix64 finaliser of Steele, Lea and Flood, applied to the counter),
+// turned into a normal deviate by the Box-Muller transform.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ float normal_draw(uint64_t key) {
+    const uint64_t h1 = mix64(key * 2 + 1), h2 = mix64(key * 2 + 2);
+    const float u1 = ((float)(h1 >> 40) + 1.0f) * (1.0f / 16777216.0f);      // (0, 1]
+    const float u2 = (float)(h2 >> 40) * (1.0f / 16777216.0f);               // [0, 1)
+    return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+template <bool DIV>
+__global__ void k_pack_input(const float* __restrict__ u, __nv_bfloat16* __restrict__ X, int H, int W, long long npix,
+                             int C, ChanScale in, const ChanScale* noise, uint64_t noise_key) {
+    const long long plane = (long long)H * W;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
     const long long b = p / plane, q = p - b * plane;
     __align__(16) __nv_bfloat16 e[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) e[c] = __float2bfloat16_rn(0.0f);
-    e[0] = __float2bfloat16_rn(u[(b * 2 + 0) * plane + q]);
-    e[1] = __float2bfloat16_rn(u[(b * 2 + 1) * plane + q]);
+    for (int c = 0; c < 16; ++c)
+        e[c] = __float2bfloat16_rn(c < C ? u[(b * C + c) * plane + q] * in.v[c] : 0.0f);
+    if (DIV) {
+        const int x = (int)(q % W), y = (int)(q / W);
+        const int xp = x + 1 == W ? 0 : x + 1, xm = x == 0 ? W - 1 : x - 1;
+        const int yp = y + 1 == H ? 0 : y + 1, ym = y == 0 ? H - 1 : y - 1;
+        const float* ux = u + b * C * plane;
+        const float* uy = ux + plane;
+        const float d = 0.5f * (ux[(long long)y * W + xp] - ux[(long long)y * W + xm]) +
+                        0.5f * (uy[(long long)yp * W + x] - uy[(long long)ym * W + x]);
+        e[C] = __float2bfloat16_rn(d * in.v[C]);
+    }
+    if (noise) {
+        const int n_in = C + (DIV ? 1 : 0);
+        for (int c = 0; c < n_in; ++c) {
+            const float sg = noise->v[c];
+            if (sg != 0.0f) {
+                const float x = __bfloat162float(e[c]) + sg * normal_draw(noise_key + (uint64_t)(p * 16 + c));
+                e[c] = __float2bfloat16_rn(x);
+            }
+        }
+    }
     reinterpret_cast<uint4*>(X + p * 16)[0] = reinterpret_cast<const uint4*>(e)[0];
     reinterpret_cast<uint4*>(X + p * 16)[1] = reinterpret_cast<const uint4*>(e)[1];
 }
 
-// Y [B][H][W][16] BF16 (channels 0, 1) -> du [B][2][H][W] FP32
-__global__ void k_unpack_output(const __nv_bfloat16* __restrict__ Y, float* __restrict__ du, long long plane,
-                                long long npix) {
+// Y [B][H][W][16] BF16 (channels 0 .. C-1) -> out [B][C][H][W] FP32 = base + sc.v[c] Y
+// (base may be NULL: out = sc.v[c] Y).  out may alias base.
+__global__ void k_unpack_output(const __nv_bfloat16* __restrict__ Y, const float* base, float* out, ChanScale sc,
+                                long long plane, long long npix, int C) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
     const long long b = p / plane, q = p - b * plane;
-    du[(b * 2 + 0) * plane + q] = __bfloat162float(Y[p * 16 + 0]);
-    du[(b * 2 + 1) * plane + q] = __bfloat162float(Y[p * 16 + 1]);
+    for (int c = 0; c < C; ++c) {
+        const long long i = (b * C + c) * plane + q;
+        const float y = sc.v[c] * __bfloat162float(Y[p * 16 + c]);
+        out[i] = base ? base[i] + y : y;
+    }
 }
 
-// Mean-squared loss of output channels 0, 1 against t [B][2][H][W]; dY (16 ch) and sum of squares.
+// Average pooling by an integer factor F of fields [B][C][H F][W F] -> [B][C][H][W], FP32;
+// the F x F sum is taken in a fixed order (rows, then columns) in FP32.
+__global__ void k_pool(const float* __restrict__ in, float* __restrict__ out, long long n_out, int H, int W, int F) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_out) return;
+    const int x = (int)(i % W);
+    const long long r = i / W;
+    const int y = (int)(r % H);
+    const long long bc = r / H;
+    const long long Wf = (long long)W * F;
+    const float* src = in + (bc * H * F + (long long)y * F) * Wf + (long long)x * F;
+    float acc = 0.0f;
+    for (int dy = 0; dy < F; ++dy)
+        for (int dx = 0; dx < F; ++dx) acc += src[dy * Wf + dx];
+    out[i] = acc / (float)(F * F);
+}
+
+// Training pairs from a snapshot store snaps [n][C][plane]: for entry b,
+// u[b] = snaps[idx[b]], target[b][c] = (snaps[idx[b] + 1][c] - snaps[idx[b]][c]) * inv.v[c].
+__global__ void k_gather_pairs(const float* __restrict__ snaps, const int64_t* __restrict__ idx, float* __restrict__ u,
+                               float* __restrict__ target, long long plane, int C, int batch, ChanScale inv) {
+    const long long per_field = plane * C;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= per_field * batch) return;
+    const long long b = i / per_field, q = i - b * per_field;
+    const long long k = idx[b];
+    const float a = snaps[k * per_field + q], c = snaps[(k + 1) * per_field + q];
+    u[i] = a;
+    target[i] = (c - a) * inv.v[q / plane];
+}
+
+// Per-field sums of squares of a - b and of b: out[f][0] += sum (a - b)^2,
+// out[f][1] += sum b^2 over the first n values of field f, fields ld values apart
+// (FP64 atomics; out zeroed by the caller).
+__global__ void k_diff_norms(const float* __restrict__ a, const float* __restrict__ b, double* __restrict__ out,
+                             long long n, long long ld) {
+    const int f = blockIdx.y;
+    const float* pa = a + (long long)f * ld;
+    const float* pb = b + (long long)f * ld;
+    double d = 0.0, r = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double x = (double)pa[i] - (double)pb[i], y = pb[i];
+        d += x * x;
+        r += y * y;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        d += __shfl_xor_sync(0xffffffffu, d, off);
+        r += __shfl_xor_sync(0xffffffffu, r, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out + 2 * f, d);
+        atomicAdd(out + 2 * f + 1, r);
+    }
+}
+
+// Per-field statistics of the velocity channels 0, 1 of u [B][C][H][W] (periodic, unit spacing):
+//   out[b][0] = sum (u_x^2 + u_y^2) / 2
+//   out[b][1] = sum (d_x u_x + d_y u_y)^2            (central differences)
+//   out[b][2] = sum |grad u|^2                        (same differences, all four)
+// accumulated in FP64 with atomics into out (zeroed by the caller).
+__global__ void k_field_stats(const float* __restrict__ u, double* __restrict__ out, int C, int H, int W) {
+    const int b = blockIdx.y;
+    const long long plane = (long long)H * W;
+    const float* ux = u + (long long)b * C * plane;
+    const float* uy = ux + plane;
+    double e = 0.0, d = 0.0, g = 0.0;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < plane; q += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(q % W), y = (int)(q / W);
+        const int xp = x + 1 == W ? 0 : x + 1, xm = x == 0 ? W - 1 : x - 1;
+        const int yp = y + 1 == H ? 0 : y + 1, ym = y == 0 ? H - 1 : y - 1;
+        const long long r = (long long)y * W;
+        const float a = ux[q], c = uy[q];
+        const float axx = 0.5f * (ux[r + xp] - ux[r + xm]), axy = 0.5f * (ux[(long long)yp * W + x] - ux[(long long)ym * W + x]);
+        const float cxx = 0.5f * (uy[r + xp] - uy[r + xm]), cxy = 0.5f * (uy[(long long)yp * W + x] - uy[(long long)ym * W + x]);
+        e += 0.5 * ((double)a * a + (double)c * c);
+        const double dv = (double)axx + (double)cxy;
+        d += dv * dv;
+        g += (double)axx * axx + (double)axy * axy + (double)cxx * cxx + (double)cxy * cxy;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, off);
+        d += __shfl_xor_sync(0xffffffffu, d, off);
+        g += __shfl_xor_sync(0xffffffffu, g, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out + b * 3 + 0, e);
+        atomicAdd(out + b * 3 + 1, d);
+        atomicAdd(out + b * 3 + 2, g);
+    }
+}
+
+// Mean-squared loss of output channels 0 .. C-1 against t [B][C][H][W]; dY (16 ch) and sum of squares.
 __global__ void k_mse_grad(const __nv_bfloat16* __restrict__ Y, const float* __restrict__ t,
                            __nv_bfloat16* __restrict__ dY, double* __restrict__ sse, long long plane, long long npix,
-                           float inv_count) {
+                           float inv_count, int C) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     float local = 0.0f;
     if (p < npix) {
@@ -402,9 +545,8 @@ __global__ void k_mse_grad(const __nv_bfloat16* __restrict__ Y, const float* __r
         __align__(16) __nv_bfloat16 e[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) e[c] = __float2bfloat16_rn(0.0f);
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const float d = __bfloat162float(Y[p * 16 + c]) - t[(b * 2 + c) * plane + q];
+        for (int c = 0; c < C; ++c) {
+            const float d = __bfloat162float(Y[p * 16 + c]) - t[(b * C + c) * plane + q];
             local += d * d;
             e[c] = __float2bfloat16_rn(2.0f * d * inv_count);
         }
@@ -518,7 +660,12 @@ int wgrad_any(int cin, int cout, const void* X, const void* dZ, float* G, float*
 }  // namespace
 
 struct vlbm_sur {
-    int H = 0, W = 0, maxB = 0;
+    int H = 0, W = 0, C = 2, maxB = 0;
+    int features = 0, n_in = 2;
+    ChanScale* noise_dev = nullptr;
+    bool use_noise = false;
+    uint64_t noise_seed = 0, noise_draws = 0;
+    ChanScale in_scale{}, out_scale{};
     cudaStream_t stream = nullptr;
     long long off_w[kLayers] = {}, off_b[kLayers] = {}, nparams = 0;
     float* params = nullptr;
@@ -540,8 +687,15 @@ struct vlbm_sur {
 
 namespace {
 
+uint64_t mix64_host(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 void free_sur(vlbm_sur* s) {
-    void* ptrs[] = {s->params, s->grads, s->adam_m, s->adam_v, s->X0, s->dA, s->dB, s->zero_bias, s->sse, s->err};
+    void* ptrs[] = {s->params, s->grads, s->adam_m, s->adam_v, s->X0,  s->dA,
+                    s->dB,     s->zero_bias, s->sse, s->err,    s->noise_dev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int l = 0; l < kLayers; ++l) {
@@ -569,10 +723,23 @@ int check_err(vlbm_sur* s) {
     return e ? VLBM_ETIMEOUT : VLBM_OK;
 }
 
-// Forward pass of `batch` fields; keeps the pre-activations when `train`.
+// Forward pass of `batch` fields; keeps the pre-activations (and adds the training
+// noise to the inputs, when set) when `train`.
 int sur_forward(vlbm_sur* s, const float* u, int batch, bool train) {
     const long long plane = (long long)s->H * s->W, npix = plane * batch;
-    k_pack_input<<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(u, s->X0, plane, npix);
+    const ChanScale* noise = nullptr;
+    uint64_t key = 0;
+    if (train && s->use_noise) {
+        noise = s->noise_dev;
+        key = mix64_host(s->noise_seed) + s->noise_draws;
+        s->noise_draws += (uint64_t)npix * 16;
+    }
+    if (s->features & VLBM_SUR_FEATURE_DIV)
+        k_pack_input<true><<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(u, s->X0, s->H, s->W, npix, s->C,
+                                                                                  s->in_scale, noise, key);
+    else
+        k_pack_input<false><<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(u, s->X0, s->H, s->W, npix, s->C,
+                                                                                   s->in_scale, noise, key);
     const void* x = s->X0;
     for (int l = 0; l < kLayers; ++l) {
         const bool act = l < kLayers - 1;
@@ -593,13 +760,22 @@ extern "C" int vlbm_sur_conv3x3_wgrad(const void* X, const void* dZ, float* G, f
     return wgrad_any(cin, cout, X, dZ, G, Gb, B, H, Wd, err_dev, (cudaStream_t)stream);
 }
 
-extern "C" int vlbm_sur_create(int32_t H, int32_t W, int32_t max_batch, uint64_t seed, void* stream, vlbm_sur** out) {
-    if (!out || H < 1 || W < 1 || max_batch < 1) return VLBM_EINVAL;
+extern "C" int vlbm_sur_create(int32_t H, int32_t W, int32_t channels, int32_t features, int32_t max_batch,
+                               uint64_t seed, void* stream, vlbm_sur** out) {
+    if (!out || H < 1 || W < 1 || max_batch < 1 || channels < 1 || channels > 16) return VLBM_EINVAL;
+    if (features & ~VLBM_SUR_FEATURE_DIV) return VLBM_EINVAL;
+    const int n_in = channels + ((features & VLBM_SUR_FEATURE_DIV) ? 1 : 0);
+    if (n_in > 16 || ((features & VLBM_SUR_FEATURE_DIV) && channels < 2)) return VLBM_EINVAL;
+    if ((long long)H * W * max_batch >= (1ll << 31)) return VLBM_EINVAL;
     *out = nullptr;
     vlbm_sur* s = new (std::nothrow) vlbm_sur();
     if (!s) return VLBM_ENOMEM;
     s->H = H;
     s->W = W;
+    s->C = channels;
+    s->features = features;
+    s->n_in = n_in;
+    for (int c = 0; c < 16; ++c) s->in_scale.v[c] = s->out_scale.v[c] = 1.0f;
     s->maxB = max_batch;
     s->stream = (cudaStream_t)stream;
     long long off = 0;
@@ -625,6 +801,7 @@ extern "C" int vlbm_sur_create(int32_t H, int32_t W, int32_t max_batch, uint64_t
     alloc((void**)&s->zero_bias, 64 * 4);
     alloc((void**)&s->sse, sizeof(double));
     alloc((void**)&s->err, sizeof(int));
+    alloc((void**)&s->noise_dev, sizeof(ChanScale));
     for (int l = 0; l < kLayers; ++l) {
         alloc((void**)&s->Wb[l], (size_t)kCout[l] * 9 * kCin[l] * 2);
         alloc((void**)&s->Wflip[l], (size_t)kCout[l] * 9 * kCin[l] * 2);
@@ -638,12 +815,13 @@ extern "C" int vlbm_sur_create(int32_t H, int32_t W, int32_t max_batch, uint64_t
         return VLBM_ENOMEM;
     }
     // seeded initialisation: uniform(-a, a), a = sqrt(6 / fan_in) over the real input
-    // channels; the padded input channels of layer 1 and outputs of layer 5 are 0,
-    // and layer 5 starts at a tenth of that scale so that the first increments are small
+    // channels; the padded input channels of layer 1 and outputs of layer 5 (beyond
+    // `channels`) are 0, and layer 5 starts at a tenth of that scale so that the first
+    // increments are small
     std::vector<float> h(off, 0.0f);
     uint64_t st = seed;
     for (int l = 0; l < kLayers; ++l) {
-        const int real_in = l == 0 ? 2 : kCin[l], real_out = l == kLayers - 1 ? 2 : kCout[l];
+        const int real_in = l == 0 ? n_in : kCin[l], real_out = l == kLayers - 1 ? channels : kCout[l];
         const float a = std::sqrt(6.0f / (9.0f * real_in)) * (l == kLayers - 1 ? 0.1f : 1.0f);
         for (int co = 0; co < kCout[l]; ++co)
             for (int t = 0; t < 9; ++t)
@@ -684,7 +862,97 @@ extern "C" int vlbm_sur_forward(vlbm_sur* s, const float* u, float* du, int32_t 
     int rc = sur_forward(s, u, batch, false);
     if (rc) return rc;
     const long long plane = (long long)s->H * s->W, npix = plane * batch;
-    k_unpack_output<<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(s->Y[kLayers - 1], du, plane, npix);
+    ChanScale one{};
+    for (int c = 0; c < 16; ++c) one.v[c] = 1.0f;
+    k_unpack_output<<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(s->Y[kLayers - 1], nullptr, du, one,
+                                                                            plane, npix, s->C);
+    return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
+}
+
+extern "C" int vlbm_sur_set_scaling(vlbm_sur* s, const float* in_scale, const float* out_scale) {
+    if (!s) return VLBM_EINVAL;
+    for (int c = 0; c < s->n_in; ++c) {
+        const float a = in_scale ? in_scale[c] : 1.0f;
+        if (!std::isfinite(a)) return VLBM_EINVAL;
+        s->in_scale.v[c] = a;
+    }
+    for (int c = 0; c < s->C; ++c) {
+        const float b = out_scale ? out_scale[c] : 1.0f;
+        if (!std::isfinite(b)) return VLBM_EINVAL;
+        s->out_scale.v[c] = b;
+    }
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_sur_set_train_noise(vlbm_sur* s, const float* sigma, uint64_t seed) {
+    if (!s) return VLBM_EINVAL;
+    ChanScale h{};
+    bool any = false;
+    for (int c = 0; c < s->n_in; ++c) {
+        const float v = sigma ? sigma[c] : 0.0f;
+        if (!(v >= 0.0f) || !std::isfinite(v)) return VLBM_EINVAL;
+        h.v[c] = v;
+        any = any || v > 0.0f;
+    }
+    if (cudaMemcpyAsync(s->noise_dev, &h, sizeof(h), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return VLBM_ECUDA;
+    s->use_noise = any;
+    s->noise_seed = seed;
+    s->noise_draws = 0;
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_sur_advance(vlbm_sur* s, const float* u, float* u_next, int32_t batch) {
+    if (!s || !u || !u_next || batch < 1 || batch > s->maxB) return VLBM_EINVAL;
+    int rc = sur_forward(s, u, batch, false);
+    if (rc) return rc;
+    const long long plane = (long long)s->H * s->W, npix = plane * batch;
+    k_unpack_output<<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(s->Y[kLayers - 1], u, u_next,
+                                                                            s->out_scale, plane, npix, s->C);
+    return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
+}
+
+extern "C" int vlbm_field_pool(const float* in, float* out, int64_t B, int64_t C, int64_t H, int64_t W, int32_t factor,
+                               void* stream) {
+    if (!in || !out || B < 1 || C < 1 || H < 1 || W < 1 || factor < 1) return VLBM_EINVAL;
+    const long long n = B * C * H * W;
+    k_pool<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, out, n, (int)H, (int)W, factor);
+    return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
+}
+
+extern "C" int vlbm_sur_gather_pairs(const float* snaps, const int64_t* idx, float* u, float* target,
+                                     int32_t channels, int64_t H, int64_t W, int32_t batch, const float* inv_scale,
+                                     void* stream) {
+    if (!snaps || !idx || !u || !target || !inv_scale || channels < 1 || channels > 16 || H < 1 || W < 1 || batch < 1)
+        return VLBM_EINVAL;
+    ChanScale inv{};
+    for (int c = 0; c < channels; ++c) inv.v[c] = inv_scale[c];
+    const long long n = (long long)channels * H * W * batch;
+    k_gather_pairs<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(snaps, idx, u, target, H * W,
+                                                                                   channels, batch, inv);
+    return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
+}
+
+extern "C" int vlbm_field_diff_norms(const float* a, const float* b, double* out, int32_t nfields, int64_t n,
+                                     int64_t ld, void* stream) {
+    if (!a || !b || !out || nfields < 1 || nfields > 65535 || n < 1 || ld < n) return VLBM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(out, 0, sizeof(double) * 2 * nfields, st) != cudaSuccess) return VLBM_ECUDA;
+    const unsigned gx = (unsigned)std::min<long long>((n + 255) / 256, 148);
+    k_diff_norms<<<dim3(gx, nfields), 256, 0, st>>>(a, b, out, n, ld);
+    return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
+}
+
+extern "C" int vlbm_field_stats(const float* u, double* out, int32_t batch, int32_t channels, int64_t H, int64_t W,
+                                void* stream) {
+    if (!u || !out || batch < 1 || batch > 65535 || channels < 2 || H < 1 || W < 1 || H * W >= (1ll << 31))
+        return VLBM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(out, 0, sizeof(double) * 3 * batch, st) != cudaSuccess) return VLBM_ECUDA;
+    const long long plane = H * W;
+    const unsigned gx = (unsigned)std::min<long long>((plane + 255) / 256, 148);
+    k_field_stats<<<dim3(gx, batch), 256, 0, st>>>(u, out, channels, (int)H, (int)W);
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
 }
 
@@ -699,7 +967,7 @@ extern "C" int vlbm_sur_train_step(vlbm_sur* s, const float* u, const float* tar
         return VLBM_ECUDA;
     const unsigned eb = (unsigned)((npix + 255) / 256);
     k_mse_grad<<<eb, 256, 0, s->stream>>>(s->Y[kLayers - 1], target, s->dA, s->sse, plane, npix,
-                                          1.0f / (float)(2 * npix));
+                                          1.0f / (float)((long long)s->C * npix), s->C);
     // backward, last layer first: dA holds dZ of layer l (its pre-activation gradient)
     for (int l = kLayers - 1; l >= 0; --l) {
         const void* xin = l == 0 ? (const void*)s->X0 : (const void*)s->Y[l - 1];
@@ -728,7 +996,7 @@ extern "C" int vlbm_sur_train_step(vlbm_sur* s, const float* u, const float* tar
             return VLBM_ECUDA;
         rc = check_err(s);
         if (rc) return rc;
-        *loss = (float)(h / (double)(2 * npix));
+        *loss = (float)(h / (double)((long long)s->C * npix));
     }
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
 }
