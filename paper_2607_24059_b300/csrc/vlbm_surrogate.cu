@@ -99,137 +99,414 @@ k_tc_gemm_bf16(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restr
 }
 
 // ---------------------------------------------------------------------------
-// 3x3 convolution with periodic padding as an implicit GEMM on tcgen05.
-// Activations are NHWC BF16, weights [COUT][9][CIN] BF16 with tap = 3 (dy + 1)
-// + (dx + 1).  A CTA computes 128 consecutive output pixels (flattened
-// b, y, x) for every output channel: M = 128 pixels, N = COUT, K = 9 CIN.  The
-// weight tile (COUT x 9 CIN) is staged once; for each tap the 128 source pixels'
-// CIN channels are staged and CIN / 16 MMAs accumulate into tensor memory.  The
-// epilogue adds the bias, optionally stores the pre-activation Z, applies GELU
-// when ACT and stores Y.
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// GELU in its tanh form, 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))), with the
+// hardware tanh approximation (tanh.approx.f32, relative error ~2^-11, below the
+// BF16 rounding of every activation).
+__device__ __forceinline__ float tanh_fast(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float kGeluK0 = 0.7978845608028654f;   // sqrt(2 / pi)
+constexpr float kGeluK1 = 0.044715f;
+__device__ __forceinline__ float gelu(float x) {
+    return 0.5f * x * (1.0f + tanh_fast(kGeluK0 * (x + kGeluK1 * x * x * x)));
+}
+__device__ __forceinline__ float gelu_grad(float z) {
+    const float t = tanh_fast(kGeluK0 * (z + kGeluK1 * z * z * z));
+    return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * kGeluK0 * (1.0f + 3.0f * kGeluK1 * z * z);
+}
 
 constexpr int align1k(int b) { return (b + 1023) & ~1023; }
 
+// ---------------------------------------------------------------------------
+// 3x3 convolution with periodic padding as an implicit GEMM on tcgen05.
+//
+// Work unit: image b, a segment of 128 pixels of the row, R consecutive rows,
+// walked by persistent warp-specialised CTAs.  A row segment is the M = 128
+// side of the MMAs; K runs over the input channels of one tap.
+//
+// Input rows ("halo rows": the segment and one pixel either side, wrapped
+// periodically) live in a ring of kRing shared-memory slots, stored channel-
+// granule-major: for each group of 8 channels the 130 pixels' 16 bytes are
+// contiguous.  Consecutive pixels are then 16 bytes apart, so the A operand of
+// a tap with column shift dx - 128 consecutive pixels starting at pixel 1 + dx -
+// is a plain descriptor offset (leading byte offset 130 * 16 between channel
+// granules, stride byte offset 128 between 8-pixel groups).
+//
+// Output rows are computed in groups of G.  Output row j reads halo rows j,
+// j + 1, j + 2 (taps dy = -1, 0, +1), so one halo row i feeds up to three
+// output rows of a group, each through its own tap: the weights are stored
+// per column shift dx as three consecutive blocks [dy = +1; dy = 0; dy = -1]
+// of COUT x CIN, and one MMA with N = COUT x (number of output rows fed)
+// multiplies halo row i by the consecutive blocks of those rows into their
+// consecutive accumulator columns.  For COUT = 64 that is mostly N = 192, at
+// the tensor core's full rate, against N = 64 for one row at a time (measured:
+// 48 cycles per 128 x 64 x 16 MMA, 64 per 128 x 128 x 16).  The accumulator of
+// a group (G COUT columns) is zeroed by the epilogue after reading, so every
+// MMA accumulates.
+//
+// Roles, connected by mbarriers (every wait bounded, plus a shared abort flag):
+//   producer warps  fill halo rows with cp.async, up to kMaxPending rows in
+//                   flight; full[slot] when a row has landed, empty[slot]
+//                   when its last MMA has completed
+//   MMA warp        one thread issues, per halo row of a group, the MMAs of
+//                   the 3 column shifts x CIN / 16 channel slices, then commits
+//                   acc_full[a] at the end of the group
+//   epilogue warps  per output row of a finished group (warp w: TMEM lanes
+//                   32 (w % 4).., half w / 4 of the COUT columns): bias, GELU
+//                   (when ACT), Y (and the pre-activation Z when asked),
+//                   staged through shared memory (16-byte chunks XOR-swizzled
+//                   by pixel) and written as contiguous runs; then the group's
+//                   columns are zeroed and the accumulator released
+constexpr int kEpiWarps = 8;
+constexpr int kProdWarps = 3;
+constexpr int kMmaWarp = kEpiWarps;
+constexpr int kConvThreads = 32 * (kEpiWarps + 1 + kProdWarps);
+constexpr int kHaloPix = 130;
+constexpr int kRing = 6;
+constexpr int kMaxPending = 3;      // halo rows in flight per producer thread (<= kRing - 3)
+
 template <int CIN, int COUT>
-constexpr int conv_smem_bytes() { return align1k(COUT * 9 * CIN * 2) + 128 * CIN * 2; }
+struct ConvRows {
+    static constexpr int G = COUT >= 64 ? 4 : 8;                // output rows per group
+    static constexpr int KT = 9 * CIN;
+    static constexpr int GR = CIN / 8;                          // 16-byte channel granules per pixel
+    static constexpr int kSlot = GR * kHaloPix * 16;            // bytes of one halo row
+    static constexpr int kW = align1k(COUT * KT * 2);           // bytes of the weight blocks
+    static constexpr int KC = COUT / 8;                         // 16-byte chunks of one output pixel
+    static constexpr int kStage = 32 * COUT * 2;                // bytes of one staged 32-pixel block
+    static constexpr int kSmem = kW + kRing * kSlot + 4 * 2 * kStage;
+    static constexpr uint32_t kAcc = G * COUT;                  // accumulator columns of a group
+    static constexpr uint32_t kTmem = 2 * kAcc;                 // two accumulators
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 64, "tile shape");
+    static_assert(kTmem <= 512 && (kTmem & (kTmem - 1)) == 0, "tensor memory");
+    static_assert(3 * COUT <= 256, "MMA N");
+    static_assert((KC & (KC - 1)) == 0, "chunk swizzle needs a power of two");
+    static_assert(kSmem <= 227 * 1024, "shared memory");
+};
+
+// Bounded wait that also gives up once another role has raised `abort`.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    for (long long i = 0; i < kWaitPolls; i += 256) {
+        if (tc::mbar_wait(bar, parity, 256)) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void raise_abort(volatile int* abort, int* err) {
+    *abort = 1;
+    atomicExch(err, 1);
+}
+
+// The work unit sequence every role walks.  A unit of `rows` output rows has
+// ceil(rows / G) groups and reads ceil(rows / G) G + 2 halo rows (rows past
+// the unit wrap periodically; their outputs are discarded).
+struct ConvUnits {
+    int H, Wd, R, G, nseg, nchunk;
+    long long n;
+    __device__ ConvUnits(int B, int H_, int W_, int R_, int G_) : H(H_), Wd(W_), R(R_), G(G_) {
+        nseg = (Wd + 127) / 128;
+        nchunk = (H + R - 1) / R;
+        n = (long long)B * nseg * nchunk;
+    }
+    __device__ void decode(long long unit, int& b, int& y0, int& rows, int& x0) const {
+        const int seg = (int)(unit % nseg);
+        const long long t = unit / nseg;
+        const int chunk = (int)(t % nchunk);
+        b = (int)(t / nchunk);
+        y0 = chunk * R;
+        rows = min(R, H - y0);
+        x0 = seg * 128;
+    }
+    __device__ int groups(int rows) const { return (rows + G - 1) / G; }
+    __device__ int halos(int rows) const { return groups(rows) * G + 2; }
+};
 
 template <int CIN, int COUT, bool ACT, bool STORE_Z>
-__global__ void __launch_bounds__(kTcThreads)
+__global__ void __launch_bounds__(kConvThreads, 1)
 k_conv3x3(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ bias,
-          __nv_bfloat16* __restrict__ Y, __nv_bfloat16* __restrict__ Z, int B, int H, int Wd, int* __restrict__ err) {
-    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 256, "tile shape");
-    constexpr int KT = 9 * CIN;
-    constexpr uint32_t NCOL = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : (COUT <= 128 ? 128 : 256));
+          __nv_bfloat16* __restrict__ Y, __nv_bfloat16* __restrict__ Z, int B, int H, int Wd, int R,
+          int* __restrict__ err) {
+    using Cfg = ConvRows<CIN, COUT>;
+    constexpr int G = Cfg::G;
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* sB = smem;
-    uint8_t* sA = smem + align1k(COUT * KT * 2);
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t full[kRing], empty[kRing], acc_full[2], acc_empty[2], mma_done;
     __shared__ uint32_t s_taddr;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    __shared__ int s_abort;
+    volatile int* abort = &s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) {
-        tc::tmem_alloc(&s_taddr, NCOL);
+        tc::tmem_alloc(&s_taddr, Cfg::kTmem);
         tc::tmem_relinquish();
     }
-    if (tid == 0) tc::mbar_init(&bar, 1);
-    for (int i = tid; i < COUT * (KT / 8); i += kTcThreads) {
-        const int row = i / (KT / 8), kb = i % (KT / 8);
-        *reinterpret_cast<uint4*>(sB + tc::kmajor_offset(row, kb * 8, KT)) =
-            *reinterpret_cast<const uint4*>(Wt + (long long)row * KT + kb * 8);
+    if (tid == 0) {
+        s_abort = 0;
+        for (int i = 0; i < kRing; ++i) {
+            tc::mbar_init(&full[i], 32 * kProdWarps);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&acc_full[i], 1);
+            tc::mbar_init(&acc_empty[i], 32 * kEpiWarps);
+        }
+        tc::mbar_init(&mma_done, 1);
     }
+    // weight blocks: block ((dx + 1) * 3 + (1 - dy)) holds W[.][tap (dy, dx)][.] as COUT x CIN,
+    // K-major core matrices over the stacked 9 COUT rows (stride byte offset 16 CIN)
+    const uint32_t w0 = tc::smem_addr(smem), ring0 = w0 + Cfg::kW;
+    for (int i = tid; i < 9 * COUT * (CIN / 8); i += kConvThreads) {
+        const int row = i / (CIN / 8), kb = i - row * (CIN / 8);
+        const int blk = row / COUT, co = row - blk * COUT;
+        const int dxi = blk / 3, dy = 1 - (blk - dxi * 3);
+        const int tap = 3 * (dy + 1) + dxi;
+        tc::cp_async16(w0 + tc::kmajor_offset(row, kb * 8, CIN), Wt + ((long long)co * 9 + tap) * CIN + kb * 8);
+    }
+    tc::cp_async_commit();
+    __syncthreads();                    // barrier inits and s_taddr visible
+    const uint32_t taddr = s_taddr;
+    if (warp < kEpiWarps) {             // both accumulators start at zero
+        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+        for (uint32_t c = (uint32_t)(warp >> 2) * 32; c < Cfg::kTmem; c += 64) {
+            if constexpr (Cfg::kTmem >= 64) tc::tmem_zero32(taddr + lanes + c);
+        }
+    }
+    tc::cp_async_wait<0>();
+    tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t taddr = s_taddr;
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
+    const ConvUnits U(B, H, Wd, R, G);
 
-    const long long npix = (long long)B * H * Wd;
-    const long long pix = (long long)blockIdx.x * 128 + tid;
-    const bool valid = pix < npix;
-    const int x = (int)(pix % Wd);
-    const long long by = pix / Wd;
-    const int y = (int)(by % H);
-    const long long b = by / H;
-    uint32_t phase = 0;
-    bool ok = true;
-    for (int tap = 0; tap < 9 && ok; ++tap) {
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        const int ys = y + dy < 0 ? H - 1 : (y + dy >= H ? 0 : y + dy);
-        const int xs = x + dx < 0 ? Wd - 1 : (x + dx >= Wd ? 0 : x + dx);
-        const __nv_bfloat16* src = X + ((b * H + ys) * Wd + xs) * CIN;
-#pragma unroll
-        for (int kb = 0; kb < CIN / 8; ++kb) {
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (valid) v = *reinterpret_cast<const uint4*>(src + kb * 8);
-            *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(tid, kb * 8, CIN)) = v;
-        }
-        tc::fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after_sync();
-            const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
-#pragma unroll
-            for (int s = 0; s < CIN / 16; ++s) {
-                const uint64_t da = tc::smem_desc(a0 + s * 256, 128, CIN * 16);
-                const uint64_t db = tc::smem_desc(b0 + ((tap * CIN + 16 * s) / 8) * 128, 128, KT * 16);
-                tc::mma_bf16(taddr, da, db, idesc, (tap > 0 || s > 0) ? 1u : 0u);
-            }
-            tc::mma_commit(&bar);
-        }
-        if (!tc::mbar_wait(&bar, phase, kWaitPolls)) {
-            ok = false;
-            atomicExch(err, 1);
-        }
-        phase ^= 1;
-        __syncthreads();
-    }
-    if (ok) {
-        tc::fence_after_sync();
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-#pragma unroll
-        for (int c = 0; c < COUT; c += 16) {
-            float v[16];
-            tc::tmem_ld16(taddr + lane_base + (uint32_t)c, v);
-            if (valid) {
-                __align__(16) __nv_bfloat16 zo[16], yo[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float z = v[j] + bias[c + j];
-                    zo[j] = __float2bfloat16_rn(z);
-                    yo[j] = __float2bfloat16_rn(ACT ? gelu(z) : z);
+    if (warp > kMmaWarp) {
+        // ---------------- producers ----------------
+        // Halo rows are issued in stream order h = 0, 1, ...; a row is announced
+        // (full[slot]) as soon as this thread's copies of it have landed, also
+        // while the producer waits for a free slot, so that announcing never
+        // depends on the consumer releasing a later slot.
+        const int pt = tid - 32 * (kMmaWarp + 1);
+        constexpr int np = 32 * kProdWarps;
+        uint32_t h = 0, announced = 0;
+        bool ok = true;
+        auto announce_oldest = [&]() {
+            tc::cp_async_wait_dyn((int)(h - announced) - 1);
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&full[announced % kRing]);
+            ++announced;
+        };
+        for (long long unit = blockIdx.x; unit < U.n && ok; unit += gridDim.x) {
+            int b, y0, rows, x0;
+            U.decode(unit, b, y0, rows, x0);
+            const __nv_bfloat16* Xb = X + (long long)b * H * Wd * CIN;
+            const int nh = U.halos(rows);
+            for (int i = 0; i < nh; ++i, ++h) {
+                const uint32_t slot = h % kRing, par = ((h / kRing) & 1u) ^ 1u;
+                while (announced < h && (h - announced >= (uint32_t)kMaxPending || !tc::mbar_test(&empty[slot], par)))
+                    announce_oldest();
+                if (!wait_or_abort(&empty[slot], par, abort)) {
+                    raise_abort(abort, err);
+                    ok = false;
+                    break;
                 }
-                uint4* yd = reinterpret_cast<uint4*>(Y + pix * COUT + c);
-                yd[0] = reinterpret_cast<const uint4*>(yo)[0];
-                yd[1] = reinterpret_cast<const uint4*>(yo)[1];
-                if (STORE_Z) {
-                    uint4* zd = reinterpret_cast<uint4*>(Z + pix * COUT + c);
-                    zd[0] = reinterpret_cast<const uint4*>(zo)[0];
-                    zd[1] = reinterpret_cast<const uint4*>(zo)[1];
+                int yi = (y0 - 1 + i) % H;
+                yi = yi < 0 ? yi + H : yi;
+                const __nv_bfloat16* src = Xb + (long long)yi * Wd * CIN;
+                const uint32_t dst = ring0 + slot * Cfg::kSlot;
+                for (int idx = pt; idx < kHaloPix * Cfg::GR; idx += np) {
+                    const int pix = idx / Cfg::GR, g = idx - pix * Cfg::GR;
+                    int x = x0 - 1 + pix;
+                    x = x < 0 ? x + Wd : (x >= Wd ? x % Wd : x);
+                    tc::cp_async16(dst + (uint32_t)(g * (kHaloPix * 16) + pix * 16),
+                                   src + (long long)x * CIN + g * 8);
+                }
+                tc::cp_async_commit();
+            }
+        }
+        while (announced < h) announce_oldest();
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            uint32_t idesc[3];
+#pragma unroll
+            for (int n = 0; n < 3; ++n) idesc[n] = tc::idesc_bf16_f32(128, COUT * (n + 1));
+            uint32_t hb = 0, gc = 0;
+            bool ok = true;
+            for (long long unit = blockIdx.x; unit < U.n && ok; unit += gridDim.x) {
+                int b, y0, rows, x0;
+                U.decode(unit, b, y0, rows, x0);
+                const int ng = U.groups(rows);
+                int waited = 0;                       // halo rows of this unit already waited for
+                for (int g = 0; g < ng && ok; ++g, ++gc) {
+                    const uint32_t a = gc & 1u, u = gc >> 1;
+                    ok = wait_or_abort(&acc_empty[a], (u & 1u) ^ 1u, abort);
+                    const int j0 = g * G;
+                    for (int i = j0; i < j0 + G + 2 && ok; ++i) {
+                        const uint32_t hh = hb + (uint32_t)i, slot = hh % kRing;
+                        if (i >= waited) {
+                            ok = wait_or_abort(&full[slot], (hh / kRing) & 1u, abort);
+                            waited = i + 1;
+                            tc::fence_proxy_async_smem();
+                        }
+                        if (!ok) break;
+                        tc::fence_after_sync();
+                        // output rows jlo..jhi of the group read halo row i, through blocks b0.. of each dx
+                        const int jlo = max(j0, i - 2), jhi = min(j0 + G - 1, i);
+                        const int nr = jhi - jlo + 1, b0 = jlo - i + 2;
+                        const uint32_t id = nr == 1 ? idesc[0] : (nr == 2 ? idesc[1] : idesc[2]);
+                        const uint32_t dcol = taddr + a * Cfg::kAcc + (uint32_t)(COUT * (jlo - j0));
+                        const uint32_t arow = ring0 + slot * Cfg::kSlot;
+#pragma unroll
+                        for (int dxi = 0; dxi < 3; ++dxi) {
+                            const uint32_t brow = w0 + (uint32_t)(((dxi * 3 + b0) * COUT / 8) * (CIN * 16));
+#pragma unroll
+                            for (int sk = 0; sk < CIN / 16; ++sk) {
+                                const uint64_t da = tc::smem_desc(arow + (uint32_t)(dxi * 16 + 2 * sk * kHaloPix * 16),
+                                                                  kHaloPix * 16, 128);
+                                const uint64_t db = tc::smem_desc(brow + (uint32_t)(256 * sk), 128, CIN * 16);
+                                tc::mma_bf16(dcol, da, db, id, 1u);
+                            }
+                        }
+                        // halo row i is released by the group of output row i (the unit's last group
+                        // for the rows past it)
+                        if (min(i / G, ng - 1) == g) tc::mma_commit(&empty[slot]);
+                    }
+                    if (ok) tc::mma_commit(&acc_full[a]);
+                }
+                hb += (uint32_t)U.halos(rows);
+            }
+            if (!ok) raise_abort(abort, err);
+            // every MMA this thread issued has completed before TMEM is released
+            tc::mma_commit(&mma_done);
+            if (!tc::mbar_wait(&mma_done, 0, kWaitPolls)) raise_abort(abort, err);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue ----------------
+        constexpr int CH = COUT / 2, KC = Cfg::KC;
+        const int q = warp & 3, half = warp >> 2, pt = half * 32 + lane;
+        uint8_t* stage = smem + Cfg::kW + kRing * Cfg::kSlot + q * 2 * Cfg::kStage;
+        int sbuf = 0;
+        // stage this thread's CH values (packed BF16) of pixel `lane`, then copy the pair's
+        // 32 pixels to dst (pixel 0 of the block) as 16-byte chunks, nvalid pixels
+        auto emit = [&](const uint32_t (&pk)[CH / 2], __nv_bfloat16* dst, int nvalid) {
+            uint8_t* st = stage + sbuf * Cfg::kStage;
+#pragma unroll
+            for (int c0 = 0; c0 < CH; c0 += 8) {
+                const int k = (half * CH + c0) / 8;
+                *reinterpret_cast<uint4*>(st + lane * (KC * 16) + ((k ^ (lane & (KC - 1))) * 16)) =
+                    make_uint4(pk[c0 / 2], pk[c0 / 2 + 1], pk[c0 / 2 + 2], pk[c0 / 2 + 3]);
+            }
+            asm volatile("bar.sync %0, 64;" ::"r"(1 + q) : "memory");
+            for (int idx = pt; idx < 32 * KC; idx += 64) {
+                const int p = idx / KC, k = idx - p * KC;
+                if (p < nvalid)
+                    *reinterpret_cast<uint4*>(dst + (long long)p * COUT + k * 8) =
+                        *reinterpret_cast<const uint4*>(st + p * (KC * 16) + ((k ^ (p & (KC - 1))) * 16));
+            }
+            sbuf ^= 1;
+        };
+        float breg[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) breg[c] = bias[half * CH + c];
+        const uint32_t lanes = (uint32_t)(q * 32) << 16;
+        // After a failure the warp keeps walking its rows without waiting or storing, so
+        // that the pair's named barriers stay matched.
+        uint32_t gc = 0;
+        bool ok = true;
+        for (long long unit = blockIdx.x; unit < U.n; unit += gridDim.x) {
+            int b, y0, rows, x0;
+            U.decode(unit, b, y0, rows, x0);
+            const int ng = U.groups(rows);
+            for (int g = 0; g < ng; ++g, ++gc) {
+                const uint32_t a = gc & 1u, u = gc >> 1;
+                if (ok && !wait_or_abort(&acc_full[a], u & 1u, abort)) {
+                    raise_abort(abort, err);
+                    ok = false;
+                }
+                if (ok) tc::fence_after_sync();
+                const int nvalid = ok ? min(32, Wd - (x0 + q * 32)) : 0;
+                for (int k = 0; k < G && g * G + k < rows; ++k) {
+                    float v[CH];
+                    if (ok) {
+                        const uint32_t tb = taddr + lanes + a * Cfg::kAcc + (uint32_t)(k * COUT + half * CH);
+                        if constexpr (CH == 32) {
+                            tc::tmem_ld32(tb, v);
+                        } else {
+                            static_assert(CH == 8, "column split");
+                            tc::tmem_ld8(tb, v);
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) v[c] = 0.0f;
+                    }
+                    const long long pix0 = ((long long)b * H + y0 + g * G + k) * Wd + x0 + q * 32;
+                    uint32_t pz[CH / 2], py[CH / 2];
+#pragma unroll
+                    for (int c = 0; c < CH; c += 2) {
+                        const float z0 = v[c] + breg[c], z1 = v[c + 1] + breg[c + 1];
+                        const __nv_bfloat162 zz = __floats2bfloat162_rn(z0, z1);
+                        pz[c / 2] = *reinterpret_cast<const uint32_t*>(&zz);
+                        const __nv_bfloat162 yy = ACT ? __floats2bfloat162_rn(gelu(z0), gelu(z1)) : zz;
+                        py[c / 2] = *reinterpret_cast<const uint32_t*>(&yy);
+                    }
+                    emit(py, Y + pix0 * COUT, nvalid);
+                    if (STORE_Z) emit(pz, Z + pix0 * COUT, nvalid);
+                }
+                if (ok) {
+                    // zero the group's columns of these lanes for the next use, then release
+                    for (uint32_t c = (uint32_t)half * 32; c < Cfg::kAcc; c += 64) tc::tmem_zero32(taddr + lanes + a * Cfg::kAcc + c);
+                    tc::fence_before_sync();
+                    tc::mbar_arrive(&acc_empty[a]);
                 }
             }
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(taddr, NCOL);
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(taddr, Cfg::kTmem);
+    }
 }
 
 template <int CIN, int COUT, bool ACT, bool STORE_Z>
 int launch_conv(const void* X, const void* W, const float* bias, void* Y, void* Z, long long B, long long H,
                 long long Wd, int* err, cudaStream_t s) {
-    constexpr int smem = conv_smem_bytes<CIN, COUT>();
-    static bool configured = false;
-    if (!configured) {
-        if (cudaFuncSetAttribute(k_conv3x3<CIN, COUT, ACT, STORE_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem) != cudaSuccess)
+    using Cfg = ConvRows<CIN, COUT>;
+    static int slots = 0;                    // resident CTAs on the device
+    if (!slots) {
+        auto fn = k_conv3x3<CIN, COUT, ACT, STORE_Z>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem) != cudaSuccess)
             return VLBM_ECUDA;
-        configured = true;
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kConvThreads, Cfg::kSmem) != cudaSuccess)
+            return VLBM_ECUDA;
+        // resident CTAs per SM: their accumulators must fit the 512 TMEM columns
+        per_sm = std::max(1, std::min(per_sm, (int)(512 / Cfg::kTmem)));
+        slots = sms * per_sm;
     }
-    const long long npix = B * H * Wd;
-    k_conv3x3<CIN, COUT, ACT, STORE_Z><<<(unsigned)((npix + 127) / 128), kTcThreads, smem, s>>>(
+    // rows per unit (a multiple of the group size): fewest waves of units, counting the
+    // two halo rows of each unit
+    const long long nseg = (Wd + 127) / 128;
+    constexpr int G = Cfg::G;
+    int R = G;
+    double best = 1e300;
+    for (int r : {8 * G, 4 * G, 2 * G, G}) {
+        const long long units = B * nseg * ((H + r - 1) / r);
+        const double cost = (double)((units + slots - 1) / slots) * (r + 2);
+        if (cost < best - 1e-9) {
+            best = cost;
+            R = r;
+        }
+    }
+    const long long units = B * nseg * ((H + R - 1) / R);
+    const unsigned grid = (unsigned)std::min<long long>(units, slots);
+    k_conv3x3<CIN, COUT, ACT, STORE_Z><<<grid, kConvThreads, Cfg::kSmem, s>>>(
         (const __nv_bfloat16*)X, (const __nv_bfloat16*)W, bias, (__nv_bfloat16*)Y, (__nv_bfloat16*)Z, (int)B, (int)H,
-        (int)Wd, err);
+        (int)Wd, R, err);
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
 }
 
@@ -364,9 +641,6 @@ k_conv3x3_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __rest
 
 // ---------------------------------------------------------------------------
 // Elementwise kernels of the surrogate's training step.
-__device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * __expf(-0.5f * z * z);
-}
 
 // Per-channel factors passed by value (channels <= 16).
 struct ChanScale {
