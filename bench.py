@@ -44,6 +44,7 @@ WORKLOADS = {
     "dsl2d": (2, 15, 4096, 1e-4),
     "tgv3d": (3, 28, 256, 1.0 / 1600.0),
     "batch512": (2, 15, 0, None),      # 512 problems: sides and nu drawn per problem
+    "sur256": (2, 15, 1024, 1e-3),     # learned surrogate on 256^2, pooled from 1024^2 runs
 }
 
 
@@ -86,12 +87,20 @@ def parse_args():
     ap.add_argument("--count", type=int, default=512, help="problems of the batch512 workload")
     ap.add_argument("--split-lanes", type=int, choices=[2, 4], default=None,
                     help="nodes per lane of the 2D split kernels (tuning)")
+    ap.add_argument("--sur-trajectories", type=int, default=200, help="sur256: training trajectories (100 pairs each)")
+    ap.add_argument("--sur-epochs", type=float, default=8.0, help="sur256: training epochs")
+    ap.add_argument("--sur-batch", type=int, default=32, help="sur256: states advanced together in the timed rollouts")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--reference-seconds", type=float, default=150.0, help="cap on the reference arm's timed steps")
     args = ap.parse_args()
     if args.n is None:
         args.n = WORKLOADS[args.workload][2]
+    if args.workload == "sur256":
+        if "--steps" not in sys.argv:
+            args.steps = 10
+        if "--warmup" not in sys.argv:
+            args.warmup = 3
     if args.workload == "batch512" and args.precision == "fp32" and "--precision" not in sys.argv:
         args.precision = "fp16split"     # the batched workload stores 16-bit populations by default
     return args
@@ -220,14 +229,19 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+# sources that define the stream-collide step kernels (the surrogate's and the
+# no-allocation entry's files do not change them)
+STEP_SOURCES = ("vlbm_device.cuh", "vlbm_kernels_2d.cuh", "vlbm_kernels_3d.cuh", "vlbm_split.cuh", "vlbm_api.cu",
+                "vlbm_batch.cu", "vlbm_host.hpp")
+
+
 def source_digest():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2607_24059_b300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, fn), "rb") as fh:
-                h.update(fn.encode())
-                h.update(fh.read())
+    for fn in STEP_SOURCES:
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fn.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -484,12 +498,138 @@ def run_batch(args):
     return 0
 
 
+def run_surrogate(args):
+    """Learned surrogate (256^2 states pooled 4x from 1024^2 runs of the scheme; u_x, u_y, phi):
+    one step of this workload is a checked rollout of --sur-batch states by 100 surrogate steps
+    (100 x 32 fine lattice steps).  value = time-to-t speedup per state over the plain FP32
+    scheme on the 1024^2 lattice on the same GPU, at the L2 velocity error stated in config."""
+    import torch
+    import paper_2607_24059_b300 as vlbm
+    from paper_2607_24059_b300 import surrogate as sg
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    cfg = sg.Config(fine=args.n, train_trajectories=args.sur_trajectories, epochs=args.sur_epochs)
+    tr = sg.train_surrogate(cfg, log=lambda m: print(m, file=sys.stderr, flush=True))
+    net, nb, steps = tr.net, args.sur_batch, cfg.rollout_steps
+    ref = tr.test_snaps.transpose(0, 1).contiguous()              # (steps + 1, states, C, c, c)
+    ntest = ref.shape[1]
+    ro = sg.Rollout(net, cfg, max(nb, ntest), div_limit=tr.div_limit)
+    # accuracy against the fine scheme, checked and unchecked
+    _, acc = ro.run(ref[0].contiguous(), steps, check=True, reference=ref, every=steps)
+    _, acc_free = ro.run(ref[0].contiguous(), steps, check=False, reference=ref, every=steps)
+    _, coarse_err = sg.coarse_scheme(cfg, ref[0].contiguous(), steps, reference=ref[-1])
+    t_fine = sg.fine_time_to_t(cfg, cfg.test_seeds()[0])
+    u0 = ref[0][torch.arange(nb) % ntest].contiguous()
+    for _ in range(max(args.warmup, 3)):
+        ro.run(u0, steps)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    l0, c0 = vlbm.vlbm_sur_launch_count(), ro.coarse.launch_count()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fallbacks = 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for _ in range(args.steps):
+            _, info = ro.run(u0, steps)
+            fallbacks += sum(info["fallbacks"])
+        end.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = max_over_ranks(start.elapsed_time(end) / 1e3, dist, "cuda")
+    launches = (vlbm.vlbm_sur_launch_count() - l0) + (ro.coarse.launch_count() - c0)
+    ms_per_state = elapsed / args.steps / nb * 1e3
+    value = world * t_fine / ms_per_state
+    # end to end: states from pinned host memory, the checked rollout, states back to pinned host
+    h_in = u0.cpu().pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_in = torch.empty_like(u0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        d_in.copy_(h_in, non_blocking=True)
+        out, _ = ro.run(d_in, steps)
+        h_out.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = world * t_fine / (e2e_el / args.steps / nb * 1e3)
+    # roofline of the dominant kernel: the 64 -> 64 periodic conv of the rollout, timed alone
+    c = cfg.coarse
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    X = torch.randn(nb, c, c, 64, device="cuda").to(torch.bfloat16)
+    Wt = (0.05 * torch.randn(64, 9, 64, device="cuda")).to(torch.bfloat16)
+    bias = torch.zeros(64, device="cuda")
+    Yc = torch.empty_like(X)
+    for _ in range(3):
+        vlbm.vlbm_sur_conv3x3(X, Wt, bias, Yc, err, act=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 50
+    e0.record(stream)
+    for _ in range(reps):
+        vlbm.vlbm_sur_conv3x3(X, Wt, bias, Yc, err, act=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    conv_ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * nb * c * c * 9 * 64 * 64
+    peaks = {}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            peaks = json.load(fh)
+    peak = float(peaks.get("bf16_tflops", 1800.0))
+    peak_kind = "measured (cuBLAS bf16 burst)" if "bf16_tflops" in peaks else "fallback"
+    achieved = flops / (conv_ms * 1e-3) / 1e12
+    ro.close()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": "x time-to-t speedup per state vs plain FP32 LBM 1024^2",
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 (FP32 accumulate)", "data": "synthetic (scheme-generated)",
+        "config": {
+            "workload": f"learned surrogate: 5 periodic 3x3 convs (64 ch, GELU) on {c}^2 states (u_x, u_y, phi) "
+                        f"pooled {cfg.factor}x from {cfg.fine}^2 FP32 runs of the scheme, nu = {cfg.nu}; "
+                        f"{steps} surrogate steps of {cfg.k_fine} fine steps each, checked (energy, divergence) "
+                        "with the plain coarse-lattice scheme as fallback",
+            "states_per_step": nb, "training_pairs": cfg.train_trajectories * cfg.pairs_per_trajectory,
+            "train_seconds": tr.summary["seconds"], "train_steps": tr.summary["steps"],
+            "l2_rel_error_checked": acc["curve"][-1][1], "l2_rel_error_unchecked": acc_free["curve"][-1][1],
+            "l2_rel_error_coarse_scheme": float(np.mean(coarse_err)),
+            "fallbacks_per_state_step": fallbacks / (args.steps * nb * steps),
+            "fine_fp32_ms_per_state": t_fine, "surrogate_ms_per_state": ms_per_state,
+            "l2": "rollout states 32 x 3 x 256^2 FP32 = 25 MB (L2-resident, as in use)"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "kernel": "k_conv3x3<64, 64, true, false>", "avg_launch_ms": conv_ms,
+                     "flops_per_launch": flops},
+        "e2e": {"value": e2e_value, "unit": "x time-to-t speedup per state vs plain FP32 LBM 1024^2",
+                "h2d_bytes_per_step": h_in.numel() * 4, "d2h_bytes_per_step": h_out.numel() * 4},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    net.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch512":
         return run_batch(args)
+    if args.workload == "sur256":
+        return run_surrogate(args)
     return run_vlbm(args)
 
 

@@ -375,6 +375,10 @@ int vlbm_field_stats(const float* u, double* out, int32_t batch, int32_t channel
 int vlbm_field_diff_norms(const float* a, const float* b, double* out, int32_t nfields, int64_t n, int64_t ld,
                           void* stream);
 
+/* Kernels launched by the surrogate and field-utility entry points above since
+ * the library was loaded (all handles, all threads). */
+int64_t vlbm_sur_launch_count(void);
+
 /* Static text of a status code; message of the last failure of h. */
 const char* vlbm_strerror(int code);
 const char* vlbm_last_error(const vlbm_handle* h);

@@ -65,7 +65,7 @@ EXPORTED = [
     "vlbm_batch_last_error", "vlbm_tc_gemm_bf16", "vlbm_sur_conv3x3", "vlbm_sur_conv3x3_wgrad",
     "vlbm_sur_create", "vlbm_sur_destroy", "vlbm_sur_num_params", "vlbm_sur_forward", "vlbm_sur_train_step",
     "vlbm_sur_get_params", "vlbm_sur_get_grads", "vlbm_sur_set_params", "vlbm_sur_status", "vlbm_sur_advance",
-    "vlbm_sur_set_scaling", "vlbm_sur_set_train_noise",
+    "vlbm_sur_set_scaling", "vlbm_sur_set_train_noise", "vlbm_sur_launch_count",
     "vlbm_field_pool", "vlbm_sur_gather_pairs", "vlbm_field_stats", "vlbm_field_diff_norms",
 ]
 
@@ -136,6 +136,8 @@ lib.vlbm_sur_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, 
                                 ctypes.c_uint64, _V, ctypes.POINTER(_H)]
 lib.vlbm_sur_set_scaling.argtypes = [_H, _V, _V]
 lib.vlbm_sur_set_train_noise.argtypes = [_H, _V, ctypes.c_uint64]
+lib.vlbm_sur_launch_count.argtypes = []
+lib.vlbm_sur_launch_count.restype = ctypes.c_int64
 lib.vlbm_sur_destroy.argtypes = [_H]
 lib.vlbm_sur_destroy.restype = None
 lib.vlbm_sur_num_params.argtypes = [_H]
@@ -470,6 +472,10 @@ def vlbm_sur_destroy(h) -> None:
 def vlbm_sur_set_train_noise(h, sigma=None, seed: int = 0) -> None:
     """Per-input-channel standard deviation of the training-input noise (None = off)."""
     _check(lib.vlbm_sur_set_train_noise(h, _float_array(sigma), int(seed)), "vlbm_sur_set_train_noise")
+
+
+def vlbm_sur_launch_count() -> int:
+    return int(lib.vlbm_sur_launch_count())
 
 
 def vlbm_sur_num_params(h) -> int:

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <new>
@@ -20,6 +21,9 @@ namespace {
 constexpr int kTcThreads = 128;          // one warpgroup: TMEM lanes 0..127
 constexpr int kKChunk = 64;              // K columns staged per round
 constexpr long long kWaitPolls = 1 << 22;
+
+// Kernels launched by this file's entry points since the library was loaded.
+std::atomic<long long> g_launches{0};
 
 // D[M x N] = A[M x K] B[N x K]^T for one 128-row block of A.  A, B row-major
 // BF16 (K contiguous), D row-major FP32.  N % 16 == 0, 16 <= N <= 256, K % 64 == 0.
@@ -504,6 +508,7 @@ int launch_conv(const void* X, const void* W, const float* bias, void* Y, void* 
     }
     const long long units = B * nseg * ((H + R - 1) / R);
     const unsigned grid = (unsigned)std::min<long long>(units, slots);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     k_conv3x3<CIN, COUT, ACT, STORE_Z><<<grid, kConvThreads, Cfg::kSmem, s>>>(
         (const __nv_bfloat16*)X, (const __nv_bfloat16*)W, bias, (__nv_bfloat16*)Y, (__nv_bfloat16*)Z, (int)B, (int)H,
         (int)Wd, R, err);
@@ -871,6 +876,7 @@ extern "C" int vlbm_tc_gemm_bf16(const void* A, const void* B, float* D, int64_t
                                  int32_t* err_dev, void* stream) {
     if (!A || !B || !D || !err_dev || M <= 0 || M % 128 || N < 16 || N > 256 || N % 16 || K <= 0 || K % kKChunk)
         return VLBM_EINVAL;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     k_tc_gemm_bf16<<<(unsigned)(M / 128), kTcThreads, 0, (cudaStream_t)stream>>>(
         (const __nv_bfloat16*)A, (const __nv_bfloat16*)B, D, (int)N, (int)K, err_dev);
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
@@ -913,6 +919,7 @@ int launch_wgrad(const void* X, const void* dZ, float* G, float* Gb, long long B
                  cudaStream_t s) {
     const long long npix = B * H * W;
     const dim3 grid((unsigned)((npix + kPixPerWgradCta - 1) / kPixPerWgradCta), (unsigned)((9 * CIN + 1 + 127) / 128));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     k_conv3x3_wgrad<CIN, COUT><<<grid, kTcThreads, 0, s>>>((const __nv_bfloat16*)X, (const __nv_bfloat16*)dZ, G, Gb,
                                                            (int)B, (int)H, (int)W, kPixPerWgradCta, err);
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
@@ -983,6 +990,7 @@ void free_sur(vlbm_sur* s) {
 int refresh_all(vlbm_sur* s) {
     for (int l = 0; l < kLayers; ++l) {
         const int n = kCout[l] * 9 * kCin[l];
+        g_launches.fetch_add(1, std::memory_order_relaxed);
         k_refresh_weights<<<(n + 255) / 256, 256, 0, s->stream>>>(s->params + s->off_w[l], s->Wb[l], s->Wflip[l],
                                                                   kCin[l], kCout[l]);
     }
@@ -1008,6 +1016,7 @@ int sur_forward(vlbm_sur* s, const float* u, int batch, bool train) {
         key = mix64_host(s->noise_seed) + s->noise_draws;
         s->noise_draws += (uint64_t)npix * 16;
     }
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     if (s->features & VLBM_SUR_FEATURE_DIV)
         k_pack_input<true><<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(u, s->X0, s->H, s->W, npix, s->C,
                                                                                   s->in_scale, noise, key);
@@ -1138,6 +1147,7 @@ extern "C" int vlbm_sur_forward(vlbm_sur* s, const float* u, float* du, int32_t 
     const long long plane = (long long)s->H * s->W, npix = plane * batch;
     ChanScale one{};
     for (int c = 0; c < 16; ++c) one.v[c] = 1.0f;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     k_unpack_output<<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(s->Y[kLayers - 1], nullptr, du, one,
                                                                             plane, npix, s->C);
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
@@ -1182,6 +1192,7 @@ extern "C" int vlbm_sur_advance(vlbm_sur* s, const float* u, float* u_next, int3
     int rc = sur_forward(s, u, batch, false);
     if (rc) return rc;
     const long long plane = (long long)s->H * s->W, npix = plane * batch;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     k_unpack_output<<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(s->Y[kLayers - 1], u, u_next,
                                                                             s->out_scale, plane, npix, s->C);
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
@@ -1191,6 +1202,7 @@ extern "C" int vlbm_field_pool(const float* in, float* out, int64_t B, int64_t C
                                void* stream) {
     if (!in || !out || B < 1 || C < 1 || H < 1 || W < 1 || factor < 1) return VLBM_EINVAL;
     const long long n = B * C * H * W;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     k_pool<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, out, n, (int)H, (int)W, factor);
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
 }
@@ -1203,6 +1215,7 @@ extern "C" int vlbm_sur_gather_pairs(const float* snaps, const int64_t* idx, flo
     ChanScale inv{};
     for (int c = 0; c < channels; ++c) inv.v[c] = inv_scale[c];
     const long long n = (long long)channels * H * W * batch;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     k_gather_pairs<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(snaps, idx, u, target, H * W,
                                                                                    channels, batch, inv);
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
@@ -1214,6 +1227,7 @@ extern "C" int vlbm_field_diff_norms(const float* a, const float* b, double* out
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(out, 0, sizeof(double) * 2 * nfields, st) != cudaSuccess) return VLBM_ECUDA;
     const unsigned gx = (unsigned)std::min<long long>((n + 255) / 256, 148);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     k_diff_norms<<<dim3(gx, nfields), 256, 0, st>>>(a, b, out, n, ld);
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
 }
@@ -1226,6 +1240,7 @@ extern "C" int vlbm_field_stats(const float* u, double* out, int32_t batch, int3
     if (cudaMemsetAsync(out, 0, sizeof(double) * 3 * batch, st) != cudaSuccess) return VLBM_ECUDA;
     const long long plane = H * W;
     const unsigned gx = (unsigned)std::min<long long>((plane + 255) / 256, 148);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     k_field_stats<<<dim3(gx, batch), 256, 0, st>>>(u, out, channels, (int)H, (int)W);
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
 }
@@ -1240,6 +1255,7 @@ extern "C" int vlbm_sur_train_step(vlbm_sur* s, const float* u, const float* tar
         cudaMemsetAsync(s->grads, 0, s->nparams * 4, s->stream) != cudaSuccess)
         return VLBM_ECUDA;
     const unsigned eb = (unsigned)((npix + 255) / 256);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     k_mse_grad<<<eb, 256, 0, s->stream>>>(s->Y[kLayers - 1], target, s->dA, s->sse, plane, npix,
                                           1.0f / (float)((long long)s->C * npix), s->C);
     // backward, last layer first: dA holds dZ of layer l (its pre-activation gradient)
@@ -1254,12 +1270,14 @@ extern "C" int vlbm_sur_train_step(vlbm_sur* s, const float* u, const float* tar
                       s->err, s->stream);
         if (rc) return rc;
         const long long n = npix * kCin[l];
+        g_launches.fetch_add(1, std::memory_order_relaxed);
         k_gelu_back<<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>(s->dB, s->Z[l - 1], s->dA, n);
     }
     s->adam_t++;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f / (1.0f - std::pow(b1, (float)s->adam_t));
     const float c2 = 1.0f / (1.0f - std::pow(b2, (float)s->adam_t));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     k_adam<<<(unsigned)((s->nparams + 255) / 256), 256, 0, s->stream>>>(s->params, s->adam_m, s->adam_v, s->grads,
                                                                          s->nparams, lr, b1, b2, 1e-8f, c1, c2);
     rc = refresh_all(s);
@@ -1301,3 +1319,5 @@ extern "C" int vlbm_sur_set_params(vlbm_sur* s, const float* src) {
     return cudaStreamSynchronize(s->stream) == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
 }
 extern "C" int vlbm_sur_status(vlbm_sur* s) { return s ? check_err(s) : VLBM_EINVAL; }
+
+extern "C" int64_t vlbm_sur_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }

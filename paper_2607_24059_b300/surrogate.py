@@ -63,8 +63,8 @@ class Config:
     net_seed: int = 1
     energy_step_tol: float = 2e-3     # |E_{k+1} / E_k - 1| allowed per surrogate step
     energy_drift_tol: float = 5e-2    # |E_k / E_0 - 1| allowed over the rollout
-    div_factor: float = 2.0           # divergence / gradient ratio allowed: max(div_factor r_0, div_floor)
-    div_floor: float = 1e-3
+    div_factor: float = 1.5           # divergence / gradient ratio allowed: div_factor times the largest
+    div_floor: float = 1e-3           # ratio of the training states (at least div_floor)
 
     @property
     def coarse(self) -> int:
@@ -158,6 +158,20 @@ def divergence_rms(snaps: torch.Tensor, chunk: int = 256) -> float:
     return math.sqrt(total / (T * P1 * c * c))
 
 
+def divergence_ratio_max(snaps: torch.Tensor, chunk: int = 256) -> float:
+    """Largest divergence-to-gradient ratio sqrt(sum div^2 / sum |grad u|^2) over the states of the store."""
+    T, P1, C, c, _ = snaps.shape
+    flat = snaps.view(T * P1, C, c, c)
+    st = torch.empty(chunk, 3, dtype=torch.float64, device=snaps.device)
+    best = 0.0
+    for i in range(0, T * P1, chunk):
+        n = min(chunk, T * P1 - i)
+        B.vlbm_field_stats(flat[i:i + n], st[:n])
+        h = st[:n].cpu().numpy()
+        best = max(best, float(np.sqrt(h[:, 1] / h[:, 2]).max()))
+    return best
+
+
 def scaling(cfg: Config, snaps: torch.Tensor):
     """(input factors, output factors) of the network from the training store: inputs divided by
     their RMS, increments by theirs, the phi increment additionally by sqrt(phi_weight) so that
@@ -241,9 +255,11 @@ def velocity_errors(a: torch.Tensor, ref: torch.Tensor, nrm: torch.Tensor) -> li
 class Rollout:
     """Checked surrogate rollout of a batch of coarse states with the plain scheme as fallback."""
 
-    def __init__(self, net: Surrogate, cfg: Config, batch: int, device="cuda"):
+    def __init__(self, net: Surrogate, cfg: Config, batch: int, device="cuda", div_limit=None):
+        """div_limit: largest divergence-to-gradient ratio a state may reach (None: div_factor
+        times the starting state's ratio)."""
         c, C = cfg.coarse, cfg.channels
-        self.net, self.cfg = net, cfg
+        self.net, self.cfg, self.div_limit = net, cfg, div_limit
         self.u = torch.empty(batch, C, c, c, dtype=torch.float32, device=device)
         self.nxt = torch.empty_like(self.u)
         self.stats = torch.empty(batch, 3, dtype=torch.float64, device=device)
@@ -282,11 +298,14 @@ class Rollout:
         u.copy_(u0)
         fallbacks = np.zeros(n, dtype=np.int64)
         reasons = {"energy_step": 0, "energy_drift": 0, "divergence": 0}
-        curve = []
+        curve, div_curve = [], []
         if check:
             e0, r0 = self._read_stats(u)
             e_prev = e0.copy()
-            r_max = np.maximum(cfg.div_factor * r0, cfg.div_floor)
+            if self.div_limit is None:
+                r_max = np.maximum(cfg.div_factor * r0, cfg.div_floor)
+            else:
+                r_max = np.full(n, max(self.div_limit, cfg.div_floor))
         for k in range(steps):
             self.net.advance(u, out=nxt)
             if check:
@@ -309,9 +328,11 @@ class Rollout:
             if reference is not None and ((k + 1) % every == 0 or k + 1 == steps):
                 errs = velocity_errors(u, reference[k + 1], self.nrm)
                 curve.append((k + 1, float(np.mean(errs)), errs))
+                div_curve.append((k + 1, float(np.mean(self._read_stats(u)[1]))))
         if u.data_ptr() != self.u.data_ptr():
             self.u[:n].copy_(u)
-        return self.u[:n], {"fallbacks": fallbacks.tolist(), "reasons": reasons, "curve": curve}
+        return self.u[:n], {"fallbacks": fallbacks.tolist(), "reasons": reasons, "curve": curve,
+                            "div_ratio": div_curve}
 
 
 def coarse_scheme(cfg: Config, u0: torch.Tensor, steps: int, reference=None) -> tuple:
@@ -343,12 +364,11 @@ def _event_ms(fn, repeats=1):
     return e0.elapsed_time(e1) / repeats
 
 
-def time_to_t(cfg: Config, net: Surrogate, u0_coarse: torch.Tensor, seed: int, batch: int = 32) -> dict:
-    """Wall time on this GPU to advance one state by rollout_steps K fine steps, per state: the
-    plain FP32 scheme on the fine lattice (steps, macros, pooling), the surrogate rollout with its
-    checks (one state, and `batch` states at once), and the plain scheme on the coarse lattice."""
+def fine_time_to_t(cfg: Config, seed: int, repeats: int = 2) -> float:
+    """Milliseconds for the plain FP32 scheme on the fine lattice to advance one state (u, phi)
+    by rollout_steps K fine steps and return its pooled state (steps, macros, pooling)."""
     f, c, C, steps = cfg.fine, cfg.coarse, cfg.channels, cfg.rollout_steps
-    dev = u0_coarse.device
+    dev = torch.device("cuda")
     lat = Lattice((f, f), 2 * math.pi / f, cfg.nu, precision="fp32")
     ufine = torch.empty(2, f, f, dtype=torch.float32, device=dev)
     pfine = torch.empty(1, f, f, dtype=torch.float32, device=dev)
@@ -367,10 +387,20 @@ def time_to_t(cfg: Config, net: Surrogate, u0_coarse: torch.Tensor, seed: int, b
             if C > 2:
                 B.vlbm_field_pool(pfine, pooled[:, 2:3], cfg.factor)
         fine_run()
-        t_fine = _event_ms(fine_run, 2)
+        return _event_ms(fine_run, repeats)
     finally:
         lat.close()
-    ro = Rollout(net, cfg, batch)
+
+
+def time_to_t(cfg: Config, net: Surrogate, u0_coarse: torch.Tensor, seed: int, batch: int = 32,
+              div_limit=None) -> dict:
+    """Wall time on this GPU to advance one state by rollout_steps K fine steps, per state: the
+    plain FP32 scheme on the fine lattice (steps, macros, pooling), the surrogate rollout with its
+    checks (one state, and `batch` states at once), and the plain scheme on the coarse lattice."""
+    c, C, steps = cfg.coarse, cfg.channels, cfg.rollout_steps
+    dev = u0_coarse.device
+    t_fine = fine_time_to_t(cfg, seed)
+    ro = Rollout(net, cfg, batch, div_limit=div_limit)
     try:
         one = u0_coarse[:1].contiguous()
         many = u0_coarse[torch.arange(batch) % u0_coarse.shape[0]].contiguous()
@@ -397,50 +427,76 @@ def time_to_t(cfg: Config, net: Surrogate, u0_coarse: torch.Tensor, seed: int, b
             "coarse_fp32_ms": t_coarse, "speedup_b1": t_fine / t_sur1, f"speedup_b{batch}": t_fine / t_surb}
 
 
-def run_pipeline(cfg: Config, log=print, weights_out=None) -> dict:
-    """Data, training, evaluation and timing; returns the report."""
+@dataclass
+class Trained:
+    """A trained surrogate with its data and the quantities derived from them."""
+    net: Surrogate
+    train_snaps: torch.Tensor
+    test_snaps: torch.Tensor
+    in_scale: list
+    out_scale: list
+    div_limit: float
+    summary: dict
+    data_seconds: float
+
+
+def train_surrogate(cfg: Config, log=print, max_seconds=None) -> Trained:
+    """Generate the training and test data with the scheme, then train a network on them."""
     t0 = time.perf_counter()
     torch.cuda.synchronize()
     train_snaps = generate(cfg, cfg.train_seeds(), cfg.pairs_per_trajectory)
     test_snaps = generate(cfg, cfg.test_seeds(), cfg.rollout_steps)
     t_data = time.perf_counter() - t0
     in_scale, out_scale = scaling(cfg, train_snaps)
+    div_limit = cfg.div_factor * divergence_ratio_max(train_snaps)
     log(f"data: {tuple(train_snaps.shape)} + {tuple(test_snaps.shape)} in {t_data:.1f} s; input factors {in_scale}, "
-        f"output factors {out_scale}")
+        f"output factors {out_scale}, divergence-ratio limit {div_limit:.3e}")
     net = Surrogate(cfg.coarse, cfg.coarse, max(cfg.batch, 32), channels=cfg.channels,
                     divergence_input=cfg.divergence_input, seed=cfg.net_seed)
     net.set_scaling(in_scale, out_scale)
     sigma = [cfg.noise_u, cfg.noise_u] + [cfg.noise_phi] * (cfg.channels - 2) + ([cfg.noise_div] if cfg.divergence_input else [])
     net.set_train_noise(sigma, seed=cfg.seed_base + 11)
-    tr = train(net, train_snaps, cfg, out_scale, log=log)
-    val = one_step_error(net, test_snaps, out_scale)
+    summary = train(net, train_snaps, cfg, out_scale, log=log, max_seconds=max_seconds)
+    return Trained(net, train_snaps, test_snaps, in_scale, out_scale, div_limit, summary, t_data)
+
+
+def run_pipeline(cfg: Config, log=print, weights_out=None) -> dict:
+    """Data, training, evaluation and timing; returns the report."""
+    t0 = time.perf_counter()
+    tr = train_surrogate(cfg, log)
+    net = tr.net
+    val = one_step_error(net, tr.test_snaps, tr.out_scale)
     log(f"one-step relative increment error on test pairs, per channel: {val}")
-    ref = test_snaps.transpose(0, 1).contiguous()             # (steps + 1, states, C, c, c)
+    ref = tr.test_snaps.transpose(0, 1).contiguous()          # (steps + 1, states, C, c, c)
     u0 = ref[0].contiguous()
-    ro = Rollout(net, cfg, u0.shape[0])
+    ro = Rollout(net, cfg, u0.shape[0], div_limit=tr.div_limit)
     try:
         _, checked = ro.run(u0, cfg.rollout_steps, check=True, reference=ref, every=10)
         _, free = ro.run(u0, cfg.rollout_steps, check=False, reference=ref, every=10)
+        ref_div = [(k, float(np.mean(ro._read_stats(ref[k].contiguous())[1])))
+                   for k in range(10, cfg.rollout_steps + 1, 10)]
     finally:
         ro.close()
     _, coarse_err = coarse_scheme(cfg, u0, cfg.rollout_steps, reference=ref[-1])
     # persistence (s(t) = s(0)) as the floor any useful surrogate must beat
     nrm = torch.empty(u0.shape[0], 2, dtype=torch.float64, device=u0.device)
     persistence = velocity_errors(u0, ref[-1], nrm)
-    timing = time_to_t(cfg, net, u0, cfg.test_seeds()[0])
+    timing = time_to_t(cfg, net, u0, cfg.test_seeds()[0], div_limit=tr.div_limit)
     if weights_out:
-        torch.save({"params": net.params().cpu(), "in_scale": in_scale, "out_scale": out_scale,
-                    "config": asdict(cfg)}, weights_out)
+        torch.save({"params": net.params().cpu(), "in_scale": tr.in_scale, "out_scale": tr.out_scale,
+                    "div_limit": tr.div_limit, "config": asdict(cfg)}, weights_out)
     net.status()
     net.close()
-    return {"config": asdict(cfg), "in_scale": in_scale, "out_scale": out_scale, "data_seconds": t_data,
-            "train": {k: v for k, v in tr.items() if k != "losses"}, "loss_curve": tr["losses"],
+    return {"config": asdict(cfg), "in_scale": tr.in_scale, "out_scale": tr.out_scale, "div_limit": tr.div_limit,
+            "data_seconds": tr.data_seconds,
+            "train": {k: v for k, v in tr.summary.items() if k != "losses"}, "loss_curve": tr.summary["losses"],
             "one_step_rel_error": val,
             "rollout_checked": {"l2_rel_final": checked["curve"][-1][2], "l2_rel_final_mean": checked["curve"][-1][1],
                                 "curve": [(k, m) for k, m, _ in checked["curve"]], "fallbacks": checked["fallbacks"],
-                                "reasons": checked["reasons"]},
+                                "reasons": checked["reasons"], "div_ratio": checked["div_ratio"]},
             "rollout_unchecked": {"l2_rel_final": free["curve"][-1][2], "l2_rel_final_mean": free["curve"][-1][1],
-                                  "curve": [(k, m) for k, m, _ in free["curve"]]},
+                                  "curve": [(k, m) for k, m, _ in free["curve"]], "div_ratio": free["div_ratio"]},
+            "reference_div_ratio": ref_div,
             "coarse_scheme_l2_rel_final": coarse_err, "persistence_l2_rel_final": persistence,
             "timing": timing, "seconds": time.perf_counter() - t0}
 
