@@ -309,9 +309,17 @@ typedef struct vlbm_sur vlbm_sur;
  * channels 0, 1 (unit spacing), taken in FP32 before the input is rounded to
  * BF16.  It becomes input channel `channels`. */
 #define VLBM_SUR_FEATURE_DIV 1
+/* Divergence-free velocity increments: output channel 0 is a stream function
+ * psi, the increment of channels 0, 1 is out_scale[0] (D_y psi, -D_x psi) with
+ * periodic central differences D_y psi = (psi(y+1) - psi(y-1)) / 2 (rows y),
+ * which the same differences see as exactly divergence-free; output channel 1
+ * is unused.  Training targets of channels 0, 1 are the velocity increments
+ * divided by out_scale[0]; the loss compares them with (D_y psi, -D_x psi), so
+ * the network fits their solenoidal part. */
+#define VLBM_SUR_FEATURE_CURL 2
 
 /* 1 <= channels, channels + derived features <= 16, H W max_batch < 2^31.
- * features: 0 or VLBM_SUR_FEATURE_DIV (needs channels >= 2).  Seeded
+ * features: an OR of VLBM_SUR_FEATURE_* (both need channels >= 2).  Seeded
  * initialisation (uniform, scaled by the fan-in), scales 1.  Synchronises. */
 int vlbm_sur_create(int32_t H, int32_t W, int32_t channels, int32_t features, int32_t max_batch, uint64_t seed,
                     void* stream, vlbm_sur** out);
@@ -336,9 +344,13 @@ int64_t vlbm_sur_num_params(const vlbm_sur* s);
 /* du = net(in_scale * u) (no output scaling) for 1 <= batch <= max_batch
  * states; device pointers; asynchronous. */
 int vlbm_sur_forward(vlbm_sur* s, const float* u, float* du, int32_t batch);
-/* One surrogate step: u_next = u + out_scale * net(in_scale * u); u_next may
- * alias u.  Asynchronous. */
+/* One surrogate step: u_next = u + out_scale * net(in_scale * u) (with
+ * VLBM_SUR_FEATURE_CURL the velocity channels take the curl of channel 0, and
+ * u_next must not alias u); otherwise u_next may alias u.  Asynchronous. */
 int vlbm_sur_advance(vlbm_sur* s, const float* u, float* u_next, int32_t batch);
+/* The scaled increment alone: du = u_next - u of vlbm_sur_advance (du must not
+ * alias u).  Asynchronous. */
+int vlbm_sur_increment(vlbm_sur* s, const float* u, float* du, int32_t batch);
 /* One Adam step on the mean squared error of net(in_scale * u) against target
  * (both [batch][C][H][W] FP32 device arrays) with learning rate lr.  When
  * loss is not NULL the loss before the update is written there (host float)

@@ -181,16 +181,20 @@ class Surrogate:
     accumulation, trained with Adam.
 
     States are (B, channels, H, W) FP32 CUDA tensors.  With divergence_input the network also
-    reads in_scale[channels] times the divergence of channels 0, 1.  forward(u) = net(in_scale u);
+    reads in_scale[channels] times the divergence of channels 0, 1; with curl_output its channel 0
+    is a stream function whose central-difference curl is the velocity increment (divergence-free
+    in those differences).  forward(u) = net(in_scale u);
     advance(u) = u + out_scale net(in_scale u); train_step(u, target, lr) takes one Adam step on
     the mean squared error of net(in_scale u) against target (an increment divided by out_scale).
     """
 
     LAYERS = ((16, 64), (64, 64), (64, 64), (64, 64), (64, 16))
 
-    def __init__(self, H, W, max_batch, channels=2, divergence_input=False, seed=0, stream=None):
+    def __init__(self, H, W, max_batch, channels=2, divergence_input=False, curl_output=False, seed=0, stream=None):
         self.H, self.W, self.max_batch, self.channels = int(H), int(W), int(max_batch), int(channels)
-        features = _binding.VLBM_SUR_FEATURE_DIV if divergence_input else 0
+        self.curl_output = bool(curl_output)
+        features = (_binding.VLBM_SUR_FEATURE_DIV if divergence_input else 0) | \
+            (_binding.VLBM_SUR_FEATURE_CURL if curl_output else 0)
         self.inputs = self.channels + (1 if divergence_input else 0)
         self.handle = _binding.vlbm_sur_create(self.H, self.W, self.channels, features, self.max_batch, int(seed),
                                                stream)
@@ -234,6 +238,14 @@ class Surrogate:
         nxt = torch.empty_like(u) if out is None else out
         _binding.vlbm_sur_advance(self.handle, u, nxt, u.shape[0])
         return nxt
+
+    def increment(self, u, out=None):
+        """advance(u) - u, computed directly (out must not be u)."""
+        import torch
+        self._check_fields(u)
+        du = torch.empty_like(u) if out is None else out
+        _binding.vlbm_sur_increment(self.handle, u, du, u.shape[0])
+        return du
 
     def train_step(self, u, target, lr, want_loss=True):
         self._check_fields(u)

@@ -65,7 +65,7 @@ EXPORTED = [
     "vlbm_batch_last_error", "vlbm_tc_gemm_bf16", "vlbm_sur_conv3x3", "vlbm_sur_conv3x3_wgrad",
     "vlbm_sur_create", "vlbm_sur_destroy", "vlbm_sur_num_params", "vlbm_sur_forward", "vlbm_sur_train_step",
     "vlbm_sur_get_params", "vlbm_sur_get_grads", "vlbm_sur_set_params", "vlbm_sur_status", "vlbm_sur_advance",
-    "vlbm_sur_set_scaling", "vlbm_sur_set_train_noise", "vlbm_sur_launch_count",
+    "vlbm_sur_set_scaling", "vlbm_sur_set_train_noise", "vlbm_sur_launch_count", "vlbm_sur_increment",
     "vlbm_field_pool", "vlbm_sur_gather_pairs", "vlbm_field_stats", "vlbm_field_diff_norms",
 ]
 
@@ -149,6 +149,7 @@ lib.vlbm_sur_get_grads.argtypes = [_H, _V]
 lib.vlbm_sur_set_params.argtypes = [_H, _V]
 lib.vlbm_sur_status.argtypes = [_H]
 lib.vlbm_sur_advance.argtypes = [_H, _V, _V, ctypes.c_int32]
+lib.vlbm_sur_increment.argtypes = [_H, _V, _V, ctypes.c_int32]
 lib.vlbm_field_pool.argtypes = [_V, _V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                 _V]
 lib.vlbm_sur_gather_pairs.argtypes = [_V, _V, _V, _V, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
@@ -444,6 +445,7 @@ def vlbm_sur_conv3x3_wgrad(X, dZ, G, Gb, err, stream=None) -> None:
 
 
 VLBM_SUR_FEATURE_DIV = 1
+VLBM_SUR_FEATURE_CURL = 2
 
 
 def vlbm_sur_create(H: int, W: int, channels: int, features: int, max_batch: int, seed: int, stream=None):
@@ -511,6 +513,10 @@ def vlbm_sur_status(h) -> None:
 
 def vlbm_sur_advance(h, u, u_next, batch: int) -> None:
     _check(lib.vlbm_sur_advance(h, _V(u.data_ptr()), _V(u_next.data_ptr()), batch), "vlbm_sur_advance")
+
+
+def vlbm_sur_increment(h, u, du, batch: int) -> None:
+    _check(lib.vlbm_sur_increment(h, _V(u.data_ptr()), _V(du.data_ptr()), batch), "vlbm_sur_increment")
 
 
 def vlbm_field_pool(x, out, factor: int, stream=None) -> None:

@@ -720,6 +720,84 @@ __global__ void k_unpack_output(const __nv_bfloat16* __restrict__ Y, const float
     }
 }
 
+// Curl output (VLBM_SUR_FEATURE_CURL): channel 0 of Y is a stream function psi and the
+// velocity increment is (D_y psi, -D_x psi) with periodic central differences
+// D_y psi = (psi(y+1) - psi(y-1)) / 2, which the same differences see as divergence-free.
+// out = base + sc.v[0] (D_y psi, -D_x psi) for channels 0, 1 and base + sc.v[c] Y[c] for c >= 2.
+__device__ __forceinline__ float psi_at(const __nv_bfloat16* Y, long long img, int y, int x, int W) {
+    return __bfloat162float(Y[(img + (long long)y * W + x) * 16]);
+}
+__global__ void k_unpack_curl(const __nv_bfloat16* __restrict__ Y, const float* base, float* out, ChanScale sc,
+                              int H, int W, long long npix, int C) {
+    const long long plane = (long long)H * W;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const long long b = p / plane, q = p - b * plane, img = b * plane;
+    const int x = (int)(q % W), y = (int)(q / W);
+    const int xp = x + 1 == W ? 0 : x + 1, xm = x == 0 ? W - 1 : x - 1;
+    const int yp = y + 1 == H ? 0 : y + 1, ym = y == 0 ? H - 1 : y - 1;
+    const float dy = 0.5f * (psi_at(Y, img, yp, x, W) - psi_at(Y, img, ym, x, W));
+    const float dx = 0.5f * (psi_at(Y, img, y, xp, W) - psi_at(Y, img, y, xm, W));
+    const float inc[2] = {sc.v[0] * dy, -sc.v[0] * dx};
+    for (int c = 0; c < C; ++c) {
+        const long long i = (b * C + c) * plane + q;
+        const float d = c < 2 ? inc[c] : sc.v[c] * __bfloat162float(Y[p * 16 + c]);
+        out[i] = base ? base[i] + d : d;
+    }
+}
+
+// Curl-output loss, first pass: residuals r = prediction - target of the two velocity
+// channels (FP32, r[p][2]) and of channels c >= 2 (kept in r2 [p][14]); sum of squares into sse.
+__global__ void k_curl_residual(const __nv_bfloat16* __restrict__ Y, const float* __restrict__ t,
+                                float* __restrict__ r, double* __restrict__ sse, int H, int W, long long npix, int C) {
+    const long long plane = (long long)H * W;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float local = 0.0f;
+    if (p < npix) {
+        const long long b = p / plane, q = p - b * plane, img = b * plane;
+        const int x = (int)(q % W), y = (int)(q / W);
+        const int xp = x + 1 == W ? 0 : x + 1, xm = x == 0 ? W - 1 : x - 1;
+        const int yp = y + 1 == H ? 0 : y + 1, ym = y == 0 ? H - 1 : y - 1;
+        const float dy = 0.5f * (psi_at(Y, img, yp, x, W) - psi_at(Y, img, ym, x, W));
+        const float dx = 0.5f * (psi_at(Y, img, y, xp, W) - psi_at(Y, img, y, xm, W));
+        const float rx = dy - t[(b * C + 0) * plane + q], ry = -dx - t[(b * C + 1) * plane + q];
+        r[p * 16 + 0] = rx;
+        r[p * 16 + 1] = ry;
+        local = rx * rx + ry * ry;
+        for (int c = 2; c < C; ++c) {
+            const float rc = __bfloat162float(Y[p * 16 + c]) - t[(b * C + c) * plane + q];
+            r[p * 16 + c] = rc;
+            local += rc * rc;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(sse, (double)local);
+}
+
+// Curl-output loss, second pass: dY = d(loss)/dY with loss = sum r^2 * inv_count.
+// Channel 0 (psi): d(sum r^2)/d psi(p) = r_x(p - y) - r_x(p + y) + r_y(p + x) - r_y(p - x) (the factor 2 of
+// the square and the 1/2 of the central difference cancel).
+__global__ void k_curl_grad(const float* __restrict__ r, __nv_bfloat16* __restrict__ dY, int H, int W, long long npix,
+                            int C, float inv_count) {
+    const long long plane = (long long)H * W;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const long long b = p / plane, q = p - b * plane, img = b * plane;
+    const int x = (int)(q % W), y = (int)(q / W);
+    const int xp = x + 1 == W ? 0 : x + 1, xm = x == 0 ? W - 1 : x - 1;
+    const int yp = y + 1 == H ? 0 : y + 1, ym = y == 0 ? H - 1 : y - 1;
+    auto at = [&](int yy, int xx, int c) { return r[(img + (long long)yy * W + xx) * 16 + c]; };
+    const float g = at(ym, x, 0) - at(yp, x, 0) + at(y, xp, 1) - at(y, xm, 1);
+    __align__(16) __nv_bfloat16 e[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) e[c] = __float2bfloat16_rn(0.0f);
+    e[0] = __float2bfloat16_rn(g * inv_count);
+    for (int c = 2; c < C; ++c) e[c] = __float2bfloat16_rn(2.0f * r[p * 16 + c] * inv_count);
+    reinterpret_cast<uint4*>(dY + p * 16)[0] = reinterpret_cast<const uint4*>(e)[0];
+    reinterpret_cast<uint4*>(dY + p * 16)[1] = reinterpret_cast<const uint4*>(e)[1];
+}
+
 // Average pooling by an integer factor F of fields [B][C][H F][W F] -> [B][C][H][W], FP32;
 // the F x F sum is taken in a fixed order (rows, then columns) in FP32.
 __global__ void k_pool(const float* __restrict__ in, float* __restrict__ out, long long n_out, int H, int W, int F) {
@@ -962,6 +1040,7 @@ struct vlbm_sur {
     __nv_bfloat16* dA = nullptr;
     __nv_bfloat16* dB = nullptr;
     float* zero_bias = nullptr;
+    float* resid = nullptr;             // curl-output loss residuals [pixels][16] (curl mode only)
     double* sse = nullptr;
     int* err = nullptr;
 };
@@ -976,7 +1055,7 @@ uint64_t mix64_host(uint64_t z) {
 
 void free_sur(vlbm_sur* s) {
     void* ptrs[] = {s->params, s->grads, s->adam_m, s->adam_v, s->X0,  s->dA,
-                    s->dB,     s->zero_bias, s->sse, s->err,    s->noise_dev};
+                    s->dB,     s->zero_bias, s->sse, s->err,    s->noise_dev, s->resid};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int l = 0; l < kLayers; ++l) {
@@ -1046,9 +1125,10 @@ extern "C" int vlbm_sur_conv3x3_wgrad(const void* X, const void* dZ, float* G, f
 extern "C" int vlbm_sur_create(int32_t H, int32_t W, int32_t channels, int32_t features, int32_t max_batch,
                                uint64_t seed, void* stream, vlbm_sur** out) {
     if (!out || H < 1 || W < 1 || max_batch < 1 || channels < 1 || channels > 16) return VLBM_EINVAL;
-    if (features & ~VLBM_SUR_FEATURE_DIV) return VLBM_EINVAL;
+    if (features & ~(VLBM_SUR_FEATURE_DIV | VLBM_SUR_FEATURE_CURL)) return VLBM_EINVAL;
     const int n_in = channels + ((features & VLBM_SUR_FEATURE_DIV) ? 1 : 0);
-    if (n_in > 16 || ((features & VLBM_SUR_FEATURE_DIV) && channels < 2)) return VLBM_EINVAL;
+    if (n_in > 16 || ((features & (VLBM_SUR_FEATURE_DIV | VLBM_SUR_FEATURE_CURL)) && channels < 2))
+        return VLBM_EINVAL;
     if ((long long)H * W * max_batch >= (1ll << 31)) return VLBM_EINVAL;
     *out = nullptr;
     vlbm_sur* s = new (std::nothrow) vlbm_sur();
@@ -1085,6 +1165,7 @@ extern "C" int vlbm_sur_create(int32_t H, int32_t W, int32_t channels, int32_t f
     alloc((void**)&s->sse, sizeof(double));
     alloc((void**)&s->err, sizeof(int));
     alloc((void**)&s->noise_dev, sizeof(ChanScale));
+    if (features & VLBM_SUR_FEATURE_CURL) alloc((void**)&s->resid, npix * 16 * sizeof(float));
     for (int l = 0; l < kLayers; ++l) {
         alloc((void**)&s->Wb[l], (size_t)kCout[l] * 9 * kCin[l] * 2);
         alloc((void**)&s->Wflip[l], (size_t)kCout[l] * 9 * kCin[l] * 2);
@@ -1187,14 +1268,35 @@ extern "C" int vlbm_sur_set_train_noise(vlbm_sur* s, const float* sigma, uint64_
     return VLBM_OK;
 }
 
+extern "C" int vlbm_sur_increment(vlbm_sur* s, const float* u, float* du, int32_t batch) {
+    if (!s || !u || !du || batch < 1 || batch > s->maxB || du == u) return VLBM_EINVAL;
+    int rc = sur_forward(s, u, batch, false);
+    if (rc) return rc;
+    const long long plane = (long long)s->H * s->W, npix = plane * batch;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (s->features & VLBM_SUR_FEATURE_CURL)
+        k_unpack_curl<<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(s->Y[kLayers - 1], nullptr, du,
+                                                                              s->out_scale, s->H, s->W, npix, s->C);
+    else
+        k_unpack_output<<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(s->Y[kLayers - 1], nullptr, du,
+                                                                                s->out_scale, plane, npix, s->C);
+    return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
+}
+
 extern "C" int vlbm_sur_advance(vlbm_sur* s, const float* u, float* u_next, int32_t batch) {
     if (!s || !u || !u_next || batch < 1 || batch > s->maxB) return VLBM_EINVAL;
     int rc = sur_forward(s, u, batch, false);
     if (rc) return rc;
     const long long plane = (long long)s->H * s->W, npix = plane * batch;
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    k_unpack_output<<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(s->Y[kLayers - 1], u, u_next,
-                                                                            s->out_scale, plane, npix, s->C);
+    if (s->features & VLBM_SUR_FEATURE_CURL) {
+        if (u_next == u) return VLBM_EINVAL;     // the curl reads neighbours of the output's source
+        k_unpack_curl<<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(s->Y[kLayers - 1], u, u_next,
+                                                                              s->out_scale, s->H, s->W, npix, s->C);
+    } else {
+        k_unpack_output<<<(unsigned)((npix + 255) / 256), 256, 0, s->stream>>>(s->Y[kLayers - 1], u, u_next,
+                                                                                s->out_scale, plane, npix, s->C);
+    }
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
 }
 
@@ -1256,8 +1358,16 @@ extern "C" int vlbm_sur_train_step(vlbm_sur* s, const float* u, const float* tar
         return VLBM_ECUDA;
     const unsigned eb = (unsigned)((npix + 255) / 256);
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    k_mse_grad<<<eb, 256, 0, s->stream>>>(s->Y[kLayers - 1], target, s->dA, s->sse, plane, npix,
-                                          1.0f / (float)((long long)s->C * npix), s->C);
+    if (s->features & VLBM_SUR_FEATURE_CURL) {
+        k_curl_residual<<<eb, 256, 0, s->stream>>>(s->Y[kLayers - 1], target, s->resid, s->sse, s->H, s->W, npix,
+                                                   s->C);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        k_curl_grad<<<eb, 256, 0, s->stream>>>(s->resid, s->dA, s->H, s->W, npix, s->C,
+                                               1.0f / (float)((long long)s->C * npix));
+    } else {
+        k_mse_grad<<<eb, 256, 0, s->stream>>>(s->Y[kLayers - 1], target, s->dA, s->sse, plane, npix,
+                                              1.0f / (float)((long long)s->C * npix), s->C);
+    }
     // backward, last layer first: dA holds dZ of layer l (its pre-activation gradient)
     for (int l = kLayers - 1; l >= 0; --l) {
         const void* xin = l == 0 ? (const void*)s->X0 : (const void*)s->Y[l - 1];

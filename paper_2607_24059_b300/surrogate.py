@@ -47,6 +47,7 @@ class Config:
     warmup: int = 20                  # surrogate steps run before the first snapshot (phi settles)
     channels: int = 3                 # u_x, u_y, phi
     divergence_input: bool = False    # FP32 divergence of u as an extra input channel (rollouts go unstable)
+    curl_output: bool = True          # velocity increment = curl of a predicted stream function
     phi_weight: float = 0.1           # weight of the phi channel in the training loss
     noise_u: float = 0.0              # training-input noise (std, scaled units): velocity channels
     noise_phi: float = 0.0            # ... phi channel
@@ -182,6 +183,8 @@ def scaling(cfg: Config, snaps: torch.Tensor):
     if cfg.divergence_input:
         in_scale.append(1.0 / divergence_rms(snaps))
     out_scale = list(inc_rms)
+    if cfg.curl_output:                  # one scale for both velocity channels of the curl
+        out_scale[0] = out_scale[1] = math.sqrt(0.5 * (inc_rms[0] ** 2 + inc_rms[1] ** 2))
     if cfg.channels > 2:
         out_scale[2] = inc_rms[2] / math.sqrt(cfg.phi_weight)
     return in_scale, out_scale
@@ -223,9 +226,9 @@ def train(net: Surrogate, snaps: torch.Tensor, cfg: Config, out_scale, log=None,
             "loss_first": losses[0][1], "loss_last": losses[-1][1], "losses": losses}
 
 
-def one_step_error(net: Surrogate, snaps: torch.Tensor, out_scale, chunk: int = 32) -> list:
-    """Per-channel relative L2 error |net(s_k) - (s_{k+1} - s_k) / S| / |(s_{k+1} - s_k) / S| over
-    every pair of snaps."""
+def one_step_error(net: Surrogate, snaps: torch.Tensor, chunk: int = 32) -> list:
+    """Per-channel relative L2 error |du_pred - (s_{k+1} - s_k)| / |s_{k+1} - s_k| of the predicted
+    increment over every pair of snaps."""
     T, P1, C, c, _ = snaps.shape
     flat = snaps.view(T * P1, C, c, c)
     idx = torch.from_numpy(pair_starts(snaps)).to(snaps.device)
@@ -235,8 +238,8 @@ def one_step_error(net: Surrogate, snaps: torch.Tensor, out_scale, chunk: int = 
     err, ref = np.zeros(C), np.zeros(C)
     for i in range(0, len(idx), chunk):
         n = min(chunk, len(idx) - i)
-        B.vlbm_sur_gather_pairs(flat, idx[i:i + n], u[:n], tgt[:n], [1.0 / x for x in out_scale])
-        net.forward(u[:n], out=y[:n])
+        B.vlbm_sur_gather_pairs(flat, idx[i:i + n], u[:n], tgt[:n], [1.0] * C)
+        net.increment(u[:n], out=y[:n])
         B.vlbm_field_diff_norms(y[:n].view(n * C, c, c), tgt[:n].view(n * C, c, c), nrm[:n * C])
         h = nrm[:n * C].view(n, C, 2).sum(0).cpu().numpy()
         err += h[:, 0]
@@ -452,7 +455,7 @@ def train_surrogate(cfg: Config, log=print, max_seconds=None) -> Trained:
     log(f"data: {tuple(train_snaps.shape)} + {tuple(test_snaps.shape)} in {t_data:.1f} s; input factors {in_scale}, "
         f"output factors {out_scale}, divergence-ratio limit {div_limit:.3e}")
     net = Surrogate(cfg.coarse, cfg.coarse, max(cfg.batch, 32), channels=cfg.channels,
-                    divergence_input=cfg.divergence_input, seed=cfg.net_seed)
+                    divergence_input=cfg.divergence_input, curl_output=cfg.curl_output, seed=cfg.net_seed)
     net.set_scaling(in_scale, out_scale)
     sigma = [cfg.noise_u, cfg.noise_u] + [cfg.noise_phi] * (cfg.channels - 2) + ([cfg.noise_div] if cfg.divergence_input else [])
     net.set_train_noise(sigma, seed=cfg.seed_base + 11)
@@ -465,7 +468,7 @@ def run_pipeline(cfg: Config, log=print, weights_out=None) -> dict:
     t0 = time.perf_counter()
     tr = train_surrogate(cfg, log)
     net = tr.net
-    val = one_step_error(net, tr.test_snaps, tr.out_scale)
+    val = one_step_error(net, tr.test_snaps)
     log(f"one-step relative increment error on test pairs, per channel: {val}")
     ref = tr.test_snaps.transpose(0, 1).contiguous()          # (steps + 1, states, C, c, c)
     u0 = ref[0].contiguous()

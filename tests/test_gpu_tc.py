@@ -95,12 +95,13 @@ def ste_bf16(t):
     return t + (t.to(torch.bfloat16).float() - t).detach()
 
 
-def torch_surrogate(params, u):
-    """FP32 reference of the surrogate network with the kernels' BF16 roundings of weights and activations."""
+def torch_surrogate(params, u, channels=2):
+    """FP32 reference of the surrogate network with the kernels' BF16 roundings of weights and activations;
+    returns the first `channels` output channels."""
     import torch.nn.functional as F
-    B, _, H, W = u.shape
+    B, C, H, W = u.shape
     x = torch.zeros(B, 16, H, W, device=u.device)
-    x = torch.cat([u, x[:, 2:]], dim=1)
+    x = torch.cat([u, x[:, C:]], dim=1)
     x = ste_bf16(x)
     layers = v.Surrogate.split_params(params)
     for l, (Wl, bl) in enumerate(layers):
@@ -108,7 +109,7 @@ def torch_surrogate(params, u):
         w = ste_bf16(Wl).reshape(cout, 3, 3, cin).permute(0, 3, 1, 2)
         z = F.conv2d(F.pad(x, (1, 1, 1, 1), mode="circular"), w) + bl.view(1, -1, 1, 1)
         x = ste_bf16(F.gelu(z, approximate="tanh") if l < len(layers) - 1 else z)
-    return x[:, :2]
+    return x[:, :channels]
 
 
 def smooth_fields(B, H, W, seed):
@@ -197,3 +198,56 @@ def test_surrogate_training_reduces_loss():
     assert torch.equal(net2.forward(u), net.forward(u))
     net.close()
     net2.close()
+
+
+def curl_increment(y, s0=1.0):
+    """(D_y psi, -D_x psi) of psi = y[:, 0] with periodic central differences; channels >= 2 unchanged."""
+    psi = y[:, 0]
+    dx = 0.5 * (psi.roll(-1, 2) - psi.roll(1, 2))
+    dy = 0.5 * (psi.roll(-1, 1) - psi.roll(1, 1))
+    return torch.cat([(s0 * dy)[:, None], (-s0 * dx)[:, None], y[:, 2:]], 1)
+
+
+def test_curl_increment_matches_torch_and_is_divergence_free():
+    B, H, W = 2, 24, 40
+    net = v.Surrogate(H, W, max_batch=B, channels=3, curl_output=True, seed=8)
+    net.set_scaling([1.0, 1.0, 0.5], [0.3, 0.3, 0.2])
+    u = smooth_fields(B, H, W, seed=2)
+    u = torch.cat([u, 0.5 * u[:, :1]], 1).contiguous()
+    y = net.forward(u)
+    du = net.increment(u)
+    ref = curl_increment(y, 0.3)
+    ref[:, 2] *= 0.2
+    assert torch.allclose(du, ref, rtol=1e-6, atol=1e-7)
+    nxt = net.advance(u)
+    assert torch.allclose(nxt, u + ref, rtol=1e-6, atol=1e-6)
+    st = torch.empty(B, 3, dtype=torch.float64, device="cuda")
+    v.vlbm_field_stats(du, st)
+    assert (st[:, 1] / st[:, 2]).max().item() <= 1e-10      # central-difference divergence vanishes
+    net.close()
+
+
+def test_curl_gradients_match_autograd(no_tf32):
+    B, H, W = 2, 24, 32
+    net = v.Surrogate(H, W, max_batch=B, channels=3, curl_output=True, seed=4)
+    p0 = net.params()
+    u = smooth_fields(B, H, W, seed=6)
+    u = torch.cat([u, 0.5 * u[:, 1:2]], 1).contiguous()
+    target = torch.cat([0.05 * laplacian(u[:, :2]), 0.1 * u[:, 2:3]], 1).contiguous()
+    loss = net.train_step(u, target, lr=0.0)
+    grads = net.grads()
+    w = p0.clone().requires_grad_(True)
+    pred = curl_increment(torch_surrogate(w, u, channels=3))
+    ref_loss = ((pred - target) ** 2).mean()
+    ref_loss.backward()
+    assert abs(loss - ref_loss.item()) <= 1e-2 * ref_loss.item()
+    for l, ((gk, bk), (gr, br)) in enumerate(zip(v.Surrogate.split_params(grads), v.Surrogate.split_params(w.grad))):
+        for a, b in ((gk, gr), (bk, br)):
+            nb = b.norm().item()
+            if nb == 0.0:
+                assert a.abs().max().item() == 0.0
+                continue
+            assert (a - b).norm().item() <= 5e-2 * nb, f"layer {l}"
+    g = v.Surrogate.split_params(grads)
+    assert g[4][0][1].abs().max().item() == 0.0 and g[4][1][1].item() == 0.0     # channel 1 unused
+    net.close()
