@@ -47,7 +47,8 @@ class Config:
     warmup: int = 20                  # surrogate steps run before the first snapshot (phi settles)
     channels: int = 3                 # u_x, u_y, phi
     divergence_input: bool = False    # FP32 divergence of u as an extra input channel (rollouts go unstable)
-    curl_output: bool = True          # velocity increment = curl of a predicted stream function
+    curl_output: bool = False         # velocity increment = curl of a predicted stream function (no
+                                      # divergence fallbacks, but unstable past ~40 steps when fully trained)
     phi_weight: float = 0.1           # weight of the phi channel in the training loss
     noise_u: float = 0.0              # training-input noise (std, scaled units): velocity channels
     noise_phi: float = 0.0            # ... phi channel
