@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libvlbm.so")
 if not os.path.exists(LIB_PATH):
     raise ImportError(
         f"{LIB_PATH} is missing: build the CUDA library first "
-        "(python -m paper_2607_24059_b300.build, or __graft_entry__.build())")
+        "(python paper_2607_24059_b300/build.py, or __graft_entry__.build())")
 
 lib = ctypes.CDLL(LIB_PATH)
 
