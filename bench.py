@@ -90,6 +90,8 @@ def parse_args():
     ap.add_argument("--sur-trajectories", type=int, default=200, help="sur256: training trajectories (100 pairs each)")
     ap.add_argument("--sur-epochs", type=float, default=8.0, help="sur256: training epochs")
     ap.add_argument("--sur-batch", type=int, default=32, help="sur256: states advanced together in the timed rollouts")
+    ap.add_argument("--conv-only", action="store_true",
+                    help="sur256: time only the dominant kernel (the 64 -> 64 conv of the rollout), no training")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--reference-seconds", type=float, default=150.0, help="cap on the reference arm's timed steps")
@@ -498,6 +500,43 @@ def run_batch(args):
     return 0
 
 
+def conv_roofline(nb, c, stream, reps=50):
+    """The rollout's dominant kernel, the 64 -> 64 periodic 3x3 conv with GELU on nb states of
+    c^2 pixels, timed alone with CUDA events (reps launches after 3 warm-up launches)."""
+    import torch
+    import paper_2607_24059_b300 as vlbm
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(7)
+    X = torch.randn(nb, c, c, 64, device="cuda", generator=g).to(torch.bfloat16)
+    Wt = (0.05 * torch.randn(64, 9, 64, device="cuda", generator=g)).to(torch.bfloat16)
+    bias = torch.zeros(64, device="cuda")
+    Yc = torch.empty_like(X)
+    for _ in range(3):
+        vlbm.vlbm_sur_conv3x3(X, Wt, bias, Yc, err, act=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        vlbm.vlbm_sur_conv3x3(X, Wt, bias, Yc, err, act=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    conv_ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * nb * c * c * 9 * 64 * 64
+    peaks = {}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            peaks = json.load(fh)
+    peak = float(peaks.get("bf16_tflops", 1800.0))
+    achieved = flops / (conv_ms * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_kind": "measured (cuBLAS bf16 burst)" if "bf16_tflops" in peaks else "fallback",
+            "traffic": None, "kernel": "k_conv3x3<64, 64, true, false>", "avg_launch_ms": conv_ms,
+            "flops_per_launch": flops, "launches_timed": reps,
+            "algorithmic_bytes_per_launch": nb * c * c * 64 * 2 * 2}
+
+
 def run_surrogate(args):
     """Learned surrogate (256^2 states pooled 4x from 1024^2 runs of the scheme; u_x, u_y, phi):
     one step of this workload is a checked rollout of --sur-batch states by 100 surrogate steps
@@ -508,6 +547,12 @@ def run_surrogate(args):
     from paper_2607_24059_b300 import surrogate as sg
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    if args.conv_only:
+        if rank == 0:
+            print(json.dumps({"workload": "sur256 dominant kernel alone", "states": args.sur_batch,
+                              "roofline": conv_roofline(args.sur_batch, args.n // 4, torch.cuda.current_stream())}),
+                  flush=True)
+        return 0
     dist = dist_init(world, "nccl")
     cfg = sg.Config(fine=args.n, train_trajectories=args.sur_trajectories, epochs=args.sur_epochs)
     tr = sg.train_surrogate(cfg, log=lambda m: print(m, file=sys.stderr, flush=True))
@@ -525,7 +570,7 @@ def run_surrogate(args):
         ro.run(u0, steps)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    l0, c0 = vlbm.vlbm_sur_launch_count(), ro.coarse.launch_count()
+    l0, c0 = vlbm.vlbm_sur_launch_count(), ro.coarse.info()[2]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     fallbacks = 0
     if dist:
@@ -541,7 +586,7 @@ def run_surrogate(args):
     if dist:
         dist.barrier()
     elapsed = max_over_ranks(start.elapsed_time(end) / 1e3, dist, "cuda")
-    launches = (vlbm.vlbm_sur_launch_count() - l0) + (ro.coarse.launch_count() - c0)
+    launches = (vlbm.vlbm_sur_launch_count() - l0) + (ro.coarse.info()[2] - c0)
     ms_per_state = elapsed / args.steps / nb * 1e3
     value = world * t_fine / ms_per_state
     # end to end: states from pinned host memory, the checked rollout, states back to pinned host
@@ -557,33 +602,8 @@ def run_surrogate(args):
     torch.cuda.synchronize()
     e2e_el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e_value = world * t_fine / (e2e_el / args.steps / nb * 1e3)
-    # roofline of the dominant kernel: the 64 -> 64 periodic conv of the rollout, timed alone
     c = cfg.coarse
-    err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    X = torch.randn(nb, c, c, 64, device="cuda").to(torch.bfloat16)
-    Wt = (0.05 * torch.randn(64, 9, 64, device="cuda")).to(torch.bfloat16)
-    bias = torch.zeros(64, device="cuda")
-    Yc = torch.empty_like(X)
-    for _ in range(3):
-        vlbm.vlbm_sur_conv3x3(X, Wt, bias, Yc, err, act=True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 50
-    e0.record(stream)
-    for _ in range(reps):
-        vlbm.vlbm_sur_conv3x3(X, Wt, bias, Yc, err, act=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    assert int(err.item()) == 0
-    conv_ms = e0.elapsed_time(e1) / reps
-    flops = 2.0 * nb * c * c * 9 * 64 * 64
-    peaks = {}
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(path):
-        with open(path) as fh:
-            peaks = json.load(fh)
-    peak = float(peaks.get("bf16_tflops", 1800.0))
-    peak_kind = "measured (cuBLAS bf16 burst)" if "bf16_tflops" in peaks else "fallback"
-    achieved = flops / (conv_ms * 1e-3) / 1e12
+    roof = conv_roofline(nb, c, stream)
     ro.close()
     if rank != 0:
         if dist:
@@ -606,10 +626,7 @@ def run_surrogate(args):
             "fallbacks_per_state_step": fallbacks / (args.steps * nb * steps),
             "fine_fp32_ms_per_state": t_fine, "surrogate_ms_per_state": ms_per_state,
             "l2": "rollout states 32 x 3 x 256^2 FP32 = 25 MB (L2-resident, as in use)"},
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                     "kernel": "k_conv3x3<64, 64, true, false>", "avg_launch_ms": conv_ms,
-                     "flops_per_launch": flops},
+        "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "x time-to-t speedup per state vs plain FP32 LBM 1024^2",
                 "h2d_bytes_per_step": h_in.numel() * 4, "d2h_bytes_per_step": h_out.numel() * 4},
         "gpu_launches": launches,

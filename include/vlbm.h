@@ -255,6 +255,18 @@ int vlbm_batch_set_config(vlbm_batch* b, int32_t threads, int32_t blocks_per_sm,
  * may be NULL).  Synchronises the batch's stream. */
 int vlbm_batch_autotune(vlbm_batch* b, int32_t repeats, int32_t* config_out, double* best_ms);
 
+/* Masked initialisation of equally sized 2D problems (same n, dx, gamma,
+ * rho_bar) from one device state array states [count][channels][ny][nx] FP32:
+ * every problem p with mask[p] != 0 (device uint8 array of count entries) is
+ * set to the equilibrium of u = channels 0, 1 and phi = channel 2 (0 when
+ * channels == 2), as vlbm_batch_init does for one problem.  One launch,
+ * asynchronous.  VLBM_EINVAL for unequal problems or host pointers. */
+int vlbm_batch_init_states(vlbm_batch* b, const float* states, int32_t channels, const uint8_t* mask);
+/* Masked read-out into the same kind of array: u of problem p into channels
+ * 0, 1 of states[p] and, when channels >= 3, phi into channel 2, for every p
+ * with mask[p] != 0; other entries are left untouched.  One launch. */
+int vlbm_batch_macros_states(vlbm_batch* b, float* states, int32_t channels, const uint8_t* mask);
+
 /* Total nodes, steps taken and kernel launches issued; any pointer may be NULL. */
 int vlbm_batch_info(const vlbm_batch* b, int64_t* nodes_total, int64_t* step, int64_t* launches);
 const char* vlbm_batch_last_error(const vlbm_batch* b);

@@ -62,7 +62,7 @@ EXPORTED = [
     "vlbm_strerror", "vlbm_last_error", "vlbm_invariants_noalloc",
     "vlbm_batch_create", "vlbm_batch_destroy", "vlbm_batch_init", "vlbm_batch_step", "vlbm_batch_macros",
     "vlbm_batch_invariants", "vlbm_batch_set_config", "vlbm_batch_autotune", "vlbm_batch_info",
-    "vlbm_batch_last_error", "vlbm_tc_gemm_bf16", "vlbm_sur_conv3x3", "vlbm_sur_conv3x3_wgrad",
+    "vlbm_batch_last_error", "vlbm_batch_init_states", "vlbm_batch_macros_states", "vlbm_tc_gemm_bf16", "vlbm_sur_conv3x3", "vlbm_sur_conv3x3_wgrad",
     "vlbm_sur_create", "vlbm_sur_destroy", "vlbm_sur_num_params", "vlbm_sur_forward", "vlbm_sur_train_step",
     "vlbm_sur_get_params", "vlbm_sur_get_grads", "vlbm_sur_set_params", "vlbm_sur_status", "vlbm_sur_advance",
     "vlbm_sur_set_scaling", "vlbm_sur_set_train_noise", "vlbm_sur_launch_count", "vlbm_sur_increment",
@@ -125,6 +125,8 @@ lib.vlbm_batch_set_config.argtypes = [_H, ctypes.c_int32, ctypes.c_int32, ctypes
 lib.vlbm_batch_autotune.argtypes = [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
 lib.vlbm_batch_info.argtypes = [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int64)]
+lib.vlbm_batch_init_states.argtypes = [_H, _V, ctypes.c_int32, _V]
+lib.vlbm_batch_macros_states.argtypes = [_H, _V, ctypes.c_int32, _V]
 lib.vlbm_batch_last_error.argtypes = [_H]
 lib.vlbm_batch_last_error.restype = ctypes.c_char_p
 lib.vlbm_tc_gemm_bf16.argtypes = [_V, _V, _V, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _V, _V]
@@ -407,6 +409,18 @@ def vlbm_batch_info(b):
     n, s, l = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _bcheck(lib.vlbm_batch_info(b, ctypes.byref(n), ctypes.byref(s), ctypes.byref(l)), "vlbm_batch_info", b)
     return n.value, s.value, l.value
+
+
+def vlbm_batch_init_states(b, states, mask) -> None:
+    """Masked init of equal problems from states (count, C, ny, nx) fp32 and mask (count,) uint8, on the device."""
+    _check(lib.vlbm_batch_init_states(b, _V(states.data_ptr()), states.shape[1], _V(mask.data_ptr())),
+           "vlbm_batch_init_states")
+
+
+def vlbm_batch_macros_states(b, states, mask) -> None:
+    """Masked read-out of u (and phi) of equal problems into states (count, C, ny, nx) fp32."""
+    _check(lib.vlbm_batch_macros_states(b, _V(states.data_ptr()), states.shape[1], _V(mask.data_ptr())),
+           "vlbm_batch_macros_states")
 
 
 def vlbm_batch_last_error(b) -> str:

@@ -75,6 +75,40 @@ k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
     }
 }
 
+// Masked initialisation / read-out of equally sized problems against one state
+// array states [count][channels][ny][nx] FP32: channels 0, 1 = u, channel 2 =
+// phi when channels >= 3.  blockIdx.y = problem; problems with mask 0 are skipped.
+template <class S, bool SPLIT>
+__global__ void __launch_bounds__(kThreads)
+k_batch_init_states(char* __restrict__ level, const BatchProblem<typename Storage<S>::C>* __restrict__ probs,
+                    const float* __restrict__ states, int channels, const uint8_t* __restrict__ mask, double dx,
+                    double gamma, double rho_bar, double p_bar) {
+    const int p = blockIdx.y;
+    if (!mask[p]) return;
+    const BatchProblem<typename Storage<S>::C>& P = probs[p];
+    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= P.plane) return;
+    const float* st = states + (long long)p * channels * P.plane;
+    init_node_2d<S, SPLIT, float>(Layout<S, SPLIT, 5>{level + P.offset, P.plane}, P.plane, node, st,
+                                  channels > 2 ? st + 2 * P.plane : nullptr, P.k, dx, gamma, rho_bar, p_bar);
+}
+
+template <class S, bool SPLIT>
+__global__ void __launch_bounds__(kThreads)
+k_batch_macros_states(const char* __restrict__ level, const BatchProblem<typename Storage<S>::C>* __restrict__ probs,
+                      float* __restrict__ states, int channels, const uint8_t* __restrict__ mask, double dx,
+                      double gamma, double rho_bar, double p_bar) {
+    const int p = blockIdx.y;
+    if (!mask[p]) return;
+    const BatchProblem<typename Storage<S>::C>& P = probs[p];
+    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= P.plane) return;
+    float* st = states + (long long)p * channels * P.plane;
+    macros_node_2d<S, SPLIT, float>(Layout<S, SPLIT, 5>{const_cast<char*>(level) + P.offset, P.plane}, P.plane, node,
+                                    nullptr, st, channels > 2 ? st + 2 * P.plane : nullptr, P.k, dx, gamma, rho_bar,
+                                    p_bar);
+}
+
 }  // namespace
 
 struct vlbm_batch {
@@ -460,6 +494,58 @@ extern "C" int vlbm_batch_macros(vlbm_batch* b, int32_t problem, void* rho, void
             if (host[i]) VLBM_BCUDA(b, cudaMemcpyAsync(out[i], dev[i], bytes[i], cudaMemcpyDeviceToHost, b->stream));
         VLBM_BCUDA(b, cudaStreamSynchronize(b->stream));
     }
+    return VLBM_OK;
+}
+
+namespace {
+
+// The masked state entry points need problems of one size and one dx, gamma, rho_bar.
+bool uniform_problems(const vlbm_batch* b) {
+    for (int i = 1; i < b->count; ++i) {
+        const vlbm_params &a = b->p[0], &q = b->p[i];
+        if (q.n[0] != a.n[0] || q.n[1] != a.n[1] || q.dx != a.dx || q.gamma != a.gamma || q.rho_bar != a.rho_bar)
+            return false;
+    }
+    return true;
+}
+
+template <class S, bool SPLIT>
+void launch_init_states(vlbm_batch* b, const float* states, int channels, const uint8_t* mask) {
+    const vlbm_params& p = b->p[0];
+    const dim3 grid((unsigned)((b->d[0].nodes + kThreads - 1) / kThreads), (unsigned)b->count);
+    k_batch_init_states<S, SPLIT><<<grid, kThreads, 0, b->stream>>>(
+        b->level[b->cur], (const BatchProblem<typename Storage<S>::C>*)b->table, states, channels, mask, p.dx,
+        p.gamma, p.rho_bar, std::pow(p.rho_bar, p.gamma));
+}
+
+template <class S, bool SPLIT>
+void launch_macros_states(vlbm_batch* b, float* states, int channels, const uint8_t* mask) {
+    const vlbm_params& p = b->p[0];
+    const dim3 grid((unsigned)((b->d[0].nodes + kThreads - 1) / kThreads), (unsigned)b->count);
+    k_batch_macros_states<S, SPLIT><<<grid, kThreads, 0, b->stream>>>(
+        b->level[b->cur], (const BatchProblem<typename Storage<S>::C>*)b->table, states, channels, mask, p.dx,
+        p.gamma, p.rho_bar, std::pow(p.rho_bar, p.gamma));
+}
+
+}  // namespace
+
+extern "C" int vlbm_batch_init_states(vlbm_batch* b, const float* states, int32_t channels, const uint8_t* mask) {
+    if (!b || !states || !mask || channels < 2 || b->count > 65535) return VLBM_EINVAL;
+    if (b->p[0].dim != 2 || !uniform_problems(b) || !device_pointer(states) || !device_pointer(mask))
+        return VLBM_EINVAL;
+    VLBM_BATCH_DISPATCH(b, launch_init_states, b, states, channels, mask);
+    VLBM_BCUDA(b, cudaGetLastError());
+    b->launches++;
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_batch_macros_states(vlbm_batch* b, float* states, int32_t channels, const uint8_t* mask) {
+    if (!b || !states || !mask || channels < 2 || b->count > 65535) return VLBM_EINVAL;
+    if (b->p[0].dim != 2 || !uniform_problems(b) || !device_pointer(states) || !device_pointer(mask))
+        return VLBM_EINVAL;
+    VLBM_BATCH_DISPATCH(b, launch_macros_states, b, states, channels, mask);
+    VLBM_BCUDA(b, cudaGetLastError());
+    b->launches++;
     return VLBM_OK;
 }
 

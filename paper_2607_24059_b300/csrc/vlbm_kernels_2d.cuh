@@ -226,14 +226,13 @@ k_stream_collide_2d_generic(const char* __restrict__ fin_b, char* __restrict__ f
 // q = rho u, g = f^eq(rho, q) - F.  The density deviation is formed in FP64:
 // gamma = 1 gives dr = dx^2 rho_bar phi exactly; otherwise
 // dr = rho_bar expm1(log1p(dx^2 rho_bar phi / P(rho_bar)) / gamma).
+// Equilibrium state of one node from u (planes x, y) and phi (may be NULL).
 template <class S, bool SPLIT, class T>
-__global__ void __launch_bounds__(kThreads)
-k_init_2d(char* __restrict__ f_b, long long plane, const T* __restrict__ u, const T* __restrict__ phi,
-          Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
+__device__ __forceinline__ void init_node_2d(const Layout<S, SPLIT, 5>& f, long long plane, long long node,
+                                             const T* __restrict__ u, const T* __restrict__ phi,
+                                             const Coef<typename Storage<S>::C>& k, double dx, double gamma,
+                                             double rho_bar, double p_bar) {
     using C = typename Storage<S>::C;
-    const Layout<S, SPLIT, 5> f{f_b, plane};
-    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= plane) return;
     const double ph = phi ? (double)phi[node] : 0.0;
     const double lift = dx * dx * rho_bar * ph;
     const double dr = (gamma == 1.0) ? lift : rho_bar * expm1(log1p(lift / p_bar) / gamma);
@@ -255,14 +254,22 @@ k_init_2d(char* __restrict__ f_b, long long plane, const T* __restrict__ u, cons
     }
 }
 
-// Macroscopic fields of the state (moments of g*(t) = moments of g(t)), in FP64.
 template <class S, bool SPLIT, class T>
 __global__ void __launch_bounds__(kThreads)
-k_macros_2d(const char* __restrict__ f_b, long long plane, T* __restrict__ rho, T* __restrict__ u, T* __restrict__ phi,
-            Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
-    const Layout<S, SPLIT, 5> f{const_cast<char*>(f_b), plane};
+k_init_2d(char* __restrict__ f_b, long long plane, const T* __restrict__ u, const T* __restrict__ phi,
+          Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= plane) return;
+    init_node_2d<S, SPLIT, T>(Layout<S, SPLIT, 5>{f_b, plane}, plane, node, u, phi, k, dx, gamma, rho_bar, p_bar);
+}
+
+// Macroscopic fields of the state (moments of g*(t) = moments of g(t)), in FP64.
+// rho, u (planes x, y) and phi of one node; any output may be NULL.
+template <class S, bool SPLIT, class T>
+__device__ __forceinline__ void macros_node_2d(const Layout<S, SPLIT, 5>& f, long long plane, long long node,
+                                               T* __restrict__ rho, T* __restrict__ u, T* __restrict__ phi,
+                                               const Coef<typename Storage<S>::C>& k, double dx, double gamma,
+                                               double rho_bar, double p_bar) {
     double m[3];
 #pragma unroll
     for (int fld = 0; fld < 3; ++fld) {
@@ -285,6 +292,16 @@ k_macros_2d(const char* __restrict__ f_b, long long plane, T* __restrict__ rho, 
         const double dP = (gamma == 1.0) ? m[0] : p_bar * expm1(gamma * log1p(m[0] / rho_bar));
         phi[node] = (T)(dP / (dx * dx * rho_bar));
     }
+}
+
+template <class S, bool SPLIT, class T>
+__global__ void __launch_bounds__(kThreads)
+k_macros_2d(const char* __restrict__ f_b, long long plane, T* __restrict__ rho, T* __restrict__ u, T* __restrict__ phi,
+            Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
+    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= plane) return;
+    macros_node_2d<S, SPLIT, T>(Layout<S, SPLIT, 5>{const_cast<char*>(f_b), plane}, plane, node, rho, u, phi, k, dx,
+                                gamma, rho_bar, p_bar);
 }
 
 // Invariant partials over the stored lattice (no transport), grid-stride.

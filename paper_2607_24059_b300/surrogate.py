@@ -35,7 +35,7 @@ import numpy as np
 import torch
 
 from . import _binding as B
-from . import Lattice, Surrogate
+from . import Batch, Lattice, Surrogate
 
 
 @dataclass
@@ -269,7 +269,12 @@ class Rollout:
         self.stats = torch.empty(batch, 3, dtype=torch.float64, device=device)
         self.stats_h = torch.empty(batch, 3, dtype=torch.float64).pin_memory()
         self.nrm = torch.empty(batch, 2, dtype=torch.float64, device=device)
-        self.coarse = Lattice((c, c), 2 * math.pi / c, cfg.nu, precision="fp32")
+        # the fallback: one coarse problem per state, advanced together; a failing step
+        # re-initialises the flagged problems from their (u, phi) and reads them back
+        # with one masked launch each
+        self.coarse = Batch([dict(n=(c, c), dx=2 * math.pi / c, nu=cfg.nu)] * batch, precision="fp32")
+        self.mask_h = torch.zeros(batch, dtype=torch.uint8).pin_memory()
+        self.mask_d = torch.zeros(batch, dtype=torch.uint8, device=device)
 
     def close(self):
         self.coarse.close()
@@ -282,13 +287,15 @@ class Rollout:
         ratio = np.sqrt(s[:, 1] / np.maximum(s[:, 2], 1e-300))
         return s[:, 0].copy(), ratio
 
-    def _fallback_into(self, u, nxt, b):
-        """Plain scheme on the coarse lattice for state b: u[b] -> nxt[b], coarse_steps steps."""
-        lat = self.coarse
-        phi = u[b, 2] if self.cfg.channels > 2 else None
-        lat.init(u[b, 0:2], phi)
-        lat.step(self.cfg.coarse_steps)
-        B.vlbm_macros(lat.handle, None, nxt[b, 0:2], nxt[b, 2] if self.cfg.channels > 2 else None)
+    def _fallback_into(self, u, nxt, bad):
+        """Plain scheme on the coarse lattice for the flagged states: u[b] -> nxt[b], coarse_steps steps."""
+        n = u.shape[0]
+        self.mask_h.zero_()
+        self.mask_h[:n] = torch.from_numpy(bad.astype(np.uint8))
+        self.mask_d.copy_(self.mask_h, non_blocking=True)
+        B.vlbm_batch_init_states(self.coarse.handle, u, self.mask_d)
+        self.coarse.step(self.cfg.coarse_steps)
+        B.vlbm_batch_macros_states(self.coarse.handle, nxt, self.mask_d)
 
     def run(self, u0: torch.Tensor, steps: int, check=True, reference=None, every=1):
         """Advance u0 (batch, C, c, c) by `steps` surrogate steps.
@@ -323,9 +330,8 @@ class Rollout:
                 reasons["energy_drift"] += int(b_drift.sum())
                 reasons["divergence"] += int(b_div.sum())
                 if bad.any():
-                    for b in np.nonzero(bad)[0]:
-                        self._fallback_into(u, nxt, int(b))
-                        fallbacks[b] += 1
+                    self._fallback_into(u, nxt, bad)
+                    fallbacks += bad
                     e, _ = self._read_stats(nxt)
                 e_prev = e
             u, nxt = nxt, u

@@ -99,9 +99,33 @@ def test_rollout_fallback_is_the_plain_coarse_scheme():
             lat.init(s[0:2], s[2])
             lat.step(cfg.coarse_steps)
             v.vlbm_macros(lat.handle, None, s[0:2], s[2])
-        assert torch.equal(out[b], s)
+        assert torch.allclose(out[b], s, rtol=1e-6, atol=1e-7)
     lat.close()
     net.close()
+
+
+def test_batch_state_entry_points_match_single_problem_calls():
+    """Masked init / read-out of a batch equal the per-problem calls, and skip unmasked problems."""
+    c, n = 16, 3
+    cfg = tiny_config()
+    st = sg.generate(cfg, [21, 22, 23], 0)[:, 0].contiguous()          # (3, 3, 16, 16)
+    bt = v.Batch([dict(n=(c, c), dx=2 * math.pi / c, nu=1e-3)] * n, precision="fp32")
+    mask = torch.tensor([1, 0, 1], dtype=torch.uint8, device="cuda")
+    v.vlbm_batch_init_states(bt.handle, st, mask)
+    bt.init(1, st[1, 0:2], st[1, 2])
+    bt.step(2)
+    out = torch.full_like(st, 7.0)
+    v.vlbm_batch_macros_states(bt.handle, out, mask)
+    assert torch.equal(out[1], torch.full_like(out[1], 7.0))        # unmasked: untouched
+    lat = v.Lattice((c, c), 2 * math.pi / c, 1e-3, precision="fp32")
+    for b in (0, 2):
+        lat.init(st[b, 0:2], st[b, 2])
+        lat.step(2)
+        ref = torch.empty(3, c, c, device="cuda")
+        v.vlbm_macros(lat.handle, None, ref[0:2], ref[2])
+        assert torch.allclose(out[b], ref, rtol=1e-6, atol=1e-7)
+    lat.close()
+    bt.close()
 
 
 def test_rollout_without_fallback_is_the_surrogate():
