@@ -149,8 +149,10 @@ __device__ __forceinline__ void warp_stream_collide_2d(const Layout<S, SPLIT, 5>
     }
 }
 
+// 16-bit storage moves half the bytes per node, so it needs more warps in flight to
+// cover the memory latency: three resident blocks per SM (at most 85 registers).
 template <class S, bool SPLIT, bool DIAG>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(S) == 2 ? 3 : 1)
 k_stream_collide_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
                         int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
     using C = typename Storage<S>::C;
