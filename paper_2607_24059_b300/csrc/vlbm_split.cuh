@@ -375,7 +375,7 @@ __device__ __forceinline__ void pulled_d3q7_l(const Coef<C>& k, int l, const C (
 // Vectorised along x with V = kSplitV3 nodes per lane: sources x -+ 1 by warp
 // shuffle (memory at the warp edge), y -+ 1 rows, z -+ 1 slabs.
 template <class S, bool DIAG>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 k_split_step_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
                     long long plane, int warps_per_row, Coef<typename Storage<S>::C> k,
                     double* __restrict__ partials) {
