@@ -132,12 +132,23 @@ __device__ __forceinline__ C pressure_dev(const Coef<C>& k, C dr) {
 // division sequence.
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+// The hardware's approximate reciprocal (PTX rcp.approx.ftz.f32, about 1 ulp): one
+// instruction instead of the correctly rounded sequence.  Used where APPROX is set (the
+// moment-split kernels, which are bound by their arithmetic); FP64 keeps recip().
+template <bool APPROX, class C>
+__device__ __forceinline__ C recip_sel(C x) { return recip(x); }
+template <>
+__device__ __forceinline__ float recip_sel<true, float>(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // Equilibrium deviations g^eq of one D2Q5 node, fields (rho, q_x, q_y) x
 // velocities (rest, +x, -x, +y, -y): e[5k + l].
-template <class C>
+template <class C, bool APPROX = false>
 __device__ __forceinline__ void equilibrium_d2q5(const Coef<C>& k, C dr, C Qx, C Qy, C (&e)[15]) {
-    const C r = recip(k.rho_bar + dr);
+    const C r = recip_sel<APPROX>(k.rho_bar + dr);
     const C dP = pressure_dev(k, dr) * k.i2m;
     const C hx = Qx * k.i2m, hy = Qy * k.i2m;
     const C xx = Qx * Qx * r * k.i2m;
@@ -204,9 +215,9 @@ __device__ __forceinline__ void relax_d2q5(const Coef<C>& k, C (&g)[15], C dr, C
 // velocities (rest, +x, -x, +y, -y, +z, -z): e[7k + l].  The paper gives the
 // 2D equilibria and states that 3D follows from the Cartesian structure; this
 // is the direction-by-direction extension (rest weight 1 - 6 alpha).
-template <class C>
+template <class C, bool APPROX = false>
 __device__ __forceinline__ void equilibrium_d3q7(const Coef<C>& k, C dr, const C (&Q)[3], C (&e)[28]) {
-    const C r = recip(k.rho_bar + dr);
+    const C r = recip_sel<APPROX>(k.rho_bar + dr);
     const C dP = pressure_dev(k, dr) * k.i2m;
     const C ar = k.al[0] * dr;
     e[0] = k.rest[0] * dr;

@@ -31,7 +31,8 @@ namespace vlbm {
 constexpr int kSplitV2 = 4;
 constexpr int kSplitV3 = 2;
 
-// Equilibrium deviations of every field along one moving velocity l
+// Equilibrium deviations of every field along one moving velocity l (the split kernels take
+// 1 / rho from the hardware's approximate reciprocal)
 // (axis a = (l - 1) / 2, sign +1 for odd l) from the moments m of one node:
 //   rho field  a_rho dr +- Q_a / (2 mu)
 //   q_j field  a_j Q_j +- (Q_j Q_a / rho + delta_ja dP) / (2 mu)
@@ -40,7 +41,7 @@ template <class C, int F, int L>
 __device__ __forceinline__ void equilibrium_dir(const Coef<C>& k, const C (&m)[F], C (&e)[F]) {
     constexpr int a = (L - 1) / 2;
     const C s = (L & 1) ? C(1) : C(-1);
-    const C r = recip(k.rho_bar + m[0]);
+    const C r = recip_sel<true>(k.rho_bar + m[0]);
     const C dP = pressure_dev(k, m[0]) * k.i2m;
     const C Qa = m[1 + a];
     e[0] = k.al[0] * m[0] + s * (Qa * k.i2m);
@@ -93,7 +94,7 @@ __device__ __forceinline__ void split_update_d2q5(const Coef<C>& k, C (&m)[3], C
         m[f] = m[f] + ((pulled - (C(1) - k.rest[f]) * m[f]) - nown[f]);
     }
     C e[15];
-    equilibrium_d2q5(k, m[0], m[1], m[2], e);
+    equilibrium_d2q5<C, true>(k, m[0], m[1], m[2], e);
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         const C w = C(1) - k.om[f];
@@ -342,7 +343,7 @@ __device__ __forceinline__ void split_update_d3q7(const Coef<C>& k, C (&m)[4], C
     }
     C e[28];
     const C Q[3] = {m[1], m[2], m[3]};
-    equilibrium_d3q7(k, m[0], Q, e);
+    equilibrium_d3q7<C, true>(k, m[0], Q, e);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const C w = C(1) - k.om[f];
