@@ -197,10 +197,10 @@ __device__ __forceinline__ void moments_d2q5(const C (&g)[15], C& dr, C& Qx, C& 
 // it is small, while rest m and g_0 are both of the size of m, and their
 // difference would keep only the rounding of rest m.  At FP32 that rounding is
 // systematic for a slowly varying field and grows linearly with the steps.
-template <class C>
+template <class C, bool APPROX = false>
 __device__ __forceinline__ void relax_d2q5(const Coef<C>& k, C (&g)[15], C dr, C Qx, C Qy) {
     C e[15];
-    equilibrium_d2q5(k, dr, Qx, Qy, e);
+    equilibrium_d2q5<C, APPROX>(k, dr, Qx, Qy, e);
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         C* h = g + 5 * f;
@@ -255,10 +255,10 @@ __device__ __forceinline__ void moments_d3q7(const C (&g)[28], C& dr, C (&Q)[3])
 }
 
 // Relaxation of one D3Q7 node; rest-population increment formed as in relax_d2q5.
-template <class C>
+template <class C, bool APPROX = false>
 __device__ __forceinline__ void relax_d3q7(const Coef<C>& k, C (&g)[28], C dr, const C (&Q)[3]) {
     C e[28];
-    equilibrium_d3q7(k, dr, Q, e);
+    equilibrium_d3q7<C, APPROX>(k, dr, Q, e);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         C* h = g + 7 * f;

@@ -121,7 +121,7 @@ __device__ __forceinline__ void warp_stream_collide_2d(const Layout<S, SPLIT, 5>
                 const C Q[2] = {Qx, Qy};
                 accumulate_node(acc, moments_finite(dr, Q, 2), dr, Q, 2, k.rho_bar);
             }
-            relax_d2q5(k, gn, dr, Qx, Qy);
+            relax_d2q5<C, sizeof(S) == 2>(k, gn, dr, Qx, Qy);
 #pragma unroll
             for (int p = 0; p < 15; ++p) g[p][i] = gn[p];
         }
@@ -216,7 +216,7 @@ k_stream_collide_2d_generic(const char* __restrict__ fin_b, char* __restrict__ f
             const C Q[2] = {Qx, Qy};
             accumulate_node(acc, moments_finite(dr, Q, 2), dr, Q, 2, k.rho_bar);
         }
-        relax_d2q5(k, g, dr, Qx, Qy);
+        relax_d2q5<C, sizeof(S) == 2>(k, g, dr, Qx, Qy);
 #pragma unroll
         for (int p = 0; p < 15; ++p) store_pop(fout, p / 5, p % 5, node, g[p], k);
     }

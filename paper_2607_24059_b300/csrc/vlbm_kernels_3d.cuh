@@ -89,7 +89,7 @@ k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
             C dr, Q[3];
             moments_d3q7(gn, dr, Q);
             if (DIAG && active) accumulate_node(acc, moments_finite(dr, Q, 3), dr, Q, 3, k.rho_bar);
-            relax_d3q7(k, gn, dr, Q);
+            relax_d3q7<C, sizeof(S) == 2>(k, gn, dr, Q);
 #pragma unroll
             for (int p = 0; p < 28; ++p) g[p][i] = gn[p];
         }
@@ -149,7 +149,7 @@ k_stream_collide_3d_generic(const char* __restrict__ fin_b, char* __restrict__ f
         C dr, Q[3];
         moments_d3q7(g, dr, Q);
         if (DIAG) accumulate_node(acc, moments_finite(dr, Q, 3), dr, Q, 3, k.rho_bar);
-        relax_d3q7(k, g, dr, Q);
+        relax_d3q7<C, sizeof(S) == 2>(k, g, dr, Q);
 #pragma unroll
         for (int p = 0; p < 28; ++p) store_pop(fout, p / 7, p % 7, node, g[p], k);
     }
