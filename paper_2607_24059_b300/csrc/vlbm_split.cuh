@@ -261,8 +261,10 @@ __device__ __forceinline__ void warp_split_step_2d(const Layout<S, true, 5>& fin
     }
 }
 
+// At least two resident blocks per SM (at most 128 registers): the BF16 instantiation with
+// fused diagnostics needs 131 and would otherwise run one block per SM.
 template <class S, int V, bool DIAG>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_split_step_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
                     int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
     using C = typename Storage<S>::C;
