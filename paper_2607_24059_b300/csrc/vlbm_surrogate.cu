@@ -527,121 +527,173 @@ int launch_conv_act(const void* X, const void* W, const float* bias, void* Y, vo
 // Weight and bias gradients of a periodic 3x3 convolution, on tcgen05:
 //   G[co][tap * CIN + ci] += sum_p X[p + tap][ci] dZ[p][co],   Gb[co] += sum_p dZ[p][co]
 // as a GEMM with M = rows (tap, ci) plus one row of ones (which yields the bias
-// gradient), N = COUT and K = pixels.  blockIdx.y picks a 128-row tile,
-// blockIdx.x a range of pixels (split K); partial results are added to G / Gb
-// with FP32 atomics.  Staging transposes pixel-major activations into the
-// K-major layout (each thread: one pixel, 8-channel groups).
+// gradient), N = COUT and K = pixels.  Both operands are MN-major: NHWC memory
+// holds the channels of a pixel contiguously, so each 16-byte granule (8
+// channels of one pixel) is copied unchanged by cp.async to its place in the
+// no-swizzle MN-major layout, with no transposition.  A stage holds KP pixels:
+//   A: [row group = tap * CIN / 8 + channel group][pixel][16 B], groups KP * 16 bytes
+//      apart, then constant groups (the row of ones, zeros up to whole 128-row tiles);
+//   B: [output channel group][pixel][16 B].
+// Each CTA accumulates all 128-row tiles of M in tensor memory (TILES x COUT
+// columns) over a contiguous range of pixels (split K), through a STAGES-deep
+// cp.async pipeline, and adds its partial sums to G / Gb with FP32 atomics.
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kTcThreads)
+struct WgradCfg {
+    static constexpr int THREADS = 256;
+    static constexpr int KP = 32;                         // pixels per stage: two K = 16 MMA steps
+    static constexpr int KT = 9 * CIN;                    // rows (tap, ci); row KT is the row of ones
+    static constexpr int TILES = (KT + 1 + 127) / 128;
+    static constexpr int CG = CIN / 8, BG = COUT / 8;     // 16-byte channel groups of X and dZ
+    static constexpr int GROUP = KP * 16;                 // bytes of one group over the stage's pixels
+    static constexpr int A_BYTES = TILES * 16 * GROUP;
+    static constexpr int CONST0 = 9 * CG * GROUP;         // first constant group of A
+    static constexpr int STAGE = A_BYTES + BG * GROUP;
+    static constexpr int STAGES = 200 * 1024 / STAGE < 4 ? 200 * 1024 / STAGE : 4;
+    static constexpr int SMEM = STAGES * STAGE;
+    static constexpr int COLS = TILES * COUT;
+    static constexpr uint32_t NCOL = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
+    static constexpr int TSTEP = THREADS / (KP * CG);     // taps one pass of the block covers
+    static_assert(CIN % 8 == 0 && COUT % 16 == 0 && COUT <= 256, "operand shapes");
+    static_assert(THREADS % (KP * CG) == 0 && KP * BG <= THREADS, "one granule per thread and pass");
+    static_assert(COLS <= 512 && STAGES >= 2, "tensor memory / shared memory budget");
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(WgradCfg<CIN, COUT>::THREADS)
 k_conv3x3_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dZ, float* __restrict__ G,
-                float* __restrict__ Gb, int B, int H, int Wd, int pix_per_cta, int* __restrict__ err) {
-    constexpr int KT = 9 * CIN;
-    constexpr uint32_t NCOL = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);
-    __shared__ __align__(1024) uint8_t sA[128 * 64 * 2];
-    __shared__ __align__(1024) uint8_t sB[COUT * 64 * 2];
-    __shared__ __align__(8) uint64_t bar;
+                float* __restrict__ Gb, int B, int H, int Wd, int chunks_per_cta, int* __restrict__ err) {
+    using C = WgradCfg<CIN, COUT>;
+    constexpr int S = C::STAGES;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t bar[S];
     __shared__ uint32_t s_taddr;
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int npix = B * H * Wd;
+    const int nchunks = (npix + C::KP - 1) / C::KP;
+    const int c_begin = blockIdx.x * chunks_per_cta;
+    const int n = max(0, min(c_begin + chunks_per_cta, nchunks) - c_begin);
     if (warp == 0) {
-        tc::tmem_alloc(&s_taddr, NCOL);
+        tc::tmem_alloc(&s_taddr, C::NCOL);
         tc::tmem_relinquish();
     }
-    if (tid == 0) tc::mbar_init(&bar, 1);
+    if (tid == 0)
+        for (int s = 0; s < S; ++s) tc::mbar_init(&bar[s], 1);
+    // constant groups of every stage: group 0 holds row KT (1.0 in its first element), the rest zeros
+    constexpr int kConstGranules = (C::A_BYTES - C::CONST0) / 16;
+    for (int i = tid; i < S * kConstGranules; i += C::THREADS) {
+        const int s = i / kConstGranules, j = i - s * kConstGranules;
+        *reinterpret_cast<uint4*>(smem + s * C::STAGE + C::CONST0 + j * 16) =
+            make_uint4(j < C::KP ? 0x00003F80u : 0u, 0u, 0u, 0u);
+    }
+    tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = s_taddr;
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
-    const long long npix = (long long)B * H * Wd;
-    const long long p_begin = (long long)blockIdx.x * pix_per_cta;
-    const long long p_end = p_begin + pix_per_cta < npix ? p_begin + pix_per_cta : npix;
-    const int row0 = blockIdx.y * 128;
-    const int k = tid & 63, half = tid >> 6;
-    uint32_t phase = 0;
+    const uint32_t sbase = tc::smem_addr(smem);
+
+    // this thread's granules: pixel pa, channel group ga of taps ta0, ta0 + TSTEP, ...; dZ pixel pb, group gb
+    const int pa = (tid % (C::KP * C::CG)) / C::CG, ga = tid % C::CG, ta0 = tid / (C::KP * C::CG);
+    const bool b_thread = tid < C::KP * C::BG;
+    const int pb = tid / C::BG, gb = tid % C::BG;
+    auto load = [&](int chunk, int s) {
+        const uint32_t sa = sbase + s * C::STAGE;
+        const int q = chunk * C::KP + pa;
+        const bool valid = q < npix;
+        int x = 0, y = 0, b = 0;
+        if (valid) {
+            x = q % Wd;
+            const int t = q / Wd;
+            y = t % H;
+            b = t / H;
+        }
+        const int ys[3] = {y == 0 ? H - 1 : y - 1, y, y == H - 1 ? 0 : y + 1};
+        const int xs[3] = {x == 0 ? Wd - 1 : x - 1, x, x == Wd - 1 ? 0 : x + 1};
+#pragma unroll
+        for (int i = 0; i < (9 + C::TSTEP - 1) / C::TSTEP; ++i) {
+            const int tap = ta0 + i * C::TSTEP;
+            if (tap < 9) {
+                const __nv_bfloat16* src = X + ((long long)(b * H + ys[tap / 3]) * Wd + xs[tap % 3]) * CIN + ga * 8;
+                tc::cp_async16_ca_zfill(sa + (tap * C::CG + ga) * C::GROUP + pa * 16, valid ? src : X,
+                                        valid ? 16u : 0u);
+            }
+        }
+        if (b_thread) {
+            const int qb = chunk * C::KP + pb;
+            const bool vb = qb < npix;
+            tc::cp_async16_ca_zfill(sa + C::A_BYTES + gb * C::GROUP + pb * 16,
+                                    vb ? dZ + (long long)qb * COUT + gb * 8 : dZ, vb ? 16u : 0u);
+        }
+    };
+
+    constexpr uint32_t idesc = tc::idesc_bf16_f32_mn(128, COUT);
     bool ok = true;
-    int round = 0;
-    for (long long c0 = p_begin; c0 < p_end && ok; c0 += 64, ++round) {
-        const long long p = c0 + k;
-        const bool valid = p < p_end;
-        const int x = (int)(p % Wd);
-        const long long by = p / Wd;
-        const int y = (int)(by % H);
-        const long long b = by / H;
-        // A: rows half * 64 .. half * 64 + 63 of this tile, column k
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            const int lr = half * 64 + 8 * g;          // local row of the group
-            const int r = row0 + lr;                   // global row (tap, ci) or the ones row
-            __align__(16) __nv_bfloat16 e[8];
-            if (valid && r < KT) {
-                const int tap = r / CIN, ci0 = r % CIN;
-                const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-                const int ys = y + dy < 0 ? H - 1 : (y + dy >= H ? 0 : y + dy);
-                const int xs = x + dx < 0 ? Wd - 1 : (x + dx >= Wd ? 0 : x + dx);
-                *reinterpret_cast<uint4*>(e) =
-                    *reinterpret_cast<const uint4*>(X + ((b * H + ys) * Wd + xs) * CIN + ci0);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) e[j] = __float2bfloat16_rn((valid && r + j == KT) ? 1.0f : 0.0f);
+    for (int j = 0; j < S - 1; ++j) {
+        if (j < n) load(c_begin + j, j);
+        tc::cp_async_commit();
+    }
+    for (int c = 0; c < n; ++c) {
+        const int s = c % S;
+        const int nxt = c + S - 1;                       // refills the stage chunk c - 1 was read from
+        if (nxt < n) {
+            if (c >= 1 && !tc::mbar_wait(&bar[(c - 1) % S], ((c - 1) / S) & 1, kWaitPolls)) {
+                atomicExch(err, 1);
+                ok = false;
             }
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                *reinterpret_cast<__nv_bfloat16*>(sA + tc::kmajor_offset(lr + j, k, 64)) = e[j];
+            if (ok) load(c_begin + nxt, nxt % S);
         }
-        // B: output channels half * COUT/2 .., column k
-#pragma unroll
-        for (int g = 0; g < COUT / 16; ++g) {
-            const int co = half * (COUT / 2) + 8 * g;
-            __align__(16) __nv_bfloat16 e[8];
-            if (valid) *reinterpret_cast<uint4*>(e) = *reinterpret_cast<const uint4*>(dZ + p * COUT + co);
-            else {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) e[j] = __float2bfloat16_rn(0.0f);
-            }
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(co + j, k, 64)) = e[j];
-        }
+        tc::cp_async_commit();
+        tc::cp_async_wait<S - 1>();                      // this thread's copies of chunk c have landed
         tc::fence_proxy_async_smem();
-        __syncthreads();
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
         if (tid == 0) {
             tc::fence_after_sync();
-            const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
+            const uint32_t a0 = sbase + s * C::STAGE, b0 = a0 + C::A_BYTES;
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const uint64_t da = tc::smem_desc(a0 + s * 256, 128, 64 * 16);
-                const uint64_t db = tc::smem_desc(b0 + s * 256, 128, 64 * 16);
-                tc::mma_bf16(taddr, da, db, idesc, (round > 0 || s > 0) ? 1u : 0u);
-            }
-            tc::mma_commit(&bar);
+            for (int t = 0; t < C::TILES; ++t)
+#pragma unroll
+                for (int k = 0; k < C::KP / 16; ++k) {
+                    const uint64_t da = tc::smem_desc(a0 + t * 16 * C::GROUP + k * 256, 128, C::GROUP);
+                    const uint64_t db = tc::smem_desc(b0 + k * 256, 128, C::GROUP);
+                    tc::mma_bf16(taddr + (uint32_t)(t * COUT), da, db, idesc, (c > 0 || k > 0) ? 1u : 0u);
+                }
+            tc::mma_commit(&bar[s]);
         }
-        if (!tc::mbar_wait(&bar, phase, kWaitPolls)) {
-            ok = false;
-            atomicExch(err, 1);
-        }
-        phase ^= 1;
-        __syncthreads();
     }
-    if (ok && round > 0) {
+    if (ok && n > 0) {
+        const int last = n - 1;
+        if (!tc::mbar_wait(&bar[last % S], (last / S) & 1, kWaitPolls)) {
+            atomicExch(err, 1);
+            ok = false;
+        }
+    }
+    tc::cp_async_wait<0>();
+    ok = __syncthreads_and(ok);
+    if (ok && n > 0) {
         tc::fence_after_sync();
-        const int r = row0 + warp * 32 + (tid & 31);
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const int quarter = warp & 3;                    // a warp reads TMEM lanes 32 * (warp % 4) ..
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        for (int t = warp >> 2; t < C::TILES; t += C::THREADS / 128) {
+            const int r = t * 128 + quarter * 32 + (tid & 31);
 #pragma unroll
-        for (int c = 0; c < COUT; c += 16) {
-            float v[16];
-            tc::tmem_ld16(taddr + lane_base + (uint32_t)c, v);
-            if (r < KT) {
+            for (int c = 0; c < COUT; c += 16) {
+                float v[16];
+                tc::tmem_ld16(taddr + lane_base + (uint32_t)(t * COUT + c), v);
+                if (r < C::KT) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) atomicAdd(G + (long long)(c + j) * KT + r, v[j]);
-            } else if (r == KT) {
+                    for (int j = 0; j < 16; ++j) atomicAdd(G + (long long)(c + j) * C::KT + r, v[j]);
+                } else if (r == C::KT) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) atomicAdd(Gb + c + j, v[j]);
+                    for (int j = 0; j < 16; ++j) atomicAdd(Gb + c + j, v[j]);
+                }
             }
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(taddr, NCOL);
+    if (warp == 0) tc::tmem_dealloc(taddr, C::NCOL);
 }
 
 // ---------------------------------------------------------------------------
@@ -983,7 +1035,6 @@ namespace {
 constexpr int kLayers = 5;
 constexpr int kCin[kLayers] = {16, 64, 64, 64, 64};
 constexpr int kCout[kLayers] = {64, 64, 64, 64, 16};
-constexpr int kPixPerWgradCta = 4096;
 
 uint64_t splitmix64(uint64_t& s) {
     uint64_t z = (s += 0x9E3779B97F4A7C15ull);
@@ -995,11 +1046,30 @@ uint64_t splitmix64(uint64_t& s) {
 template <int CIN, int COUT>
 int launch_wgrad(const void* X, const void* dZ, float* G, float* Gb, long long B, long long H, long long W, int* err,
                  cudaStream_t s) {
+    using C = WgradCfg<CIN, COUT>;
+    static int slots = 0;
+    if (!slots) {
+        auto fn = k_conv3x3_wgrad<CIN, COUT>;
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess ||
+            cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+                cudaSuccess ||
+            cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, C::THREADS, C::SMEM) != cudaSuccess)
+            return VLBM_ECUDA;
+        // resident CTAs must also fit in the 512 tensor-memory columns of an SM
+        per_sm = std::max(1, std::min(per_sm, (int)(512 / C::NCOL)));
+        slots = sms * per_sm;
+    }
     const long long npix = B * H * W;
-    const dim3 grid((unsigned)((npix + kPixPerWgradCta - 1) / kPixPerWgradCta), (unsigned)((9 * CIN + 1 + 127) / 128));
+    if (npix == 0) return VLBM_OK;
+    const long long nchunks = (npix + C::KP - 1) / C::KP;
+    const long long per = (nchunks + slots - 1) / slots;      // one wave: contiguous chunk ranges
+    const unsigned grid = (unsigned)((nchunks + per - 1) / per);
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    k_conv3x3_wgrad<CIN, COUT><<<grid, kTcThreads, 0, s>>>((const __nv_bfloat16*)X, (const __nv_bfloat16*)dZ, G, Gb,
-                                                           (int)B, (int)H, (int)W, kPixPerWgradCta, err);
+    k_conv3x3_wgrad<CIN, COUT><<<grid, C::THREADS, C::SMEM, s>>>((const __nv_bfloat16*)X, (const __nv_bfloat16*)dZ, G,
+                                                                  Gb, (int)B, (int)H, (int)W, (int)per, err);
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
 }
 

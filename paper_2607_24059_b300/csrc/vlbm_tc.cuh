@@ -98,6 +98,15 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
            | ((uint32_t)(M >> 4) << 24);      // M / 16
 }
 
+// The same with both operands MN-major (M or N contiguous in shared memory).
+// MN-major no-swizzle layout: 8 consecutive M (or N) elements fill 16 bytes,
+// 8 consecutive K rows of those sit 16 bytes apart (one 128-byte core matrix),
+// groups of 8 along K are LBO bytes apart and groups of 8 along M (N) SBO
+// bytes apart.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N) {
+    return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
+}
+
 // D[tmem] (+)= A[smem] x B[smem]^T, one K = 16 slice; issued by one thread.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -186,6 +195,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // ---- asynchronous 16-byte global -> shared copies (cp.async) ------------------
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gptr) : "memory");
+}
+// 16 bytes through L1 (neighbouring taps re-read the same lines); src_bytes = 0
+// copies nothing and fills the destination with zeros.
+__device__ __forceinline__ void cp_async16_ca_zfill(uint32_t saddr, const void* gptr, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(gptr), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>

@@ -72,7 +72,7 @@ def ref_wgrad(X, dZ):
 
 
 @pytest.mark.parametrize("cin,cout", [(16, 64), (64, 64), (64, 16)])
-@pytest.mark.parametrize("shape", [(2, 16, 32), (3, 40, 72), (1, 5, 7)])
+@pytest.mark.parametrize("shape", [(2, 16, 32), (3, 40, 72), (1, 5, 7), (3, 97, 131)])
 def test_conv3x3_wgrad_matches_fp64(cin, cout, shape):
     B, H, Wd = shape
     g = torch.Generator(device="cuda").manual_seed(cin + cout * 3 + H * Wd)
