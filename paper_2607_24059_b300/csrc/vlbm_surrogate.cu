@@ -529,44 +529,69 @@ int launch_conv_act(const void* X, const void* W, const float* bias, void* Y, vo
 // as a GEMM with M = rows (tap, ci) plus one row of ones (which yields the bias
 // gradient), N = COUT and K = pixels.  Both operands are MN-major: NHWC memory
 // holds the channels of a pixel contiguously, so each 16-byte granule (8
-// channels of one pixel) is copied unchanged by cp.async to its place in the
-// no-swizzle MN-major layout, with no transposition.  A stage holds KP pixels:
-//   A: [row group = tap * CIN / 8 + channel group][pixel][16 B], groups KP * 16 bytes
-//      apart, then constant groups (the row of ones, zeros up to whole 128-row tiles);
-//   B: [output channel group][pixel][16 B].
+// channels of one pixel) is copied unchanged by cp.async to its place, with no
+// transposition.  A stage holds KP pixels:
+//   A: 128-byte swizzled MN-major atoms of 64 rows (tap, ci) x KP pixels, one
+//      128-byte row per pixel: the 8 granules one pixel contributes to an atom
+//      land in 8 different bank groups.  Rows from KT on are constant: the row of
+//      ones, then zeros up to whole 128-row tiles;
+//   B: the same for dZ when COUT is a multiple of 64, else no-swizzle MN-major
+//      [output channel group][pixel][16 B].
 // Each CTA accumulates all 128-row tiles of M in tensor memory (TILES x COUT
-// columns) over a contiguous range of pixels (split K), through a STAGES-deep
-// cp.async pipeline, and adds its partial sums to G / Gb with FP32 atomics.
+// columns) over a contiguous range of pixels (split K) and adds its partial
+// sums to G / Gb with FP32 atomics.  Roles, connected by mbarriers (every wait
+// bounded, plus a shared abort flag): 8 producer warps fill STAGES stages with
+// cp.async, up to kWgradPending chunks in flight per thread (full[stage] once a
+// chunk has landed); one thread issues the chunk's TILES x KP / 16 MMAs and
+// releases the stage (empty[stage]); at the end the producer warps read the
+// accumulators.
+constexpr int kWgradPending = 3;    // chunks in flight per producer thread (cp.async groups waited on: <= 3)
+
 template <int CIN, int COUT>
 struct WgradCfg {
-    static constexpr int THREADS = 256;
+    static constexpr int PRODUCERS = 256;                 // 8 warps copy (and add the sums at the end)
+    static constexpr int THREADS = PRODUCERS + 32;        // + 1 warp whose first thread issues the MMAs
     static constexpr int KP = 32;                         // pixels per stage: two K = 16 MMA steps
     static constexpr int KT = 9 * CIN;                    // rows (tap, ci); row KT is the row of ones
     static constexpr int TILES = (KT + 1 + 127) / 128;
     static constexpr int CG = CIN / 8, BG = COUT / 8;     // 16-byte channel groups of X and dZ
-    static constexpr int GROUP = KP * 16;                 // bytes of one group over the stage's pixels
-    static constexpr int A_BYTES = TILES * 16 * GROUP;
-    static constexpr int CONST0 = 9 * CG * GROUP;         // first constant group of A
-    static constexpr int STAGE = A_BYTES + BG * GROUP;
-    static constexpr int STAGES = 200 * 1024 / STAGE < 4 ? 200 * 1024 / STAGE : 4;
-    static constexpr int SMEM = STAGES * STAGE;
+    static constexpr int ATOM = KP * 128;                  // one swizzled atom of 64 rows over the stage's pixels
+    static constexpr int GROUP = KP * 16;                 // no-swizzle B: one 8-channel group over the pixels
+    static constexpr bool B_SW = COUT % 64 == 0;
+    static constexpr int A_BYTES = TILES * 2 * ATOM;
+    static constexpr int B_BYTES = B_SW ? COUT / 64 * ATOM : BG * GROUP;
+    static constexpr int CONST_ATOM = KT / 64;            // first atom holding constant rows
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int STAGES = 225 * 1024 / STAGE < 5 ? 225 * 1024 / STAGE : 5;
+    static constexpr int SMEM = STAGES * STAGE + 1024;    // + slack for 1024-byte alignment
     static constexpr int COLS = TILES * COUT;
     static constexpr uint32_t NCOL = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
-    static constexpr int TSTEP = THREADS / (KP * CG);     // taps one pass of the block covers
+    static constexpr int TSTEP = PRODUCERS / (KP * CG);   // taps one pass of the producers covers
     static_assert(CIN % 8 == 0 && COUT % 16 == 0 && COUT <= 256, "operand shapes");
-    static_assert(THREADS % (KP * CG) == 0 && KP * BG <= THREADS, "one granule per thread and pass");
-    static_assert(COLS <= 512 && STAGES >= 2, "tensor memory / shared memory budget");
+    static_assert(PRODUCERS % (KP * CG) == 0 && KP * BG <= PRODUCERS, "one granule per thread and pass");
+    static_assert(COLS <= 512 && STAGES > kWgradPending, "tensor memory / shared memory budget");
+    static_assert(KT % 8 == 0 && STAGE % 1024 == 0 && KP % 16 == 0, "atom alignment");
 };
 
+// Byte offset of granule (8 rows starting at row r0, pixel p) in a stage's swizzled operand.
+template <int KP>
+__device__ __forceinline__ uint32_t sw128_granule(int r0, int p) {
+    return (uint32_t)((r0 >> 6) * (KP * 128) + p * 128 + ((((r0 >> 3) & 7) ^ (p & 7)) << 4));
+}
+
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(WgradCfg<CIN, COUT>::THREADS)
+__global__ void __launch_bounds__(WgradCfg<CIN, COUT>::THREADS, 1)
 k_conv3x3_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dZ, float* __restrict__ G,
                 float* __restrict__ Gb, int B, int H, int Wd, int chunks_per_cta, int* __restrict__ err) {
     using C = WgradCfg<CIN, COUT>;
     constexpr int S = C::STAGES;
-    extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t bar[S];
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // swizzle atoms need 1024-byte aligned shared addresses
+    uint8_t* smem = smem_raw + ((1024u - (tc::smem_addr(smem_raw) & 1023u)) & 1023u);
+    __shared__ __align__(8) uint64_t full[S], empty[S], done;
     __shared__ uint32_t s_taddr;
+    __shared__ int s_abort;
+    volatile int* abort = &s_abort;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int npix = B * H * Wd;
     const int nchunks = (npix + C::KP - 1) / C::KP;
@@ -576,14 +601,22 @@ k_conv3x3_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __rest
         tc::tmem_alloc(&s_taddr, C::NCOL);
         tc::tmem_relinquish();
     }
-    if (tid == 0)
-        for (int s = 0; s < S; ++s) tc::mbar_init(&bar[s], 1);
-    // constant groups of every stage: group 0 holds row KT (1.0 in its first element), the rest zeros
-    constexpr int kConstGranules = (C::A_BYTES - C::CONST0) / 16;
-    for (int i = tid; i < S * kConstGranules; i += C::THREADS) {
-        const int s = i / kConstGranules, j = i - s * kConstGranules;
-        *reinterpret_cast<uint4*>(smem + s * C::STAGE + C::CONST0 + j * 16) =
-            make_uint4(j < C::KP ? 0x00003F80u : 0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(&full[s], C::PRODUCERS);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(&done, 1);
+        s_abort = 0;
+    }
+    // constant rows of every stage: row KT is 1.0 (first element of its granule), later rows zero
+    constexpr int kConstGroups = (C::TILES * 128 - C::CONST_ATOM * 64) / 8;
+    for (int i = tid; i < S * kConstGroups * C::KP; i += C::THREADS) {
+        const int s = i / (kConstGroups * C::KP), j = i - s * (kConstGroups * C::KP);
+        const int r0 = C::CONST_ATOM * 64 + 8 * (j / C::KP), p = j % C::KP;
+        if (r0 >= C::KT)
+            *reinterpret_cast<uint4*>(smem + s * C::STAGE + sw128_granule<C::KP>(r0, p)) =
+                make_uint4(r0 == C::KT ? 0x00003F80u : 0u, 0u, 0u, 0u);
     }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
@@ -592,103 +625,118 @@ k_conv3x3_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __rest
     const uint32_t taddr = s_taddr;
     const uint32_t sbase = tc::smem_addr(smem);
 
-    // this thread's granules: pixel pa, channel group ga of taps ta0, ta0 + TSTEP, ...; dZ pixel pb, group gb
-    const int pa = (tid % (C::KP * C::CG)) / C::CG, ga = tid % C::CG, ta0 = tid / (C::KP * C::CG);
-    const bool b_thread = tid < C::KP * C::BG;
-    const int pb = tid / C::BG, gb = tid % C::BG;
-    auto load = [&](int chunk, int s) {
-        const uint32_t sa = sbase + s * C::STAGE;
-        const int q = chunk * C::KP + pa;
-        const bool valid = q < npix;
-        int x = 0, y = 0, b = 0;
-        if (valid) {
-            x = q % Wd;
-            const int t = q / Wd;
+    if (warp < C::PRODUCERS / 32) {
+        // ---------------- producers ----------------
+        // this thread's granules: pixel pa, channel group ga of taps ta0, ta0 + TSTEP, ...; dZ pixel pb, group gb.
+        // A chunk is announced (full[stage]) once this thread's copies of it have landed, also while the
+        // thread waits for a free stage, so that announcing never depends on a later stage being released.
+        const int pa = (tid % (C::KP * C::CG)) / C::CG, ga = tid % C::CG, ta0 = tid / (C::KP * C::CG);
+        const bool b_thread = tid < C::KP * C::BG;
+        const int pb = tid / C::BG, gb = tid % C::BG;
+        const uint32_t b_off = C::A_BYTES + (C::B_SW ? sw128_granule<C::KP>(8 * gb, pb) : (uint32_t)(gb * C::GROUP + pb * 16));
+        int qa = c_begin * C::KP + pa, qb = c_begin * C::KP + pb;
+        int x = 0, y = 0, b = 0;                          // coordinates of pixel qa, advanced by KP per chunk
+        if (qa < npix) {
+            x = qa % Wd;
+            const int t = qa / Wd;
             y = t % H;
             b = t / H;
         }
-        const int ys[3] = {y == 0 ? H - 1 : y - 1, y, y == H - 1 ? 0 : y + 1};
-        const int xs[3] = {x == 0 ? Wd - 1 : x - 1, x, x == Wd - 1 ? 0 : x + 1};
-#pragma unroll
-        for (int i = 0; i < (9 + C::TSTEP - 1) / C::TSTEP; ++i) {
-            const int tap = ta0 + i * C::TSTEP;
-            if (tap < 9) {
-                const __nv_bfloat16* src = X + ((long long)(b * H + ys[tap / 3]) * Wd + xs[tap % 3]) * CIN + ga * 8;
-                tc::cp_async16_ca_zfill(sa + (tap * C::CG + ga) * C::GROUP + pa * 16, valid ? src : X,
-                                        valid ? 16u : 0u);
+        int issued = 0, announced = 0;
+        auto announce_oldest = [&]() {
+            tc::cp_async_wait_dyn(issued - announced - 1);
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&full[announced % S]);
+            ++announced;
+        };
+        for (int c = 0; c < n; ++c) {
+            const int s = c % S;
+            const uint32_t par = ((c / S) & 1) ^ 1;
+            while (announced < issued && (issued - announced >= kWgradPending || !tc::mbar_test(&empty[s], par)))
+                announce_oldest();
+            if (!wait_or_abort(&empty[s], par, abort)) {
+                raise_abort(abort, err);
+                break;
             }
-        }
-        if (b_thread) {
-            const int qb = chunk * C::KP + pb;
-            const bool vb = qb < npix;
-            tc::cp_async16_ca_zfill(sa + C::A_BYTES + gb * C::GROUP + pb * 16,
-                                    vb ? dZ + (long long)qb * COUT + gb * 8 : dZ, vb ? 16u : 0u);
-        }
-    };
-
-    constexpr uint32_t idesc = tc::idesc_bf16_f32_mn(128, COUT);
-    bool ok = true;
+            const uint32_t sa = sbase + s * C::STAGE;
+            const bool valid = qa < npix;
+            const int ys[3] = {y == 0 ? H - 1 : y - 1, y, y == H - 1 ? 0 : y + 1};
+            const int xs[3] = {x == 0 ? Wd - 1 : x - 1, x, x == Wd - 1 ? 0 : x + 1};
 #pragma unroll
-    for (int j = 0; j < S - 1; ++j) {
-        if (j < n) load(c_begin + j, j);
-        tc::cp_async_commit();
-    }
-    for (int c = 0; c < n; ++c) {
-        const int s = c % S;
-        const int nxt = c + S - 1;                       // refills the stage chunk c - 1 was read from
-        if (nxt < n) {
-            if (c >= 1 && !tc::mbar_wait(&bar[(c - 1) % S], ((c - 1) / S) & 1, kWaitPolls)) {
-                atomicExch(err, 1);
+            for (int i = 0; i < (9 + C::TSTEP - 1) / C::TSTEP; ++i) {
+                const int tap = ta0 + i * C::TSTEP;
+                if (tap < 9) {
+                    const __nv_bfloat16* src = X + ((long long)(b * H + ys[tap / 3]) * Wd + xs[tap % 3]) * CIN + ga * 8;
+                    tc::cp_async16_ca_zfill(sa + sw128_granule<C::KP>(tap * CIN + 8 * ga, pa), valid ? src : X,
+                                            valid ? 16u : 0u);
+                }
+            }
+            if (b_thread) {
+                const bool vb = qb < npix;
+                tc::cp_async16_ca_zfill(sa + b_off, vb ? dZ + (long long)qb * COUT + gb * 8 : dZ, vb ? 16u : 0u);
+            }
+            tc::cp_async_commit();
+            ++issued;
+            qa += C::KP;
+            qb += C::KP;
+            for (x += C::KP; x >= Wd; x -= Wd)
+                if (++y == H) {
+                    y = 0;
+                    ++b;
+                }
+        }
+        while (announced < issued) announce_oldest();
+    } else if ((tid & 31) == 0) {
+        // ---------------- MMA issuer ----------------
+        constexpr uint32_t idesc = tc::idesc_bf16_f32_mn(128, COUT);
+        bool ok = true;
+        for (int c = 0; c < n && ok; ++c) {
+            const int s = c % S;
+            if (!wait_or_abort(&full[s], (c / S) & 1, abort)) {
+                raise_abort(abort, err);
                 ok = false;
+                break;
             }
-            if (ok) load(c_begin + nxt, nxt % S);
-        }
-        tc::cp_async_commit();
-        tc::cp_async_wait<S - 1>();                      // this thread's copies of chunk c have landed
-        tc::fence_proxy_async_smem();
-        ok = __syncthreads_and(ok);
-        if (!ok) break;
-        if (tid == 0) {
+            tc::fence_proxy_async_smem();
             tc::fence_after_sync();
             const uint32_t a0 = sbase + s * C::STAGE, b0 = a0 + C::A_BYTES;
 #pragma unroll
             for (int t = 0; t < C::TILES; ++t)
 #pragma unroll
                 for (int k = 0; k < C::KP / 16; ++k) {
-                    const uint64_t da = tc::smem_desc(a0 + t * 16 * C::GROUP + k * 256, 128, C::GROUP);
-                    const uint64_t db = tc::smem_desc(b0 + k * 256, 128, C::GROUP);
+                    // 16 pixels = two 8-row groups further along K
+                    const uint64_t da = tc::smem_desc_sw128(a0 + t * 2 * C::ATOM + k * 2048, C::ATOM, 1024);
+                    const uint64_t db = C::B_SW ? tc::smem_desc_sw128(b0 + k * 2048, C::ATOM, 1024)
+                                                : tc::smem_desc(b0 + k * 256, 128, C::GROUP);
                     tc::mma_bf16(taddr + (uint32_t)(t * COUT), da, db, idesc, (c > 0 || k > 0) ? 1u : 0u);
                 }
-            tc::mma_commit(&bar[s]);
+            tc::mma_commit(&empty[s]);
         }
+        if (ok && n > 0) tc::mma_commit(&done);          // arrives once every MMA above has completed
     }
-    if (ok && n > 0) {
-        const int last = n - 1;
-        if (!tc::mbar_wait(&bar[last % S], (last / S) & 1, kWaitPolls)) {
-            atomicExch(err, 1);
-            ok = false;
-        }
-    }
-    tc::cp_async_wait<0>();
-    ok = __syncthreads_and(ok);
-    if (ok && n > 0) {
-        tc::fence_after_sync();
-        const int quarter = warp & 3;                    // a warp reads TMEM lanes 32 * (warp % 4) ..
-        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-        for (int t = warp >> 2; t < C::TILES; t += C::THREADS / 128) {
-            const int r = t * 128 + quarter * 32 + (tid & 31);
+    // ---------------- epilogue: the producer warps add the partial sums ----------------
+    if (warp < C::PRODUCERS / 32 && n > 0) {
+        if (wait_or_abort(&done, 0, abort)) {
+            tc::fence_after_sync();
+            const int quarter = warp & 3;                // a warp reads TMEM lanes 32 * (warp % 4) ..
+            const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+            for (int t = warp >> 2; t < C::TILES; t += C::PRODUCERS / 128) {
+                const int r = t * 128 + quarter * 32 + (tid & 31);
 #pragma unroll
-            for (int c = 0; c < COUT; c += 16) {
-                float v[16];
-                tc::tmem_ld16(taddr + lane_base + (uint32_t)(t * COUT + c), v);
-                if (r < C::KT) {
+                for (int c = 0; c < COUT; c += 16) {
+                    float v[16];
+                    tc::tmem_ld16(taddr + lane_base + (uint32_t)(t * COUT + c), v);
+                    if (r < C::KT) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) atomicAdd(G + (long long)(c + j) * C::KT + r, v[j]);
-                } else if (r == C::KT) {
+                        for (int j = 0; j < 16; ++j) atomicAdd(G + (long long)(c + j) * C::KT + r, v[j]);
+                    } else if (r == C::KT) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) atomicAdd(Gb + c + j, v[j]);
+                        for (int j = 0; j < 16; ++j) atomicAdd(Gb + c + j, v[j]);
+                    }
                 }
             }
+        } else {
+            raise_abort(abort, err);
         }
     }
     tc::fence_before_sync();

@@ -88,6 +88,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;                 // base offset 0, swizzle none
 }
 
+// The same for a 128-byte swizzled operand: atoms of 8 rows x 128 bytes,
+// 1024-byte aligned, the 16-byte granule g of row r stored at granule
+// g ^ (r mod 8).  MN-major: a row holds 64 consecutive M (N) elements of one K;
+// LBO = bytes between 64-element atoms along M (N), SBO = bytes between groups
+// of 8 rows along K.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return smem_desc(saddr, lbo, sbo) | ((uint64_t)2 << 61);
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B (both K-major), FP32
 // accumulator, M x N tile.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
