@@ -91,7 +91,8 @@ def parse_args():
     ap.add_argument("--sur-epochs", type=float, default=8.0, help="sur256: training epochs")
     ap.add_argument("--sur-batch", type=int, default=32, help="sur256: states advanced together in the timed rollouts")
     ap.add_argument("--conv-only", action="store_true",
-                    help="sur256: time only the dominant kernel (the 64 -> 64 conv of the rollout), no training")
+                    help="sur256: time only the dominant kernel (the 64 -> 64 conv of the rollout) and the "
+                         "training step's weight gradient of that conv, no training")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--reference-seconds", type=float, default=150.0, help="cap on the reference arm's timed steps")
@@ -542,6 +543,33 @@ def conv_roofline(nb, c, stream, reps=50):
             "algorithmic_bytes_per_launch": nb * c * c * 64 * 2 * 2}
 
 
+def wgrad_roofline(nb, c, stream, reps=20):
+    """The training step's largest kernel, the weight and bias gradients of the 64 -> 64 conv on nb
+    states of c^2 pixels, timed alone with CUDA events (reps launches after 3 warm-up launches)."""
+    import torch
+    import paper_2607_24059_b300 as vlbm
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(8)
+    X = torch.randn(nb, c, c, 64, device="cuda", generator=g).to(torch.bfloat16)
+    dZ = torch.randn(nb, c, c, 64, device="cuda", generator=g).to(torch.bfloat16)
+    G = torch.zeros(64, 9, 64, device="cuda")
+    Gb = torch.zeros(64, device="cuda")
+    for _ in range(3):
+        vlbm.vlbm_sur_conv3x3_wgrad(X, dZ, G, Gb, err)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        vlbm.vlbm_sur_conv3x3_wgrad(X, dZ, G, Gb, err)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * nb * c * c * 9 * 64 * 64
+    return {"kernel": "k_conv3x3_wgrad<64, 64>", "avg_launch_ms": ms, "flops_per_launch": flops,
+            "achieved_tflops": flops / (ms * 1e-3) / 1e12, "launches_timed": reps}
+
+
 def run_surrogate(args):
     """Learned surrogate (256^2 states pooled 4x from 1024^2 runs of the scheme; u_x, u_y, phi):
     one step of this workload is a checked rollout of --sur-batch states by 100 surrogate steps
@@ -554,9 +582,10 @@ def run_surrogate(args):
     torch.cuda.set_device(local)
     if args.conv_only:
         if rank == 0:
+            stream = torch.cuda.current_stream()
             print(json.dumps({"workload": "sur256 dominant kernel alone", "states": args.sur_batch,
-                              "roofline": conv_roofline(args.sur_batch, args.n // 4, torch.cuda.current_stream())}),
-                  flush=True)
+                              "roofline": conv_roofline(args.sur_batch, args.n // 4, stream),
+                              "wgrad": wgrad_roofline(args.sur_batch, args.n // 4, stream)}), flush=True)
         return 0
     dist = dist_init(world, "nccl")
     cfg = sg.Config(fine=args.n, train_trajectories=args.sur_trajectories, epochs=args.sur_epochs)
