@@ -274,8 +274,8 @@ const char* vlbm_batch_last_error(const vlbm_batch* b);
 /* ---- tensor-core building block of the surrogate ---------------------------
  * D = A B^T on the fifth-generation tensor cores (tcgen05, BF16 operands,
  * FP32 accumulation in tensor memory): A [M][K] and B [N][K] row-major BF16
- * device arrays, D [M][N] row-major FP32 device array.  M % 128 == 0,
- * 16 <= N <= 256 with N % 16 == 0, K % 64 == 0.  *err_dev (device int) is set
+ * device arrays (16-byte aligned), D [M][N] row-major FP32 device array.
+ * M % 128 == 0, 16 <= N <= 256 with N % 16 == 0, K % 64 == 0.  *err_dev (device int) is set
  * to 1 if a bounded wait for the tensor core gave up.  Asynchronous on stream.
  * Not an operation of the paper: the GEMM the learned surrogate is built on. */
 int vlbm_tc_gemm_bf16(const void* A, const void* B, float* D, int64_t M, int64_t N, int64_t K, int32_t* err_dev,
@@ -284,8 +284,10 @@ int vlbm_tc_gemm_bf16(const void* A, const void* B, float* D, int64_t M, int64_t
 /* 3x3 convolution with periodic padding on the tensor cores (implicit GEMM):
  *   Y[b][y][x][co] = act(bias[co] + sum_{dy,dx,ci} W[co][3(dy+1)+(dx+1)][ci] X[b][y+dy][x+dx][ci])
  * with indices wrapped periodically.  X [B][H][W][cin] and Y, Z [B][H][W][cout]
- * are BF16 NHWC device arrays, W [cout][9][cin] BF16, bias [cout] FP32.
- * act = 1 applies GELU (erf form) and, when Z is not NULL, also stores the
+ * are BF16 NHWC device arrays, W [cout][9][cin] BF16, bias [cout] FP32;
+ * X, W, Y and Z 16-byte aligned (VLBM_EINVAL otherwise).
+ * act = 1 applies GELU (tanh form, 0.5 x (1 + tanh(sqrt(2/pi)(x + 0.044715 x^3))))
+ * and, when Z is not NULL, also stores the
  * pre-activation in Z; act = 0 stores the affine result.  (cin, cout) in
  * {16, 64} x {16, 64}.  *err_dev is set to 1 if a wait for the tensor core
  * gave up.  Asynchronous on stream. */
@@ -296,7 +298,7 @@ int vlbm_sur_conv3x3(const void* X, const void* W, const float* bias, void* Y, v
  *   G[co][3(dy+1)+(dx+1)][ci] += sum_{b,y,x} X[b][y+dy][x+dx][ci] dZ[b][y][x][co]
  *   Gb[co]                   += sum_{b,y,x} dZ[b][y][x][co]
  * (periodic indices) on the tensor cores.  X [B][H][W][cin], dZ [B][H][W][cout]
- * BF16 NHWC device arrays; G [cout][9][cin] and Gb [cout] FP32 device arrays
+ * BF16 NHWC device arrays, 16-byte aligned; G [cout][9][cin] and Gb [cout] FP32 device arrays
  * that the caller zeroes first.  (cin, cout) in {(16,64), (64,64), (64,16)};
  * B H W < 2^31.  Asynchronous on stream; *err_dev as above. */
 int vlbm_sur_conv3x3_wgrad(const void* X, const void* dZ, float* G, float* Gb, int64_t B, int64_t H, int64_t Wd,

@@ -25,6 +25,9 @@ constexpr long long kWaitPolls = 1 << 22;
 // Kernels launched by this file's entry points since the library was loaded.
 std::atomic<long long> g_launches{0};
 
+// Device pointers the kernels access in vectors of `bytes` must be aligned to them.
+bool misaligned(const void* p, uintptr_t bytes) { return reinterpret_cast<uintptr_t>(p) % bytes != 0; }
+
 // D[M x N] = A[M x K] B[N x K]^T for one 128-row block of A.  A, B row-major
 // BF16 (K contiguous), D row-major FP32.  N % 16 == 0, 16 <= N <= 256, K % 64 == 0.
 __global__ void __launch_bounds__(kTcThreads)
@@ -1054,6 +1057,7 @@ extern "C" int vlbm_tc_gemm_bf16(const void* A, const void* B, float* D, int64_t
                                  int32_t* err_dev, void* stream) {
     if (!A || !B || !D || !err_dev || M <= 0 || M % 128 || N < 16 || N > 256 || N % 16 || K <= 0 || K % kKChunk)
         return VLBM_EINVAL;
+    if (misaligned(A, 16) || misaligned(B, 16)) return VLBM_EINVAL;
     g_launches.fetch_add(1, std::memory_order_relaxed);
     k_tc_gemm_bf16<<<(unsigned)(M / 128), kTcThreads, 0, (cudaStream_t)stream>>>(
         (const __nv_bfloat16*)A, (const __nv_bfloat16*)B, D, (int)N, (int)K, err_dev);
@@ -1064,6 +1068,8 @@ extern "C" int vlbm_sur_conv3x3(const void* X, const void* W, const float* bias,
                                 int64_t H, int64_t Wd, int32_t cin, int32_t cout, int32_t act, int32_t* err_dev,
                                 void* stream) {
     if (!X || !W || !bias || !Y || !err_dev || B < 1 || H < 1 || Wd < 1) return VLBM_EINVAL;
+    // 16-byte copies of X and W and 16-byte stores of Y and Z
+    if (misaligned(X, 16) || misaligned(W, 16) || misaligned(Y, 16) || (Z && misaligned(Z, 16))) return VLBM_EINVAL;
     const cudaStream_t s = (cudaStream_t)stream;
     if (cin == 16 && cout == 64) return launch_conv_act<16, 64>(X, W, bias, Y, Z, B, H, Wd, act, err_dev, s);
     if (cin == 64 && cout == 64) return launch_conv_act<64, 64>(X, W, bias, Y, Z, B, H, Wd, act, err_dev, s);
@@ -1237,6 +1243,7 @@ extern "C" int vlbm_sur_conv3x3_wgrad(const void* X, const void* dZ, float* G, f
                                       int64_t Wd, int32_t cin, int32_t cout, int32_t* err_dev, void* stream) {
     if (!X || !dZ || !G || !Gb || !err_dev || B < 1 || H < 1 || Wd < 1) return VLBM_EINVAL;
     if ((unsigned long long)(B * H * Wd) >= (1ull << 31)) return VLBM_EINVAL;
+    if (misaligned(X, 16) || misaligned(dZ, 16)) return VLBM_EINVAL;      // 16-byte cp.async copies
     return wgrad_any(cin, cout, X, dZ, G, Gb, B, H, Wd, err_dev, (cudaStream_t)stream);
 }
 

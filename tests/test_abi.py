@@ -107,3 +107,19 @@ def test_null_pointers_are_einval():
     assert b.lib.vlbm_invariants(None, None) == v.VLBM_EINVAL
     assert b.lib.vlbm_state_bytes(None) == 0
     b.lib.vlbm_destroy(None)
+
+
+def test_tensor_core_entry_points_reject_misaligned_arrays():
+    """Alignment is checked on the host before any launch, so fake addresses are never dereferenced."""
+    a = 0x100000                                   # 16-byte aligned
+    # conv: X, W, Y and Z 16-byte aligned
+    assert b.lib.vlbm_sur_conv3x3(a + 8, a, a, a, None, 1, 8, 8, 64, 64, 1, a, None) == v.VLBM_EINVAL
+    assert b.lib.vlbm_sur_conv3x3(a, a + 8, a, a, None, 1, 8, 8, 64, 64, 1, a, None) == v.VLBM_EINVAL
+    assert b.lib.vlbm_sur_conv3x3(a, a, a, a + 8, None, 1, 8, 8, 64, 64, 1, a, None) == v.VLBM_EINVAL
+    assert b.lib.vlbm_sur_conv3x3(a, a, a, a, a + 8, 1, 8, 8, 64, 64, 1, a, None) == v.VLBM_EINVAL
+    # weight gradient: X and dZ 16-byte aligned
+    assert b.lib.vlbm_sur_conv3x3_wgrad(a + 8, a, a, a, 1, 8, 8, 64, 64, a, None) == v.VLBM_EINVAL
+    assert b.lib.vlbm_sur_conv3x3_wgrad(a, a + 8, a, a, 1, 8, 8, 64, 64, a, None) == v.VLBM_EINVAL
+    # GEMM: A and B 16-byte aligned
+    assert b.lib.vlbm_tc_gemm_bf16(a + 8, a, a, 128, 16, 64, a, None) == v.VLBM_EINVAL
+    assert b.lib.vlbm_tc_gemm_bf16(a, a + 8, a, 128, 16, 64, a, None) == v.VLBM_EINVAL
