@@ -395,6 +395,18 @@ int vlbm_sur_gather_pairs(const float* snaps, const int64_t* idx, float* u, floa
  * of |grad u|^2.  The surrogate's rollout check reads these.  Asynchronous. */
 int vlbm_field_stats(const float* u, double* out, int32_t batch, int32_t channels, int64_t H, int64_t W,
                      void* stream);
+/* The surrogate rollout's per-state check on the device (not an operation of
+ * the paper; the fallback rule of the learned surrogate).  stats and prev
+ * [n][3] FP64 device arrays as vlbm_field_stats writes them, for the new
+ * states and the states they were advanced from; e0 [n] the starting
+ * energies, r_max [n] the largest admitted divergence-to-gradient ratios.
+ * State b fails when |E/E_prev - 1| > step_tol, |E/E_0 - 1| > drift_tol or
+ * sqrt(D / max(G, 1e-300)) > r_max[b], NaN counting as a failure; then
+ * mask[b] = 1 (else 0) and counts[b] += 1.  counts [n + 3] int64 device array:
+ * per-state failures, then the failing tests (energy step, energy drift,
+ * divergence), accumulated.  Asynchronous on stream; no host round trip. */
+int vlbm_sur_rollout_check(const double* stats, const double* prev, const double* e0, const double* r_max, int32_t n,
+                           double step_tol, double drift_tol, uint8_t* mask, int64_t* counts, void* stream);
 /* Per-field error sums over the first n FP32 values of nfields fields that
  * lie ld values apart (device arrays a, b): out[f][0] = sum (a - b)^2,
  * out[f][1] = sum b^2, FP64 device array out [nfields][2].  Asynchronous. */

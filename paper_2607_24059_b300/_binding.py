@@ -66,7 +66,7 @@ EXPORTED = [
     "vlbm_sur_create", "vlbm_sur_destroy", "vlbm_sur_num_params", "vlbm_sur_forward", "vlbm_sur_train_step",
     "vlbm_sur_get_params", "vlbm_sur_get_grads", "vlbm_sur_set_params", "vlbm_sur_status", "vlbm_sur_advance",
     "vlbm_sur_set_scaling", "vlbm_sur_set_train_noise", "vlbm_sur_launch_count", "vlbm_sur_increment",
-    "vlbm_field_pool", "vlbm_sur_gather_pairs", "vlbm_field_stats", "vlbm_field_diff_norms",
+    "vlbm_field_pool", "vlbm_sur_gather_pairs", "vlbm_field_stats", "vlbm_sur_rollout_check", "vlbm_field_diff_norms",
 ]
 
 
@@ -157,6 +157,7 @@ lib.vlbm_field_pool.argtypes = [_V, _V, ctypes.c_int64, ctypes.c_int64, ctypes.c
 lib.vlbm_sur_gather_pairs.argtypes = [_V, _V, _V, _V, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                       _V, _V]
 lib.vlbm_field_stats.argtypes = [_V, _V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _V]
+lib.vlbm_sur_rollout_check.argtypes = [_V, _V, _V, _V, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _V, _V, _V]
 lib.vlbm_field_diff_norms.argtypes = [_V, _V, _V, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _V]
 lib.vlbm_strerror.argtypes = [ctypes.c_int]
 lib.vlbm_strerror.restype = ctypes.c_char_p
@@ -560,6 +561,17 @@ def vlbm_field_stats(u, out, stream=None) -> None:
     B, C, H, W = u.shape
     s = current_stream() if stream is None else stream
     _check(lib.vlbm_field_stats(_V(u.data_ptr()), _V(out.data_ptr()), B, C, H, W, _V(s)), "vlbm_field_stats")
+
+
+def vlbm_sur_rollout_check(stats, prev, e0, r_max, step_tol, drift_tol, mask, counts, stream=None) -> None:
+    """Per-state rollout check on the device: stats, prev (n, 3) fp64; e0, r_max (n,) fp64;
+    mask (n,) uint8 out; counts (n + 3,) int64 accumulated (per-state failures, then the failing
+    energy-step, energy-drift and divergence tests)."""
+    n = stats.shape[0]
+    s = current_stream() if stream is None else stream
+    _check(lib.vlbm_sur_rollout_check(_V(stats.data_ptr()), _V(prev.data_ptr()), _V(e0.data_ptr()),
+                                      _V(r_max.data_ptr()), n, float(step_tol), float(drift_tol),
+                                      _V(mask.data_ptr()), _V(counts.data_ptr()), _V(s)), "vlbm_sur_rollout_check")
 
 
 def vlbm_field_diff_norms(a, b, out, n=None, stream=None) -> None:

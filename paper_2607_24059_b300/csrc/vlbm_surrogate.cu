@@ -994,6 +994,35 @@ __global__ void k_field_stats(const float* __restrict__ u, double* __restrict__ 
     }
 }
 
+// The rollout's per-state check, decided on the device so that a checked rollout needs no host round
+// trip per step.  From the statistics of the new state (stats) and of the state it was advanced from
+// (prev), both [n][3] as k_field_stats writes them:
+//   energy step   |E / E_prev - 1| <= step_tol
+//   energy drift  |E / E_0 - 1| <= drift_tol
+//   divergence    sqrt(D / max(G, 1e-300)) <= r_max[b]
+// A state fails when any test fails, NaN included (every comparison with NaN is false; the max
+// propagates NaN like numpy's maximum).  mask[b] = 1 for a failing state; counts[b] (b < n) counts
+// its failures, counts[n .. n + 2] the failing tests (energy step, energy drift, divergence).
+__global__ void k_rollout_check(const double* __restrict__ stats, const double* __restrict__ prev,
+                                const double* __restrict__ e0, const double* __restrict__ r_max, int n,
+                                double step_tol, double drift_tol, uint8_t* __restrict__ mask,
+                                unsigned long long* __restrict__ counts) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const double e = stats[3 * b], g = stats[3 * b + 2];
+    const double gm = (g != g) ? g : (g > 1e-300 ? g : 1e-300);
+    const double r = sqrt(stats[3 * b + 1] / gm);
+    const bool b_step = !(fabs(e / prev[3 * b] - 1.0) <= step_tol);
+    const bool b_drift = !(fabs(e / e0[b] - 1.0) <= drift_tol);
+    const bool b_div = !(r <= r_max[b]);
+    const bool bad = b_step || b_drift || b_div;
+    mask[b] = bad ? 1 : 0;
+    if (bad) counts[b] += 1;
+    if (b_step) atomicAdd(counts + n, 1ull);
+    if (b_drift) atomicAdd(counts + n + 1, 1ull);
+    if (b_div) atomicAdd(counts + n + 2, 1ull);
+}
+
 // Mean-squared loss of output channels 0 .. C-1 against t [B][C][H][W]; dY (16 ch) and sum of squares.
 __global__ void k_mse_grad(const __nv_bfloat16* __restrict__ Y, const float* __restrict__ t,
                            __nv_bfloat16* __restrict__ dY, double* __restrict__ sse, long long plane, long long npix,
@@ -1469,6 +1498,16 @@ extern "C" int vlbm_field_stats(const float* u, double* out, int32_t batch, int3
     const unsigned gx = (unsigned)std::min<long long>((plane + 255) / 256, 148);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     k_field_stats<<<dim3(gx, batch), 256, 0, st>>>(u, out, channels, (int)H, (int)W);
+    return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
+}
+
+extern "C" int vlbm_sur_rollout_check(const double* stats, const double* prev, const double* e0, const double* r_max,
+                                      int32_t n, double step_tol, double drift_tol, uint8_t* mask, int64_t* counts,
+                                      void* stream) {
+    if (!stats || !prev || !e0 || !r_max || !mask || !counts || n < 1) return VLBM_EINVAL;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    k_rollout_check<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+        stats, prev, e0, r_max, n, step_tol, drift_tol, mask, reinterpret_cast<unsigned long long*>(counts));
     return cudaGetLastError() == cudaSuccess ? VLBM_OK : VLBM_ECUDA;
 }
 

@@ -267,13 +267,16 @@ class Rollout:
         self.u = torch.empty(batch, C, c, c, dtype=torch.float32, device=device)
         self.nxt = torch.empty_like(self.u)
         self.stats = torch.empty(batch, 3, dtype=torch.float64, device=device)
+        self.stats_prev = torch.empty_like(self.stats)
         self.stats_h = torch.empty(batch, 3, dtype=torch.float64).pin_memory()
+        self.e0 = torch.empty(batch, dtype=torch.float64, device=device)
+        self.r_max = torch.empty(batch, dtype=torch.float64, device=device)
+        self.counts = torch.zeros(batch + 3, dtype=torch.int64, device=device)
         self.nrm = torch.empty(batch, 2, dtype=torch.float64, device=device)
         # the fallback: one coarse problem per state, advanced together; a failing step
         # re-initialises the flagged problems from their (u, phi) and reads them back
         # with one masked launch each
         self.coarse = Batch([dict(n=(c, c), dx=2 * math.pi / c, nu=cfg.nu)] * batch, precision="fp32")
-        self.mask_h = torch.zeros(batch, dtype=torch.uint8).pin_memory()
         self.mask_d = torch.zeros(batch, dtype=torch.uint8, device=device)
 
     def close(self):
@@ -287,53 +290,42 @@ class Rollout:
         ratio = np.sqrt(s[:, 1] / np.maximum(s[:, 2], 1e-300))
         return s[:, 0].copy(), ratio
 
-    def _fallback_into(self, u, nxt, bad):
-        """Plain scheme on the coarse lattice for the flagged states: u[b] -> nxt[b], coarse_steps steps."""
-        n = u.shape[0]
-        self.mask_h.zero_()
-        self.mask_h[:n] = torch.from_numpy(bad.astype(np.uint8))
-        self.mask_d.copy_(self.mask_h, non_blocking=True)
-        B.vlbm_batch_init_states(self.coarse.handle, u, self.mask_d)
-        self.coarse.step(self.cfg.coarse_steps)
-        B.vlbm_batch_macros_states(self.coarse.handle, nxt, self.mask_d)
-
     def run(self, u0: torch.Tensor, steps: int, check=True, reference=None, every=1):
         """Advance u0 (batch, C, c, c) by `steps` surrogate steps.
 
-        reference: optional (steps + 1, batch, C, c, c) states to measure the relative L2
+        With check, every step is decided on the device (vlbm_sur_rollout_check) and the flagged
+        states are advanced by the coarse scheme through masked launches: no host round trip per
+        step.  reference: optional (steps + 1, batch, C, c, c) states to measure the relative L2
         velocity error against every `every` steps.  Returns (final states, info dict).
         """
         cfg = self.cfg
         n = u0.shape[0]
         u, nxt = self.u[:n], self.nxt[:n]
         u.copy_(u0)
-        fallbacks = np.zeros(n, dtype=np.int64)
-        reasons = {"energy_step": 0, "energy_drift": 0, "divergence": 0}
         curve, div_curve = [], []
         if check:
-            e0, r0 = self._read_stats(u)
-            e_prev = e0.copy()
+            cur, prev = self.stats[:n], self.stats_prev[:n]
+            mask, counts = self.mask_d, self.counts[:n + 3]
+            mask.zero_()                                       # entries past n stay unmasked
+            counts.zero_()
+            B.vlbm_field_stats(u, prev)
+            self.e0[:n].copy_(prev[:, 0])
             if self.div_limit is None:
-                r_max = np.maximum(cfg.div_factor * r0, cfg.div_floor)
+                r0 = torch.sqrt(prev[:, 1] / torch.clamp(prev[:, 2], min=1e-300))
+                self.r_max[:n].copy_(torch.clamp(cfg.div_factor * r0, min=cfg.div_floor))
             else:
-                r_max = np.full(n, max(self.div_limit, cfg.div_floor))
+                self.r_max[:n].fill_(max(self.div_limit, cfg.div_floor))
         for k in range(steps):
             self.net.advance(u, out=nxt)
             if check:
-                e, r = self._read_stats(nxt)
-                with np.errstate(invalid="ignore", divide="ignore"):
-                    b_step = ~(np.abs(e / e_prev - 1.0) <= cfg.energy_step_tol)
-                    b_drift = ~(np.abs(e / e0 - 1.0) <= cfg.energy_drift_tol)
-                    b_div = ~(r <= r_max)
-                bad = b_step | b_drift | b_div
-                reasons["energy_step"] += int(b_step.sum())
-                reasons["energy_drift"] += int(b_drift.sum())
-                reasons["divergence"] += int(b_div.sum())
-                if bad.any():
-                    self._fallback_into(u, nxt, bad)
-                    fallbacks += bad
-                    e, _ = self._read_stats(nxt)
-                e_prev = e
+                B.vlbm_field_stats(nxt, cur)
+                B.vlbm_sur_rollout_check(cur, prev, self.e0[:n], self.r_max[:n], cfg.energy_step_tol,
+                                         cfg.energy_drift_tol, mask[:n], counts)
+                # the plain scheme on the coarse lattice for the flagged states: u[b] -> nxt[b]
+                B.vlbm_batch_init_states(self.coarse.handle, u, mask)
+                self.coarse.step(cfg.coarse_steps)
+                B.vlbm_batch_macros_states(self.coarse.handle, nxt, mask)
+                B.vlbm_field_stats(nxt, prev)                  # the accepted states: next step's reference
             u, nxt = nxt, u
             if reference is not None and ((k + 1) % every == 0 or k + 1 == steps):
                 errs = velocity_errors(u, reference[k + 1], self.nrm)
@@ -341,8 +333,12 @@ class Rollout:
                 div_curve.append((k + 1, float(np.mean(self._read_stats(u)[1]))))
         if u.data_ptr() != self.u.data_ptr():
             self.u[:n].copy_(u)
-        return self.u[:n], {"fallbacks": fallbacks.tolist(), "reasons": reasons, "curve": curve,
-                            "div_ratio": div_curve}
+        fallbacks, reasons = [0] * n, {"energy_step": 0, "energy_drift": 0, "divergence": 0}
+        if check:
+            c = counts.cpu().tolist()
+            fallbacks = c[:n]
+            reasons = {"energy_step": c[n], "energy_drift": c[n + 1], "divergence": c[n + 2]}
+        return self.u[:n], {"fallbacks": fallbacks, "reasons": reasons, "curve": curve, "div_ratio": div_curve}
 
 
 def coarse_scheme(cfg: Config, u0: torch.Tensor, steps: int, reference=None) -> tuple:

@@ -128,6 +128,45 @@ def test_batch_state_entry_points_match_single_problem_calls():
     bt.close()
 
 
+def test_rollout_check_matches_the_host_rule():
+    """The device check flags exactly the states the FP64 host rule flags, NaN included, and
+    accumulates its counts."""
+    rng = np.random.default_rng(5)
+    n = 40
+    stats = np.abs(rng.normal(1.0, 0.01, (n, 3)))
+    stats[:, 1] *= rng.uniform(0.5, 2.0, n) * 1e-4
+    prev = np.abs(rng.normal(1.0, 0.01, (n, 3)))
+    prev[:, 0] = stats[:, 0] * (1.0 + rng.normal(0.0, 3e-3, n))
+    e0 = np.abs(rng.normal(1.0, 0.05, n))
+    r_max = np.full(n, 0.012)
+    stats[3, 0] = np.nan
+    stats[5, 1] = np.nan
+    stats[7, 2] = 0.0
+    stats[9, 2] = np.nan
+    prev[11, 0] = stats[11, 0]
+    tol_step, tol_drift = 5e-3, 5e-2
+    e = stats[:, 0]
+    with np.errstate(all="ignore"):
+        ratio = np.sqrt(stats[:, 1] / np.maximum(stats[:, 2], 1e-300))
+        b_step = ~(np.abs(e / prev[:, 0] - 1.0) <= tol_step)
+        b_drift = ~(np.abs(e / e0 - 1.0) <= tol_drift)
+        b_div = ~(ratio <= r_max)
+    bad = b_step | b_drift | b_div
+    assert 0 < bad.sum() < n and 0 < b_step.sum() and 0 < b_drift.sum() and 0 < b_div.sum()
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    mask = torch.full((n,), 7, dtype=torch.uint8, device="cuda")
+    counts = torch.zeros(n + 3, dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        v.vlbm_sur_rollout_check(dev(stats), dev(prev), dev(e0), dev(r_max), tol_step, tol_drift, mask, counts)
+    assert np.array_equal(mask.cpu().numpy(), bad.astype(np.uint8))
+    c = counts.cpu().numpy()
+    assert np.array_equal(c[:n], 2 * bad.astype(np.int64))
+    assert list(c[n:]) == [2 * int(b_step.sum()), 2 * int(b_drift.sum()), 2 * int(b_div.sum())]
+
+
 def test_rollout_without_fallback_is_the_surrogate():
     cfg = tiny_config(energy_step_tol=1e9, energy_drift_tol=1e9, div_factor=1e9)
     net = v.Surrogate(16, 16, max_batch=4, channels=3, seed=2)
