@@ -961,7 +961,9 @@ __global__ void k_diff_norms(const float* __restrict__ a, const float* __restric
 //   out[b][0] = sum (u_x^2 + u_y^2) / 2
 //   out[b][1] = sum (d_x u_x + d_y u_y)^2            (central differences)
 //   out[b][2] = sum |grad u|^2                        (same differences, all four)
-// accumulated in FP64 with atomics into out (zeroed by the caller).
+// Each pixel's three terms are formed in FP32 (one rounding each, ~6e-8 relative) and summed in
+// FP64 with atomics into out (zeroed by the caller); per-pixel FP64 products would run on the
+// GPU's slow FP64 pipe.
 __global__ void k_field_stats(const float* __restrict__ u, double* __restrict__ out, int C, int H, int W) {
     const int b = blockIdx.y;
     const long long plane = (long long)H * W;
@@ -976,10 +978,10 @@ __global__ void k_field_stats(const float* __restrict__ u, double* __restrict__ 
         const float a = ux[q], c = uy[q];
         const float axx = 0.5f * (ux[r + xp] - ux[r + xm]), axy = 0.5f * (ux[(long long)yp * W + x] - ux[(long long)ym * W + x]);
         const float cxx = 0.5f * (uy[r + xp] - uy[r + xm]), cxy = 0.5f * (uy[(long long)yp * W + x] - uy[(long long)ym * W + x]);
-        e += 0.5 * ((double)a * a + (double)c * c);
-        const double dv = (double)axx + (double)cxy;
-        d += dv * dv;
-        g += (double)axx * axx + (double)axy * axy + (double)cxx * cxx + (double)cxy * cxy;
+        const float dv = axx + cxy;
+        e += (double)(0.5f * (a * a + c * c));
+        d += (double)(dv * dv);
+        g += (double)((axx * axx + axy * axy) + (cxx * cxx + cxy * cxy));
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
