@@ -21,9 +21,10 @@ factor^2 fine steps long (dt = dx^2 / mu), so K / factor^2 coarse steps.
 
 Every array operation on this path is one of the library's kernels (lattice
 steps and macros, pooling, pair gathering, the network's forward, backward and
-Adam, field statistics and error norms); torch only provides device memory and
-the host runs the loops, draws the minibatch indices and takes the fallback
-decisions.
+Adam, field statistics, the rollout check and error norms); torch only provides
+device memory, and the host runs the loops and draws the minibatch indices.  The
+fallback decisions are taken on the device, so a rollout has no host round trip
+between its steps.
 """
 from __future__ import annotations
 
