@@ -93,9 +93,11 @@ k_batch_init_states(char* __restrict__ level, const BatchProblem<typename Storag
                                   channels > 2 ? st + 2 * P.plane : nullptr, P.k, dx, gamma, rho_bar, p_bar);
 }
 
-// The read-out writes FP32: the moments are summed in FP64 (the populations can cancel), then
-// the divisions by dx rho and dx^2 rho_bar are FP32 (a correctly rounded reciprocal times the
-// rounded moment, about 1.5 ulp), instead of three FP64 divisions per node on the slow FP64 pipe.
+// The read-out writes FP32.  With FP32 (or 16-bit) storage the five populations of a moment are
+// summed in FP32 with error-free transformations (Knuth's TwoSum; the compensated sum is as
+// accurate as an FP64 sum rounded to FP32, also when the populations cancel), and the divisions
+// by dx rho and dx^2 rho_bar are FP32 (a correctly rounded reciprocal times the moment, about
+// 1.5 ulp): the FP64 form of these sums and divisions runs on the GPU's slow FP64 pipe.
 template <class S, bool SPLIT>
 __global__ void __launch_bounds__(kThreads)
 k_batch_macros_states(const char* __restrict__ level, const BatchProblem<typename Storage<S>::C>* __restrict__ probs,
@@ -108,24 +110,35 @@ k_batch_macros_states(const char* __restrict__ level, const BatchProblem<typenam
     if (node >= P.plane) return;
     float* st = states + (long long)p * channels * P.plane;
     const Layout<S, SPLIT, 5> f{const_cast<char*>(level) + P.offset, P.plane};
-    double m[3];
+    using C = typename Storage<S>::C;
+    if constexpr (sizeof(C) == 8) {
+        macros_node_2d<S, SPLIT, float>(f, P.plane, node, nullptr, st, channels > 2 ? st + 2 * P.plane : nullptr,
+                                        P.k, dx, gamma, rho_bar, p_bar);
+    } else {
+        float m[3];
 #pragma unroll
-    for (int fld = 0; fld < 3; ++fld) {
-        if constexpr (SPLIT) {
-            m[fld] = (double)f.rest(fld)[node];
-        } else {
-            double mv = 0.0;
+        for (int fld = 0; fld < 3; ++fld) {
+            if constexpr (SPLIT) {
+                m[fld] = f.rest(fld)[node];
+            } else {
+                float sum = load_pop(f, fld, 0, node, P.k), err = 0.0f;
 #pragma unroll
-            for (int l = 1; l < 5; ++l) mv += (double)load_pop(f, fld, l, node, P.k);
-            m[fld] = (double)load_pop(f, fld, 0, node, P.k) + mv;
+                for (int l = 1; l < 5; ++l) {
+                    const float x = load_pop(f, fld, l, node, P.k);
+                    const float t = __fadd_rn(sum, x), bp = __fsub_rn(t, sum);
+                    err = __fadd_rn(err, __fadd_rn(__fsub_rn(sum, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+                    sum = t;
+                }
+                m[fld] = __fadd_rn(sum, err);
+            }
         }
-    }
-    const float inv = 1.0f / (float)(dx * (rho_bar + m[0]));
-    st[node] = (float)m[1] * inv;
-    st[P.plane + node] = (float)m[2] * inv;
-    if (channels > 2) {
-        const double dP = (gamma == 1.0) ? m[0] : p_bar * expm1(gamma * log1p(m[0] / rho_bar));
-        st[2 * P.plane + node] = (float)dP * (1.0f / (float)(dx * dx * rho_bar));
+        const float inv = 1.0f / ((float)dx * ((float)rho_bar + m[0]));
+        st[node] = m[1] * inv;
+        st[P.plane + node] = m[2] * inv;
+        if (channels > 2) {
+            const float dP = (gamma == 1.0) ? m[0] : (float)p_bar * expm1f((float)gamma * log1pf(m[0] / (float)rho_bar));
+            st[2 * P.plane + node] = dP * (1.0f / (float)(dx * dx * rho_bar));
+        }
     }
 }
 

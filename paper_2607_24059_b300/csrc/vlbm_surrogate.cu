@@ -961,15 +961,17 @@ __global__ void k_diff_norms(const float* __restrict__ a, const float* __restric
 //   out[b][0] = sum (u_x^2 + u_y^2) / 2
 //   out[b][1] = sum (d_x u_x + d_y u_y)^2            (central differences)
 //   out[b][2] = sum |grad u|^2                        (same differences, all four)
-// Each pixel's three terms are formed in FP32 (one rounding each, ~6e-8 relative) and summed in
-// FP64 with atomics into out (zeroed by the caller); per-pixel FP64 products would run on the
-// GPU's slow FP64 pipe.
-__global__ void k_field_stats(const float* __restrict__ u, double* __restrict__ out, int C, int H, int W) {
+// Each thread sums its few pixels' terms in FP32 (one rounding per term, ~6e-8 relative); the
+// block reduces the partial sums in FP64 and adds them to out (zeroed by the caller) with one
+// atomic per value: FP64 arithmetic per pixel, or an atomic per warp, would leave the kernel
+// bound by the GPU's slow FP64 pipe and by contention on the 3 addresses of a state.
+__global__ void __launch_bounds__(256)
+k_field_stats(const float* __restrict__ u, double* __restrict__ out, int C, int H, int W) {
     const int b = blockIdx.y;
     const long long plane = (long long)H * W;
     const float* ux = u + (long long)b * C * plane;
     const float* uy = ux + plane;
-    double e = 0.0, d = 0.0, g = 0.0;
+    float ef = 0.0f, df = 0.0f, gf = 0.0f;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < plane; q += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(q % W), y = (int)(q / W);
         const int xp = x + 1 == W ? 0 : x + 1, xm = x == 0 ? W - 1 : x - 1;
@@ -979,20 +981,29 @@ __global__ void k_field_stats(const float* __restrict__ u, double* __restrict__ 
         const float axx = 0.5f * (ux[r + xp] - ux[r + xm]), axy = 0.5f * (ux[(long long)yp * W + x] - ux[(long long)ym * W + x]);
         const float cxx = 0.5f * (uy[r + xp] - uy[r + xm]), cxy = 0.5f * (uy[(long long)yp * W + x] - uy[(long long)ym * W + x]);
         const float dv = axx + cxy;
-        e += (double)(0.5f * (a * a + c * c));
-        d += (double)(dv * dv);
-        g += (double)((axx * axx + axy * axy) + (cxx * cxx + cxy * cxy));
+        ef += 0.5f * (a * a + c * c);
+        df += dv * dv;
+        gf += (axx * axx + axy * axy) + (cxx * cxx + cxy * cxy);
     }
+    double e = ef, d = df, g = gf;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         e += __shfl_xor_sync(0xffffffffu, e, off);
         d += __shfl_xor_sync(0xffffffffu, d, off);
         g += __shfl_xor_sync(0xffffffffu, g, off);
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(out + b * 3 + 0, e);
-        atomicAdd(out + b * 3 + 1, d);
-        atomicAdd(out + b * 3 + 2, g);
+    __shared__ double red[3][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = e;
+        red[1][warp] = d;
+        red[2][warp] = g;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += red[threadIdx.x][w];
+        atomicAdd(out + b * 3 + threadIdx.x, t);
     }
 }
 
