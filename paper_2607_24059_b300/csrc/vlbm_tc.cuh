@@ -3,11 +3,14 @@
 // descriptors, BF16 x BF16 -> FP32 MMA issued by one thread, commit to an
 // mbarrier, bounded waits, and accumulator loads from tensor memory.
 //
-// Operand layout used throughout (K-major, no swizzle): a tile of R rows
-// (M or N) by K columns of BF16 is stored as 8 x 8 "core matrices" of 128
-// contiguous bytes (8 rows of 16 bytes); core matrix (rb, kb) starts at
-// rb * SBO + kb * LBO bytes from the tile base, with LBO = 128 (neighbours
-// along K adjacent) and SBO = 128 * K / 8 (next 8-row group after all of K).
+// Operand layouts.  K-major, no swizzle (the GEMM and the forward convolution):
+// a tile of R rows (M or N) by K columns of BF16 is stored as 8 x 8 "core
+// matrices" of 128 contiguous bytes (8 rows of 16 bytes); core matrix (rb, kb)
+// starts at rb * SBO + kb * LBO bytes from the tile base, with LBO = 128
+// (neighbours along K adjacent) and SBO = 128 * K / 8 (next 8-row group after
+// all of K).  MN-major with 128-byte swizzle (the weight gradient, whose
+// operands are channel-contiguous NHWC data): see smem_desc_sw128 and
+// idesc_bf16_f32_mn below.
 #pragma once
 
 #include <cuda_bf16.h>
