@@ -9,9 +9,12 @@
 // population lattice and the 8-double result; this entry point needs no
 // handle, so it allocates nothing at all: the per-block FP64 partial sums live
 // in the file-scope array below, which every GPU that loads the library keeps
-// until the process exits ((8192 + 1) x 8 doubles, about 512 KiB).  One block
-// reduces 8192 nodes, so lattices of up to 8192 x 8192 = 67,108,864 nodes are
-// accepted; larger ones get VLBM_EINVAL.
+// until the process exits ((8192 + 128 + 1) x 8 doubles, about 520 KiB).  One
+// block reduces 8192 nodes, so lattices of up to 8192 x 8192 = 67,108,864 nodes
+// are accepted; larger ones get VLBM_EINVAL.  Above 256 partial rows the rows
+// are first folded by 128 blocks into 128 rows of the same array (as the
+// handle's reduction does), so that the FP64 additions spread over many SMs.
+// The lattice and a device `out` must be memory of the current device.
 //
 // Host code must not pass the array's name to a kernel: on the host that name
 // is only a stand-in, not a device address.  The device address is looked up
@@ -35,12 +38,15 @@ using namespace vlbm;
 
 namespace {
 
-constexpr int kNoAllocMaxBlocks = 8192;           // partial rows; one more row holds a host-bound result
+constexpr int kNoAllocMaxBlocks = 8192;           // partial rows
+constexpr int kNoAllocStageRows = 128;            // first-stage rows when many partial rows are folded
 constexpr int kNodesPerThread = 32;               // grid: one block per kThreads * 32 nodes
 constexpr long long kNodesPerBlock = (long long)kThreads * kNodesPerThread;
 constexpr int kMaxDevices = 64;
 
-static __device__ __align__(256) double g_noalloc_partials[(kNoAllocMaxBlocks + 1) * 8];
+// Layout: kNoAllocMaxBlocks partial rows, kNoAllocStageRows first-stage rows, one
+// row for a result bound for host memory; 8 doubles per row.
+static __device__ __align__(256) double g_noalloc_partials[(kNoAllocMaxBlocks + kNoAllocStageRows + 1) * 8];
 
 std::mutex g_setup_mutex;
 double* g_partials_ptr[kMaxDevices] = {};
@@ -86,6 +92,20 @@ void launch_partials(const vlbm_params& p, const void* lattice, long long nodes,
         k_invariants_3d<S, M><<<blocks, kThreads, 0, s>>>((const char*)lattice, nodes, k, partials);
 }
 
+// Where a pointer lives: 1 device memory of device `dev` (or managed memory),
+// 0 host memory, -1 device memory of another device or an unknown pointer.
+// A failed query's error is cleared here (it concerns only this query).
+int pointer_home(const void* ptr, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev ? 1 : -1;
+    return 0;
+}
+
 }  // namespace
 
 extern "C" int vlbm_invariants_noalloc(const vlbm_params* p, const void* lattice, double* out, void* stream) {
@@ -95,18 +115,16 @@ extern "C" int vlbm_invariants_noalloc(const vlbm_params* p, const void* lattice
     const long long nodes = d.nodes;
     const long long blocks = (nodes + kNodesPerBlock - 1) / kNodesPerBlock;
     if (blocks > kNoAllocMaxBlocks) return VLBM_EINVAL;   // more than kNoAllocMaxBlocks * 8192 nodes
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return VLBM_ECUDA;
+    if (pointer_home(lattice, dev) != 1) return VLBM_EINVAL;   // device memory of the current device only
+    const int out_home = pointer_home(out, dev);
+    if (out_home < 0) return VLBM_EINVAL;                      // another device's memory
+    const bool out_on_device = out_home == 1;
+    // an error left by the caller's earlier work is reported, not swallowed
+    if (cudaPeekAtLastError() != cudaSuccess) return VLBM_ECUDA;
     double* partials = nullptr;
     if (partials_address(&partials) != cudaSuccess) return VLBM_ECUDA;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, lattice) != cudaSuccess ||
-        (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
-        cudaGetLastError();
-        return VLBM_EINVAL;                                // the lattice must be device memory
-    }
-    bool out_on_device = false;
-    if (cudaPointerGetAttributes(&a, out) == cudaSuccess)
-        out_on_device = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-    cudaGetLastError();
     cudaStream_t s = (cudaStream_t)stream;
     switch (p->precision) {
         case VLBM_FP64: launch_partials<double, false>(*p, lattice, nodes, (int)blocks, partials, s); break;
@@ -118,11 +136,18 @@ extern "C" int vlbm_invariants_noalloc(const vlbm_params* p, const void* lattice
         case VLBM_FP16_SPLIT: launch_partials<__half, true>(*p, lattice, nodes, (int)blocks, partials, s); break;
         default: launch_partials<__nv_bfloat16, true>(*p, lattice, nodes, (int)blocks, partials, s); break;
     }
-    // the row after the partials holds the result when `out` is host memory
-    double* result = out_on_device ? out : partials + (size_t)kNoAllocMaxBlocks * 8;
+    const double* rows = partials;
+    int nrows = (int)blocks;
+    if (nrows > 2 * kNoAllocStageRows) {   // fold the rows over many SMs first
+        double* stage = partials + (size_t)kNoAllocMaxBlocks * 8;
+        k_invariants_stage<<<kNoAllocStageRows, 256, 0, s>>>(partials, nrows, stage);
+        rows = stage;
+        nrows = kNoAllocStageRows;
+    }
+    // the last row holds the result when `out` is host memory
+    double* result = out_on_device ? out : partials + (size_t)(kNoAllocMaxBlocks + kNoAllocStageRows) * 8;
     const double scale_e = p->dim == 3 ? p->dx : 1.0;
-    k_invariants_final<<<1, 1024, 0, s>>>(partials, (int)blocks, result, (double)nodes, p->rho_bar, 1.0 / p->dx,
-                                          scale_e);
+    k_invariants_final<<<1, 1024, 0, s>>>(rows, nrows, result, (double)nodes, p->rho_bar, 1.0 / p->dx, scale_e);
     if (cudaGetLastError() != cudaSuccess) return VLBM_ECUDA;
     if (!out_on_device) {
         if (cudaMemcpyAsync(out, result, 8 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
