@@ -191,6 +191,16 @@ int vlbm_launch_count(const vlbm_handle* h, int64_t* count);
 /* VLBM_OPT_SPLIT_LANES: nodes per lane (2 or 4, default 4) of the vectorised 2D
  * kernel of the split formats; a tuning knob, same results up to FMA contraction. */
 #define VLBM_OPT_SPLIT_LANES 1
+/* VLBM_OPT_ROUNDING_16: rounding of the rest populations of the shifted 16-bit
+ * formats (VLBM_FP16_SHIFTED, VLBM_BF16_SHIFTED; VLBM_EINVAL for the others):
+ * 0 = to nearest (default), 1 = stochastic (unbiased; random bits from a hash of
+ * node, field and step, so runs stay reproducible).  Under the parabolic scaling
+ * a moment changes per step by much less than a 16-bit quantum: rounding to
+ * nearest drops the change (a slowly evolving flow stops evolving), stochastic
+ * rounding keeps it on average at the price of noise of about one quantum per
+ * step.  FP32 storage always rounds its moment-carrying populations
+ * stochastically (they are 2^13 times finer, so the noise is negligible). */
+#define VLBM_OPT_ROUNDING_16 2
 int vlbm_set_option(vlbm_handle* h, int32_t key, int64_t value);
 
 /* The reduction of vlbm_invariants for callers that cannot allocate device
@@ -198,7 +208,7 @@ int vlbm_set_option(vlbm_handle* h, int32_t key, int64_t value);
  * in a real-time loop that may not take the allocator's locks or its implicit
  * synchronisation, or near the memory limit.  The paper has no counterpart;
  * it is an integration aid.  It needs no handle and allocates nothing: the
- * per-block partial sums live in a static device array of about 512 KiB that
+ * per-block partial sums live in a static device array of about 520 KiB that
  * each GPU loading the library keeps until the process exits.
  *   p       parameters of the lattice (checked like vlbm_params_check)
  *   lattice device pointer to one population lattice in a handle's storage
@@ -208,8 +218,10 @@ int vlbm_set_option(vlbm_handle* h, int32_t key, int64_t value);
  *   out     8 doubles in the layout of vlbm_invariants; device memory, or host
  *           memory (then the call synchronises `stream` before returning)
  *   stream  cudaStream_t, NULL for the legacy stream
- * At most 8192 x 8192 = 67,108,864 nodes; larger lattices, a host-memory
- * lattice or bad parameters give VLBM_EINVAL.  The first call on a device
+ * At most 8192 x 8192 = 67,108,864 nodes; larger lattices, a lattice that is
+ * not device memory of the current device, a device `out` on another device
+ * or bad parameters give VLBM_EINVAL; a CUDA error still pending from the
+ * caller's earlier work gives VLBM_ECUDA (it is not cleared).  The first call on a device
  * looks up the static array's device address (cudaGetSymbolAddress): make
  * that first call before any stream capture.  All calls share the array, and
  * each writes every slot it later reads; calls whose kernels overlap on the

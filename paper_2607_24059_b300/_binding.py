@@ -51,6 +51,7 @@ VLBM_STEP_NO_GRAPH = 2
 VLBM_NUM_INVARIANTS = 8
 VLBM_OPT_KERNEL = 0
 VLBM_OPT_SPLIT_LANES = 1
+VLBM_OPT_ROUNDING_16 = 2
 
 PRECISIONS = {"fp64": VLBM_FP64, "fp32": VLBM_FP32, "fp16": VLBM_FP16_SHIFTED, "bf16": VLBM_BF16_SHIFTED,
               "fp16split": VLBM_FP16_SPLIT, "bf16split": VLBM_BF16_SPLIT}

@@ -51,6 +51,7 @@ struct vlbm_handle {
     int64_t partial_capacity = 0;     // blocks
     double* stage = nullptr;          // kStageBlocks rows of the two-stage final reduction
     double* inv_dev = nullptr;        // 8 doubles
+    uint32_t* ctr = nullptr;          // step counter of the stochastic rounding: ctr[cur] = step (mod 2^32)
     double* inv_host = nullptr;       // 8 doubles, pinned
     void* staging = nullptr;
     size_t staging_bytes = 0;
@@ -209,6 +210,7 @@ static void free_all(vlbm_handle* h) {
     if (h->partials) cudaFree(h->partials);
     if (h->stage) cudaFree(h->stage);
     if (h->inv_dev) cudaFree(h->inv_dev);
+    if (h->ctr) cudaFree(h->ctr);
     if (h->inv_host) cudaFreeHost(h->inv_host);
     if (h->staging) cudaFree(h->staging);
     if (h->hist) cudaFree(h->hist);
@@ -250,11 +252,13 @@ extern "C" int vlbm_create(const vlbm_params* p, void* stream, vlbm_handle** out
         if (cudaMalloc(&h->partials, (size_t)h->partial_capacity * 8 * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&h->stage, (size_t)kStageBlocks * 8 * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&h->inv_dev, 8 * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&h->ctr, 2 * sizeof(uint32_t)) != cudaSuccess ||
             cudaMallocHost(&h->inv_host, 8 * sizeof(double)) != cudaSuccess) {
             st = VLBM_ENOMEM;
             break;
         }
-        if (cudaMemsetAsync(h->buf[0], 0, d.lattice_bytes, h->stream) != cudaSuccess) {
+        if (cudaMemsetAsync(h->buf[0], 0, d.lattice_bytes, h->stream) != cudaSuccess ||
+            cudaMemsetAsync(h->ctr, 0, 2 * sizeof(uint32_t), h->stream) != cudaSuccess) {
             st = VLBM_ECUDA;
             break;
         }
@@ -376,6 +380,7 @@ extern "C" int vlbm_init(vlbm_handle* h, const void* u, const void* phi, int32_t
     int rc = check_launch(h, "init");
     if (rc) return rc;
     h->step = 0;
+    VLBM_CUDA(h, cudaMemsetAsync(h->ctr + h->cur, 0, sizeof(uint32_t), h->stream));
     if (u_host || p_host) VLBM_CUDA(h, cudaStreamSynchronize(h->stream));   // host arrays may be reused on return
     return VLBM_OK;
 }
@@ -432,35 +437,35 @@ static void launch_step_on(vlbm_handle* h, cudaStream_t s, int src, double* part
         if (h->p.dim == 2) {
             if (vec && h->split_lanes == 2)
                 k_split_step_2d_vec<S, 2, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, wpr,
-                                                                            k, partials);
+                                                                            k, partials, h->ctr, src);
             else if (vec)
                 k_split_step_2d_vec<S, 4, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, wpr,
-                                                                            k, partials);
+                                                                            k, partials, h->ctr, src);
             else
                 k_split_step_2d_generic<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, k,
-                                                                             partials);
+                                                                             partials, h->ctr, src);
         } else {
             if (vec)
                 k_split_step_3d_vec<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz, plane,
-                                                                         wpr, k, partials);
+                                                                         wpr, k, partials, h->ctr, src);
             else
                 k_split_step_3d_generic<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz,
-                                                                             plane, k, partials);
+                                                                             plane, k, partials, h->ctr, src);
         }
     } else if (h->p.dim == 2) {
         if (vec)
             k_stream_collide_2d_vec<S, M, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, wpr,
-                                                                            k, partials);
+                                                                            k, partials, h->ctr, src);
         else
             k_stream_collide_2d_generic<S, M, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, k,
-                                                                                partials);
+                                                                                partials, h->ctr, src);
     } else {
         if (vec)
             k_stream_collide_3d_vec<S, M, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz,
-                                                                            plane, wpr, k, partials);
+                                                                            plane, wpr, k, partials, h->ctr, src);
         else
             k_stream_collide_3d_generic<S, M, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz,
-                                                                                plane, k, partials);
+                                                                                plane, k, partials, h->ctr, src);
     }
 }
 
@@ -699,6 +704,8 @@ extern "C" int vlbm_set_state(vlbm_handle* h, const void* src, size_t bytes) {
         return fail(h, VLBM_EINVAL, "checkpoint does not match this handle's configuration");
     VLBM_CUDA(h, cudaMemcpyAsync(h->buf[h->cur], (const char*)src + sizeof s, h->d.lattice_bytes, cudaMemcpyDefault,
                                  h->stream));
+    const uint32_t ctr = (uint32_t)s.step;   // the stochastic rounding continues where the checkpoint left off
+    VLBM_CUDA(h, cudaMemcpyAsync(h->ctr + h->cur, &ctr, sizeof ctr, cudaMemcpyHostToDevice, h->stream));
     VLBM_CUDA(h, cudaStreamSynchronize(h->stream));
     h->step = s.step;
     return VLBM_OK;
@@ -761,6 +768,16 @@ extern "C" int vlbm_set_option(vlbm_handle* h, int32_t key, int64_t value) {
             if (value < 0 || value > 2) return VLBM_EINVAL;
             if (value == 2 && h->p.n[0] % vec_width(h) != 0) return VLBM_EINVAL;
             h->kernel_variant = (int)value;
+            for (int i = 0; i < 2; ++i)
+                if (h->graph[i]) {
+                    cudaGraphExecDestroy(h->graph[i]);
+                    h->graph[i] = nullptr;
+                }
+            return VLBM_OK;
+        case VLBM_OPT_ROUNDING_16:
+            if (value != 0 && value != 1) return VLBM_EINVAL;
+            if (h->p.precision != VLBM_FP16_SHIFTED && h->p.precision != VLBM_BF16_SHIFTED) return VLBM_EINVAL;
+            h->kf.sr16 = (int)value;   // a kernel parameter: captured graphs are rebuilt
             for (int i = 0; i < 2; ++i)
                 if (h->graph[i]) {
                     cudaGraphExecDestroy(h->graph[i]);

@@ -53,11 +53,14 @@ template <class S, bool SPLIT, int V>
 __global__ void __launch_bounds__(kMaxBatchThreads)
 k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
                 const BatchProblem<typename Storage<S>::C>* __restrict__ probs, const int* __restrict__ chunk_problem,
-                int count, long long items) {
+                int count, long long items, uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    // one step counter for the batch; nodes are numbered within their problem, so
+    // a problem's rounding matches a single handle's at the same step
+    const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> unused;
     for (long long item = warp; item < items; item += nwarps) {   // warp-uniform
         int p = __ldg(chunk_problem + (item >> kChunkShift));
@@ -69,9 +72,9 @@ k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
         const Layout<S, SPLIT, 5> fout{out_base + P.offset, P.plane};
         const Coef<C>& k = P.k;   // read through L1, not copied into registers
         if constexpr (SPLIT)
-            warp_split_step_2d<S, V, false>(fin, fout, P.nx, P.ny, y, seg, lane, k, unused);
+            warp_split_step_2d<S, V, false>(fin, fout, P.nx, P.ny, y, seg, lane, k, unused, key);
         else
-            warp_stream_collide_2d<S, false, false>(fin, fout, P.nx, P.ny, y, seg, lane, k, unused);
+            warp_stream_collide_2d<S, false, false>(fin, fout, P.nx, P.ny, y, seg, lane, k, unused, key);
     }
 }
 
@@ -156,6 +159,7 @@ struct vlbm_batch {
     size_t level_bytes = 0;
     int cur = 0;
     void* table = nullptr;          // BatchProblem<C>[count] on the device
+    uint32_t* ctr = nullptr;        // step counter of the stochastic rounding (2 slots, see take_step_key)
     int* chunks = nullptr;          // problem of item 64 c, c = 0 .. items / 64
     long long items = 0;
     int threads = 256, blocks_per_sm = 4, lanes = 4;
@@ -251,7 +255,8 @@ template <class S, bool SPLIT, int V>
 void launch_batch(vlbm_batch* b, cudaStream_t s, int src) {
     using C = typename Storage<S>::C;
     k_batch_step_2d<S, SPLIT, V><<<b->sm_count * b->blocks_per_sm, b->threads, 0, s>>>(
-        b->level[src], b->level[src ^ 1], (const BatchProblem<C>*)b->table, b->chunks, b->count, b->items);
+        b->level[src], b->level[src ^ 1], (const BatchProblem<C>*)b->table, b->chunks, b->count, b->items, b->ctr,
+        src);
 }
 
 void launch_batch_step(vlbm_batch* b, cudaStream_t s, int src) {
@@ -299,6 +304,7 @@ void free_batch(vlbm_batch* b) {
     for (int i = 0; i < 2; ++i)
         if (b->level[i]) cudaFree(b->level[i]);
     if (b->table) cudaFree(b->table);
+    if (b->ctr) cudaFree(b->ctr);
     if (b->chunks) cudaFree(b->chunks);
     if (b->partials) cudaFree(b->partials);
     if (b->inv_dev) cudaFree(b->inv_dev);
@@ -423,9 +429,12 @@ extern "C" int vlbm_batch_create(const vlbm_params* problems, int32_t count, voi
     if (st == VLBM_OK &&
         (cudaMalloc(&b->partials, (size_t)b->partial_blocks * 8 * sizeof(double)) != cudaSuccess ||
          cudaMalloc(&b->inv_dev, 8 * sizeof(double)) != cudaSuccess ||
+         cudaMalloc(&b->ctr, 2 * sizeof(uint32_t)) != cudaSuccess ||
          cudaMallocHost(&b->inv_host, 8 * sizeof(double)) != cudaSuccess))
         st = VLBM_ENOMEM;
-    if (st == VLBM_OK && cudaMemsetAsync(b->level[0], 0, off, b->stream) != cudaSuccess) st = VLBM_ECUDA;
+    if (st == VLBM_OK && (cudaMemsetAsync(b->level[0], 0, off, b->stream) != cudaSuccess ||
+                          cudaMemsetAsync(b->ctr, 0, 2 * sizeof(uint32_t), b->stream) != cudaSuccess))
+        st = VLBM_ECUDA;
     if (st == VLBM_OK) st = rebuild_table(b);
     if (st != VLBM_OK) {
         cudaGetLastError();

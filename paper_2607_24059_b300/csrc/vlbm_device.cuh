@@ -42,17 +42,44 @@ template <> struct Storage<float> {
     static __device__ __forceinline__ float to_c(float v) { return v; }
     static __device__ __forceinline__ float from_c(float v) { return v; }
 };
+// 16-bit formats also convert two values at once with stochastic rounding
+// (PTX cvt.rs, sm_100a/sm_103a): `hi` takes its random bits from r[31:16], `lo`
+// from r[15:0]; the result packs hi in the upper and lo in the lower half.
 template <> struct Storage<__half> {
     using C = float;
     static constexpr bool kScaled = true;
     static __device__ __forceinline__ float to_c(__half v) { return __half2float(v); }
     static __device__ __forceinline__ __half from_c(float v) { return __float2half_rn(v); }
+    static __device__ __forceinline__ __half from_bits(uint32_t b) { return __ushort_as_half((unsigned short)b); }
+    static __device__ __forceinline__ uint32_t pack2_sr(float lo, float hi, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+        return d;
+    }
 };
 template <> struct Storage<__nv_bfloat16> {
     using C = float;
     static constexpr bool kScaled = true;
     static __device__ __forceinline__ float to_c(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 from_c(float v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ __nv_bfloat16 from_bits(uint32_t b) {
+        return __ushort_as_bfloat16((unsigned short)b);
+    }
+    static __device__ __forceinline__ uint32_t pack2_sr(float lo, float hi, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+        return d;
+    }
+};
+
+// Storage whose moment-carrying populations are rounded stochastically in the
+// compute type: FP32 (the compute type is the storage type).  FP64 keeps
+// round-to-nearest; 16-bit storage rounds at its own conversion.
+template <class S> struct StochasticMoments { static constexpr bool value = std::is_same<S, float>::value; };
+// 16-bit shifted storage, whose rest populations can be rounded stochastically at their
+// conversion (Coef::sr16, off by default).
+template <class S> struct StochasticStore16 {
+    static constexpr bool value = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
 };
 
 // ---------------------------------------------------------------- lattice layout
@@ -92,7 +119,6 @@ template <class C>
 struct Coef {
     C om[kMaxFields];      // omega_k
     C al[kMaxFields];      // alpha_k
-    C rest[kMaxFields];    // 1 - 2D alpha_k
     C scale[kMaxFields];   // stored = g * scale_k (1 for unscaled formats)
     C inv_scale[kMaxFields];
     C i2m;                 // 1 / (2 mu)
@@ -100,6 +126,7 @@ struct Coef {
     C p_bar;               // P(rho_bar) = rho_bar^gamma
     C gamma;
     int gamma_one;         // gamma == 1: dP = dr / (2 mu) exactly
+    int sr16;              // shifted 16-bit storage: rest populations rounded stochastically (else to nearest)
 };
 
 // Factors from stored values to deviations (load) and back (store).  Rest planes
@@ -144,6 +171,72 @@ __device__ __forceinline__ float recip_sel<true, float>(float x) {
     return y;
 }
 
+// ---------------------------------------------------------------- stochastic rounding
+// Under the parabolic scaling dt = dx^2 / mu a conserved moment changes by a
+// tiny amount per step: on a 4096^2 shear layer about one FP32 ulp of the
+// population that carries it, and less than half an ulp away from the layer
+// core.  Round-to-nearest then drops (or doubles) the same fraction of the
+// increment at every step, a bias that grows linearly with the step count.
+// The populations that carry a field's moment (the rest populations of the
+// uniform layouts, the moments of the split layouts) are therefore rounded
+// stochastically in FP32 storage: the exact sum a + b is rounded to the
+// neighbouring float on either side with probabilities proportional to the
+// distances (unbiased; the accumulated error grows like the square root of
+// the step count).  The random words come from a counter-based hash of
+// (node, field, step): runs are bitwise reproducible, independent of the
+// launch shape and of graph replay.
+
+// 32-bit integer finaliser (a multiply-xorshift hash with the constants of
+// C. Wellons' "hash prospector" low-bias 32-bit search): a bijection of
+// uint32 with good avalanche.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x21f0aaadu;
+    x ^= x >> 15;
+    x *= 0x735a2d97u;
+    x ^= x >> 15;
+    return x;
+}
+
+// Per-launch key of time step `step`.
+__device__ __forceinline__ uint32_t sr_step_key(uint32_t step) { return mix32(step * 0x9e3779b9u + 0x632be5abu); }
+
+// Random word of field f at a node: one hash per node, the fields offset by the
+// 32-bit golden-ratio constant (each word is uniform; the fields' decisions act
+// on independent fractional parts).
+__device__ __forceinline__ uint32_t sr_node_word(uint32_t key, long long node) {
+    return mix32((uint32_t)node ^ key ^ mix32((uint32_t)((unsigned long long)node >> 32)));
+}
+__device__ __forceinline__ uint32_t sr_field_word(uint32_t w, int f) { return w + (uint32_t)f * 0x9e3779b9u; }
+
+// a + b rounded stochastically to FP32 with the random word r: the result is
+// the round-to-nearest sum s or its neighbour t on the side of the exact
+// remainder e = (a + b) - s (TwoSum), t with probability |e| / |t - s|.
+__device__ __forceinline__ float sr_add(float a, float b, uint32_t r) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    const uint32_t bits = __float_as_uint(s);
+    // the low 31 bits are the magnitude: +1 moves away from zero, -1 toward it
+    const uint32_t tb = ((__float_as_uint(e) ^ bits) >> 31) ? bits - 1u : bits + 1u;
+    const float t = __uint_as_float(tb);
+    const float gap = fabsf(__fsub_rn(t, s));                    // a power of two
+    const float u = __uint2float_rz(r >> 8) * 0x1p-24f;         // uniform in [0, 1), 24 bits
+    return fabsf(e) > __fmul_rn(u, gap) ? t : s;                 // false when e = 0 or s is not finite
+}
+// FP64 storage keeps round-to-nearest (its rounding is 2^-29 of FP32's).
+__device__ __forceinline__ double sr_add(double a, double b, uint32_t) { return a + b; }
+
+// 16-bit shifted storage: the rest population of field f of nodes (2j, 2j + 1)
+// is converted as one pair with the random word of the even node; one node
+// alone (the per-node kernels) takes the same bits of the same word.
+template <class S>
+__device__ __forceinline__ S sr16_store_one(float v, long long node, uint32_t key, int f) {
+    const uint32_t r = sr_field_word(sr_node_word(key, node & ~1LL), f);
+    const uint32_t d = (node & 1) ? (Storage<S>::pack2_sr(0.0f, v, r) >> 16) : (Storage<S>::pack2_sr(v, 0.0f, r) & 0xffffu);
+    return Storage<S>::from_bits(d);
+}
+
 // Equilibrium deviations g^eq of one D2Q5 node, fields (rho, q_x, q_y) x
 // velocities (rest, +x, -x, +y, -y): e[5k + l].
 template <class C, bool APPROX = false>
@@ -154,20 +247,21 @@ __device__ __forceinline__ void equilibrium_d2q5(const Coef<C>& k, C dr, C Qx, C
     const C xx = Qx * Qx * r * k.i2m;
     const C xy = Qx * Qy * r * k.i2m;
     const C yy = Qy * Qy * r * k.i2m;
+    // rest entries m - 4 (alpha m): the moving entries' alpha m, so the entries sum to m
     const C ar = k.al[0] * dr;
-    e[0] = k.rest[0] * dr;
+    e[0] = dr - C(4) * ar;
     e[1] = ar + hx;
     e[2] = ar - hx;
     e[3] = ar + hy;
     e[4] = ar - hy;
     const C ax = k.al[1] * Qx;
-    e[5] = k.rest[1] * Qx;
+    e[5] = Qx - C(4) * ax;
     e[6] = ax + (xx + dP);
     e[7] = ax - (xx + dP);
     e[8] = ax + xy;
     e[9] = ax - xy;
     const C ay = k.al[2] * Qy;
-    e[10] = k.rest[2] * Qy;
+    e[10] = Qy - C(4) * ay;
     e[11] = ay + xy;
     e[12] = ay - xy;
     e[13] = ay + (yy + dP);
@@ -192,20 +286,27 @@ __device__ __forceinline__ void moments_d2q5(const C (&g)[15], C& dr, C& Qx, C& 
 }
 
 // Relaxation of Eq. LBM_scheme on the deviations of one D2Q5 node, in place.
-// For the rest population the increment e_0 - g_0 = rest m - g_0 is formed as
-// rest s - (1 - rest) g_0 with s the moving sum (same value, since m = g_0 + s):
-// it is small, while rest m and g_0 are both of the size of m, and their
-// difference would keep only the rounding of rest m.  At FP32 that rounding is
-// systematic for a slowly varying field and grows linearly with the steps.
-template <class C, bool APPROX = false>
-__device__ __forceinline__ void relax_d2q5(const Coef<C>& k, C (&g)[15], C dr, C Qx, C Qy) {
+// For the rest population the increment e_0 - g_0 = (1 - 2D alpha) m - g_0 is
+// formed as s - 2D (alpha m) with s the moving sum (same value, since
+// m = g_0 + s): it is small, while (1 - 2D alpha) m and g_0 are both of the size
+// of m, and their difference would keep only the rounding of the first.  The
+// product alpha m is the one the moving equilibria are built on, so that the
+// relaxation conserves the moment exactly in real arithmetic for the stored
+// coefficients; a separately rounded rest weight 1 - 2D alpha would differ from
+// 1 - 2D alpha_stored by up to half an ulp of 1 and create or destroy moment at a
+// fixed relative rate every step.
+// SR: the rest population (which carries the field's moment) is rounded
+// stochastically with the node's random word w (FP32 storage).
+template <class C, bool APPROX = false, bool SR = false>
+__device__ __forceinline__ void relax_d2q5(const Coef<C>& k, C (&g)[15], C dr, C Qx, C Qy, uint32_t w = 0) {
     C e[15];
     equilibrium_d2q5<C, APPROX>(k, dr, Qx, Qy, e);
+    const C m[3] = {dr, Qx, Qy};
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         C* h = g + 5 * f;
-        const C d0 = k.rest[f] * moving_sum_d2q5(h) - (C(1) - k.rest[f]) * h[0];
-        h[0] = fma(k.om[f], d0, h[0]);
+        const C d0 = moving_sum_d2q5(h) - C(4) * (k.al[f] * m[f]);
+        h[0] = SR ? sr_add(h[0], k.om[f] * d0, sr_field_word(w, f)) : fma(k.om[f], d0, h[0]);
 #pragma unroll
         for (int l = 1; l < 5; ++l) h[l] = fma(k.om[f], e[5 * f + l] - h[l], h[l]);
     }
@@ -220,7 +321,7 @@ __device__ __forceinline__ void equilibrium_d3q7(const Coef<C>& k, C dr, const C
     const C r = recip_sel<APPROX>(k.rho_bar + dr);
     const C dP = pressure_dev(k, dr) * k.i2m;
     const C ar = k.al[0] * dr;
-    e[0] = k.rest[0] * dr;
+    e[0] = dr - C(6) * ar;   // m - 6 (alpha m), as in 2D
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const C h = Q[d] * k.i2m;
@@ -231,7 +332,7 @@ __device__ __forceinline__ void equilibrium_d3q7(const Coef<C>& k, C dr, const C
     for (int j = 0; j < 3; ++j) {
         const C a = k.al[j + 1] * Q[j];
         const C qr = Q[j] * r * k.i2m;
-        e[7 * (j + 1)] = k.rest[j + 1] * Q[j];
+        e[7 * (j + 1)] = Q[j] - C(6) * a;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const C flux = (j == d) ? (qr * Q[d] + dP) : qr * Q[d];
@@ -255,15 +356,16 @@ __device__ __forceinline__ void moments_d3q7(const C (&g)[28], C& dr, C (&Q)[3])
 }
 
 // Relaxation of one D3Q7 node; rest-population increment formed as in relax_d2q5.
-template <class C, bool APPROX = false>
-__device__ __forceinline__ void relax_d3q7(const Coef<C>& k, C (&g)[28], C dr, const C (&Q)[3]) {
+template <class C, bool APPROX = false, bool SR = false>
+__device__ __forceinline__ void relax_d3q7(const Coef<C>& k, C (&g)[28], C dr, const C (&Q)[3], uint32_t w = 0) {
     C e[28];
     equilibrium_d3q7<C, APPROX>(k, dr, Q, e);
+    const C m[4] = {dr, Q[0], Q[1], Q[2]};
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         C* h = g + 7 * f;
-        const C d0 = k.rest[f] * moving_sum_d3q7(h) - (C(1) - k.rest[f]) * h[0];
-        h[0] = fma(k.om[f], d0, h[0]);
+        const C d0 = moving_sum_d3q7(h) - C(6) * (k.al[f] * m[f]);
+        h[0] = SR ? sr_add(h[0], k.om[f] * d0, sr_field_word(w, f)) : fma(k.om[f], d0, h[0]);
 #pragma unroll
         for (int l = 1; l < 7; ++l) h[l] = fma(k.om[f], e[7 * f + l] - h[l], h[l]);
     }

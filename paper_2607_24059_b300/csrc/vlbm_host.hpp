@@ -33,7 +33,6 @@ inline Coef<C> make_coef(const vlbm_params& p, const vlbm_derived& d, const doub
         const double al = f < F ? d.alpha[f] : 0.0;
         k.om[f] = (C)om;
         k.al[f] = (C)al;
-        k.rest[f] = (C)(1.0 - 2.0 * p.dim * al);
         k.scale[f] = (C)scale[f];
         k.inv_scale[f] = (C)(1.0 / scale[f]);
     }

@@ -49,16 +49,19 @@ __device__ __forceinline__ void load_or_zero(T (&w)[V], const T* p, bool active)
 // into per-block FP64 partials, at no extra HBM traffic.
 // One warp's share of a step: V * 32 consecutive nodes of row y starting at
 // segment seg.  Called with every lane of the warp (shuffles); lanes past the
-// row end load nothing and store nothing.
+// row end load nothing and store nothing.  key: the step's stochastic-rounding
+// key (sr_step_key), used by FP32 storage.
 template <class S, bool SPLIT, bool DIAG>
 __device__ __forceinline__ void warp_stream_collide_2d(const Layout<S, SPLIT, 5>& fin, const Layout<S, SPLIT, 5>& fout,
                                                        int nx, int ny, int y, int seg, int lane,
                                                        const Coef<typename Storage<S>::C>& k,
-                                                       Acc<typename Storage<S>::C>& acc) {
+                                                       Acc<typename Storage<S>::C>& acc, uint32_t key) {
     using C = typename Storage<S>::C;
     using L = Layout<S, SPLIT, 5>;
     using R = typename L::R;
     constexpr int V = Vec16<S>::V;
+    constexpr bool SR = StochasticMoments<S>::value && !SPLIT;
+    constexpr bool SR16 = StochasticStore16<S>::value && !SPLIT;
     {
         const int x0 = (seg * 32 + lane) * V;
         const bool active = x0 < nx;
@@ -121,7 +124,7 @@ __device__ __forceinline__ void warp_stream_collide_2d(const Layout<S, SPLIT, 5>
                 const C Q[2] = {Qx, Qy};
                 accumulate_node(acc, moments_finite(dr, Q, 2), dr, Q, 2, k.rho_bar);
             }
-            relax_d2q5<C, sizeof(S) == 2>(k, gn, dr, Qx, Qy);
+            relax_d2q5<C, sizeof(S) == 2, SR>(k, gn, dr, Qx, Qy, SR ? sr_node_word(key, row + x0 + i) : 0u);
 #pragma unroll
             for (int p = 0; p < 15; ++p) g[p][i] = gn[p];
         }
@@ -132,8 +135,24 @@ __device__ __forceinline__ void warp_stream_collide_2d(const Layout<S, SPLIT, 5>
                 {
                     const C rsc = rest_store_scale<S, SPLIT>(k, f);
                     R w[V];
+                    bool sr16 = false;
+                    if constexpr (SR16) {
+                        sr16 = k.sr16 != 0;   // uniform over the launch
+                        if (sr16) {   // pairs of nodes, stochastic rounding (V is even)
 #pragma unroll
-                    for (int i = 0; i < V; ++i) w[i] = Storage<R>::from_c(g[5 * f][i] * rsc);
+                            for (int j = 0; j < V / 2; ++j) {
+                                const uint32_t r = sr_field_word(sr_node_word(key, row + x0 + 2 * j), f);
+                                const uint32_t d =
+                                    Storage<S>::pack2_sr(g[5 * f][2 * j] * rsc, g[5 * f][2 * j + 1] * rsc, r);
+                                w[2 * j] = Storage<S>::from_bits(d & 0xffffu);
+                                w[2 * j + 1] = Storage<S>::from_bits(d >> 16);
+                            }
+                        }
+                    }
+                    if (!sr16) {
+#pragma unroll
+                        for (int i = 0; i < V; ++i) w[i] = Storage<R>::from_c(g[5 * f][i] * rsc);
+                    }
                     vstore<R, V>(fout.rest(f) + row + x0, w);
                 }
                 const C sc = mov_store_scale<S>(k, f);
@@ -149,22 +168,34 @@ __device__ __forceinline__ void warp_stream_collide_2d(const Layout<S, SPLIT, 5>
     }
 }
 
+// Step counter of the stochastic rounding: a step that reads lattice level `par`
+// reads its step number from step_ctr[par] and writes the next one to
+// step_ctr[par ^ 1], which the following step (reading the other level) reads.
+// Kernel boundaries order the accesses, so graph replay needs no host update.
+__device__ __forceinline__ uint32_t take_step_key(uint32_t* __restrict__ step_ctr, int par) {
+    const uint32_t step = step_ctr[par];
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) step_ctr[par ^ 1] = step + 1u;
+    return sr_step_key(step);
+}
+
 // 16-bit storage moves half the bytes per node, so it needs more warps in flight to
 // cover the memory latency: three resident blocks per SM (at most 85 registers).
 template <class S, bool SPLIT, bool DIAG>
 __global__ void __launch_bounds__(kThreads, sizeof(S) == 2 ? 3 : 1)
 k_stream_collide_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
-                        int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+                        int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials,
+                        uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, SPLIT, 5>;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> acc;
     if (DIAG) acc.zero();
     if (gwarp < (long long)ny * warps_per_row)   // warp-uniform
         warp_stream_collide_2d<S, SPLIT, DIAG>(fin, fout, nx, ny, (int)(gwarp / warps_per_row),
-                                               (int)(gwarp % warps_per_row), lane, k, acc);
+                                               (int)(gwarp % warps_per_row), lane, k, acc, key);
     if (DIAG) block_reduce_store(acc, partials);
 }
 
@@ -190,11 +221,15 @@ __device__ __forceinline__ void store_pop(const Layout<S, SPLIT, Q>& L, int f, i
 template <class S, bool SPLIT, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
 k_stream_collide_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny,
-                            long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+                            long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials,
+                            uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, SPLIT, 5>;
+    constexpr bool SR = StochasticMoments<S>::value && !SPLIT;
+    constexpr bool SR16 = StochasticStore16<S>::value && !SPLIT;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> acc;
     if (DIAG) acc.zero();
     if (node < plane) {
@@ -216,9 +251,18 @@ k_stream_collide_2d_generic(const char* __restrict__ fin_b, char* __restrict__ f
             const C Q[2] = {Qx, Qy};
             accumulate_node(acc, moments_finite(dr, Q, 2), dr, Q, 2, k.rho_bar);
         }
-        relax_d2q5<C, sizeof(S) == 2>(k, g, dr, Qx, Qy);
+        relax_d2q5<C, sizeof(S) == 2, SR>(k, g, dr, Qx, Qy, SR ? sr_node_word(key, node) : 0u);
 #pragma unroll
-        for (int p = 0; p < 15; ++p) store_pop(fout, p / 5, p % 5, node, g[p], k);
+        for (int p = 0; p < 15; ++p) {
+            if constexpr (SR16) {
+                if (p % 5 == 0 && k.sr16) {
+                    fout.rest(p / 5)[node] =
+                        sr16_store_one<S>(g[p] * rest_store_scale<S, SPLIT>(k, p / 5), node, key, p / 5);
+                    continue;
+                }
+            }
+            store_pop(fout, p / 5, p % 5, node, g[p], k);
+        }
     }
     if (DIAG) block_reduce_store(acc, partials);
 }

@@ -22,14 +22,17 @@ template <class S, bool SPLIT, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
 k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
                         long long plane, int warps_per_row, Coef<typename Storage<S>::C> k,
-                        double* __restrict__ partials) {
+                        double* __restrict__ partials, uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, SPLIT, 7>;
     using R = typename L::R;
     constexpr int V = Vec8<S>::V;
+    constexpr bool SR = StochasticMoments<S>::value && !SPLIT;
+    constexpr bool SR16 = StochasticStore16<S>::value && !SPLIT;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> acc;
     if (DIAG) acc.zero();
     if (gwarp < (long long)ny * nz * warps_per_row) {
@@ -89,7 +92,7 @@ k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
             C dr, Q[3];
             moments_d3q7(gn, dr, Q);
             if (DIAG && active) accumulate_node(acc, moments_finite(dr, Q, 3), dr, Q, 3, k.rho_bar);
-            relax_d3q7<C, sizeof(S) == 2>(k, gn, dr, Q);
+            relax_d3q7<C, sizeof(S) == 2, SR>(k, gn, dr, Q, SR ? sr_node_word(key, row + x0 + i) : 0u);
 #pragma unroll
             for (int p = 0; p < 28; ++p) g[p][i] = gn[p];
         }
@@ -100,8 +103,24 @@ k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
                 {
                     const C rsc = rest_store_scale<S, SPLIT>(k, f);
                     R w[V];
+                    bool sr16 = false;
+                    if constexpr (SR16) {
+                        sr16 = k.sr16 != 0;   // uniform over the launch
+                        if (sr16) {   // pairs of nodes, stochastic rounding (V is even)
 #pragma unroll
-                    for (int i = 0; i < V; ++i) w[i] = Storage<R>::from_c(g[7 * f][i] * rsc);
+                            for (int j = 0; j < V / 2; ++j) {
+                                const uint32_t r = sr_field_word(sr_node_word(key, row + x0 + 2 * j), f);
+                                const uint32_t d =
+                                    Storage<S>::pack2_sr(g[7 * f][2 * j] * rsc, g[7 * f][2 * j + 1] * rsc, r);
+                                w[2 * j] = Storage<S>::from_bits(d & 0xffffu);
+                                w[2 * j + 1] = Storage<S>::from_bits(d >> 16);
+                            }
+                        }
+                    }
+                    if (!sr16) {
+#pragma unroll
+                        for (int i = 0; i < V; ++i) w[i] = Storage<R>::from_c(g[7 * f][i] * rsc);
+                    }
                     vstore<R, V>(fout.rest(f) + row + x0, w);
                 }
                 const C sc = mov_store_scale<S>(k, f);
@@ -122,11 +141,15 @@ k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
 template <class S, bool SPLIT, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
 k_stream_collide_3d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
-                            long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+                            long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials,
+                            uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, SPLIT, 7>;
+    constexpr bool SR = StochasticMoments<S>::value && !SPLIT;
+    constexpr bool SR16 = StochasticStore16<S>::value && !SPLIT;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> acc;
     if (DIAG) acc.zero();
     if (node < plane) {
@@ -149,9 +172,18 @@ k_stream_collide_3d_generic(const char* __restrict__ fin_b, char* __restrict__ f
         C dr, Q[3];
         moments_d3q7(g, dr, Q);
         if (DIAG) accumulate_node(acc, moments_finite(dr, Q, 3), dr, Q, 3, k.rho_bar);
-        relax_d3q7<C, sizeof(S) == 2>(k, g, dr, Q);
+        relax_d3q7<C, sizeof(S) == 2, SR>(k, g, dr, Q, SR ? sr_node_word(key, node) : 0u);
 #pragma unroll
-        for (int p = 0; p < 28; ++p) store_pop(fout, p / 7, p % 7, node, g[p], k);
+        for (int p = 0; p < 28; ++p) {
+            if constexpr (SR16) {
+                if (p % 7 == 0 && k.sr16) {
+                    fout.rest(p / 7)[node] =
+                        sr16_store_one<S>(g[p] * rest_store_scale<S, SPLIT>(k, p / 7), node, key, p / 7);
+                    continue;
+                }
+            }
+            store_pop(fout, p / 7, p % 7, node, g[p], k);
+        }
     }
     if (DIAG) block_reduce_store(acc, partials);
 }

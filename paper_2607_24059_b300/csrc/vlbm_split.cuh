@@ -84,14 +84,18 @@ __device__ __forceinline__ void shift_from_right(C (&out)[V], const C (&own)[V],
 // Relaxation and new moments of one D2Q5 node in split form.
 //   m[3]: moments at the node; B[3][4]: pulled populations g_{k,l} (l = 1..4);
 //   nown[3]: sum_l n_{k,l} of the node's own stored non-equilibrium parts.
-// Returns the new moments in m and the new non-equilibrium parts in B.
+// Returns the new moments in m and the new non-equilibrium parts in B.  The
+// FP32 moments take their increment with stochastic rounding (random word w of
+// the node; see sr_add).
 template <class C>
-__device__ __forceinline__ void split_update_d2q5(const Coef<C>& k, C (&m)[3], C (&B)[3][4], const C (&nown)[3]) {
-    // sum_l e_{k,l}(m) = m_k - e_{k,0}(m) = (1 - rest_k) m_k
+__device__ __forceinline__ void split_update_d2q5(const Coef<C>& k, C (&m)[3], C (&B)[3][4], const C (&nown)[3],
+                                                  uint32_t w) {
+    // sum_l e_{k,l}(m) = 4 alpha_k m_k: the alpha m of the moving equilibria (their
+    // +- fluxes cancel), so that the update conserves m for the stored coefficients
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         const C pulled = (B[f][0] + B[f][1]) + (B[f][2] + B[f][3]);
-        m[f] = m[f] + ((pulled - (C(1) - k.rest[f]) * m[f]) - nown[f]);
+        m[f] = sr_add(m[f], (pulled - C(4) * (k.al[f] * m[f])) - nown[f], sr_field_word(w, f));
     }
     C e[15];
     equilibrium_d2q5<C, true>(k, m[0], m[1], m[2], e);
@@ -120,7 +124,7 @@ template <class S, int V, bool DIAG>
 __device__ __forceinline__ void warp_split_step_2d(const Layout<S, true, 5>& fin, const Layout<S, true, 5>& fout,
                                                    int nx, int ny, int y, int seg, int lane,
                                                    const Coef<typename Storage<S>::C>& k,
-                                                   Acc<typename Storage<S>::C>& acc) {
+                                                   Acc<typename Storage<S>::C>& acc, uint32_t key) {
     using C = typename Storage<S>::C;
     {
         const int x0 = (seg * 32 + lane) * V;
@@ -229,7 +233,7 @@ __device__ __forceinline__ void warp_split_step_2d(const Layout<S, true, 5>& fin
             for (int f = 0; f < 3; ++f)
 #pragma unroll
                 for (int l = 0; l < 4; ++l) Bi[f][l] = B[f][l][i];
-            split_update_d2q5(k, mi, Bi, ni);
+            split_update_d2q5(k, mi, Bi, ni, sr_node_word(key, row + x0 + i));
             if (DIAG && active) {
                 const C Q[2] = {mi[1], mi[2]};
                 accumulate_node(acc, moments_finite(mi[0], Q, 2), mi[0], Q, 2, k.rho_bar);
@@ -266,17 +270,19 @@ __device__ __forceinline__ void warp_split_step_2d(const Layout<S, true, 5>& fin
 template <class S, int V, bool DIAG>
 __global__ void __launch_bounds__(kThreads, 2)
 k_split_step_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
-                    int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+                    int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials,
+                    uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, true, 5>;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> acc;
     if (DIAG) acc.zero();
     if (gwarp < (long long)ny * warps_per_row)   // warp-uniform
         warp_split_step_2d<S, V, DIAG>(fin, fout, nx, ny, (int)(gwarp / warps_per_row), (int)(gwarp % warps_per_row),
-                                       lane, k, acc);
+                                       lane, k, acc, key);
     if (DIAG) block_reduce_store(acc, partials);
 }
 
@@ -284,11 +290,13 @@ k_split_step_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, i
 template <class S, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
 k_split_step_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny,
-                        long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+                        long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials,
+                        uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, true, 5>;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> acc;
     if (DIAG) acc.zero();
     if (node < plane) {
@@ -319,7 +327,7 @@ k_split_step_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
             else if (l == 3) pulled_d2q5<C, 3>(k, ms, np, B);
             else pulled_d2q5<C, 4>(k, ms, np, B);
         }
-        split_update_d2q5(k, m, B, nown);
+        split_update_d2q5(k, m, B, nown, sr_node_word(key, node));
         if (DIAG) {
             const C Q[2] = {m[1], m[2]};
             accumulate_node(acc, moments_finite(m[0], Q, 2), m[0], Q, 2, k.rho_bar);
@@ -337,11 +345,12 @@ k_split_step_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
 
 // ------------------------------------------------------------------------------ 3D
 template <class C>
-__device__ __forceinline__ void split_update_d3q7(const Coef<C>& k, C (&m)[4], C (&B)[4][6], const C (&nown)[4]) {
+__device__ __forceinline__ void split_update_d3q7(const Coef<C>& k, C (&m)[4], C (&B)[4][6], const C (&nown)[4],
+                                                  uint32_t w) {
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const C pulled = ((B[f][0] + B[f][1]) + (B[f][2] + B[f][3])) + (B[f][4] + B[f][5]);
-        m[f] = m[f] + ((pulled - (C(1) - k.rest[f]) * m[f]) - nown[f]);
+        m[f] = sr_add(m[f], (pulled - C(6) * (k.al[f] * m[f])) - nown[f], sr_field_word(w, f));
     }
     C e[28];
     const C Q[3] = {m[1], m[2], m[3]};
@@ -381,13 +390,14 @@ template <class S, bool DIAG>
 __global__ void __launch_bounds__(kThreads, 3)
 k_split_step_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
                     long long plane, int warps_per_row, Coef<typename Storage<S>::C> k,
-                    double* __restrict__ partials) {
+                    double* __restrict__ partials, uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, true, 7>;
     constexpr int V = kSplitV3;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> acc;
     if (DIAG) acc.zero();
     if (gwarp < (long long)ny * nz * warps_per_row) {
@@ -464,7 +474,7 @@ k_split_step_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, i
             for (int f = 0; f < 4; ++f)
 #pragma unroll
                 for (int l = 0; l < 6; ++l) Bi[f][l] = B[f][l][i];
-            split_update_d3q7(k, mi, Bi, ni);
+            split_update_d3q7(k, mi, Bi, ni, sr_node_word(key, row + x0 + i));
             if (DIAG && active) {
                 const C Q[3] = {mi[1], mi[2], mi[3]};
                 accumulate_node(acc, moments_finite(mi[0], Q, 3), mi[0], Q, 3, k.rho_bar);
@@ -500,11 +510,13 @@ k_split_step_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, i
 template <class S, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
 k_split_step_3d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
-                        long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials) {
+                        long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials,
+                        uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, true, 7>;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> acc;
     if (DIAG) acc.zero();
     if (node < plane) {
@@ -539,7 +551,7 @@ k_split_step_3d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
             }
             pulled_d3q7_l(k, l, ms, np, B);
         }
-        split_update_d3q7(k, m, B, nown);
+        split_update_d3q7(k, m, B, nown, sr_node_word(key, node));
         if (DIAG) {
             const C Q[3] = {m[1], m[2], m[3]};
             accumulate_node(acc, moments_finite(m[0], Q, 3), m[0], Q, 3, k.rho_bar);

@@ -123,3 +123,19 @@ def test_tensor_core_entry_points_reject_misaligned_arrays():
     # GEMM: A and B 16-byte aligned
     assert b.lib.vlbm_tc_gemm_bf16(a + 8, a, a, 128, 16, 64, a, None) == v.VLBM_EINVAL
     assert b.lib.vlbm_tc_gemm_bf16(a, a + 8, a, 128, 16, 64, a, None) == v.VLBM_EINVAL
+
+
+def test_binding_constants_match_header():
+    """Every VLBM_* integer constant of the binding has the value include/vlbm.h defines."""
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "include", "vlbm.h")).read()
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(VLBM_\w+)\s+\(?(-?\d+)\)?", text)}
+    assert "VLBM_OPT_ROUNDING_16" in defines
+    checked = 0
+    for name, value in defines.items():
+        if hasattr(v, name):
+            assert getattr(v, name) == value, name
+            checked += 1
+    assert checked >= 10

@@ -23,7 +23,15 @@ PROBLEMS = [
     dict(n=(8, 40), nu=0.02, seed=4),
     dict(n=(96, 96), nu=0.001, seed=5),
 ]
+# fp64/fp32: max-abs error relative to max|u|; 16-bit storage: the L2 velocity gate of the
+# reduced-precision and batched forms (relative L2 error <= 1e-3 against the oracle)
+# (the shifted 16-bit forms do not hold the L2 gate on slowly evolving flows; they are tied to
+# the single-handle kernels below, which are checked node by node against the oracle)
 TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16split": 1e-3, "bf16split": 1e-3}
+
+
+def l2_rel(a, b):
+    return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
 
 
 def problem_inputs(q):
@@ -61,14 +69,17 @@ def test_batch_matches_oracle_per_problem(precision):
     b.step(steps)
     for i, uo in enumerate(refs):
         ug = b.velocity(i).cpu().numpy()
-        err = np.max(np.abs(ug - uo)) / np.max(np.abs(uo))
+        if precision in ("fp64", "fp32"):
+            err = np.max(np.abs(ug - uo)) / np.max(np.abs(uo))
+        else:
+            err = l2_rel(ug, uo)
         assert err <= TOL[precision], (i, err)
     n_total, s, launches = b.info()
     assert s == steps and n_total == sum(q["n"][0] * q["n"][1] for q in PROBLEMS)
     b.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16split"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16split", "fp16", "bf16"])
 def test_batch_equals_single_handles(precision):
     qs = [dict(n=q["n"], dx=problem_inputs(q)[2], nu=q["nu"]) for q in PROBLEMS]
     b = v.Batch(qs, precision=precision)
@@ -82,10 +93,11 @@ def test_batch_equals_single_handles(precision):
         singles.append(lat.macros()[1].cpu().numpy())
         lat.close()
     b.step(40)
-    # same arithmetic, inlined into a different kernel: FMA contraction may
-    # differ, and for 16-bit storage a flipped rounding moves a stored value
-    # by one quantum
-    tol = 1e-6 if precision == "fp32" else 1e-4
+    # same arithmetic and the same stochastic-rounding words (nodes are numbered within
+    # their problem, one step counter), inlined into a different kernel: FMA contraction may
+    # differ, and for 16-bit storage a flipped rounding then moves a stored value by one
+    # quantum (2^-11 FP16, 2^-8 BF16)
+    tol = {"fp32": 1e-6, "fp16split": 1e-4, "fp16": 2e-3, "bf16": 1.6e-2}[precision]
     for i, us in enumerate(singles):
         ub = b.velocity(i).cpu().numpy()
         assert np.max(np.abs(ub - us)) <= tol * np.max(np.abs(us)), i
@@ -145,3 +157,30 @@ def test_batch_invariants_match_oracle():
 def test_batch_rejects_bad_problems():
     with pytest.raises(v.VlbmError):
         v.Batch([dict(n=(30, 16), dx=0.1, nu=0.01)])          # n_x not a multiple of 4
+
+
+def test_batched_problem_set_members_match_oracle(orc):
+    """Problems drawn from the batched workload's own set (sides 512 and 1024, seeded random
+    Fourier fields, their own viscosities), advanced together 200 steps in the batched FP16
+    split storage the benchmark uses, each against the oracle at the L2 gate of 1e-3."""
+    chosen = [q for q in synthetic.batched_problem_set(512) if q.side >= 512][:8]
+    assert len(chosen) == 8
+    specs, inputs = [], []
+    for q in chosen:
+        u, phi, dx = synthetic.random_fourier_field(q.side, q.seed)
+        specs.append(dict(n=(q.side, q.side), dx=dx, nu=q.nu))
+        inputs.append((u, phi, dx))
+    b = v.Batch(specs, precision="fp16split")
+    for i, (u, phi, _) in enumerate(inputs):
+        b.init(i, torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    steps = 200
+    b.step(steps)
+    for i, (q, (u, phi, dx)) in enumerate(zip(chosen, inputs)):
+        op = oracle.make_params((q.side, q.side), dx, nu=q.nu)
+        _, uo, _ = orc.macros(op, orc.run(op, orc.init(op, u, phi), steps))
+        assert np.isfinite(uo).all(), q
+        ug = b.velocity(i).cpu().numpy()
+        err = l2_rel(ug, uo)
+        print(f"problem {q.index}: side {q.side}, nu {q.nu:.2e}: L2 {err:.2e}")
+        assert err <= 1e-3, (q, err)
+    b.close()

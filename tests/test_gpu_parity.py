@@ -4,8 +4,12 @@ Tolerances:
   FP64 storage: 1e-12 of max|u| (the CUDA path works on deviations from the rest
     equilibrium, the oracle on raw populations: rounding orders differ, the
     difference stays at a few hundred ulps after 1000 steps).
-  FP32 storage: 1e-5 of max|u| after 1000 steps of the 64^2 Taylor-Green vortex
-    (the gate the FP32 form must meet against FP64).
+  FP32 storage: 1e-5 of max|u| after 1000 steps, on the 64^2 Taylor-Green vortex
+    against the oracle and on the 4096^2 double shear layer (the benchmark lattice)
+    against FP64 storage, which is itself tied to the oracle at that size.  FP32
+    storage rounds the populations that carry the conserved moments
+    stochastically (unbiased), without which the per-step increments below half
+    an ulp are lost systematically and the error grows linearly with the steps.
 Inputs are seeded and synthetic (synthetic/), shared by both sides; no expected
 value comes from the CUDA path.
 """
@@ -116,15 +120,23 @@ def test_vector_and_generic_kernels_bitwise(n, precision):
     op = resolved(n, 0.05, nu=0.02)
     a = gpu_run(op, precision, u, phi, 77, variant=1)
     b = gpu_run(op, precision, u, phi, 77, variant=2)
-    for x, y in zip(a, b):
-        if precision.endswith("split"):
-            # the split kernels inline the same arithmetic into different code, where
-            # the compiler may contract a different multiply-add pair into an FMA:
-            # FP32 rounding differences, compared on the velocity and density
-            # (a flipped FP32 rounding can move a BF16 value by one quantum, 2^-8)
-            rel = 1e-5 if precision.startswith("fp16") else 1e-3
-            assert np.max(np.abs(x - y)) <= rel * max(np.max(np.abs(y)), 1e-30) or x.shape == a[2].shape
-        else:
+    if precision.endswith("split"):
+        # the split kernels inline the same arithmetic into different code, where
+        # the compiler may contract a different multiply-add pair into an FMA:
+        # FP32 rounding differences that occasionally flip the rounding of a 16-bit
+        # non-equilibrium part by one quantum (2^-11 FP16, 2^-8 BF16).  The velocity
+        # sees that quantum times n/m (the part against the moment it feeds); the
+        # density deviation rho - rho_bar (phi's signal, O(dx^2)) sees the rho-field
+        # parts, which carry differences of the mass flux q/(2 mu) and can be 0.1 of
+        # rho - rho_bar: one flip then moves it by ~2^-11 / 10.  u, rho - rho_bar and phi
+        # are each compared against their own maximum.
+        rel_u = 1e-5 if precision.startswith("fp16") else 1e-3
+        rel_rho = 1e-3 if precision.startswith("fp16") else 1e-2
+        (rho_a, u_a, phi_a), (rho_b, u_b, phi_b) = a, b
+        for x, y, rel in ((rho_a - 1.0, rho_b - 1.0, rel_rho), (u_a, u_b, rel_u), (phi_a, phi_b, rel_rho)):
+            assert np.max(np.abs(x - y)) <= rel * np.max(np.abs(y))
+    else:
+        for x, y in zip(a, b):
             assert np.array_equal(x, y)
 
 
@@ -339,13 +351,14 @@ def l2_rel(a, b):
     return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
 
 
-# Gates: the split layouts (FP32 moments, 16-bit non-equilibrium parts) must
-# hold L2 <= 1e-3 of the velocity against the oracle.  The pure 16-bit layouts
-# lose every per-step change smaller than half an ulp of the stored value (about
-# 2.4e-4 relative for FP16, 2e-3 for BF16): a slowly evolving flow stops
-# evolving, so their error is bounded by the change the flow makes over the run
-# (2.4 % for 1000 steps of this Taylor-Green vortex); stated here as 5e-2.
-@pytest.mark.parametrize("precision,gate", [("fp16split", 1e-3), ("bf16split", 1e-3), ("fp16", 5e-2), ("bf16", 5e-2)])
+# Gate: the split layouts (FP32 moments, 16-bit non-equilibrium parts) hold L2 <= 1e-3 of
+# the velocity against the oracle.  The shifted layouts (every population 16-bit) do not
+# on these slowly evolving flows: under the parabolic scaling a moment changes per step by
+# far less than a 16-bit quantum; round-to-nearest drops the change (the flow stops), and
+# unbiased stochastic rounding (which they use) turns it into noise whose accumulated RMS
+# exceeds 1e-3 within a few hundred steps.  They are checked below one step at a time
+# (node by node, within one stored quantum) and on the benchmark lattice over 1000 steps.
+@pytest.mark.parametrize("precision,gate", [("fp16split", 1e-3), ("bf16split", 1e-3)])
 def test_reduced_precision_tgv_64_1000_steps(orc, precision, gate):
     n = 64
     u, phi, dx = synthetic.taylor_green_2d(n)
@@ -357,7 +370,7 @@ def test_reduced_precision_tgv_64_1000_steps(orc, precision, gate):
     assert err <= gate, err
 
 
-@pytest.mark.parametrize("precision,gate", [("fp16split", 1e-3), ("bf16split", 1e-3), ("fp16", 5e-2), ("bf16", 5e-2)])
+@pytest.mark.parametrize("precision,gate", [("fp16split", 1e-3), ("bf16split", 1e-3)])
 def test_reduced_precision_shear_layer_256(orc, precision, gate):
     n = 256
     u, phi, dx = synthetic.double_shear_layer(n)
@@ -370,14 +383,75 @@ def test_reduced_precision_shear_layer_256(orc, precision, gate):
 
 
 @pytest.mark.parametrize("n", [(37, 53), (136, 10), (1, 9)])
-@pytest.mark.parametrize("precision", ["fp16split", "bf16split", "fp16", "bf16"])
+@pytest.mark.parametrize("precision", ["fp16split", "bf16split"])
 def test_reduced_precision_ragged(orc, n, precision):
     u, phi = smooth_random_state(n, seed=n[0] + 7 * n[1])
     op = resolved(n, 0.05, nu=0.02, omega_rho=1.3, omega_q=1.1)
     (_, u_o, _), _ = orc_run(orc, op, u, phi, 60)
     _, u_g, _ = gpu_run(op, precision, u, phi, 60)
-    tol = 1e-4 if precision.endswith("split") else (5e-2 if precision == "fp16" else 2e-1)
-    assert np.max(np.abs(u_g - u_o)) <= tol * max(np.max(np.abs(u_o)), 1e-3)
+    assert np.max(np.abs(u_g - u_o)) <= 1e-4 * max(np.max(np.abs(u_o)), 1e-3)
+
+
+def quantum_bound(x, mant_bits, min_spacing):
+    """Largest spacing of the 16-bit format (mant_bits explicit mantissa bits) around |x|:
+    2^(ceil(log2|x|) - mant_bits), at least the subnormal spacing."""
+    ax = np.abs(x)
+    e = np.ceil(np.log2(np.where(ax > 0, ax, 1.0)))
+    return np.maximum(np.where(ax > 0, 2.0 ** (e - mant_bits), 0.0), min_spacing)
+
+
+@pytest.mark.parametrize("n", [(64, 48), (37, 53), (136, 10), (1, 9)])
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+@pytest.mark.parametrize("rounding", [0, 1])
+def test_shifted_storage_one_step_node_by_node(orc, n, precision, rounding):
+    """Shifted 16-bit storage, one step checked node by node after 50 steps of evolution: the
+    populations pulled from the exported state are relaxed by the oracle, and every stored
+    population of the next state must lie within one quantum of the 16-bit format (at the
+    field's storage scale) of that value, plus FP32 arithmetic slack.  (Stochastic rounding
+    picks one of the two neighbours of the exact value, so it is always within one quantum.)
+    rounding: VLBM_OPT_ROUNDING_16, 0 to nearest, 1 stochastic."""
+    u, phi = smooth_random_state(n, seed=3 * n[0] + n[1])
+    op = resolved(n, 0.05, nu=0.02, omega_rho=1.3, omega_q=1.1)
+    lat = gpu_lattice(op, precision)
+    lat.set_option(v.VLBM_OPT_ROUNDING_16, rounding)
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    lat.step(50)
+    g0 = lat.populations(deviation=True).cpu().numpy()      # (3, 5, ny, nx), exact dequantised values
+    lat.step(1)
+    g1 = lat.populations(deviation=True).cpu().numpy()
+    lat.close()
+    nx, ny = n
+    fbar = orc.init(oracle.Params(n=(1, 1), dx=op.dx, mu=op.mu, omega=op.omega, alpha=op.alpha),
+                    np.zeros((2, 1, 1)), np.zeros((1, 1)))[..., 0, 0]
+    ys, xs = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    ys, xs = ys.ravel(), xs.ravel()
+    src = [(xs, ys), ((xs - 1) % nx, ys), ((xs + 1) % nx, ys), (xs, (ys - 1) % ny), (xs, (ys + 1) % ny)]
+    pulled = np.empty((xs.size, 3, 5))
+    for l, (sx, sy) in enumerate(src):
+        pulled[:, :, l] = g0[:, l, sy, sx].T
+    fstar = orc.collide_nodes(op, pulled + fbar[None]) - fbar[None]
+    got = g1[:, :, ys, xs].transpose(2, 0, 1)
+    mant, smin = (10, 2.0 ** -24) if precision == "fp16" else (7, 2.0 ** -133)
+    scale = np.array([1.0 / op.dx ** 2, 1.0 / op.dx, 1.0 / op.dx])[None, :, None]   # storage scales
+    bound = quantum_bound(fstar * scale, mant, smin) / scale
+    for k in range(3):
+        slack = 1e-6 * np.max(np.abs(fstar[:, k, :]))        # FP32 collision arithmetic
+        assert np.all(np.abs(got[:, k, :] - fstar[:, k, :]) <= bound[:, k, :] + slack), k
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "fp16split", "bf16split"])
+def test_reduced_precision_benchmark_lattice_1000_steps(precision):
+    """The benchmark lattice (4096^2 double shear layer, nu = 1e-4) in every 16-bit storage form
+    against FP64 storage (tied to the oracle by test_full_size_4096_fp32_1000_steps_against_fp64)
+    after 1000 steps: L2 velocity error <= 1e-3."""
+    n = 4096
+    u, phi, dx = synthetic.double_shear_layer(n)
+    op = resolved((n, n), dx, nu=1e-4)
+    _, u64, _ = gpu_run(op, "fp64", u, phi, 1000)
+    _, u16, _ = gpu_run(op, precision, u, phi, 1000)
+    err = l2_rel(u16, u64)
+    print(f"4096^2 shear layer, 1000 steps, {precision}: L2 {err:.3e} against FP64 storage")
+    assert err <= 1e-3, err
 
 
 # ------------------------------------------------------------ D3Q7
@@ -436,6 +510,37 @@ def test_full_size_4096_sampled_step_and_conservation(orc):
     assert abs(inv1[7] - inv0[7]) <= 1e-5 * n * n * dx * dx
     assert inv1[6] == 0.0
     lat.close()
+
+
+def test_full_size_4096_fp32_1000_steps_against_fp64(orc):
+    """The benchmark lattice over the parity horizon: 4096^2 double shear layer, nu = 1e-4,
+    FP32 storage in the vectorised launch the benchmark times, 1000 steps, against FP64
+    storage element by element (max-abs error <= 1e-5 of max|u|).  FP64 storage is tied to
+    the oracle on the same lattice (20 steps) and over the same horizon on 1024^2."""
+    n = 4096
+    u, phi, dx = synthetic.double_shear_layer(n)
+    op = resolved((n, n), dx, nu=1e-4)
+    (_, u_o, _), _ = orc_run(orc, op, u, phi, 20)
+    _, u64, _ = gpu_run(op, "fp64", u, phi, 20)
+    assert rel_err(u64, u_o) <= 1e-12
+    del u_o
+    _, u64, _ = gpu_run(op, "fp64", u, phi, 1000)
+    _, u32, _ = gpu_run(op, "fp32", u, phi, 1000, variant=2)
+    err = rel_err(u32, u64)
+    print(f"4096^2 shear layer, 1000 steps: FP32 vs FP64 storage max-abs {err:.3e} of max|u|")
+    assert err <= 1e-5, err
+    del u64, u32
+    # Over 1000 steps the oracle's own rounding sets the bound: it keeps the raw populations,
+    # whose momentum parts carry the constant +-P(rho_bar)/(2 mu) = +-1/16, so each of the five
+    # populations of a momentum field is rounded to within 2^-57 every step, up to
+    # steps * 5 * 2^-57 of dx q per node (the GPU path keeps deviations and is far more precise).
+    m, steps = 1024, 1000
+    u, phi, dx = synthetic.double_shear_layer(m)
+    op = resolved((m, m), dx, nu=1e-4)
+    (_, u_o, _), _ = orc_run(orc, op, u, phi, steps)
+    _, u64, _ = gpu_run(op, "fp64", u, phi, steps)
+    bound = steps * 5 * 2.0 ** -57 / (dx * np.max(np.abs(u_o)))
+    assert rel_err(u64, u_o) <= max(1e-12, bound), (rel_err(u64, u_o), bound)
 
 
 # ------------------------------------------------------------ 3D energy history (fused records)
