@@ -8,6 +8,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import paper_2607_24059_b300 as v  # noqa: E402
+import math  # noqa: E402
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 64, 64), (256, 16, 128), (384, 128, 576), (128, 256, 64), (128, 48, 192)])
@@ -124,6 +125,109 @@ def laplacian(u):
     return u.roll(1, 2) + u.roll(-1, 2) + u.roll(1, 3) + u.roll(-1, 3) - 4 * u
 
 
+# ------------------------------------------------------------ element-wise gradient check
+#
+# The kernels round to BF16 at fixed points: the input, every activation and pre-activation
+# (forward), the loss gradient, every data gradient and every GELU-backward product
+# (backward); the weight gradients accumulate exact BF16 products in FP32.  The reference
+# below rounds at the same points (FP32 torch arithmetic in between), so kernel and reference
+# differ only by FP32 accumulation order and the hardware tanh of the GELU, which now and then
+# flip one BF16 rounding by one unit (at most 2u relative, u = 2^-8).  Treating each term
+# dZ[p] X[p + tap] of a weight gradient as perturbed independently by at most 4u of itself
+# (a flip in either factor), the error of G has a standard deviation of at most 4u S with
+# S = sqrt(sum_p (dZ[p] X[p + tap])^2); the check allows 6 of those (24u S) plus 1e-5 of the
+# absolute sum for FP32 accumulation.  A wrong tap, channel or sign changes an element by
+# the order of |G| itself.
+BF16_U = 2.0 ** -8
+
+
+def bf16(t):
+    return t.to(torch.bfloat16).float()
+
+
+def conv_periodic_nchw(x, Wt):
+    """x (B, cin, H, W), Wt (cout, 9, cin) -> (B, cout, H, W), periodic 3x3 conv, FP32."""
+    import torch.nn.functional as F
+    cout, _, cin = Wt.shape
+    return F.conv2d(F.pad(x, (1, 1, 1, 1), mode="circular"), Wt.reshape(cout, 3, 3, cin).permute(0, 3, 1, 2))
+
+
+def gelu_tanh_grad(z):
+    k, a = math.sqrt(2.0 / math.pi), 0.044715
+    t = torch.tanh(k * (z + a * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * k * (1.0 + 3.0 * a * z * z)
+
+
+def wgrad_fp64(X, dZ):
+    """G[co][tap][ci] = sum_p dZ[p][co] X[p + tap][ci] in FP64 (X, dZ as NCHW)."""
+    G = torch.empty(dZ.shape[1], 9, X.shape[1], dtype=torch.float64, device=X.device)
+    for tap in range(9):
+        dy, dx = tap // 3 - 1, tap % 3 - 1
+        xs = torch.roll(X, shifts=(-dy, -dx), dims=(2, 3)).double()
+        G[:, tap, :] = torch.einsum("bohw,bihw->oi", dZ.double(), xs)
+    return G
+
+
+def replicated_gradients(params, u, target, channels, curl=False):
+    """Per layer (G, Gb, bound_G, bound_Gb) with the kernels' BF16 rounding points, and the loss."""
+    import torch.nn.functional as F
+    B, C, H, W = u.shape
+    layers = v.Surrogate.split_params(params)
+    X = torch.zeros(B, 16, H, W, device=u.device)
+    X[:, :C] = u
+    X = bf16(X)
+    xs, zb = [], []
+    for l, (Wl, bl) in enumerate(layers):
+        xs.append(X)
+        z = conv_periodic_nchw(X, bf16(Wl)) + bl.view(1, -1, 1, 1)
+        if l < len(layers) - 1:
+            zb.append(bf16(z))
+            X = bf16(F.gelu(z, approximate="tanh"))
+        else:
+            Y = bf16(z)
+    npix = B * H * W
+    inv = 1.0 / (C * npix)
+    dY = torch.zeros_like(Y)
+    if curl:
+        psi = Y[:, 0]
+        ddy = 0.5 * (psi.roll(-1, 1) - psi.roll(1, 1))
+        ddx = 0.5 * (psi.roll(-1, 2) - psi.roll(1, 2))
+        rx, ry = ddy - target[:, 0], -ddx - target[:, 1]
+        rc = Y[:, 2:C] - target[:, 2:C]
+        loss = float(((rx.double() ** 2).sum() + (ry.double() ** 2).sum() + (rc.double() ** 2).sum()) * inv)
+        g = rx.roll(1, 1) - rx.roll(-1, 1) + ry.roll(-1, 2) - ry.roll(1, 2)
+        dY[:, 0] = bf16(g * inv)
+        dY[:, 2:C] = bf16(2.0 * rc * inv)
+    else:
+        d = Y[:, :C] - target
+        loss = float((d.double() ** 2).sum() * inv)
+        dY[:, :C] = bf16(2.0 * d * inv)
+    out = [None] * len(layers)
+    dZ = dY
+    for l in range(len(layers) - 1, -1, -1):
+        G = wgrad_fp64(xs[l], dZ)
+        Gb = dZ.double().sum(dim=(0, 2, 3))
+        S = wgrad_fp64(xs[l] ** 2, dZ ** 2).sqrt()
+        A = wgrad_fp64(xs[l].abs(), dZ.abs())
+        Sb = (dZ.double() ** 2).sum(dim=(0, 2, 3)).sqrt()
+        Ab = dZ.double().abs().sum(dim=(0, 2, 3))
+        out[l] = (G, Gb, 24 * BF16_U * S + 1e-5 * A, 24 * BF16_U * Sb + 1e-5 * Ab)
+        if l == 0:
+            break
+        Wflip = bf16(layers[l][0]).flip(1).permute(2, 1, 0).contiguous()   # [ci][8 - tap][co]
+        dYp = bf16(conv_periodic_nchw(dZ, Wflip))
+        dZ = bf16(dYp * gelu_tanh_grad(zb[l - 1]))
+    return out, loss
+
+
+def assert_gradients_elementwise(grads, ref):
+    for l, ((gk, bk), (G, Gb, bound, bound_b)) in enumerate(zip(v.Surrogate.split_params(grads), ref)):
+        err = (gk.double() - G).abs()
+        assert torch.all(err <= bound + 1e-30), (l, float((err - bound).max()), int((err > bound).sum()))
+        errb = (bk.double() - Gb).abs()
+        assert torch.all(errb <= bound_b + 1e-30), (l, "bias", float((errb - bound_b).max()))
+
+
 @pytest.fixture
 def no_tf32():
     old = torch.backends.cudnn.allow_tf32, torch.backends.cuda.matmul.allow_tf32
@@ -165,13 +269,16 @@ def test_surrogate_gradients_match_autograd(no_tf32):
     ref_loss = ((out - target) ** 2).mean()
     ref_loss.backward()
     assert abs(loss - ref_loss.item()) <= 1e-2 * ref_loss.item()
-    for l, ((gk, bk), (gr, br)) in enumerate(zip(v.Surrogate.split_params(grads), v.Surrogate.split_params(w.grad))):
-        for a, b in ((gk, gr), (bk, br)):
+    # the replicated-rounding reference is the gradient: against autograd of the FP32 network
+    # (norm, per tensor: they differ by the backward roundings only)
+    rep, rep_loss = replicated_gradients(p0, u, target, 2)
+    for l, ((G, Gb, _, _), (gr, br)) in enumerate(zip(rep, v.Surrogate.split_params(w.grad))):
+        for a, b in ((G, gr), (Gb, br)):
             nb = b.norm().item()
-            if nb == 0.0:
-                assert a.abs().max().item() == 0.0
-                continue
-            assert (a - b).norm().item() <= 5e-2 * nb, f"layer {l}"
+            assert (a.float() - b).norm().item() <= 5e-2 * nb + 1e-30, f"reference layer {l}"
+    # the kernels element by element against the replicated reference
+    assert abs(loss - rep_loss) <= 1e-3 * rep_loss
+    assert_gradients_elementwise(grads, rep)
     # padding stays exactly zero: layer 1 inputs 2..15, layer 5 outputs 2..15
     g = v.Surrogate.split_params(grads)
     assert g[0][0][:, :, 2:].abs().max().item() == 0.0
@@ -241,13 +348,13 @@ def test_curl_gradients_match_autograd(no_tf32):
     ref_loss = ((pred - target) ** 2).mean()
     ref_loss.backward()
     assert abs(loss - ref_loss.item()) <= 1e-2 * ref_loss.item()
-    for l, ((gk, bk), (gr, br)) in enumerate(zip(v.Surrogate.split_params(grads), v.Surrogate.split_params(w.grad))):
-        for a, b in ((gk, gr), (bk, br)):
+    rep, rep_loss = replicated_gradients(p0, u, target, 3, curl=True)
+    for l, ((G, Gb, _, _), (gr, br)) in enumerate(zip(rep, v.Surrogate.split_params(w.grad))):
+        for a, b in ((G, gr), (Gb, br)):
             nb = b.norm().item()
-            if nb == 0.0:
-                assert a.abs().max().item() == 0.0
-                continue
-            assert (a - b).norm().item() <= 5e-2 * nb, f"layer {l}"
+            assert (a.float() - b).norm().item() <= 5e-2 * nb + 1e-30, f"reference layer {l}"
+    assert abs(loss - rep_loss) <= 1e-3 * rep_loss
+    assert_gradients_elementwise(grads, rep)
     g = v.Surrogate.split_params(grads)
     assert g[4][0][1].abs().max().item() == 0.0 and g[4][1][1].item() == 0.0     # channel 1 unused
     net.close()
