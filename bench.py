@@ -87,6 +87,8 @@ def parse_args():
     ap.add_argument("--count", type=int, default=512, help="problems of the batch512 workload")
     ap.add_argument("--split-lanes", type=int, choices=[2, 4], default=None,
                     help="nodes per lane of the 2D split kernels (tuning)")
+    ap.add_argument("--kernel", type=int, choices=[0, 1, 2], default=0,
+                    help="VLBM_OPT_KERNEL of the lattice: 0 automatic, 1 per node, 2 vectorised")
     ap.add_argument("--sur-trajectories", type=int, default=200, help="sur256: training trajectories (100 pairs each)")
     ap.add_argument("--sur-epochs", type=float, default=8.0, help="sur256: training epochs")
     ap.add_argument("--sur-batch", type=int, default=32, help="sur256: states advanced together in the timed rollouts")
@@ -338,6 +340,8 @@ def run_vlbm(args):
     lat = vlbm.Lattice(shape, dx, nu=WORKLOADS[args.workload][3], precision=args.precision)
     if args.split_lanes:
         lat.set_option(vlbm.VLBM_OPT_SPLIT_LANES, args.split_lanes)
+    if args.kernel:
+        lat.set_option(vlbm.VLBM_OPT_KERNEL, args.kernel)
     lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
     # warm-up: W steps, then prime the CUDA graphs of both buffer parities
     lat.step(args.warmup)

@@ -72,7 +72,7 @@ k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
         const Layout<S, SPLIT, 5> fout{out_base + P.offset, P.plane};
         const Coef<C>& k = P.k;   // read through L1, not copied into registers
         if constexpr (SPLIT)
-            warp_split_step_2d<S, V, false>(fin, fout, P.nx, P.ny, y, seg, lane, k, unused, key);
+            warp_split_step_2d<S, V, false>(fin, fout, P.nx, P.ny, y, seg, lane, k, unused);
         else
             warp_stream_collide_2d<S, false, false>(fin, fout, P.nx, P.ny, y, seg, lane, k, unused, key);
     }

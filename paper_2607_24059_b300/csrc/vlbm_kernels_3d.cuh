@@ -19,7 +19,7 @@ template <class S> struct Vec8 {
 // 32 V consecutive nodes of one (y, z) row.  x-shifts by warp shuffle as in
 // 2D; +-y are rows y -+ 1 of the same z slab, +-z the same row of slab z -+ 1.
 template <class S, bool SPLIT, bool DIAG>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, (sizeof(S) == 4 && !DIAG) ? 3 : 1)
 k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
                         long long plane, int warps_per_row, Coef<typename Storage<S>::C> k,
                         double* __restrict__ partials, uint32_t* __restrict__ step_ctr, int par) {

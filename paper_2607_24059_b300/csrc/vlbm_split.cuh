@@ -37,12 +37,11 @@ constexpr int kSplitV3 = 2;
 //   rho field  a_rho dr +- Q_a / (2 mu)
 //   q_j field  a_j Q_j +- (Q_j Q_a / rho + delta_ja dP) / (2 mu)
 // the same values as the l-th entries of equilibrium_d2q5 / _d3q7.
+// equilibrium_dir_r takes r = 1/rho and dP of the node (one reciprocal serves every direction).
 template <class C, int F, int L>
-__device__ __forceinline__ void equilibrium_dir(const Coef<C>& k, const C (&m)[F], C (&e)[F]) {
+__device__ __forceinline__ void equilibrium_dir_r(const Coef<C>& k, const C (&m)[F], C r, C dP, C (&e)[F]) {
     constexpr int a = (L - 1) / 2;
     const C s = (L & 1) ? C(1) : C(-1);
-    const C r = recip_sel<true>(k.rho_bar + m[0]);
-    const C dP = pressure_dev(k, m[0]) * k.i2m;
     const C Qa = m[1 + a];
     e[0] = k.al[0] * m[0] + s * (Qa * k.i2m);
     const C qr = Qa * r * k.i2m;
@@ -51,6 +50,11 @@ __device__ __forceinline__ void equilibrium_dir(const Coef<C>& k, const C (&m)[F
         const C flux = (j == a) ? (m[1 + j] * qr + dP) : m[1 + j] * qr;
         e[1 + j] = k.al[1 + j] * m[1 + j] + s * flux;
     }
+}
+
+template <class C, int F, int L>
+__device__ __forceinline__ void equilibrium_dir(const Coef<C>& k, const C (&m)[F], C (&e)[F]) {
+    equilibrium_dir_r<C, F, L>(k, m, recip_sel<true>(k.rho_bar + m[0]), pressure_dev(k, m[0]) * k.i2m, e);
 }
 
 template <class T, int V>
@@ -84,18 +88,18 @@ __device__ __forceinline__ void shift_from_right(C (&out)[V], const C (&own)[V],
 // Relaxation and new moments of one D2Q5 node in split form.
 //   m[3]: moments at the node; B[3][4]: pulled populations g_{k,l} (l = 1..4);
 //   nown[3]: sum_l n_{k,l} of the node's own stored non-equilibrium parts.
-// Returns the new moments in m and the new non-equilibrium parts in B.  The
-// FP32 moments take their increment with stochastic rounding (random word w of
-// the node; see sr_add).
+// Returns the new moments in m and the new non-equilibrium parts in B.  The FP32 moments
+// round to nearest: the split forms are held to the L2 gate of 1e-3, which they meet by a
+// wide margin, and these kernels are bound by their instruction count (stochastic
+// rounding, as in FP32 storage, would cost about a tenth of their throughput).
 template <class C>
-__device__ __forceinline__ void split_update_d2q5(const Coef<C>& k, C (&m)[3], C (&B)[3][4], const C (&nown)[3],
-                                                  uint32_t w) {
+__device__ __forceinline__ void split_update_d2q5(const Coef<C>& k, C (&m)[3], C (&B)[3][4], const C (&nown)[3]) {
     // sum_l e_{k,l}(m) = 4 alpha_k m_k: the alpha m of the moving equilibria (their
     // +- fluxes cancel), so that the update conserves m for the stored coefficients
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         const C pulled = (B[f][0] + B[f][1]) + (B[f][2] + B[f][3]);
-        m[f] = sr_add(m[f], (pulled - C(4) * (k.al[f] * m[f])) - nown[f], sr_field_word(w, f));
+        m[f] = m[f] + ((pulled - C(4) * (k.al[f] * m[f])) - nown[f]);
     }
     C e[15];
     equilibrium_d2q5<C, true>(k, m[0], m[1], m[2], e);
@@ -124,7 +128,7 @@ template <class S, int V, bool DIAG>
 __device__ __forceinline__ void warp_split_step_2d(const Layout<S, true, 5>& fin, const Layout<S, true, 5>& fout,
                                                    int nx, int ny, int y, int seg, int lane,
                                                    const Coef<typename Storage<S>::C>& k,
-                                                   Acc<typename Storage<S>::C>& acc, uint32_t key) {
+                                                   Acc<typename Storage<S>::C>& acc) {
     using C = typename Storage<S>::C;
     {
         const int x0 = (seg * 32 + lane) * V;
@@ -233,7 +237,7 @@ __device__ __forceinline__ void warp_split_step_2d(const Layout<S, true, 5>& fin
             for (int f = 0; f < 3; ++f)
 #pragma unroll
                 for (int l = 0; l < 4; ++l) Bi[f][l] = B[f][l][i];
-            split_update_d2q5(k, mi, Bi, ni, sr_node_word(key, row + x0 + i));
+            split_update_d2q5(k, mi, Bi, ni);
             if (DIAG && active) {
                 const C Q[2] = {mi[1], mi[2]};
                 accumulate_node(acc, moments_finite(mi[0], Q, 2), mi[0], Q, 2, k.rho_bar);
@@ -277,12 +281,12 @@ k_split_step_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, i
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t key = take_step_key(step_ctr, par);
+    take_step_key(step_ctr, par);   // keeps the step counter in step (the split forms round to nearest)
     Acc<C> acc;
     if (DIAG) acc.zero();
     if (gwarp < (long long)ny * warps_per_row)   // warp-uniform
         warp_split_step_2d<S, V, DIAG>(fin, fout, nx, ny, (int)(gwarp / warps_per_row), (int)(gwarp % warps_per_row),
-                                       lane, k, acc, key);
+                                       lane, k, acc);
     if (DIAG) block_reduce_store(acc, partials);
 }
 
@@ -296,7 +300,7 @@ k_split_step_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
     using L = Layout<S, true, 5>;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t key = take_step_key(step_ctr, par);
+    take_step_key(step_ctr, par);   // keeps the step counter in step (the split forms round to nearest)
     Acc<C> acc;
     if (DIAG) acc.zero();
     if (node < plane) {
@@ -327,7 +331,7 @@ k_split_step_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
             else if (l == 3) pulled_d2q5<C, 3>(k, ms, np, B);
             else pulled_d2q5<C, 4>(k, ms, np, B);
         }
-        split_update_d2q5(k, m, B, nown, sr_node_word(key, node));
+        split_update_d2q5(k, m, B, nown);
         if (DIAG) {
             const C Q[2] = {m[1], m[2]};
             accumulate_node(acc, moments_finite(m[0], Q, 2), m[0], Q, 2, k.rho_bar);
@@ -345,12 +349,11 @@ k_split_step_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
 
 // ------------------------------------------------------------------------------ 3D
 template <class C>
-__device__ __forceinline__ void split_update_d3q7(const Coef<C>& k, C (&m)[4], C (&B)[4][6], const C (&nown)[4],
-                                                  uint32_t w) {
+__device__ __forceinline__ void split_update_d3q7(const Coef<C>& k, C (&m)[4], C (&B)[4][6], const C (&nown)[4]) {
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const C pulled = ((B[f][0] + B[f][1]) + (B[f][2] + B[f][3])) + (B[f][4] + B[f][5]);
-        m[f] = sr_add(m[f], (pulled - C(6) * (k.al[f] * m[f])) - nown[f], sr_field_word(w, f));
+        m[f] = m[f] + ((pulled - C(6) * (k.al[f] * m[f])) - nown[f]);
     }
     C e[28];
     const C Q[3] = {m[1], m[2], m[3]};
@@ -397,7 +400,7 @@ k_split_step_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, i
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t key = take_step_key(step_ctr, par);
+    take_step_key(step_ctr, par);   // keeps the step counter in step (the split forms round to nearest)
     Acc<C> acc;
     if (DIAG) acc.zero();
     if (gwarp < (long long)ny * nz * warps_per_row) {
@@ -474,7 +477,7 @@ k_split_step_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, i
             for (int f = 0; f < 4; ++f)
 #pragma unroll
                 for (int l = 0; l < 6; ++l) Bi[f][l] = B[f][l][i];
-            split_update_d3q7(k, mi, Bi, ni, sr_node_word(key, row + x0 + i));
+            split_update_d3q7(k, mi, Bi, ni);
             if (DIAG && active) {
                 const C Q[3] = {mi[1], mi[2], mi[3]};
                 accumulate_node(acc, moments_finite(mi[0], Q, 3), mi[0], Q, 3, k.rho_bar);
@@ -516,7 +519,7 @@ k_split_step_3d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
     using L = Layout<S, true, 7>;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t key = take_step_key(step_ctr, par);
+    take_step_key(step_ctr, par);   // keeps the step counter in step (the split forms round to nearest)
     Acc<C> acc;
     if (DIAG) acc.zero();
     if (node < plane) {
@@ -551,7 +554,7 @@ k_split_step_3d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
             }
             pulled_d3q7_l(k, l, ms, np, B);
         }
-        split_update_d3q7(k, m, B, nown, sr_node_word(key, node));
+        split_update_d3q7(k, m, B, nown);
         if (DIAG) {
             const C Q[3] = {m[1], m[2], m[3]};
             accumulate_node(acc, moments_finite(m[0], Q, 3), m[0], Q, 3, k.rho_bar);
