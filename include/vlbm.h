@@ -186,7 +186,8 @@ int vlbm_launch_count(const vlbm_handle* h, int64_t* count);
  * 2D 4 (FP32, 16-bit formats) or 2 (FP64); 3D 2 or 1 (FP64)), 1 = one thread
  * per node (any size),
  * 2 = vectorised (VLBM_EINVAL when n_x does not allow it).  Both compute the
- * same arithmetic in the same order, so their results are bitwise equal. */
+ * same arithmetic in the same order and agree to rounding (the compiler may fuse
+ * a multiply and an add into one FMA in one kernel and not in the other). */
 #define VLBM_OPT_KERNEL 0
 /* VLBM_OPT_SPLIT_LANES: nodes per lane (2 or 4, default 4) of the vectorised 2D
  * kernel of the split formats; a tuning knob, same results up to FMA contraction. */

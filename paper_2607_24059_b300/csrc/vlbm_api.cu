@@ -52,6 +52,7 @@ struct vlbm_handle {
     double* stage = nullptr;          // kStageBlocks rows of the two-stage final reduction
     double* inv_dev = nullptr;        // 8 doubles
     uint32_t* ctr = nullptr;          // step counter of the stochastic rounding: ctr[cur] = step (mod 2^32)
+    unsigned int* fold_ctr = nullptr; // kStageBlocks + 1 tickets of the fused-diagnostics fold (zero between launches)
     double* inv_host = nullptr;       // 8 doubles, pinned
     void* staging = nullptr;
     size_t staging_bytes = 0;
@@ -187,11 +188,16 @@ static bool use_vec(const vlbm_handle* h) {
     return h->p.n[0] % vec_width(h) == 0 && (h->p.dim == 2 || h->p.dim == 3);
 }
 
-static int64_t step_blocks(const vlbm_handle* h) {
+// Nodes per lane of the vectorised step with fused diagnostics (DiagVec: 2 for 2D FP32).
+static int diag_vec_width(const vlbm_handle* h) {
+    return (h->p.dim == 2 && h->p.precision == VLBM_FP32) ? 2 : vec_width(h);
+}
+
+static int64_t step_blocks_v(const vlbm_handle* h, int v) {
     const int64_t nx = h->p.n[0];
     const int64_t rows = h->d.nodes / nx;
     if (use_vec(h)) {
-        const int64_t wpr = (nx / vec_width(h) + 31) / 32;
+        const int64_t wpr = (nx / v + 31) / 32;
         return (rows * wpr * 32 + kThreads - 1) / kThreads;
     }
     return blocks_for(h->d.nodes);
@@ -211,6 +217,7 @@ static void free_all(vlbm_handle* h) {
     if (h->stage) cudaFree(h->stage);
     if (h->inv_dev) cudaFree(h->inv_dev);
     if (h->ctr) cudaFree(h->ctr);
+    if (h->fold_ctr) cudaFree(h->fold_ctr);
     if (h->inv_host) cudaFreeHost(h->inv_host);
     if (h->staging) cudaFree(h->staging);
     if (h->hist) cudaFree(h->hist);
@@ -253,12 +260,14 @@ extern "C" int vlbm_create(const vlbm_params* p, void* stream, vlbm_handle** out
             cudaMalloc(&h->stage, (size_t)kStageBlocks * 8 * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&h->inv_dev, 8 * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&h->ctr, 2 * sizeof(uint32_t)) != cudaSuccess ||
+            cudaMalloc(&h->fold_ctr, (kStageBlocks + 1) * sizeof(unsigned int)) != cudaSuccess ||
             cudaMallocHost(&h->inv_host, 8 * sizeof(double)) != cudaSuccess) {
             st = VLBM_ENOMEM;
             break;
         }
         if (cudaMemsetAsync(h->buf[0], 0, d.lattice_bytes, h->stream) != cudaSuccess ||
-            cudaMemsetAsync(h->ctr, 0, 2 * sizeof(uint32_t), h->stream) != cudaSuccess) {
+            cudaMemsetAsync(h->ctr, 0, 2 * sizeof(uint32_t), h->stream) != cudaSuccess ||
+            cudaMemsetAsync(h->fold_ctr, 0, (kStageBlocks + 1) * sizeof(unsigned int), h->stream) != cudaSuccess) {
             st = VLBM_ECUDA;
             break;
         }
@@ -421,51 +430,61 @@ extern "C" int vlbm_macros(vlbm_handle* h, void* rho, void* u, void* phi, int32_
 }
 
 // ------------------------------------------------------------------ stepping
+static DiagSink diag_sink(vlbm_handle* h, double* out, int nblocks);
+
+// One step from buffer src.  Plain steps launch one warp per row segment (one thread per
+// node for the per-node kernels).  Steps with fused diagnostics (DIAG, out = where the 8
+// invariants go) launch a persistent grid of the kernel's resident blocks on every SM,
+// each warp looping over segments and accumulating before one block reduction and the
+// fold of DiagSink.
 template <class S, bool M, bool DIAG>
-static void launch_step_on(vlbm_handle* h, cudaStream_t s, int src, double* partials) {
+static void launch_step_on(vlbm_handle* h, cudaStream_t s, int src, double* out) {
     using C = typename Storage<S>::C;
     const auto& k = coef<C>(h);
     const char* fin = (const char*)h->buf[src];
     char* fout = (char*)h->buf[src ^ 1];
     const int64_t nx = h->p.n[0], ny = h->p.n[1];
     const int64_t plane = h->d.nodes;
-    const int64_t blocks = step_blocks(h);
+    const int v = DIAG ? diag_vec_width(h) : vec_width(h);
+    const int64_t blocks = step_blocks_v(h, v);
     const int64_t nz = h->p.n[2];
     const bool vec = use_vec(h);
-    const int wpr = (int)((nx / vec_width(h) + 31) / 32);
+    const int wpr = (int)((nx / v + 31) / 32);
+    auto go = [&](auto kernel, auto... args) {
+        int64_t grid = blocks;
+        DiagSink sink{};
+        if constexpr (DIAG) {
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess) per_sm = 1;
+            grid = std::min<int64_t>(blocks, (int64_t)h->sm_count * std::max(per_sm, 1));
+            sink = diag_sink(h, out, (int)grid);
+        }
+        kernel<<<(unsigned)grid, kThreads, 0, s>>>(args..., sink, h->ctr, src);
+    };
     if constexpr (M) {
         if (h->p.dim == 2) {
             if (vec && h->split_lanes == 2)
-                k_split_step_2d_vec<S, 2, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, wpr,
-                                                                            k, partials, h->ctr, src);
+                go(k_split_step_2d_vec<S, 2, DIAG>, fin, fout, (int)nx, (int)ny, plane, wpr, k);
             else if (vec)
-                k_split_step_2d_vec<S, 4, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, wpr,
-                                                                            k, partials, h->ctr, src);
+                go(k_split_step_2d_vec<S, 4, DIAG>, fin, fout, (int)nx, (int)ny, plane, wpr, k);
             else
-                k_split_step_2d_generic<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, k,
-                                                                             partials, h->ctr, src);
+                go(k_split_step_2d_generic<S, DIAG>, fin, fout, (int)nx, (int)ny, plane, k);
         } else {
             if (vec)
-                k_split_step_3d_vec<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz, plane,
-                                                                         wpr, k, partials, h->ctr, src);
+                go(k_split_step_3d_vec<S, DIAG>, fin, fout, (int)nx, (int)ny, (int)nz, plane, wpr, k);
             else
-                k_split_step_3d_generic<S, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz,
-                                                                             plane, k, partials, h->ctr, src);
+                go(k_split_step_3d_generic<S, DIAG>, fin, fout, (int)nx, (int)ny, (int)nz, plane, k);
         }
     } else if (h->p.dim == 2) {
         if (vec)
-            k_stream_collide_2d_vec<S, M, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, wpr,
-                                                                            k, partials, h->ctr, src);
+            go(k_stream_collide_2d_vec<S, M, DIAG>, fin, fout, (int)nx, (int)ny, plane, wpr, k);
         else
-            k_stream_collide_2d_generic<S, M, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, plane, k,
-                                                                                partials, h->ctr, src);
+            go(k_stream_collide_2d_generic<S, M, DIAG>, fin, fout, (int)nx, (int)ny, plane, k);
     } else {
         if (vec)
-            k_stream_collide_3d_vec<S, M, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz,
-                                                                            plane, wpr, k, partials, h->ctr, src);
+            go(k_stream_collide_3d_vec<S, M, DIAG>, fin, fout, (int)nx, (int)ny, (int)nz, plane, wpr, k);
         else
-            k_stream_collide_3d_generic<S, M, DIAG><<<blocks, kThreads, 0, s>>>(fin, fout, (int)nx, (int)ny, (int)nz,
-                                                                                plane, k, partials, h->ctr, src);
+            go(k_stream_collide_3d_generic<S, M, DIAG>, fin, fout, (int)nx, (int)ny, (int)nz, plane, k);
     }
 }
 
@@ -473,8 +492,26 @@ template <class S, bool M>
 static void step_plain(vlbm_handle* h, cudaStream_t s, int src) { launch_step_on<S, M, false>(h, s, src, nullptr); }
 
 template <class S, bool M>
-static void step_diag(vlbm_handle* h, cudaStream_t s, int src, double* partials) {
-    launch_step_on<S, M, true>(h, s, src, partials);
+static void step_diag(vlbm_handle* h, cudaStream_t s, int src, double* out) {
+    launch_step_on<S, M, true>(h, s, src, out);
+}
+
+// The fused-diagnostics sink of a step launched with nblocks blocks whose invariants go to
+// out (device, 8 doubles): groups of at least 32 partial rows, at most kStageBlocks groups.
+static DiagSink diag_sink(vlbm_handle* h, double* out, int nblocks) {
+    DiagSink k{};
+    k.partials = h->partials;
+    k.stage = h->stage;
+    k.counters = h->fold_ctr;
+    k.out = out;
+    k.nblocks = nblocks;
+    k.group = std::max<int>(32, (nblocks + kStageBlocks - 1) / kStageBlocks);
+    k.ngroups = (nblocks + k.group - 1) / k.group;
+    k.nodes = (double)h->d.nodes;
+    k.rho_bar = h->p.rho_bar;
+    k.inv_dx = 1.0 / h->p.dx;
+    k.scale_e = h->p.dim == 3 ? h->p.dx : 1.0;
+    return k;
 }
 
 static int launch_one_step(vlbm_handle* h, cudaStream_t s, int src) {
@@ -575,16 +612,13 @@ extern "C" int vlbm_step_record(vlbm_handle* h, int64_t nsteps, int64_t every, d
         }
         rec = h->hist;
     }
-    const int blocks = (int)step_blocks(h);
     for (int64_t s = 0; s < nsteps;) {
         if (s % every == 0) {
-            VLBM_DISPATCH_STORAGE(h, step_diag, h, h->stream, h->cur, h->partials);
+            // one launch: the step, its invariants and their fold (DiagSink)
+            VLBM_DISPATCH_STORAGE(h, step_diag, h, h->stream, h->cur, rec + (s / every) * 8);
             int rc = check_launch(h, "stream-collide (diagnostics)");
             if (rc) return rc;
-            launch_final(h, blocks, rec + (s / every) * 8);
-            rc = check_launch(h, "invariants final");
-            if (rc) return rc;
-            h->launches += 2;
+            h->launches += 1;
             h->cur ^= 1;
             h->step++;
             ++s;

@@ -511,4 +511,91 @@ __device__ __forceinline__ void block_reduce_store(Acc<C>& acc, double* __restri
     }
 }
 
+// The 8 invariants from the folded sums s = { sum dr, sum Q_d (3), sum |Q|^2/(2 rho),
+// max |Q|/rho, bad, 0 }: { N rho_bar + sum dr, sum Q_d / dx (3), E_kin, max|u|,
+// non-finite nodes, sum dr }.  scale_e = dx^(d-2) turns sum |Q|^2/(2 rho) into
+// 1/2 sum |q|^2/rho dx^d.
+__device__ __forceinline__ void write_invariants(double* __restrict__ out, const double* s, double nodes,
+                                                 double rho_bar, double inv_dx, double scale_e) {
+    out[0] = nodes * rho_bar + s[0];
+    out[1] = s[1] * inv_dx;
+    out[2] = s[2] * inv_dx;
+    out[3] = s[3] * inv_dx;
+    out[4] = s[4] * scale_e;
+    out[5] = s[5] * inv_dx;
+    out[6] = s[6];
+    out[7] = s[0];
+}
+
+// Where a fused-diagnostics step puts its invariants.  Every block writes its partial
+// row, then takes a ticket on its group's counter; the last block of a group folds the
+// group's rows (in row order) into stage[group], the last group folds the stage rows
+// (in order) into the 8 invariants at `out`.  The folds run in a fixed order whichever
+// block finishes last, so the result is deterministic, and no reduction kernel follows
+// the step.  The counters return to zero by the end of the launch.
+struct DiagSink {
+    double* partials;          // [nblocks][8]
+    double* stage;             // [ngroups][8]
+    unsigned int* counters;    // [ngroups + 1], zero before the launch
+    double* out;               // 8 doubles
+    int nblocks, group, ngroups;
+    double nodes, rho_bar, inv_dx, scale_e;
+};
+
+// Fold rows [first, first + count) of 8 doubles (sums, slot 5 a maximum) in a fixed
+// order with the 256 threads of the block; thread 0 returns the 8 results in res.
+// Rows written by other blocks are read past L1 (ld.global.cg).
+__device__ __forceinline__ void fold_rows(const double* rows, int first, int count, double (&res)[8]) {
+    __shared__ double sh[256];
+    const int t = threadIdx.x, slot = t & 7;
+    const bool is_max = slot == 5;
+    double a = 0.0;
+    for (int r = (t >> 3); r < count; r += 32) {
+        const double v = __ldcg(rows + (size_t)(first + r) * 8 + slot);
+        a = is_max ? fmax(a, v) : a + v;
+    }
+    sh[t] = a;
+    __syncthreads();
+    for (int stride = 16; stride > 0; stride >>= 1) {
+        if ((t >> 3) < stride) {
+            const double o = sh[t + stride * 8];
+            sh[t] = is_max ? fmax(sh[t], o) : sh[t] + o;
+        }
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int i = 0; i < 8; ++i) res[i] = sh[i];
+    __syncthreads();
+}
+
+// block_reduce_store, then the two-level fold of DiagSink (blocks of 256 threads).
+template <class C>
+__device__ __forceinline__ void block_reduce_finish(Acc<C>& acc, const DiagSink& sink) {
+    __shared__ int s_last;
+    block_reduce_store(acc, sink.partials);   // thread 0 writes this block's row
+    const int g = (int)blockIdx.x / sink.group;
+    const int gsize = min(sink.group, sink.nblocks - g * sink.group);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(sink.counters + g, 1u) == (unsigned int)(gsize - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    double res[8];
+    fold_rows(sink.partials, g * sink.group, gsize, res);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 8; ++i) sink.stage[(size_t)g * 8 + i] = res[i];
+        sink.counters[g] = 0u;
+        __threadfence();
+        s_last = atomicAdd(sink.counters + sink.ngroups, 1u) == (unsigned int)(sink.ngroups - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    fold_rows(sink.stage, 0, sink.ngroups, res);
+    if (threadIdx.x == 0) {
+        write_invariants(sink.out, res, sink.nodes, sink.rho_bar, sink.inv_dx, sink.scale_e);
+        sink.counters[sink.ngroups] = 0u;
+    }
+}
+
 }  // namespace vlbm

@@ -51,7 +51,7 @@ __device__ __forceinline__ void load_or_zero(T (&w)[V], const T* p, bool active)
 // segment seg.  Called with every lane of the warp (shuffles); lanes past the
 // row end load nothing and store nothing.  key: the step's stochastic-rounding
 // key (sr_step_key), used by FP32 storage.
-template <class S, bool SPLIT, bool DIAG>
+template <class S, bool SPLIT, bool DIAG, int V = Vec16<S>::V>
 __device__ __forceinline__ void warp_stream_collide_2d(const Layout<S, SPLIT, 5>& fin, const Layout<S, SPLIT, 5>& fout,
                                                        int nx, int ny, int y, int seg, int lane,
                                                        const Coef<typename Storage<S>::C>& k,
@@ -59,7 +59,6 @@ __device__ __forceinline__ void warp_stream_collide_2d(const Layout<S, SPLIT, 5>
     using C = typename Storage<S>::C;
     using L = Layout<S, SPLIT, 5>;
     using R = typename L::R;
-    constexpr int V = Vec16<S>::V;
     constexpr bool SR = StochasticMoments<S>::value && !SPLIT;
     constexpr bool SR16 = StochasticStore16<S>::value && !SPLIT;
     {
@@ -179,24 +178,32 @@ __device__ __forceinline__ uint32_t take_step_key(uint32_t* __restrict__ step_ct
 }
 
 // 16-bit storage moves half the bytes per node, so it needs more warps in flight to
-// cover the memory latency: three resident blocks per SM (at most 85 registers).
+// cover the memory latency: three resident blocks per SM (at most 85 registers).  The
+// FP32 step with fused diagnostics does about 1.7 times the instructions of the plain
+// one; it takes V = 2 nodes per lane (DiagVec), also at three blocks per SM.
+template <class S, bool DIAG> struct DiagVec { static constexpr int V = Vec16<S>::V; };
+template <> struct DiagVec<float, true> { static constexpr int V = 2; };
+
 template <class S, bool SPLIT, bool DIAG>
-__global__ void __launch_bounds__(kThreads, sizeof(S) == 2 ? 3 : 1)
+__global__ void __launch_bounds__(kThreads, (sizeof(S) == 2 || (sizeof(S) == 4 && DIAG)) ? 3 : 1)
 k_stream_collide_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
-                        int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials,
+                        int warps_per_row, Coef<typename Storage<S>::C> k, DiagSink sink,
                         uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, SPLIT, 5>;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> acc;
     if (DIAG) acc.zero();
-    if (gwarp < (long long)ny * warps_per_row)   // warp-uniform
-        warp_stream_collide_2d<S, SPLIT, DIAG>(fin, fout, nx, ny, (int)(gwarp / warps_per_row),
-                                               (int)(gwarp % warps_per_row), lane, k, acc, key);
-    if (DIAG) block_reduce_store(acc, partials);
+    // one row segment per warp; a smaller (persistent) grid loops, accumulating the
+    // diagnostics of all its segments before one block reduction
+    for (long long item = gwarp, items = (long long)ny * warps_per_row; item < items; item += (DIAG ? nwarps : items))   // warp-uniform
+        warp_stream_collide_2d<S, SPLIT, DIAG, DiagVec<S, DIAG>::V>(fin, fout, nx, ny, (int)(item / warps_per_row),
+                                                                    (int)(item % warps_per_row), lane, k, acc, key);
+    if (DIAG) block_reduce_finish(acc, sink);
 }
 
 // Load / store one population of one node through the layout (scaled to deviations).
@@ -221,18 +228,18 @@ __device__ __forceinline__ void store_pop(const Layout<S, SPLIT, Q>& L, int f, i
 template <class S, bool SPLIT, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
 k_stream_collide_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny,
-                            long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials,
+                            long long plane, Coef<typename Storage<S>::C> k, DiagSink sink,
                             uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, SPLIT, 5>;
     constexpr bool SR = StochasticMoments<S>::value && !SPLIT;
     constexpr bool SR16 = StochasticStore16<S>::value && !SPLIT;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
-    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> acc;
     if (DIAG) acc.zero();
-    if (node < plane) {
+    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < plane;
+         node += (DIAG ? (long long)gridDim.x * blockDim.x : plane)) {
         const int x = (int)(node % nx), y = (int)(node / nx);
         const long long row = (long long)y * nx;
         const long long src[5] = {
@@ -264,7 +271,7 @@ k_stream_collide_2d_generic(const char* __restrict__ fin_b, char* __restrict__ f
             store_pop(fout, p / 5, p % 5, node, g[p], k);
         }
     }
-    if (DIAG) block_reduce_store(acc, partials);
+    if (DIAG) block_reduce_finish(acc, sink);
 }
 
 // ------------------------------------------------------------------------------
@@ -431,16 +438,7 @@ k_invariants_final(const double* __restrict__ partials, int nblocks, double* __r
         }
         __syncthreads();
     }
-    if (t == 0) {
-        out[0] = nodes * rho_bar + sh[0];
-        out[1] = sh[1] * inv_dx;
-        out[2] = sh[2] * inv_dx;
-        out[3] = sh[3] * inv_dx;
-        out[4] = sh[4] * scale_e;
-        out[5] = sh[5] * inv_dx;
-        out[6] = sh[6];
-        out[7] = sh[0];
-    }
+    if (t == 0) write_invariants(out, sh, nodes, rho_bar, inv_dx, scale_e);
 }
 
 // Export populations in [p][node] order (p = q k + l): the stored deviation

@@ -22,7 +22,7 @@ template <class S, bool SPLIT, bool DIAG>
 __global__ void __launch_bounds__(kThreads, (sizeof(S) == 4 && !DIAG) ? 3 : 1)
 k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
                         long long plane, int warps_per_row, Coef<typename Storage<S>::C> k,
-                        double* __restrict__ partials, uint32_t* __restrict__ step_ctr, int par) {
+                        DiagSink sink, uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, SPLIT, 7>;
     using R = typename L::R;
@@ -32,13 +32,14 @@ k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> acc;
     if (DIAG) acc.zero();
-    if (gwarp < (long long)ny * nz * warps_per_row) {
-        const long long r = gwarp / warps_per_row;        // row index (z * ny + y)
+    for (long long item = gwarp, items = (long long)ny * nz * warps_per_row; item < items; item += (DIAG ? nwarps : items)) {   // warp-uniform
+        const long long r = item / warps_per_row;         // row index (z * ny + y)
         const int y = (int)(r % ny), z = (int)(r / ny);
-        const int x0 = ((int)(gwarp % warps_per_row) * 32 + lane) * V;
+        const int x0 = ((int)(item % warps_per_row) * 32 + lane) * V;
         const bool active = x0 < nx;
         const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
         const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
@@ -134,25 +135,25 @@ k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
             }
         }
     }
-    if (DIAG) block_reduce_store(acc, partials);
+    if (DIAG) block_reduce_finish(acc, sink);
 }
 
 // One thread per node, any size.
 template <class S, bool SPLIT, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
 k_stream_collide_3d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
-                            long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials,
+                            long long plane, Coef<typename Storage<S>::C> k, DiagSink sink,
                             uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, SPLIT, 7>;
     constexpr bool SR = StochasticMoments<S>::value && !SPLIT;
     constexpr bool SR16 = StochasticStore16<S>::value && !SPLIT;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
-    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> acc;
     if (DIAG) acc.zero();
-    if (node < plane) {
+    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < plane;
+         node += (DIAG ? (long long)gridDim.x * blockDim.x : plane)) {
         const int x = (int)(node % nx);
         const long long r = node / nx;
         const int y = (int)(r % ny), z = (int)(r / ny);
@@ -185,7 +186,7 @@ k_stream_collide_3d_generic(const char* __restrict__ fin_b, char* __restrict__ f
             store_pop(fout, p / 7, p % 7, node, g[p], k);
         }
     }
-    if (DIAG) block_reduce_store(acc, partials);
+    if (DIAG) block_reduce_finish(acc, sink);
 }
 
 template <class S, bool SPLIT, class T>

@@ -274,36 +274,37 @@ __device__ __forceinline__ void warp_split_step_2d(const Layout<S, true, 5>& fin
 template <class S, int V, bool DIAG>
 __global__ void __launch_bounds__(kThreads, 2)
 k_split_step_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
-                    int warps_per_row, Coef<typename Storage<S>::C> k, double* __restrict__ partials,
+                    int warps_per_row, Coef<typename Storage<S>::C> k, DiagSink sink,
                     uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, true, 5>;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     take_step_key(step_ctr, par);   // keeps the step counter in step (the split forms round to nearest)
     Acc<C> acc;
     if (DIAG) acc.zero();
-    if (gwarp < (long long)ny * warps_per_row)   // warp-uniform
-        warp_split_step_2d<S, V, DIAG>(fin, fout, nx, ny, (int)(gwarp / warps_per_row), (int)(gwarp % warps_per_row),
+    for (long long item = gwarp, items = (long long)ny * warps_per_row; item < items; item += (DIAG ? nwarps : items))   // warp-uniform
+        warp_split_step_2d<S, V, DIAG>(fin, fout, nx, ny, (int)(item / warps_per_row), (int)(item % warps_per_row),
                                        lane, k, acc);
-    if (DIAG) block_reduce_store(acc, partials);
+    if (DIAG) block_reduce_finish(acc, sink);
 }
 
 // One thread per node, any size (2D split form).
 template <class S, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
 k_split_step_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny,
-                        long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials,
+                        long long plane, Coef<typename Storage<S>::C> k, DiagSink sink,
                         uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, true, 5>;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
-    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     take_step_key(step_ctr, par);   // keeps the step counter in step (the split forms round to nearest)
     Acc<C> acc;
     if (DIAG) acc.zero();
-    if (node < plane) {
+    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < plane;
+         node += (DIAG ? (long long)gridDim.x * blockDim.x : plane)) {
         const int x = (int)(node % nx), y = (int)(node / nx);
         const long long row = (long long)y * nx;
         const long long src[5] = {
@@ -344,7 +345,7 @@ k_split_step_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
             for (int l = 0; l < 4; ++l) fout.mov(f, l + 1)[node] = Storage<S>::from_c(B[f][l] * sc);
         }
     }
-    if (DIAG) block_reduce_store(acc, partials);
+    if (DIAG) block_reduce_finish(acc, sink);
 }
 
 // ------------------------------------------------------------------------------ 3D
@@ -393,20 +394,21 @@ template <class S, bool DIAG>
 __global__ void __launch_bounds__(kThreads, 3)
 k_split_step_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
                     long long plane, int warps_per_row, Coef<typename Storage<S>::C> k,
-                    double* __restrict__ partials, uint32_t* __restrict__ step_ctr, int par) {
+                    DiagSink sink, uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, true, 7>;
     constexpr int V = kSplitV3;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     take_step_key(step_ctr, par);   // keeps the step counter in step (the split forms round to nearest)
     Acc<C> acc;
     if (DIAG) acc.zero();
-    if (gwarp < (long long)ny * nz * warps_per_row) {
-        const long long r = gwarp / warps_per_row;
+    for (long long item = gwarp, items = (long long)ny * nz * warps_per_row; item < items; item += (DIAG ? nwarps : items)) {   // warp-uniform
+        const long long r = item / warps_per_row;
         const int y = (int)(r % ny), z = (int)(r / ny);
-        const int x0 = ((int)(gwarp % warps_per_row) * 32 + lane) * V;
+        const int x0 = ((int)(item % warps_per_row) * 32 + lane) * V;
         const bool active = x0 < nx;
         const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
         const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
@@ -507,22 +509,22 @@ k_split_step_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, i
             }
         }
     }
-    if (DIAG) block_reduce_store(acc, partials);
+    if (DIAG) block_reduce_finish(acc, sink);
 }
 
 template <class S, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
 k_split_step_3d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
-                        long long plane, Coef<typename Storage<S>::C> k, double* __restrict__ partials,
+                        long long plane, Coef<typename Storage<S>::C> k, DiagSink sink,
                         uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, true, 7>;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
-    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     take_step_key(step_ctr, par);   // keeps the step counter in step (the split forms round to nearest)
     Acc<C> acc;
     if (DIAG) acc.zero();
-    if (node < plane) {
+    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < plane;
+         node += (DIAG ? (long long)gridDim.x * blockDim.x : plane)) {
         const int x = (int)(node % nx);
         const long long r = node / nx;
         const int y = (int)(r % ny), z = (int)(r / ny);
@@ -567,7 +569,7 @@ k_split_step_3d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
             for (int l = 0; l < 6; ++l) fout.mov(f, l + 1)[node] = Storage<S>::from_c(B[f][l] * sc);
         }
     }
-    if (DIAG) block_reduce_store(acc, partials);
+    if (DIAG) block_reduce_finish(acc, sink);
 }
 
 }  // namespace vlbm
