@@ -96,7 +96,10 @@ def parse_args():
                     help="sur256: time only the dominant kernel (the 64 -> 64 conv of the rollout) and the "
                          "training step's weight gradient of that conv, no training")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-history", action="store_true", help="tgv3d: skip the energy and dissipation history")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--cpu-seconds-one-core", type=float, default=8.0,
+                    help="target CPU time of the single-threaded oracle sample")
     ap.add_argument("--reference-seconds", type=float, default=150.0, help="cap on the reference arm's timed steps")
     args = ap.parse_args()
     if args.n is None:
@@ -235,8 +238,24 @@ def measured_peaks():
 
 # sources that define the stream-collide step kernels (the surrogate's and the
 # no-allocation entry's files do not change them)
-STEP_SOURCES = ("vlbm_device.cuh", "vlbm_kernels_2d.cuh", "vlbm_kernels_3d.cuh", "vlbm_split.cuh", "vlbm_api.cu",
-                "vlbm_batch.cu", "vlbm_host.hpp")
+# Sources each step kernel is compiled from (its code and its launch shape): a profiled figure stays
+# valid while these files are unchanged.
+STEP_SOURCES = {
+    "2d": ("vlbm_device.cuh", "vlbm_kernels_2d.cuh", "vlbm_api.cu", "vlbm_host.hpp"),
+    "3d": ("vlbm_device.cuh", "vlbm_kernels_2d.cuh", "vlbm_kernels_3d.cuh", "vlbm_api.cu", "vlbm_host.hpp"),
+    "split": ("vlbm_device.cuh", "vlbm_kernels_2d.cuh", "vlbm_kernels_3d.cuh", "vlbm_split.cuh", "vlbm_api.cu",
+              "vlbm_host.hpp"),
+    "batch": ("vlbm_device.cuh", "vlbm_kernels_2d.cuh", "vlbm_kernels_3d.cuh", "vlbm_split.cuh", "vlbm_batch.cu",
+              "vlbm_host.hpp"),
+}
+
+
+def source_kind(args):
+    if args.workload == "batch512":
+        return "batch"
+    if split(args):
+        return "split"
+    return "3d" if WORKLOADS[args.workload][0] == 3 else "2d"
 
 
 def l2_note(lattice_bytes: float) -> str:
@@ -246,10 +265,10 @@ def l2_note(lattice_bytes: float) -> str:
     return "working set 2 lattices x {:.1f} MB fits in the 126 MB L2 (a small case)".format(lattice_bytes / 1e6)
 
 
-def source_digest():
+def source_digest(kind):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2607_24059_b300", "csrc")
-    for fn in STEP_SOURCES:
+    for fn in STEP_SOURCES[kind]:
         with open(os.path.join(csrc, fn), "rb") as fh:
             h.update(fn.encode())
             h.update(fh.read())
@@ -270,27 +289,62 @@ def profiled_traffic(kernel, n, digest):
 
 
 # ---------------------------------------------------------------- CPU oracle baseline
-def oracle_sample(args, seconds):
-    """GLUPS of the FP64 oracle on the same lattice, on the host cores, for ~seconds."""
+def oracle_sample(args, seconds, threads=None):
+    """GLUPS of the FP64 oracle on the same lattice, on the host cores, for ~seconds
+    (threads: OpenMP threads, default all)."""
     import oracle
     import synthetic
     orc = oracle.default()
-    u, phi, dx, n = make_input(args)
-    p = oracle.make_params(n, dx, nu=WORKLOADS[args.workload][3])
-    f = orc.init(p, u, phi)
-    work = np.empty_like(f)
-    orc.run_inplace(p, f, work, 2)            # warm-up (first touch of the work lattice, thread start)
-    m = 0
-    t0 = time.perf_counter()
-    while True:                               # whole steps until the time budget is used
-        orc.run_inplace(p, f, work, 1)
-        m += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or m >= 500:
-            break
-    return {"value": nodes_of(args) * m / el / 1e9, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
-            "sample": f"{args.workload} {args.n}^{WORKLOADS[args.workload][0]}, {m} FP64 oracle steps after 2 warm-up steps "
-                      f"(plain C, OpenMP over rows, {orc.num_threads()} threads)", "seconds": el}
+    all_threads = orc.num_threads()
+    if threads:
+        orc.set_num_threads(threads)
+    try:
+        u, phi, dx, n = make_input(args)
+        p = oracle.make_params(n, dx, nu=WORKLOADS[args.workload][3])
+        f = orc.init(p, u, phi)
+        work = np.empty_like(f)
+        warm = 1 if threads == 1 else 2
+        orc.run_inplace(p, f, work, warm)     # warm-up (first touch of the work lattice, thread start)
+        m = 0
+        t0 = time.perf_counter()
+        while True:                           # whole steps until the time budget is used
+            orc.run_inplace(p, f, work, 1)
+            m += 1
+            el = time.perf_counter() - t0
+            if el >= seconds or m >= 500:
+                break
+        cores = orc.num_threads()
+    finally:
+        orc.set_num_threads(all_threads)
+    return {"value": nodes_of(args) * m / el / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{args.workload} {args.n}^{WORKLOADS[args.workload][0]}, {m} FP64 oracle steps after {warm} "
+                      f"warm-up step(s) (plain C, OpenMP over rows, {cores} thread(s))", "seconds": el}
+
+
+def tgv3d_history(lat, u, phi, nu, steps, every, torch):
+    """Kinetic energy E(t) and the dissipation of the 3D Taylor-Green vortex every `every` steps
+    over `steps` steps (both FP64 reductions on the GPU): -dE/dt from centred differences of the
+    E history against nu * sum |curl u|^2 dx^3 (centred differences of the velocity)."""
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    dt = lat.derived.dt
+    t, e, eps = [], [], []
+    for j in range(steps // every + 1):
+        if j:
+            lat.step(every)
+        t.append(lat.time()[1])
+        e.append(float(lat.invariants()[4]))
+        eps.append(nu * lat.vorticity_sq())
+    t, e, eps = np.array(t), np.array(e), np.array(eps)
+    dEdt = -(e[2:] - e[:-2]) / (t[2:] - t[:-2])
+    mism = np.abs(dEdt - eps[1:-1]) / np.abs(eps[1:-1])
+    pick = np.linspace(0, len(t) - 1, 11).round().astype(int)
+    return {"steps": steps, "every": every, "dt": dt, "reduction": "FP64 on the GPU (vlbm_invariants, vlbm_vorticity_sq)",
+            "E0": e[0], "E_end": e[-1], "t_end": t[-1],
+            "dissipation_vs_minus_dEdt_max_rel_diff": float(mism.max()),
+            "dissipation_vs_minus_dEdt_mean_rel_diff": float(mism.mean()),
+            "samples": {"t": [float(t[i]) for i in pick], "E": [float(e[i]) for i in pick],
+                        "nu_curl_sq": [float(eps[i]) for i in pick],
+                        "minus_dEdt": [float(dEdt[min(max(i - 1, 0), len(dEdt) - 1)]) for i in pick]}}
 
 
 # ---------------------------------------------------------------- the two arms
@@ -377,7 +431,7 @@ def run_vlbm(args):
     bpn = bytes_per_node(args)
     achieved = bpn * nodes / per_launch / 1e9
     peak, peak_kind = measured_peaks()
-    digest = source_digest()
+    digest = source_digest(source_kind(args))
     traffic = profiled_traffic(kernel_name(args), args.n, digest)
 
     # ---- end to end through the C ABI with host buffers
@@ -423,8 +477,13 @@ def run_vlbm(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    if args.workload == "tgv3d" and world == 1 and not args.no_history:
+        line["history"] = tgv3d_history(lat, u, phi, WORKLOADS["tgv3d"][3], 2000, 10, torch)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(args, args.cpu_seconds)
+        one = oracle_sample(args, args.cpu_seconds_one_core, threads=1)
+        line["cpu_baseline"]["one_core"] = {"value": one["value"], "unit": UNIT, "cores": one["cores"],
+                                            "sample": one["sample"]}
     print(json.dumps(line), flush=True)
     lat.close()
     if dist:

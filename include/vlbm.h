@@ -204,6 +204,16 @@ int vlbm_launch_count(const vlbm_handle* h, int64_t* count);
 #define VLBM_OPT_ROUNDING_16 2
 int vlbm_set_option(vlbm_handle* h, int32_t key, int64_t value);
 
+/* Vorticity diagnostic of the current state: out[0] = sum over nodes of
+ * |curl u|^2 dx^d, u = q / rho, with centred differences (periodic) of spacing
+ * dx; in 2D the scalar vorticity d_x u_y - d_y u_x.  With the kinetic energy E of
+ * vlbm_invariants it gives the energy balance of the incompressible limit,
+ * -dE/dt = nu * sum |curl u|^2 dx^d (not an operation of the paper: a diagnostic
+ * of its Navier-Stokes target).  The velocity is formed in FP32 in the handle's
+ * staging buffer (allocated on first use), the differences and sums in FP64.
+ * out: 1 double, host or device memory (host: the call synchronises the stream). */
+int vlbm_vorticity_sq(vlbm_handle* h, double* out);
+
 /* The reduction of vlbm_invariants for callers that cannot allocate device
  * memory: code running inside a pool or arena that owns all device memory,
  * in a real-time loop that may not take the allocator's locks or its implicit

@@ -131,6 +131,8 @@ class Oracle:
         L = self.lib
         P = ctypes.POINTER(_CParams)
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
+        L.orc_set_num_threads.restype = None
         L.orc_equilibrium.argtypes = [P, ctypes.c_double, _D, _D]
         L.orc_collide_nodes.argtypes = [P, ctypes.c_long, _D, _D, ctypes.c_int]
         L.orc_collide_lattice.argtypes = [P, _D, _D, ctypes.c_int]
@@ -142,6 +144,10 @@ class Oracle:
 
     def num_threads(self) -> int:
         return int(self.lib.orc_num_threads())
+
+    def set_num_threads(self, n: int) -> None:
+        """Threads of the OpenMP loops (timing only; results do not depend on it)."""
+        self.lib.orc_set_num_threads(int(n))
 
     def equilibrium(self, p: Params, rho: float, q) -> np.ndarray:
         c = p.to_c()

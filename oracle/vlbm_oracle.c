@@ -48,6 +48,17 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads of the OpenMP loops (timing only: the step has no reductions, so the
+ * result does not depend on the thread count). */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Pressure law P(rho) = rho^gamma, gamma >= 1 (Section 2, footnote). */
 static double pressure(const orc_params* p, double rho) { return pow(rho, p->gamma); }
 

@@ -40,6 +40,7 @@ int  orc_q(const orc_params* p);        /* velocities per field */
 int  orc_fields(const orc_params* p);   /* dim + 1 */
 long orc_nodes(const orc_params* p);
 int  orc_num_threads(void);
+void orc_set_num_threads(int n);
 
 /* Equilibrium of one node: feq[k * Q + l]. */
 void orc_equilibrium(const orc_params* p, double rho, const double* q, double* feq);

@@ -90,6 +90,10 @@ class Lattice:
     def invariants(self):
         return _binding.vlbm_invariants(self.handle)
 
+    def vorticity_sq(self):
+        """Sum over nodes of |curl u|^2 dx^d (centred differences): -dE/dt = nu times this."""
+        return _binding.vlbm_vorticity_sq(self.handle)
+
     def populations(self, deviation=False, dtype=None, device="cuda"):
         t = self._torch
         q = 2 * self.dim + 1

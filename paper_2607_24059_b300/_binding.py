@@ -60,7 +60,7 @@ EXPORTED = [
     "vlbm_params_default", "vlbm_params_check", "vlbm_create", "vlbm_destroy", "vlbm_set_stream",
     "vlbm_init", "vlbm_step", "vlbm_step_record", "vlbm_macros", "vlbm_invariants", "vlbm_time", "vlbm_state_bytes",
     "vlbm_get_state", "vlbm_set_state", "vlbm_get_populations", "vlbm_launch_count", "vlbm_set_option",
-    "vlbm_strerror", "vlbm_last_error", "vlbm_invariants_noalloc",
+    "vlbm_strerror", "vlbm_last_error", "vlbm_invariants_noalloc", "vlbm_vorticity_sq",
     "vlbm_batch_create", "vlbm_batch_destroy", "vlbm_batch_init", "vlbm_batch_step", "vlbm_batch_macros",
     "vlbm_batch_invariants", "vlbm_batch_set_config", "vlbm_batch_autotune", "vlbm_batch_info",
     "vlbm_batch_last_error", "vlbm_batch_init_states", "vlbm_batch_macros_states", "vlbm_tc_gemm_bf16", "vlbm_sur_conv3x3", "vlbm_sur_conv3x3_wgrad",
@@ -106,6 +106,7 @@ lib.vlbm_step.argtypes = [_H, ctypes.c_int64, ctypes.c_int32]
 lib.vlbm_step_record.argtypes = [_H, ctypes.c_int64, ctypes.c_int64, _V]
 lib.vlbm_macros.argtypes = [_H, _V, _V, _V, ctypes.c_int32]
 lib.vlbm_invariants.argtypes = [_H, _V]
+lib.vlbm_vorticity_sq.argtypes = [_H, _V]
 lib.vlbm_time.argtypes = [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
 lib.vlbm_state_bytes.argtypes = [_H]
 lib.vlbm_state_bytes.restype = ctypes.c_size_t
@@ -291,6 +292,20 @@ def vlbm_invariants(h, out=None):
     if dt != VLBM_DTYPE_F64:
         raise TypeError("invariants are float64")
     _check(lib.vlbm_invariants(h, _V(p)), "vlbm_invariants", h)
+    return out
+
+
+def vlbm_vorticity_sq(h, out=None):
+    """Sum over nodes of |curl u|^2 dx^d (centred differences); `out` = 1 float64 (host or
+    device), else returns a float."""
+    if out is None:
+        buf = np.zeros(1, dtype=np.float64)
+        _check(lib.vlbm_vorticity_sq(h, _V(buf.ctypes.data)), "vlbm_vorticity_sq", h)
+        return float(buf[0])
+    p, dt = _ptr_dtype(out)
+    if dt != VLBM_DTYPE_F64:
+        raise TypeError("the vorticity sum is float64")
+    _check(lib.vlbm_vorticity_sq(h, _V(p)), "vlbm_vorticity_sq", h)
     return out
 
 

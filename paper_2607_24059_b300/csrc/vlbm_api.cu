@@ -686,6 +686,35 @@ extern "C" int vlbm_invariants(vlbm_handle* h, double* out) {
     return VLBM_OK;
 }
 
+// ------------------------------------------------------------------ vorticity
+extern "C" int vlbm_vorticity_sq(vlbm_handle* h, double* out) {
+    if (!h || !out) return VLBM_EINVAL;
+    const int64_t N = h->d.nodes;
+    const int dim = h->p.dim;
+    int rc = ensure_staging(h, (size_t)dim * N * sizeof(float));
+    if (rc) return rc;
+    float* u = (float*)h->staging;
+    VLBM_DISPATCH_STORAGE(h, macros_dispatch, h, nullptr, u, nullptr, VLBM_DTYPE_F32);
+    rc = check_launch(h, "macros");
+    if (rc) return rc;
+    const int blocks = (int)inv_blocks(h);
+    k_vorticity_sq<<<blocks, kThreads, 0, h->stream>>>(u, (int)h->p.n[0], (int)h->p.n[1],
+                                                        dim == 3 ? (int)h->p.n[2] : 1, dim, h->partials);
+    const double inv2dx = 0.5 / h->p.dx;
+    const double scale = inv2dx * inv2dx * std::pow(h->p.dx, (double)dim);
+    const bool dev = is_device_pointer(out);
+    k_sum_rows<<<1, kThreads, 0, h->stream>>>(h->partials, blocks, scale, dev ? out : h->inv_dev);
+    h->launches += 3;
+    rc = check_launch(h, "vorticity");
+    if (rc) return rc;
+    if (!dev) {
+        VLBM_CUDA(h, cudaMemcpyAsync(h->inv_host, h->inv_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        VLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        *out = h->inv_host[0];
+    }
+    return VLBM_OK;
+}
+
 // ------------------------------------------------------------------ time / state
 extern "C" int vlbm_time(const vlbm_handle* h, int64_t* step, double* t) {
     if (!h) return VLBM_EINVAL;

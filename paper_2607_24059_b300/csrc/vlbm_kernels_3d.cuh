@@ -274,4 +274,59 @@ k_invariants_3d(const char* __restrict__ f_b, long long plane, Coef<typename Sto
     block_reduce_store(acc, partials);
 }
 
+// ------------------------------------------------------------------------------
+// Vorticity diagnostic: per-block FP64 sums of |curl u|^2 with centred differences
+// (periodic), u [dim][nz][ny][nx] FP32 (2D: nz = 1, the scalar d_x u_y - d_y u_x).
+// The differences are taken in FP64 from the FP32 velocities; the caller scales by
+// 1 / (2 dx)^2 and dx^d.  Used every few hundred steps, not on the step path.
+static __global__ void __launch_bounds__(kThreads)
+k_vorticity_sq(const float* __restrict__ u, int nx, int ny, int nz, int dim, double* __restrict__ partials) {
+    __shared__ double sh[kThreads];
+    const long long N = (long long)nx * ny * nz;
+    double acc = 0.0;
+    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < N;
+         node += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(node % nx);
+        const long long r = node / nx;
+        const int y = (int)(r % ny), z = (int)(r / ny);
+        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+        auto U = [&](int c, int xx, int yy, int zz) {
+            return (double)__ldg(u + (long long)c * N + ((long long)zz * ny + yy) * nx + xx);
+        };
+        if (dim == 2) {
+            const double w = (U(1, xp, y, z) - U(1, xm, y, z)) - (U(0, x, yp, z) - U(0, x, ym, z));
+            acc += w * w;
+        } else {
+            const double wx = (U(2, x, yp, z) - U(2, x, ym, z)) - (U(1, x, y, zp) - U(1, x, y, zm));
+            const double wy = (U(0, x, y, zp) - U(0, x, y, zm)) - (U(2, xp, y, z) - U(2, xm, y, z));
+            const double wz = (U(1, xp, y, z) - U(1, xm, y, z)) - (U(0, x, yp, z) - U(0, x, ym, z));
+            acc += wx * wx + wy * wy + wz * wz;
+        }
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int stride = kThreads / 2; stride > 0; stride >>= 1) {
+        if ((int)threadIdx.x < stride) sh[threadIdx.x] += sh[threadIdx.x + stride];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+// One block: out[0] = scale * (sum of rows[0 .. n)), in a fixed order.
+static __global__ void __launch_bounds__(kThreads)
+k_sum_rows(const double* __restrict__ rows, int n, double scale, double* __restrict__ out) {
+    __shared__ double sh[kThreads];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += kThreads) a += rows[i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int stride = kThreads / 2; stride > 0; stride >>= 1) {
+        if ((int)threadIdx.x < stride) sh[threadIdx.x] += sh[threadIdx.x + stride];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0] * scale;
+}
+
 }  // namespace vlbm

@@ -137,9 +137,9 @@ def test_vector_and_generic_kernels_agree(n, precision):
             assert np.max(np.abs(x - y)) <= rel * np.max(np.abs(y))
     elif precision == "fp64":
         # same arithmetic; the compiler may fuse a multiply and an add into one FMA in one
-        # kernel and not in the other (about one FP64 rounding per step)
+        # kernel and not in the other: about one FP64 rounding per step, 77 steps
         for x, y in zip(a, b):
-            assert np.max(np.abs(x - y)) <= 1e-14 * max(np.max(np.abs(y)), 1e-300)
+            assert np.max(np.abs(x - y)) <= 1e-13 * max(np.max(np.abs(y)), 1e-300)
     else:
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
@@ -577,3 +577,76 @@ def test_d3q7_energy_history_matches_oracle(orc, precision, tol):
     diss_g = -(e_gpu[2:] - e_gpu[:-2]) / (2 * dt)
     assert np.all(diss_o > 0)
     assert np.max(np.abs(diss_g - diss_o)) <= (1e-9 if precision == "fp64" else 2e-2) * np.max(diss_o)
+
+
+# ------------------------------------------------------------ vorticity diagnostic
+
+@pytest.mark.parametrize("dim,n", [(2, 64), (3, 32)])
+def test_vorticity_sq_closed_form_at_taylor_green(dim, n):
+    """At the Taylor-Green initial state the centred differences of the half-integer lattice give
+    sum |curl u|^2 dx^d = (sin(dx)/dx)^2 * integral |curl u|^2 exactly for these single modes:
+    2D curl u = 2 sin x sin y (integral 4 pi^2); 3D curl u = (-cos x sin y sin z, -sin x cos y sin z,
+    2 sin x sin y cos z) (integral 6 pi^3)."""
+    if dim == 2:
+        u, phi, dx = synthetic.taylor_green_2d(n)
+        exact = 4.0 * math.pi ** 2
+    else:
+        u, phi, dx = synthetic.taylor_green_3d(n)
+        exact = 6.0 * math.pi ** 3
+    s = math.sin(dx) / dx
+    for precision in ("fp64", "fp32"):
+        lat = v.Lattice((n,) * dim, dx, nu=0.01, precision=precision)
+        lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+        got = lat.vorticity_sq()
+        dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+        v.vlbm_vorticity_sq(lat.handle, dev)
+        lat.close()
+        assert abs(got - s * s * exact) <= 1e-6 * exact, (precision, got, s * s * exact)
+        assert dev.item() == got
+
+
+def test_vorticity_sq_matches_centred_differences_of_the_state():
+    n = (48, 40)
+    u, phi = smooth_random_state(n, seed=77)
+    op = resolved(n, 0.05, nu=0.02)
+    lat = gpu_lattice(op, "fp64")
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    lat.step(30)
+    got = lat.vorticity_sq()
+    uu = lat.macros()[1].cpu().numpy()
+    lat.close()
+    w = (np.roll(uu[1], -1, 1) - np.roll(uu[1], 1, 1)) - (np.roll(uu[0], -1, 0) - np.roll(uu[0], 1, 0))
+    ref = float(np.sum((w / (2 * op.dx)) ** 2) * op.dx ** 2)
+    assert abs(got - ref) <= 1e-6 * ref        # the kernel differences FP32 velocities
+
+
+def test_energy_balance_of_the_taylor_green_vortex(orc):
+    """Dissipation diagnostics of the 64^2 Taylor-Green vortex after 220 steps, against the oracle:
+    sum |curl u|^2 dx^2 from the oracle's velocity (centred differences), and -dE/dt from the
+    oracle's energies 20 steps before and after.  The two sides of the incompressible energy
+    balance -dE/dt = nu sum |curl u|^2 dx^2 then agree to the scheme's own discretisation and
+    compressibility error at this resolution (5 % measured; bounded here by 10 %)."""
+    n = 64
+    u, phi, dx = synthetic.taylor_green_2d(n)
+    nu = 0.01
+    op = resolved((n, n), dx, nu=nu)
+    lat = gpu_lattice(op, "fp64")
+    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    lat.step(200)
+    e0, t0 = lat.invariants()[4], lat.time()[1]
+    lat.step(20)
+    w2 = lat.vorticity_sq()
+    lat.step(20)
+    e1, t1 = lat.invariants()[4], lat.time()[1]
+    lat.close()
+    f = orc.run(op, orc.init(op, u, phi), 200)
+    e0o = orc.invariants(op, f)[4]
+    f = orc.run(op, f, 20)
+    uo = orc.macros(op, f)[1]
+    wo = (np.roll(uo[1], -1, 1) - np.roll(uo[1], 1, 1)) - (np.roll(uo[0], -1, 0) - np.roll(uo[0], 1, 0))
+    w2o = float(np.sum((wo / (2 * dx)) ** 2) * dx ** 2)
+    e1o = orc.invariants(op, orc.run(op, f, 20))[4]
+    assert abs(w2 - w2o) <= 1e-6 * w2o                    # the kernel differences FP32 velocities
+    dEdt, dEdto = -(e1 - e0) / (t1 - t0), -(e1o - e0o) / (t1 - t0)
+    assert abs(dEdt - dEdto) <= 1e-8 * dEdto              # a difference of two nearby energies
+    assert abs(dEdt - nu * w2) <= 0.1 * nu * w2
