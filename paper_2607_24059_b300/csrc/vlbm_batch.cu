@@ -74,7 +74,9 @@ k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
         if constexpr (SPLIT)
             warp_split_step_2d<S, V, false>(fin, fout, P.nx, P.ny, y, seg, lane, k, unused);
         else
-            warp_stream_collide_2d<S, false, false>(fin, fout, P.nx, P.ny, y, seg, lane, k, unused, key);
+            warp_stream_collide_2d<S, false, Vec16<S>::V, false>(reinterpret_cast<const S*>(in_base + P.offset),
+                                             reinterpret_cast<S*>(out_base + P.offset), P.plane, P.nx, P.ny, y, seg,
+                                             lane, k, unused, key);
     }
 }
 

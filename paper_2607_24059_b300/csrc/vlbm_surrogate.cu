@@ -35,7 +35,7 @@ k_tc_gemm_bf16(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restr
                int N, int K, int* __restrict__ err) {
     __shared__ __align__(1024) uint8_t sA[128 * kKChunk * 2];
     __shared__ __align__(1024) uint8_t sB[256 * kKChunk * 2];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar, drain;
     __shared__ uint32_t s_taddr;
     const int tid = threadIdx.x, warp = tid >> 5;
     const long long m0 = (long long)blockIdx.x * 128;
@@ -45,7 +45,10 @@ k_tc_gemm_bf16(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restr
         tc::tmem_alloc(&s_taddr, ncols);
         tc::tmem_relinquish();
     }
-    if (tid == 0) tc::mbar_init(&bar, 1);
+    if (tid == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::mbar_init(&drain, 1);
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -80,14 +83,13 @@ k_tc_gemm_bf16(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restr
             }
             tc::mma_commit(&bar);
         }
-        // every thread waits: the staging buffers are rewritten next round
-        if (!tc::mbar_wait(&bar, phase, kWaitPolls)) {
-            ok = false;
-            atomicExch(err, 1);
-        }
+        // every thread waits: the staging buffers are rewritten next round; a wait that gives
+        // up in any thread stops the whole block (the loop's barriers stay matched)
+        if (!tc::mbar_wait(&bar, phase, kWaitPolls)) ok = false;
         phase ^= 1;
-        __syncthreads();
+        ok = __syncthreads_and(ok);
     }
+    if (!ok && tid == 0) atomicExch(err, 1);
 
     if (ok) {
         tc::fence_after_sync();
@@ -99,6 +101,12 @@ k_tc_gemm_bf16(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restr
 #pragma unroll
             for (int j = 0; j < 16; ++j) D[row * N + c + j] = v[j];
         }
+    }
+    // also after a wait that gave up: every MMA the issuing thread committed has completed
+    // (bounded wait) before the tensor memory is released and the block exits
+    if (tid == 0) {
+        tc::mma_commit(&drain);
+        if (!tc::mbar_wait(&drain, 0, kWaitPolls)) atomicExch(err, 1);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -715,7 +723,12 @@ k_conv3x3_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __rest
                 }
             tc::mma_commit(&empty[s]);
         }
-        if (ok && n > 0) tc::mma_commit(&done);          // arrives once every MMA above has completed
+        // arrives once every MMA above has completed; the issuer waits for it (bounded) also after
+        // an abort, so that no MMA still targets the tensor memory released below
+        if (n > 0) {
+            tc::mma_commit(&done);
+            if (!tc::mbar_wait(&done, 0, kWaitPolls)) raise_abort(abort, err);
+        }
     }
     // ---------------- epilogue: the producer warps add the partial sums ----------------
     if (warp < C::PRODUCERS / 32 && n > 0) {
