@@ -92,6 +92,9 @@ def parse_args():
     ap.add_argument("--sur-trajectories", type=int, default=200, help="sur256: training trajectories (100 pairs each)")
     ap.add_argument("--sur-epochs", type=float, default=8.0, help="sur256: training epochs")
     ap.add_argument("--sur-batch", type=int, default=32, help="sur256: states advanced together in the timed rollouts")
+    ap.add_argument("--sur-k", type=int, default=32,
+                    help="sur256: fine lattice steps per surrogate step (a multiple of 16); the rollout covers "
+                         "3200 fine steps (3072 for K = 256)")
     ap.add_argument("--conv-only", action="store_true",
                     help="sur256: time only the dominant kernel (the 64 -> 64 conv of the rollout) and the "
                          "training step's weight gradient of that conv, no training")
@@ -657,7 +660,8 @@ def run_surrogate(args):
                               "wgrad": wgrad_roofline(args.sur_batch, args.n // 4, stream)}), flush=True)
         return 0
     dist = dist_init(world, "nccl")
-    cfg = sg.Config(fine=args.n, train_trajectories=args.sur_trajectories, epochs=args.sur_epochs)
+    cfg = sg.Config(fine=args.n, train_trajectories=args.sur_trajectories, epochs=args.sur_epochs,
+                    k_fine=args.sur_k, rollout_steps=max(1, 3200 // args.sur_k))
     tr = sg.train_surrogate(cfg, log=lambda m: print(m, file=sys.stderr, flush=True))
     net, nb, steps = tr.net, args.sur_batch, cfg.rollout_steps
     ref = tr.test_snaps.transpose(0, 1).contiguous()              # (steps + 1, states, C, c, c)
@@ -708,6 +712,24 @@ def run_surrogate(args):
     c = cfg.coarse
     roof = conv_roofline(nb, c, stream)
     ro.close()
+    # the plain scheme on the coarse lattice with the same batching (nb states, one launch per step)
+    cb = vlbm.Batch([dict(n=(c, c), dx=2 * math.pi / c, nu=cfg.nu)] * nb, precision="fp32")
+    mask = torch.ones(nb, dtype=torch.uint8, device=u0.device)
+    outs = torch.empty_like(u0)
+
+    def coarse_batch_run():
+        vlbm.vlbm_batch_init_states(cb.handle, u0, mask)
+        cb.step(steps * cfg.coarse_steps)
+        vlbm.vlbm_batch_macros_states(cb.handle, outs, mask)
+    coarse_batch_run()
+    c0e, c1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0e.record(stream)
+    for _ in range(args.steps):
+        coarse_batch_run()
+    c1e.record(stream)
+    torch.cuda.synchronize()
+    coarse_ms_per_state = c0e.elapsed_time(c1e) / args.steps / nb
+    cb.close()
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -728,6 +750,8 @@ def run_surrogate(args):
             "l2_rel_error_coarse_scheme": float(np.mean(coarse_err)),
             "fallbacks_per_state_step": fallbacks / (args.steps * nb * steps),
             "fine_fp32_ms_per_state": t_fine, "surrogate_ms_per_state": ms_per_state,
+            "coarse_fp32_ms_per_state_same_batching": coarse_ms_per_state,
+            "coarse_scheme_speedup_same_batching": t_fine / coarse_ms_per_state,
             "l2": "rollout states 32 x 3 x 256^2 FP32 = 25 MB (L2-resident, as in use)"},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "x time-to-t speedup per state vs plain FP32 LBM 1024^2",

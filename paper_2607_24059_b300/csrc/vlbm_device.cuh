@@ -127,7 +127,19 @@ struct Coef {
     C gamma;
     int gamma_one;         // gamma == 1: dP = dr / (2 mu) exactly
     int sr16;              // shifted 16-bit storage: rest populations rounded stochastically (else to nearest)
+    // The same coefficients in stored units, al_s = alpha scale_k and i2m_s = scale_0 / (2 mu): every
+    // term of a moving equilibrium is linear in (alpha, 1/(2 mu)), so equilibria built on them come
+    // out multiplied by the storage scale (the split layouts use one scale for every field, 1/dx^2)
+    // and can be combined with stored non-equilibrium parts without converting them.
+    C al_s[kMaxFields];
+    C i2m_s;
 };
+
+// Coefficient selection: deviation units, or stored units (Coef::al_s, i2m_s).
+template <bool STORED, class C>
+__device__ __forceinline__ C coef_alpha(const Coef<C>& k, int f) { return STORED ? k.al_s[f] : k.al[f]; }
+template <bool STORED, class C>
+__device__ __forceinline__ C coef_i2m(const Coef<C>& k) { return STORED ? k.i2m_s : k.i2m; }
 
 // Factors from stored values to deviations (load) and back (store).  Rest planes
 // of the mixed layout are FP32 and unscaled.
@@ -239,28 +251,31 @@ __device__ __forceinline__ S sr16_store_one(float v, long long node, uint32_t ke
 
 // Equilibrium deviations g^eq of one D2Q5 node, fields (rho, q_x, q_y) x
 // velocities (rest, +x, -x, +y, -y): e[5k + l].
-template <class C, bool APPROX = false>
+// STORED: the moving entries in stored units (coef_alpha / coef_i2m); the rest entries are then not
+// meaningful (the split kernels do not use them).
+template <class C, bool APPROX = false, bool STORED = false>
 __device__ __forceinline__ void equilibrium_d2q5(const Coef<C>& k, C dr, C Qx, C Qy, C (&e)[15]) {
+    const C i2m = coef_i2m<STORED>(k);
     const C r = recip_sel<APPROX>(k.rho_bar + dr);
-    const C dP = pressure_dev(k, dr) * k.i2m;
-    const C hx = Qx * k.i2m, hy = Qy * k.i2m;
-    const C xx = Qx * Qx * r * k.i2m;
-    const C xy = Qx * Qy * r * k.i2m;
-    const C yy = Qy * Qy * r * k.i2m;
+    const C dP = pressure_dev(k, dr) * i2m;
+    const C hx = Qx * i2m, hy = Qy * i2m;
+    const C xx = Qx * Qx * r * i2m;
+    const C xy = Qx * Qy * r * i2m;
+    const C yy = Qy * Qy * r * i2m;
     // rest entries m - 4 (alpha m): the moving entries' alpha m, so the entries sum to m
-    const C ar = k.al[0] * dr;
+    const C ar = coef_alpha<STORED>(k, 0) * dr;
     e[0] = dr - C(4) * ar;
     e[1] = ar + hx;
     e[2] = ar - hx;
     e[3] = ar + hy;
     e[4] = ar - hy;
-    const C ax = k.al[1] * Qx;
+    const C ax = coef_alpha<STORED>(k, 1) * Qx;
     e[5] = Qx - C(4) * ax;
     e[6] = ax + (xx + dP);
     e[7] = ax - (xx + dP);
     e[8] = ax + xy;
     e[9] = ax - xy;
-    const C ay = k.al[2] * Qy;
+    const C ay = coef_alpha<STORED>(k, 2) * Qy;
     e[10] = Qy - C(4) * ay;
     e[11] = ay + xy;
     e[12] = ay - xy;
@@ -316,22 +331,23 @@ __device__ __forceinline__ void relax_d2q5(const Coef<C>& k, C (&g)[15], C dr, C
 // velocities (rest, +x, -x, +y, -y, +z, -z): e[7k + l].  The paper gives the
 // 2D equilibria and states that 3D follows from the Cartesian structure; this
 // is the direction-by-direction extension (rest weight 1 - 6 alpha).
-template <class C, bool APPROX = false>
+template <class C, bool APPROX = false, bool STORED = false>
 __device__ __forceinline__ void equilibrium_d3q7(const Coef<C>& k, C dr, const C (&Q)[3], C (&e)[28]) {
+    const C i2m = coef_i2m<STORED>(k);
     const C r = recip_sel<APPROX>(k.rho_bar + dr);
-    const C dP = pressure_dev(k, dr) * k.i2m;
-    const C ar = k.al[0] * dr;
+    const C dP = pressure_dev(k, dr) * i2m;
+    const C ar = coef_alpha<STORED>(k, 0) * dr;
     e[0] = dr - C(6) * ar;   // m - 6 (alpha m), as in 2D
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const C h = Q[d] * k.i2m;
+        const C h = Q[d] * i2m;
         e[1 + 2 * d] = ar + h;
         e[2 + 2 * d] = ar - h;
     }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const C a = k.al[j + 1] * Q[j];
-        const C qr = Q[j] * r * k.i2m;
+        const C a = coef_alpha<STORED>(k, j + 1) * Q[j];
+        const C qr = Q[j] * r * i2m;
         e[7 * (j + 1)] = Q[j] - C(6) * a;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {

@@ -41,6 +41,8 @@ inline Coef<C> make_coef(const vlbm_params& p, const vlbm_derived& d, const doub
     k.p_bar = (C)std::pow(p.rho_bar, p.gamma);
     k.gamma = (C)p.gamma;
     k.gamma_one = p.gamma == 1.0;
+    for (int f = 0; f < kMaxFields; ++f) k.al_s[f] = (C)((f < F ? d.alpha[f] : 0.0) * scale[f]);
+    k.i2m_s = (C)(scale[0] / (2.0 * p.mu));
     return k;
 }
 

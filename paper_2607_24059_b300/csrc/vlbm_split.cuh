@@ -20,6 +20,12 @@
 // are (1 - omega) times cell-to-cell differences of the equilibria, orders of
 // magnitude smaller, and the conserved moments, whose per-step increments are
 // tiny under the parabolic scaling, keep FP32 resolution.
+//
+// The step kernels work in stored units: every field of the split layout has
+// the storage scale s = 1/dx^2, and the moving equilibria are built on the
+// stored-unit coefficients (Coef::al_s, i2m_s), which gives s e; pulled
+// populations, own parts and new parts are then combined and stored without
+// converting each part, and only the moment increment is brought back by 1/s.
 #pragma once
 
 #include "vlbm_kernels_3d.cuh"
@@ -37,24 +43,27 @@ constexpr int kSplitV3 = 2;
 //   rho field  a_rho dr +- Q_a / (2 mu)
 //   q_j field  a_j Q_j +- (Q_j Q_a / rho + delta_ja dP) / (2 mu)
 // the same values as the l-th entries of equilibrium_d2q5 / _d3q7.
-// equilibrium_dir_r takes r = 1/rho and dP of the node (one reciprocal serves every direction).
-template <class C, int F, int L>
+// equilibrium_dir_r takes r = 1/rho and dP of the node (one reciprocal serves every direction),
+// dP in the units of the result.  STORED: stored units (s e).
+template <class C, int F, int L, bool STORED = true>
 __device__ __forceinline__ void equilibrium_dir_r(const Coef<C>& k, const C (&m)[F], C r, C dP, C (&e)[F]) {
     constexpr int a = (L - 1) / 2;
     const C s = (L & 1) ? C(1) : C(-1);
+    const C i2m = coef_i2m<STORED>(k);
     const C Qa = m[1 + a];
-    e[0] = k.al[0] * m[0] + s * (Qa * k.i2m);
-    const C qr = Qa * r * k.i2m;
+    e[0] = coef_alpha<STORED>(k, 0) * m[0] + s * (Qa * i2m);
+    const C qr = Qa * r * i2m;
 #pragma unroll
     for (int j = 0; j < F - 1; ++j) {
         const C flux = (j == a) ? (m[1 + j] * qr + dP) : m[1 + j] * qr;
-        e[1 + j] = k.al[1 + j] * m[1 + j] + s * flux;
+        e[1 + j] = coef_alpha<STORED>(k, 1 + j) * m[1 + j] + s * flux;
     }
 }
 
-template <class C, int F, int L>
+template <class C, int F, int L, bool STORED = true>
 __device__ __forceinline__ void equilibrium_dir(const Coef<C>& k, const C (&m)[F], C (&e)[F]) {
-    equilibrium_dir_r<C, F, L>(k, m, recip_sel<true>(k.rho_bar + m[0]), pressure_dev(k, m[0]) * k.i2m, e);
+    equilibrium_dir_r<C, F, L, STORED>(k, m, recip_sel<true>(k.rho_bar + m[0]),
+                                       pressure_dev(k, m[0]) * coef_i2m<STORED>(k), e);
 }
 
 template <class T, int V>
@@ -88,6 +97,7 @@ __device__ __forceinline__ void shift_from_right(C (&out)[V], const C (&own)[V],
 // Relaxation and new moments of one D2Q5 node in split form.
 //   m[3]: moments at the node; B[3][4]: pulled populations g_{k,l} (l = 1..4);
 //   nown[3]: sum_l n_{k,l} of the node's own stored non-equilibrium parts.
+// B, nown and the returned parts are in stored units; m is not.
 // Returns the new moments in m and the new non-equilibrium parts in B.  The FP32 moments
 // round to nearest: the split forms are held to the L2 gate of 1e-3, which they meet by a
 // wide margin, and these kernels are bound by their instruction count (stochastic
@@ -96,13 +106,14 @@ template <class C>
 __device__ __forceinline__ void split_update_d2q5(const Coef<C>& k, C (&m)[3], C (&B)[3][4], const C (&nown)[3]) {
     // sum_l e_{k,l}(m) = 4 alpha_k m_k: the alpha m of the moving equilibria (their
     // +- fluxes cancel), so that the update conserves m for the stored coefficients
+    const C inv_s = k.inv_scale[0];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         const C pulled = (B[f][0] + B[f][1]) + (B[f][2] + B[f][3]);
-        m[f] = m[f] + ((pulled - C(4) * (k.al[f] * m[f])) - nown[f]);
+        m[f] = m[f] + inv_s * ((pulled - C(4) * (k.al_s[f] * m[f])) - nown[f]);
     }
     C e[15];
-    equilibrium_d2q5<C, true>(k, m[0], m[1], m[2], e);
+    equilibrium_d2q5<C, true, true>(k, m[0], m[1], m[2], e);
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         const C w = C(1) - k.om[f];
@@ -173,27 +184,25 @@ __device__ __forceinline__ void warp_split_step_2d(const Layout<S, true, 5>& fin
         C m[3][V], nown[3][V], B[3][4][V];
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            const C isc = mov_load_scale<S>(k, f);
             C a[V], b[V];
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
+            for (int i = 0; i < V; ++i) {   // parts stay in stored units
                 m[f][i] = (C)mo[f][i];
-                a[i] = Storage<S>::to_c(n_px[f][i]) * isc;
-                b[i] = Storage<S>::to_c(n_mx[f][i]) * isc;
-                nown[f][i] = (a[i] + b[i]) + (Storage<S>::to_c(n_py_own[f][i]) * isc +
-                                              Storage<S>::to_c(n_my_own[f][i]) * isc);
+                a[i] = Storage<S>::to_c(n_px[f][i]);
+                b[i] = Storage<S>::to_c(n_mx[f][i]);
+                nown[f][i] = (a[i] + b[i]) + (Storage<S>::to_c(n_py_own[f][i]) + Storage<S>::to_c(n_my_own[f][i]));
             }
             // pulled non-equilibrium parts, stashed in B until the equilibria are added
             C sh[V];
-            shift_from_left<C, V>(sh, a, left_edge, Storage<S>::to_c(hn_l[f]) * isc);
+            shift_from_left<C, V>(sh, a, left_edge, Storage<S>::to_c(hn_l[f]));
 #pragma unroll
             for (int i = 0; i < V; ++i) B[f][0][i] = sh[i];
-            shift_from_right<C, V>(sh, b, right_edge, Storage<S>::to_c(hn_r[f]) * isc);
+            shift_from_right<C, V>(sh, b, right_edge, Storage<S>::to_c(hn_r[f]));
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 B[f][1][i] = sh[i];
-                B[f][2][i] = Storage<S>::to_c(n_py_pull[f][i]) * isc;
-                B[f][3][i] = Storage<S>::to_c(n_my_pull[f][i]) * isc;
+                B[f][2][i] = Storage<S>::to_c(n_py_pull[f][i]);
+                B[f][3][i] = Storage<S>::to_c(n_my_pull[f][i]);
             }
         }
         // source moments of the x neighbours by warp shuffle
@@ -256,12 +265,11 @@ __device__ __forceinline__ void warp_split_step_2d(const Layout<S, true, 5>& fin
 #pragma unroll
                 for (int i = 0; i < V; ++i) wm[i] = (float)m[f][i];
                 vstore<float, V>(fout.rest(f) + row + x0, wm);
-                const C sc = mov_store_scale<S>(k, f);
 #pragma unroll
                 for (int l = 0; l < 4; ++l) {
                     S w[V];
 #pragma unroll
-                    for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(B[f][l][i] * sc);
+                    for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(B[f][l][i]);
                     vstore<S, V>(fout.mov(f, l + 1) + row + x0, w);
                 }
             }
@@ -322,10 +330,9 @@ k_split_step_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
             C ms[3], np[3];
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                const C isc = mov_load_scale<S>(k, f);
                 ms[f] = (C)fin.rest(f)[src[l]];
-                np[f] = Storage<S>::to_c(fin.mov(f, l)[src[l]]) * isc;
-                nown[f] += Storage<S>::to_c(fin.mov(f, l)[node]) * isc;
+                np[f] = Storage<S>::to_c(fin.mov(f, l)[src[l]]);      // stored units
+                nown[f] += Storage<S>::to_c(fin.mov(f, l)[node]);
             }
             if (l == 1) pulled_d2q5<C, 1>(k, ms, np, B);
             else if (l == 2) pulled_d2q5<C, 2>(k, ms, np, B);
@@ -340,9 +347,8 @@ k_split_step_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
             fout.rest(f)[node] = (float)m[f];
-            const C sc = mov_store_scale<S>(k, f);
 #pragma unroll
-            for (int l = 0; l < 4; ++l) fout.mov(f, l + 1)[node] = Storage<S>::from_c(B[f][l] * sc);
+            for (int l = 0; l < 4; ++l) fout.mov(f, l + 1)[node] = Storage<S>::from_c(B[f][l]);
         }
     }
     if (DIAG) block_reduce_finish(acc, sink);
@@ -351,14 +357,15 @@ k_split_step_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
 // ------------------------------------------------------------------------------ 3D
 template <class C>
 __device__ __forceinline__ void split_update_d3q7(const Coef<C>& k, C (&m)[4], C (&B)[4][6], const C (&nown)[4]) {
+    const C inv_s = k.inv_scale[0];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const C pulled = ((B[f][0] + B[f][1]) + (B[f][2] + B[f][3])) + (B[f][4] + B[f][5]);
-        m[f] = m[f] + ((pulled - C(6) * (k.al[f] * m[f])) - nown[f]);
+        m[f] = m[f] + inv_s * ((pulled - C(6) * (k.al_s[f] * m[f])) - nown[f]);
     }
     C e[28];
     const C Q[3] = {m[1], m[2], m[3]};
-    equilibrium_d3q7<C, true>(k, m[0], Q, e);
+    equilibrium_d3q7<C, true, true>(k, m[0], Q, e);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const C w = C(1) - k.om[f];
@@ -434,16 +441,15 @@ k_split_step_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, i
             for (int f = 0; f < 4; ++f) {
                 const float* mp = fin.rest(f);
                 const S* npl = fin.mov(f, l);
-                const C isc = mov_load_scale<S>(k, f);
                 C own[V];
-                load_vec_c<S, V>(own, npl + row + x0, active, isc);
+                load_vec_c<S, V>(own, npl + row + x0, active, C(1));   // stored units
 #pragma unroll
                 for (int i = 0; i < V; ++i) nown[f][i] += own[i];
                 if (l == 1) {
                     C em = C(0), en = C(0);
                     if (left_edge) {
                         em = (C)mp[row + xm];
-                        en = Storage<S>::to_c(npl[row + xm]) * isc;
+                        en = Storage<S>::to_c(npl[row + xm]);
                     }
                     shift_from_left<C, V>(ms[f], m[f], left_edge, em);
                     shift_from_left<C, V>(np[f], own, left_edge, en);
@@ -451,13 +457,13 @@ k_split_step_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, i
                     C em = C(0), en = C(0);
                     if (right_edge) {
                         em = (C)mp[row + xp];
-                        en = Storage<S>::to_c(npl[row + xp]) * isc;
+                        en = Storage<S>::to_c(npl[row + xp]);
                     }
                     shift_from_right<C, V>(ms[f], m[f], right_edge, em);
                     shift_from_right<C, V>(np[f], own, right_edge, en);
                 } else {
                     load_vec_c<float, V>(ms[f], mp + src_row[l] + x0, active, C(1));
-                    load_vec_c<S, V>(np[f], npl + src_row[l] + x0, active, isc);
+                    load_vec_c<S, V>(np[f], npl + src_row[l] + x0, active, C(1));
                 }
             }
 #pragma unroll
@@ -498,12 +504,11 @@ k_split_step_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, i
 #pragma unroll
                 for (int i = 0; i < V; ++i) wm[i] = (float)m[f][i];
                 vstore<float, V>(fout.rest(f) + row + x0, wm);
-                const C sc = mov_store_scale<S>(k, f);
 #pragma unroll
                 for (int l = 0; l < 6; ++l) {
                     S w[V];
 #pragma unroll
-                    for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(B[f][l][i] * sc);
+                    for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(B[f][l][i]);
                     vstore<S, V>(fout.mov(f, l + 1) + row + x0, w);
                 }
             }
@@ -549,10 +554,9 @@ k_split_step_3d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
             C ms[4], np[4];
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-                const C isc = mov_load_scale<S>(k, f);
                 ms[f] = (C)fin.rest(f)[src[l]];
-                np[f] = Storage<S>::to_c(fin.mov(f, l)[src[l]]) * isc;
-                nown[f] += Storage<S>::to_c(fin.mov(f, l)[node]) * isc;
+                np[f] = Storage<S>::to_c(fin.mov(f, l)[src[l]]);      // stored units
+                nown[f] += Storage<S>::to_c(fin.mov(f, l)[node]);
             }
             pulled_d3q7_l(k, l, ms, np, B);
         }
@@ -564,9 +568,8 @@ k_split_step_3d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             fout.rest(f)[node] = (float)m[f];
-            const C sc = mov_store_scale<S>(k, f);
 #pragma unroll
-            for (int l = 0; l < 6; ++l) fout.mov(f, l + 1)[node] = Storage<S>::from_c(B[f][l] * sc);
+            for (int l = 0; l < 6; ++l) fout.mov(f, l + 1)[node] = Storage<S>::from_c(B[f][l]);
         }
     }
     if (DIAG) block_reduce_finish(acc, sink);
