@@ -141,12 +141,15 @@ int vlbm_step(vlbm_handle* h, int64_t nsteps, int32_t flags);
  * produces (time step0 + s + 1: the moments of the transported populations,
  * which relaxation conserves) into history[(s / every) * 8 + i], in the
  * layout of vlbm_invariants.  The reduction is fused into the step kernel:
- * it reads no lattice data beyond what the step reads (row a6 of the hot
- * path), plus one small final-reduction kernel per record.  history holds
- * ceil(nsteps / every) records; it may be device memory, pinned host memory
- * (written asynchronously: valid once the handle's stream has synchronised)
- * or pageable host memory (the call synchronises before returning).
- * every >= 1; nsteps = 0 records nothing. */
+ * it reads no lattice data beyond what the step reads, and the kernel's
+ * last block folds the partial sums into the record (one launch per
+ * record).  history holds ceil(nsteps / every) records; it may be device
+ * memory, pinned host memory (written asynchronously: valid once the
+ * handle's stream has synchronised; page-locked memory mapped into the
+ * device's address space is written by the step kernel itself, other
+ * page-locked memory by a copy after each record) or pageable host memory
+ * (the call synchronises before returning).  every >= 1; nsteps = 0
+ * records nothing. */
 int vlbm_step_record(vlbm_handle* h, int64_t nsteps, int64_t every, double* history);
 
 /* Macroscopic fields at the current step: rho, u = q / rho and

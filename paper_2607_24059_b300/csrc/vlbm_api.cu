@@ -185,7 +185,10 @@ static int vec_width(const vlbm_handle* h) {
 
 static bool use_vec(const vlbm_handle* h) {
     if (h->kernel_variant == 1) return false;
-    return h->p.n[0] % vec_width(h) == 0 && (h->p.dim == 2 || h->p.dim == 3);
+    const int64_t nx = h->p.n[0], v = vec_width(h);
+    const int64_t items = h->d.nodes / nx * ((nx / v + 31) / 32);     // warp work items (32-bit in the kernels)
+    return nx % v == 0 && (h->p.dim == 2 || h->p.dim == 3) && items < (int64_t(1) << 32) &&
+           h->d.nodes < (int64_t(1) << 32);     // 32-bit node offsets
 }
 
 // Nodes per lane of the vectorised step with fused diagnostics (DiagVec: 2 for 2D FP32).
@@ -464,20 +467,21 @@ static void launch_step_on(vlbm_handle* h, cudaStream_t s, int src, double* out)
     if constexpr (M) {
         if (h->p.dim == 2) {
             if (vec && h->split_lanes == 2)
-                go(k_split_step_2d_vec<S, 2, DIAG>, fin, fout, (int)nx, (int)ny, plane, wpr, k);
+                go(k_split_step_2d_vec<S, 2, DIAG>, fin, fout, (int)nx, (int)ny, plane, FastDiv::make(wpr), k);
             else if (vec)
-                go(k_split_step_2d_vec<S, 4, DIAG>, fin, fout, (int)nx, (int)ny, plane, wpr, k);
+                go(k_split_step_2d_vec<S, 4, DIAG>, fin, fout, (int)nx, (int)ny, plane, FastDiv::make(wpr), k);
             else
                 go(k_split_step_2d_generic<S, DIAG>, fin, fout, (int)nx, (int)ny, plane, k);
         } else {
             if (vec)
-                go(k_split_step_3d_vec<S, DIAG>, fin, fout, (int)nx, (int)ny, (int)nz, plane, wpr, k);
+                go(k_split_step_3d_vec<S, DIAG>, split_planes<S, 7>(fin, fout, plane), (int)nx, (int)ny, (int)nz,
+                   FastDiv::make(wpr), FastDiv::make((uint32_t)ny), k);
             else
                 go(k_split_step_3d_generic<S, DIAG>, fin, fout, (int)nx, (int)ny, (int)nz, plane, k);
         }
     } else if (h->p.dim == 2) {
         if (vec)
-            go(k_stream_collide_2d_vec<S, M, DIAG>, fin, fout, (int)nx, (int)ny, plane, wpr, k);
+            go(k_stream_collide_2d_vec<S, M, DIAG>, fin, fout, (int)nx, (int)ny, plane, FastDiv::make(wpr), k);
         else
             go(k_stream_collide_2d_generic<S, M, DIAG>, fin, fout, (int)nx, (int)ny, plane, k);
     } else {
@@ -582,14 +586,18 @@ static void launch_final(vlbm_handle* h, int nblocks, double* out_dev);
 // Pointer kinds for outputs: device, pinned (page-locked) host, pageable host.
 enum PtrKind { kDevice, kPinned, kPageable };
 
-static PtrKind pointer_kind(const void* ptr) {
+static PtrKind pointer_kind(const void* ptr, void** device_view = nullptr) {
     cudaPointerAttributes a;
+    if (device_view) *device_view = nullptr;
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
         cudaGetLastError();
         return kPageable;
     }
     if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return kDevice;
-    if (a.type == cudaMemoryTypeHost) return kPinned;
+    if (a.type == cudaMemoryTypeHost) {
+        if (device_view) *device_view = a.devicePointer;   // page-locked memory mapped for the device
+        return kPinned;
+    }
     return kPageable;
 }
 
@@ -597,8 +605,15 @@ extern "C" int vlbm_step_record(vlbm_handle* h, int64_t nsteps, int64_t every, d
     if (!h || nsteps < 0 || every < 1 || (nsteps > 0 && !history)) return VLBM_EINVAL;
     if (nsteps == 0) return VLBM_OK;
     const int64_t records = (nsteps + every - 1) / every;
-    const PtrKind kind = pointer_kind(history);
+    void* mapped = nullptr;
+    PtrKind kind = pointer_kind(history, &mapped);
     double* rec = history;
+    if (kind == kPinned && mapped) {
+        // page-locked host memory mapped into the device's address space: the step kernel's
+        // final fold writes each record there itself, so no copy follows the step in the stream
+        rec = static_cast<double*>(mapped);
+        kind = kDevice;
+    }
     if (kind != kDevice) {
         if (h->hist_capacity < records) {
             if (h->hist) {

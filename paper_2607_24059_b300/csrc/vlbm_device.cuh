@@ -51,6 +51,18 @@ template <> struct Storage<__half> {
     static __device__ __forceinline__ float to_c(__half v) { return __half2float(v); }
     static __device__ __forceinline__ __half from_c(float v) { return __float2half_rn(v); }
     static __device__ __forceinline__ __half from_bits(uint32_t b) { return __ushort_as_half((unsigned short)b); }
+    // two packed values (element 0 in the low half) to a float pair and back, rounding to nearest
+    static __device__ __forceinline__ float2 unpack2(uint32_t w) {
+        __half2 h;
+        memcpy(&h, &w, 4);
+        return __half22float2(h);
+    }
+    static __device__ __forceinline__ uint32_t pack2(float2 v) {
+        const __half2 h = __float22half2_rn(v);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
     static __device__ __forceinline__ uint32_t pack2_sr(float lo, float hi, uint32_t r) {
         uint32_t d;
         asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
@@ -64,6 +76,16 @@ template <> struct Storage<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 from_c(float v) { return __float2bfloat16_rn(v); }
     static __device__ __forceinline__ __nv_bfloat16 from_bits(uint32_t b) {
         return __ushort_as_bfloat16((unsigned short)b);
+    }
+    // a bfloat16 is the upper half of the binary32 with the same value
+    static __device__ __forceinline__ float2 unpack2(uint32_t w) {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+    static __device__ __forceinline__ uint32_t pack2(float2 v) {
+        const __nv_bfloat162 h = __float22bfloat162_rn(v);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
     }
     static __device__ __forceinline__ uint32_t pack2_sr(float lo, float hi, uint32_t r) {
         uint32_t d;
@@ -80,6 +102,22 @@ template <class S> struct StochasticMoments { static constexpr bool value = std:
 // conversion (Coef::sr16, off by default).
 template <class S> struct StochasticStore16 {
     static constexpr bool value = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
+};
+
+// ---------------------------------------------------------------- index division
+// n / d for 32-bit unsigned n by one multiply-high: with M = ceil(2^64 / d), floor(M n / 2^64)
+// is exactly floor(n / d) for every 32-bit n and d (Lemire, Kaser and Kurz, "Faster remainder
+// by direct computation", 2019).  The kernels split a warp's work item into (segment, row, plane)
+// with it instead of 64-bit division.  d = 1 keeps M = 0 and returns n.
+struct FastDiv {
+    uint32_t d;
+    unsigned long long M;
+    static FastDiv make(uint32_t d) {
+        return FastDiv{d, d <= 1 ? 0ull : ~0ull / d + 1ull};
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t n) const {
+        return M ? (uint32_t)__umul64hi(M, (unsigned long long)n) : n;
+    }
 };
 
 // ---------------------------------------------------------------- lattice layout
@@ -133,6 +171,11 @@ struct Coef {
     // and can be combined with stored non-equilibrium parts without converting them.
     C al_s[kMaxFields];
     C i2m_s;
+    // Single-precision pairs (both halves equal) for the paired FP32 instructions of the split
+    // kernels, which update two nodes per instruction: al_s, -4 al_s (2D rest weight, exact),
+    // 1 - omega_k, -(1 - omega_k) al_s, i2m_s, rho_bar and 1 / scale.
+    float2 p_al[kMaxFields], p_nal4[kMaxFields], p_w[kMaxFields], p_nwal[kMaxFields];
+    float2 p_i2m, p_rho_bar, p_inv_s;
 };
 
 // Coefficient selection: deviation units, or stored units (Coef::al_s, i2m_s).
@@ -437,6 +480,7 @@ struct Acc {
         mx = bad = C(0);
     }
     __device__ __forceinline__ void add(int i, C x) { two_sum_acc(hi[i], lo[i], x); }
+    __device__ __forceinline__ Acc fold() const { return *this; }
 };
 
 // A node holds a non-finite population exactly when one of its field sums is
@@ -464,6 +508,94 @@ __device__ __forceinline__ void accumulate_node(Acc<C>& acc, bool finite, C dr, 
     }
     acc.add(4, C(0.5) * q2 * r);
     acc.mx = fmax(acc.mx, q2 * r * r);
+}
+
+// ---------------------------------------------------------------- paired single precision
+// Blackwell executes two independent FP32 additions, multiplications or fused multiply-adds
+// in one instruction (FADD2 / FMUL2 / FFMA2, each half rounded to nearest as its scalar
+// form).  Every node of a lane runs the same arithmetic, so the instruction-bound kernels
+// (the split steps, the fused diagnostics) let nodes (2p, 2p + 1) of a lane share each
+// instruction.  The helpers below have a scalar and a pair overload with the same rounding,
+// so one template body serves the pairs and the lone halo nodes of the warp edges, and a
+// node's outgoing populations come out bit for bit the same whichever lane computes them.
+__device__ __forceinline__ float p_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float p_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float p_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float p_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float p_neg(float a) { return -a; }
+__device__ __forceinline__ float p_rcp(float x) { return recip_sel<true>(x); }
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __fadd2_rn(a, p_neg(b)); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_rcp(float2 x) { return make_float2(recip_sel<true>(x.x), recip_sel<true>(x.y)); }
+
+// A coefficient as the operand type: its scalar, or its pre-duplicated pair.
+template <class T> __device__ __forceinline__ T p_coef(float c, float2 c2);
+template <> __device__ __forceinline__ float p_coef<float>(float c, float2) { return c; }
+template <> __device__ __forceinline__ float2 p_coef<float2>(float, float2 c2) { return c2; }
+
+// Accumulators of the node-pair kernels: the even and odd node of each pair keep their own
+// (hi, lo) pairs in the two halves of a float2, updated by the paired FP32 instructions
+// (FADD2: two additions, each rounded to nearest, in one instruction) with the same TwoSum
+// as Acc; fold() merges the halves into an Acc before the warp and block trees.
+struct AccPair {
+    float2 hi[5], lo[5];
+    float mx, bad;
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) hi[i] = lo[i] = make_float2(0.0f, 0.0f);
+        mx = bad = 0.0f;
+    }
+    __device__ __forceinline__ void add(int i, float2 x) {   // TwoSum, as two_sum_acc
+        const float2 s = p_add(hi[i], x);
+        const float2 bb = p_sub(s, hi[i]);
+        lo[i] = p_add(lo[i], p_add(p_sub(hi[i], p_sub(s, bb)), p_sub(x, bb)));
+        hi[i] = s;
+    }
+    __device__ __forceinline__ Acc<float> fold() const {
+        Acc<float> a;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            a.hi[i] = hi[i].x;
+            a.lo[i] = lo[i].x + lo[i].y;
+            two_sum_acc(a.hi[i], a.lo[i], hi[i].y);
+        }
+        a.mx = mx;
+        a.bad = bad;
+        return a;
+    }
+};
+
+// Accumulator type of a kernel: node pairs for FP32 compute, single nodes for FP64.
+template <class C> struct AccOf { using T = Acc<C>; };
+template <> struct AccOf<float> { using T = AccPair; };
+
+// accumulate_node for the two nodes of a pair (dr, Q as float pairs).  0 * v is 0 for a finite
+// v and NaN otherwise, so z flags a node with a non-finite moment; such a node is counted in
+// `bad` and enters every sum as 0 (as accumulate_node skips it).
+__device__ __forceinline__ void accumulate_pair(AccPair& acc, float2 dr, const float2* Q, int dim, float rho_bar) {
+    const float2 zero = make_float2(0.0f, 0.0f);
+    float2 z = p_mul(dr, zero);
+    for (int d = 0; d < dim; ++d) z = p_fma(Q[d], zero, z);
+    float2 q[3] = {zero, zero, zero};
+    for (int d = 0; d < dim; ++d) q[d] = Q[d];
+    if (!(z.x == 0.0f && z.y == 0.0f)) {
+        const bool f0 = z.x == 0.0f, f1 = z.y == 0.0f;
+        acc.bad += (f0 ? 0.0f : 1.0f) + (f1 ? 0.0f : 1.0f);
+        dr = make_float2(f0 ? dr.x : 0.0f, f1 ? dr.y : 0.0f);
+        for (int d = 0; d < dim; ++d) q[d] = make_float2(f0 ? q[d].x : 0.0f, f1 ? q[d].y : 0.0f);
+    }
+    const float2 rho = p_add(make_float2(rho_bar, rho_bar), dr);
+    const float2 r = make_float2(recip(rho.x), recip(rho.y));
+    float2 q2 = p_mul(q[0], q[0]);
+    for (int d = 1; d < dim; ++d) q2 = p_fma(q[d], q[d], q2);
+    acc.add(0, dr);
+    for (int d = 0; d < dim; ++d) acc.add(1 + d, q[d]);
+    acc.add(4, p_mul(p_mul(make_float2(0.5f, 0.5f), q2), r));
+    const float2 u2 = p_mul(p_mul(q2, r), r);
+    acc.mx = fmaxf(acc.mx, fmaxf(u2.x, u2.y));
 }
 
 // Warp tree on the pairs: (h1, l1) + (h2, l2) by TwoSum of the heads.

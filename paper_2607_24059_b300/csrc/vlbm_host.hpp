@@ -43,6 +43,18 @@ inline Coef<C> make_coef(const vlbm_params& p, const vlbm_derived& d, const doub
     k.gamma_one = p.gamma == 1.0;
     for (int f = 0; f < kMaxFields; ++f) k.al_s[f] = (C)((f < F ? d.alpha[f] : 0.0) * scale[f]);
     k.i2m_s = (C)(scale[0] / (2.0 * p.mu));
+    auto pair = [](double v) { return float2{(float)v, (float)v}; };
+    for (int f = 0; f < kMaxFields; ++f) {
+        const float al_s = (float)((f < F ? d.alpha[f] : 0.0) * scale[f]);
+        const float w = (float)(1.0 - (f < F ? p.omega[f] : 1.0));
+        k.p_al[f] = pair(al_s);
+        k.p_nal4[f] = pair(-4.0f * al_s);
+        k.p_w[f] = pair(w);
+        k.p_nwal[f] = pair(-(double)w * al_s);
+    }
+    k.p_i2m = pair((float)(scale[0] / (2.0 * p.mu)));
+    k.p_rho_bar = pair(p.rho_bar);
+    k.p_inv_s = pair((float)(1.0 / scale[0]));
     return k;
 }
 

@@ -57,11 +57,10 @@ __device__ __forceinline__ void load_or_zero(T (&w)[V], const T* p, bool active)
 // (FP32 0.2948 against 0.3162 ms), the interleaved order inside the persistent
 // loops of the recorded step and the batch kernel (recorded step 324 against
 // ~360 us).
-template <class S, bool DIAG, int V = Vec16<S>::V, bool LOAD_FIRST = !DIAG>
+template <class S, bool DIAG, int V = Vec16<S>::V, bool LOAD_FIRST = !DIAG, class A>
 __device__ __forceinline__ void warp_stream_collide_2d(const S* __restrict__ fin, S* __restrict__ fout, long long N,
                                                        int nx, int ny, int y, int seg, int lane,
-                                                       const Coef<typename Storage<S>::C>& k,
-                                                       Acc<typename Storage<S>::C>& acc, uint32_t key) {
+                                                       const Coef<typename Storage<S>::C>& k, A& acc, uint32_t key) {
     using C = typename Storage<S>::C;
     using R = S;
     constexpr bool SR = StochasticMoments<S>::value;
@@ -162,6 +161,7 @@ __device__ __forceinline__ void warp_stream_collide_2d(const S* __restrict__ fin
             }
         }
 
+        C mom[3][2];   // moments of the transported populations of the last node pair (diagnostics)
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             C gn[15];
@@ -169,15 +169,24 @@ __device__ __forceinline__ void warp_stream_collide_2d(const S* __restrict__ fin
             for (int p = 0; p < 15; ++p) gn[p] = g[p][i];
             C dr, Qx, Qy;
             moments_d2q5(gn, dr, Qx, Qy);
-            if (DIAG && active) {
-                const C Q[2] = {Qx, Qy};
-                accumulate_node(acc, moments_finite(dr, Q, 2), dr, Q, 2, k.rho_bar);
+            if constexpr (DIAG) {
+                mom[0][i & 1] = dr;
+                mom[1][i & 1] = Qx;
+                mom[2][i & 1] = Qy;
+                if constexpr (std::is_same<A, AccPair>::value) {   // FP32: node pairs
+                    if ((i & 1) && active) {
+                        const float2 Q[2] = {make_float2(mom[1][0], mom[1][1]), make_float2(mom[2][0], mom[2][1])};
+                        accumulate_pair(acc, make_float2(mom[0][0], mom[0][1]), Q, 2, k.rho_bar);
+                    }
+                } else if (active) {
+                    const C Q[2] = {Qx, Qy};
+                    accumulate_node(acc, moments_finite(dr, Q, 2), dr, Q, 2, k.rho_bar);
+                }
             }
             relax_d2q5<C, sizeof(S) == 2, SR>(k, gn, dr, Qx, Qy, SR ? sr_node_word(key, row + x0 + i) : 0u);
 #pragma unroll
             for (int p = 0; p < 15; ++p) g[p][i] = gn[p];
         }
-
         if (active) {
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
@@ -237,24 +246,32 @@ template <> struct DiagVec<float, true> { static constexpr int V = 2; };
 template <class S, bool SPLIT, bool DIAG>
 __global__ void __launch_bounds__(kThreads, (sizeof(S) == 2 || (sizeof(S) == 4 && DIAG)) ? 3 : 1)
 k_stream_collide_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
-                        int warps_per_row, Coef<typename Storage<S>::C> k, DiagSink sink,
+                        FastDiv wdiv, Coef<typename Storage<S>::C> k, DiagSink sink,
                         uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     static_assert(!SPLIT, "the split layouts have their own step kernels");
     const S* fin = reinterpret_cast<const S*>(fin_b);   // based on the __restrict__ parameters
     S* fout = reinterpret_cast<S*>(fout_b);
     const int lane = threadIdx.x & 31;
-    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t key = take_step_key(step_ctr, par);
-    Acc<C> acc;
+    // FP32 storage accumulates node pairs; the 16-bit shifted kernels (eight nodes per lane,
+    // bounded to 80 registers) keep the smaller single-node accumulators
+    typename std::conditional<std::is_same<S, float>::value, AccPair, Acc<C>>::type acc;
     if (DIAG) acc.zero();
     // one row segment per warp; a smaller (persistent) grid loops, accumulating the
     // diagnostics of all its segments before one block reduction
-    for (long long item = gwarp, items = (long long)ny * warps_per_row; item < items; item += (DIAG ? nwarps : items))   // warp-uniform
-        warp_stream_collide_2d<S, DIAG, DiagVec<S, DIAG>::V>(fin, fout, plane, nx, ny, (int)(item / warps_per_row),
-                                                             (int)(item % warps_per_row), lane, k, acc, key);
-    if (DIAG) block_reduce_finish(acc, sink);
+    const uint32_t items = (uint32_t)ny * wdiv.d;
+    for (uint32_t item = gwarp; item < items; item += (DIAG ? nwarps : items)) {   // warp-uniform
+        const uint32_t y = wdiv.div(item);
+        warp_stream_collide_2d<S, DIAG, DiagVec<S, DIAG>::V>(fin, fout, plane, nx, ny, (int)y,
+                                                             (int)(item - y * wdiv.d), lane, k, acc, key);
+    }
+    if (DIAG) {
+        Acc<C> a = acc.fold();
+        block_reduce_finish(a, sink);
+    }
 }
 
 // Load / store one population of one node through the layout (scaled to deviations).

@@ -66,33 +66,6 @@ __device__ __forceinline__ void equilibrium_dir(const Coef<C>& k, const C (&m)[F
                                        pressure_dev(k, m[0]) * coef_i2m<STORED>(k), e);
 }
 
-template <class T, int V>
-__device__ __forceinline__ void load_vec_c(typename Storage<T>::C (&out)[V], const T* p, bool active,
-                                           typename Storage<T>::C scale) {
-    T w[V];
-    load_or_zero<T, V>(w, p, active);
-#pragma unroll
-    for (int i = 0; i < V; ++i) out[i] = Storage<T>::to_c(w[i]) * scale;
-}
-
-// Values at x - 1 (shift_right) and x + 1 (shift_left) of a per-lane vector of
-// V consecutive nodes, taking the missing element from the neighbouring lane,
-// or from memory at the warp edge (periodic wrap handled by the caller's index).
-template <class C, int V>
-__device__ __forceinline__ void shift_from_left(C (&out)[V], const C (&own)[V], bool edge, C edge_value) {
-    C prev = __shfl_up_sync(0xffffffffu, own[V - 1], 1);
-    out[0] = edge ? edge_value : prev;
-#pragma unroll
-    for (int i = 1; i < V; ++i) out[i] = own[i - 1];
-}
-template <class C, int V>
-__device__ __forceinline__ void shift_from_right(C (&out)[V], const C (&own)[V], bool edge, C edge_value) {
-    C next = __shfl_down_sync(0xffffffffu, own[0], 1);
-#pragma unroll
-    for (int i = 0; i < V - 1; ++i) out[i] = own[i + 1];
-    out[V - 1] = edge ? edge_value : next;
-}
-
 // ------------------------------------------------------------------------------ 2D
 // Relaxation and new moments of one D2Q5 node in split form.
 //   m[3]: moments at the node; B[3][4]: pulled populations g_{k,l} (l = 1..4);
@@ -131,147 +104,325 @@ __device__ __forceinline__ void pulled_d2q5(const Coef<C>& k, const C (&ms)[3], 
     for (int f = 0; f < 3; ++f) B[f][L - 1] = e[f] + n[f];
 }
 
-// Vectorised 2D split step with V nodes per lane.  All loads of a lane are
-// issued first (its moments, the moment rows y -+ 1, the six own-row and six
-// pulled rows of non-equilibrium parts, and the warp-edge halo values), then
-// the arithmetic runs: the kernel is limited by how many bytes are in flight.
-template <class S, int V, bool DIAG>
-__device__ __forceinline__ void warp_split_step_2d(const Layout<S, true, 5>& fin, const Layout<S, true, 5>& fout,
-                                                   int nx, int ny, int y, int seg, int lane,
-                                                   const Coef<typename Storage<S>::C>& k,
-                                                   Acc<typename Storage<S>::C>& acc) {
-    using C = typename Storage<S>::C;
-    {
-        const int x0 = (seg * 32 + lane) * V;
-        const bool active = x0 < nx;
-        const long long row = (long long)y * nx;
-        const long long row_m = (long long)(y == 0 ? ny - 1 : y - 1) * nx;
-        const long long row_p = (long long)(y == ny - 1 ? 0 : y + 1) * nx;
-        const int xm = x0 == 0 ? nx - 1 : x0 - 1;
-        const int xp = x0 + V >= nx ? 0 : x0 + V;
-        const bool left_edge = lane == 0 && active;
-        const bool right_edge = active && (lane == 31 || x0 + V >= nx);
+// Plane base pointers of one split lattice, source and destination, passed to the kernels
+// by value: every plane address is then a kernel parameter, and an access costs one
+// multiply-add of its 32-bit node offset instead of 64-bit plane arithmetic.
+template <class S, int Q>
+struct SplitPlanes {
+    static constexpr int F = (Q + 1) / 2;
+    const float* rin[F];
+    const S* min[F][Q - 1];
+    float* rout[F];
+    S* mout[F][Q - 1];
+};
 
-        // ---- load phase
-        float mo[3][V], mym[3][V], myp[3][V];
-        S n_px[3][V], n_mx[3][V], n_py_pull[3][V], n_my_pull[3][V], n_py_own[3][V], n_my_own[3][V];
-        float hm_l[3], hm_r[3];
-        S hn_l[3], hn_r[3];
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            load_or_zero<float, V>(mo[f], fin.rest(f) + row + x0, active);
-            load_or_zero<float, V>(mym[f], fin.rest(f) + row_m + x0, active);
-            load_or_zero<float, V>(myp[f], fin.rest(f) + row_p + x0, active);
-            load_or_zero<S, V>(n_px[f], fin.mov(f, 1) + row + x0, active);
-            load_or_zero<S, V>(n_mx[f], fin.mov(f, 2) + row + x0, active);
-            load_or_zero<S, V>(n_py_pull[f], fin.mov(f, 3) + row_m + x0, active);
-            load_or_zero<S, V>(n_my_pull[f], fin.mov(f, 4) + row_p + x0, active);
-            load_or_zero<S, V>(n_py_own[f], fin.mov(f, 3) + row + x0, active);
-            load_or_zero<S, V>(n_my_own[f], fin.mov(f, 4) + row + x0, active);
-            hm_l[f] = hm_r[f] = 0.0f;
-            hn_l[f] = hn_r[f] = Storage<S>::from_c(C(0));
-            if (left_edge) {
-                hm_l[f] = fin.rest(f)[row + xm];
-                hn_l[f] = fin.mov(f, 1)[row + xm];
-            }
-            if (right_edge) {
-                hm_r[f] = fin.rest(f)[row + xp];
-                hn_r[f] = fin.mov(f, 2)[row + xp];
-            }
+// Host side: the planes of Layout<S, true, Q> over N nodes at in and out.
+template <class S, int Q>
+inline SplitPlanes<S, Q> split_planes(const char* in, char* out, long long N) {
+    constexpr int F = (Q + 1) / 2;
+    SplitPlanes<S, Q> P;
+    for (int f = 0; f < F; ++f) {
+        P.rin[f] = reinterpret_cast<const float*>(in) + (long long)f * N;
+        P.rout[f] = reinterpret_cast<float*>(out) + (long long)f * N;
+        for (int l = 1; l < Q; ++l) {
+            const long long plane = (long long)f * (Q - 1) + (l - 1);
+            P.min[f][l - 1] = reinterpret_cast<const S*>(reinterpret_cast<const float*>(in) + (long long)F * N) + plane * N;
+            P.mout[f][l - 1] = reinterpret_cast<S*>(reinterpret_cast<float*>(out) + (long long)F * N) + plane * N;
         }
+    }
+    return P;
+}
 
-        // ---- arithmetic
-        C m[3][V], nown[3][V], B[3][4][V];
+// Source and destination views of SplitPlanes with Layout's rest() / mov() interface.
+template <class S, int Q>
+struct PlanesIn {
+    const SplitPlanes<S, Q>& p;
+    __device__ __forceinline__ const float* rest(int f) const { return p.rin[f]; }
+    __device__ __forceinline__ const S* mov(int f, int l) const { return p.min[f][l - 1]; }
+};
+template <class S, int Q>
+struct PlanesOut {
+    const SplitPlanes<S, Q>& p;
+    __device__ __forceinline__ float* rest(int f) const { return p.rout[f]; }
+    __device__ __forceinline__ S* mov(int f, int l) const { return p.mout[f][l - 1]; }
+};
+
+// dP = P(rho_bar + dr) - P(rho_bar) in stored units (dr i2m_s for gamma = 1).
+__device__ __forceinline__ float p_pressure(const Coef<float>& k, float dr) {
+    return p_mul(k.gamma_one ? dr : pressure_dev(k, dr), k.i2m_s);
+}
+__device__ __forceinline__ float2 p_pressure(const Coef<float>& k, float2 dr) {
+    if (k.gamma_one) return p_mul(dr, k.p_i2m);
+    return p_mul(make_float2(pressure_dev(k, dr.x), pressure_dev(k, dr.y)), k.p_i2m);
+}
+
+// Moving equilibria of one D2Q5 node along one axis A (0: x, 1: y), stored units, as the
+// terms shared by the +A and -A directions: e_{k,+A} = base_k + flux_k, e_{k,-A} = base_k - flux_k
+// with base = alpha_s m and flux = (Q_A, Q_j Q_A / rho + delta_jA dP) i2m_s.  Only the flux is
+// returned; callers fold alpha_s m into a fused multiply-add.
+template <class T, int A>
+__device__ __forceinline__ void fluxes_d2q5(const Coef<float>& k, T dr, T Qx, T Qy, T (&fl)[3]) {
+    const T i2m = p_coef<T>(k.i2m_s, k.p_i2m);
+    const T r = p_rcp(p_add(p_coef<T>(k.rho_bar, k.p_rho_bar), dr));
+    const T dP = p_pressure(k, dr);
+    const T Qa = A == 0 ? Qx : Qy;
+    const T qr = p_mul(Qa, p_mul(r, i2m));            // Q_A i2m / rho
+    fl[0] = p_mul(Qa, i2m);
+    fl[1] = A == 0 ? p_fma(Qx, qr, dP) : p_mul(Qx, qr);
+    fl[2] = A == 0 ? p_mul(Qy, qr) : p_fma(Qy, qr, dP);
+}
+
+// Both axes' fluxes of one node (the new equilibrium of the collision): one reciprocal, and the
+// shared term Q_x Q_y / rho serves flux_x of field q_y and flux_y of field q_x.
+template <class T>
+__device__ __forceinline__ void fluxes_d2q5_xy(const Coef<float>& k, T dr, T Qx, T Qy, T (&fx)[3], T (&fy)[3]) {
+    const T i2m = p_coef<T>(k.i2m_s, k.p_i2m);
+    const T ri = p_mul(p_rcp(p_add(p_coef<T>(k.rho_bar, k.p_rho_bar), dr)), i2m);
+    const T dP = p_pressure(k, dr);
+    const T qxr = p_mul(Qx, ri), qyr = p_mul(Qy, ri);
+    const T xy = p_mul(Qy, qxr);
+    fx[0] = p_mul(Qx, i2m);
+    fx[1] = p_fma(Qx, qxr, dP);
+    fx[2] = xy;
+    fy[0] = p_mul(Qy, i2m);
+    fy[1] = xy;
+    fy[2] = p_fma(Qy, qyr, dP);
+}
+
+// D3Q7 fluxes of one node along axis A: (Q_A, Q_j Q_A / rho + delta_jA dP) i2m_s.
+template <class T, int A>
+__device__ __forceinline__ void fluxes_d3q7(const Coef<float>& k, const T (&m)[4], T (&fl)[4]) {
+    const T i2m = p_coef<T>(k.i2m_s, k.p_i2m);
+    const T r = p_rcp(p_add(p_coef<T>(k.rho_bar, k.p_rho_bar), m[0]));
+    const T dP = p_pressure(k, m[0]);
+    const T qr = p_mul(m[1 + A], p_mul(r, i2m));
+    fl[0] = p_mul(m[1 + A], i2m);
 #pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            C a[V], b[V];
+    for (int j = 0; j < 3; ++j) fl[1 + j] = j == A ? p_fma(m[1 + j], qr, dP) : p_mul(m[1 + j], qr);
+}
+
+// All three axes' D3Q7 fluxes of one node (the new equilibrium): one reciprocal, the cross
+// terms Q_i Q_j / rho shared between the two axes they appear in.
+template <class T>
+__device__ __forceinline__ void fluxes_d3q7_all(const Coef<float>& k, const T (&m)[4], T (&fl)[3][4]) {
+    const T i2m = p_coef<T>(k.i2m_s, k.p_i2m);
+    const T ri = p_mul(p_rcp(p_add(p_coef<T>(k.rho_bar, k.p_rho_bar), m[0])), i2m);
+    const T dP = p_pressure(k, m[0]);
+    T qr[3];
 #pragma unroll
-            for (int i = 0; i < V; ++i) {   // parts stay in stored units
-                m[f][i] = (C)mo[f][i];
-                a[i] = Storage<S>::to_c(n_px[f][i]);
-                b[i] = Storage<S>::to_c(n_mx[f][i]);
-                nown[f][i] = (a[i] + b[i]) + (Storage<S>::to_c(n_py_own[f][i]) + Storage<S>::to_c(n_my_own[f][i]));
-            }
-            // pulled non-equilibrium parts, stashed in B until the equilibria are added
-            C sh[V];
-            shift_from_left<C, V>(sh, a, left_edge, Storage<S>::to_c(hn_l[f]));
+    for (int a = 0; a < 3; ++a) {
+        qr[a] = p_mul(m[1 + a], ri);
+        fl[a][0] = p_mul(m[1 + a], i2m);
+        fl[a][1 + a] = p_fma(m[1 + a], qr[a], dP);
+    }
+    const T xy = p_mul(m[2], qr[0]), xz = p_mul(m[3], qr[0]), yz = p_mul(m[3], qr[1]);
+    fl[0][2] = xy;
+    fl[1][1] = xy;
+    fl[0][3] = xz;
+    fl[2][1] = xz;
+    fl[1][3] = yz;
+    fl[2][2] = yz;
+}
+
+// Post-relaxation populations leaving nodes with moments m and non-equilibrium parts n along
+// +A (SIGN = +1) or -A (SIGN = -1), given the fluxes along A: e_{k,l}(m) + n_{k,l}, stored units.
+template <class T, int F, int SIGN>
+__device__ __forceinline__ void outgoing(const Coef<float>& k, const T (&m)[F], const T (&fl)[F], const T (&n)[F],
+                                         T (&o)[F]) {
 #pragma unroll
-            for (int i = 0; i < V; ++i) B[f][0][i] = sh[i];
-            shift_from_right<C, V>(sh, b, right_edge, Storage<S>::to_c(hn_r[f]));
-#pragma unroll
-            for (int i = 0; i < V; ++i) {
-                B[f][1][i] = sh[i];
-                B[f][2][i] = Storage<S>::to_c(n_py_pull[f][i]);
-                B[f][3][i] = Storage<S>::to_c(n_my_pull[f][i]);
-            }
-        }
-        // source moments of the x neighbours by warp shuffle
-        C mxl[3][V], mxr[3][V];
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            shift_from_left<C, V>(mxl[f], m[f], left_edge, (C)hm_l[f]);
-            shift_from_right<C, V>(mxr[f], m[f], right_edge, (C)hm_r[f]);
-        }
-#pragma unroll
-        for (int i = 0; i < V; ++i) {
-            C e[3];
-            {
-                const C ms[3] = {mxl[0][i], mxl[1][i], mxl[2][i]};
-                equilibrium_dir<C, 3, 1>(k, ms, e);
-#pragma unroll
-                for (int f = 0; f < 3; ++f) B[f][0][i] += e[f];
-            }
-            {
-                const C ms[3] = {mxr[0][i], mxr[1][i], mxr[2][i]};
-                equilibrium_dir<C, 3, 2>(k, ms, e);
-#pragma unroll
-                for (int f = 0; f < 3; ++f) B[f][1][i] += e[f];
-            }
-            {
-                const C ms[3] = {(C)mym[0][i], (C)mym[1][i], (C)mym[2][i]};
-                equilibrium_dir<C, 3, 3>(k, ms, e);
-#pragma unroll
-                for (int f = 0; f < 3; ++f) B[f][2][i] += e[f];
-            }
-            {
-                const C ms[3] = {(C)myp[0][i], (C)myp[1][i], (C)myp[2][i]};
-                equilibrium_dir<C, 3, 4>(k, ms, e);
-#pragma unroll
-                for (int f = 0; f < 3; ++f) B[f][3][i] += e[f];
-            }
-            C mi[3] = {m[0][i], m[1][i], m[2][i]};
-            C Bi[3][4];
-            const C ni[3] = {nown[0][i], nown[1][i], nown[2][i]};
-#pragma unroll
-            for (int f = 0; f < 3; ++f)
-#pragma unroll
-                for (int l = 0; l < 4; ++l) Bi[f][l] = B[f][l][i];
-            split_update_d2q5(k, mi, Bi, ni);
-            if (DIAG && active) {
-                const C Q[2] = {mi[1], mi[2]};
-                accumulate_node(acc, moments_finite(mi[0], Q, 2), mi[0], Q, 2, k.rho_bar);
-            }
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                m[f][i] = mi[f];
-#pragma unroll
-                for (int l = 0; l < 4; ++l) B[f][l][i] = Bi[f][l];
-            }
-        }
+    for (int f = 0; f < F; ++f) {
+        const T e = p_fma(p_coef<T>(k.al_s[f], k.p_al[f]), m[f], SIGN > 0 ? fl[f] : p_neg(fl[f]));
+        o[f] = p_add(e, n[f]);
+    }
+}
+
+// Vectorised 2D split step with V nodes per lane (V even), the arithmetic in node pairs.
+// All loads of a lane are issued first (its moments, the moment rows y -+ 1, the six own-row
+// and six pulled rows of non-equilibrium parts, and the warp-edge halo values), then:
+//   outgoing +x / -x populations of the lane's own nodes, shifted by one node (warp shuffle
+//   across lanes; the edge lanes evaluate the halo node's population themselves);
+//   pulled +y / -y populations from the equilibria of rows y -+ 1;
+//   the new moments, their equilibrium and the relaxed non-equilibrium parts (Section 2's
+//   collision in the split variables).
+template <class S, int V, bool DIAG, class In, class Out, class A>
+__device__ __forceinline__ void warp_split_step_2d(const In& fin, const Out& fout, int nx, int ny, int y, int seg,
+                                                   int lane, const Coef<float>& k, A& acc) {
+    static_assert(V % 2 == 0, "node pairs");
+    constexpr int P = V / 2;
+    using W = typename RawVec<V * sizeof(S)>::T;     // V 16-bit values
+    using SW = Storage<S>;
+    const int x0 = (seg * 32 + lane) * V;
+    const bool active = x0 < nx;
+    const long long row = (long long)y * nx;
+    const long long row_m = (long long)(y == 0 ? ny - 1 : y - 1) * nx;
+    const long long row_p = (long long)(y == ny - 1 ? 0 : y + 1) * nx;
+    const int xm = x0 == 0 ? nx - 1 : x0 - 1;
+    const int xp = x0 + V >= nx ? 0 : x0 + V;
+    const bool left_edge = lane == 0 && active;
+    const bool right_edge = active && (lane == 31 || x0 + V >= nx);
+
+    // ---- load phase
+    float2 mo[3][P], mym[3][P], myp[3][P];
+    uint32_t n_px[3][P], n_mx[3][P], n_py_pull[3][P], n_my_pull[3][P], n_py_own[3][P], n_my_own[3][P];
+    float hm_l[3], hm_r[3], hn_l[3], hn_r[3];
+    auto ldm = [&](float2 (&d)[P], const float* p) {
         if (active) {
+            float t[V];
+            vload<float, V>(t, p);
 #pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                float wm[V];
+            for (int q = 0; q < P; ++q) d[q] = make_float2(t[2 * q], t[2 * q + 1]);
+        } else {
 #pragma unroll
-                for (int i = 0; i < V; ++i) wm[i] = (float)m[f][i];
-                vstore<float, V>(fout.rest(f) + row + x0, wm);
+            for (int q = 0; q < P; ++q) d[q] = make_float2(0.0f, 0.0f);
+        }
+    };
+    auto ldn = [&](uint32_t (&d)[P], const S* p) {
+        if (active) {
+            const W w = __ldg(reinterpret_cast<const W*>(p));
+            memcpy(&d[0], &w, sizeof(W));
+        } else {
 #pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    S w[V];
+            for (int q = 0; q < P; ++q) d[q] = 0u;
+        }
+    };
 #pragma unroll
-                    for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(B[f][l][i]);
-                    vstore<S, V>(fout.mov(f, l + 1) + row + x0, w);
-                }
+    for (int f = 0; f < 3; ++f) {
+        ldm(mo[f], fin.rest(f) + row + x0);
+        ldm(mym[f], fin.rest(f) + row_m + x0);
+        ldm(myp[f], fin.rest(f) + row_p + x0);
+        ldn(n_px[f], fin.mov(f, 1) + row + x0);
+        ldn(n_mx[f], fin.mov(f, 2) + row + x0);
+        ldn(n_py_pull[f], fin.mov(f, 3) + row_m + x0);
+        ldn(n_my_pull[f], fin.mov(f, 4) + row_p + x0);
+        ldn(n_py_own[f], fin.mov(f, 3) + row + x0);
+        ldn(n_my_own[f], fin.mov(f, 4) + row + x0);
+        hm_l[f] = hm_r[f] = hn_l[f] = hn_r[f] = 0.0f;
+        if (left_edge) {
+            hm_l[f] = fin.rest(f)[row + xm];
+            hn_l[f] = SW::to_c(fin.mov(f, 1)[row + xm]);
+        }
+        if (right_edge) {
+            hm_r[f] = fin.rest(f)[row + xp];
+            hn_r[f] = SW::to_c(fin.mov(f, 2)[row + xp]);
+        }
+    }
+
+    // ---- own non-equilibrium sum and the outgoing x populations of the lane's own nodes
+    float2 nown[3][P], ox_p[3][P], ox_m[3][P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        float2 a[3], b[3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            a[f] = SW::unpack2(n_px[f][q]);
+            b[f] = SW::unpack2(n_mx[f][q]);
+            nown[f][q] = p_add(p_add(a[f], b[f]), p_add(SW::unpack2(n_py_own[f][q]), SW::unpack2(n_my_own[f][q])));
+        }
+        const float2 mq[3] = {mo[0][q], mo[1][q], mo[2][q]};
+        float2 fl[3], op[3], om[3];
+        fluxes_d2q5<float2, 0>(k, mq[0], mq[1], mq[2], fl);
+        outgoing<float2, 3, +1>(k, mq, fl, a, op);
+        outgoing<float2, 3, -1>(k, mq, fl, b, om);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            ox_p[f][q] = op[f];
+            ox_m[f][q] = om[f];
+        }
+    }
+    // halo nodes x0 - 1 (+x population) and x0 + V (-x population), on the edge lanes only
+    float halo_p[3] = {0.0f, 0.0f, 0.0f}, halo_m[3] = {0.0f, 0.0f, 0.0f};
+    if (left_edge) {
+        float fl[3];
+        fluxes_d2q5<float, 0>(k, hm_l[0], hm_l[1], hm_l[2], fl);
+        outgoing<float, 3, +1>(k, hm_l, fl, hn_l, halo_p);
+    }
+    if (right_edge) {
+        float fl[3];
+        fluxes_d2q5<float, 0>(k, hm_r[0], hm_r[1], hm_r[2], fl);
+        outgoing<float, 3, -1>(k, hm_r, fl, hn_r, halo_m);
+    }
+    // pulled populations B[f][l][q] (l = 0..3 for velocities 1..4): +x from x - 1, -x from x + 1
+    float2 B[3][4][P];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        const float from_left = __shfl_up_sync(0xffffffffu, ox_p[f][P - 1].y, 1);
+        const float from_right = __shfl_down_sync(0xffffffffu, ox_m[f][0].x, 1);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            B[f][0][q] = make_float2(q == 0 ? (left_edge ? halo_p[f] : from_left) : ox_p[f][q - 1].y, ox_p[f][q].x);
+            B[f][1][q] = make_float2(ox_m[f][q].y, q == P - 1 ? (right_edge ? halo_m[f] : from_right) : ox_m[f][q + 1].x);
+        }
+    }
+    // +y from row y - 1, -y from row y + 1
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        {
+            const float2 ms[3] = {mym[0][q], mym[1][q], mym[2][q]};
+            const float2 n[3] = {SW::unpack2(n_py_pull[0][q]), SW::unpack2(n_py_pull[1][q]),
+                                 SW::unpack2(n_py_pull[2][q])};
+            float2 fl[3], o[3];
+            fluxes_d2q5<float2, 1>(k, ms[0], ms[1], ms[2], fl);
+            outgoing<float2, 3, +1>(k, ms, fl, n, o);
+#pragma unroll
+            for (int f = 0; f < 3; ++f) B[f][2][q] = o[f];
+        }
+        {
+            const float2 ms[3] = {myp[0][q], myp[1][q], myp[2][q]};
+            const float2 n[3] = {SW::unpack2(n_my_pull[0][q]), SW::unpack2(n_my_pull[1][q]),
+                                 SW::unpack2(n_my_pull[2][q])};
+            float2 fl[3], o[3];
+            fluxes_d2q5<float2, 1>(k, ms[0], ms[1], ms[2], fl);
+            outgoing<float2, 3, -1>(k, ms, fl, n, o);
+#pragma unroll
+            for (int f = 0; f < 3; ++f) B[f][3][q] = o[f];
+        }
+    }
+
+    // ---- new moments, their equilibrium, relaxed non-equilibrium parts
+    //   m' = m + (sum_l B_l - 4 alpha_s m - sum_l n_l) / s
+    //   n'_l = (1 - omega) (B_l - alpha_s m' -+ flux_l(m'))
+    uint32_t out_n[3][4][P];
+    float2 out_m[3][P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        float2 m[3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const float2 pulled = p_add(p_add(B[f][0][q], B[f][1][q]), p_add(B[f][2][q], B[f][3][q]));
+            const float2 d = p_sub(p_fma(k.p_nal4[f], mo[f][q], pulled), nown[f][q]);
+            m[f] = p_fma(k.p_inv_s, d, mo[f][q]);
+        }
+        float2 fx[3], fy[3];
+        fluxes_d2q5_xy<float2>(k, m[0], m[1], m[2], fx, fy);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const float2 base = p_mul(k.p_nwal[f], m[f]);     // -(1 - omega) alpha_s m'
+            const float2 w = k.p_w[f];
+            out_n[f][0][q] = SW::pack2(p_fma(w, p_sub(B[f][0][q], fx[f]), base));
+            out_n[f][1][q] = SW::pack2(p_fma(w, p_add(B[f][1][q], fx[f]), base));
+            out_n[f][2][q] = SW::pack2(p_fma(w, p_sub(B[f][2][q], fy[f]), base));
+            out_n[f][3][q] = SW::pack2(p_fma(w, p_add(B[f][3][q], fy[f]), base));
+            out_m[f][q] = m[f];
+        }
+        if constexpr (DIAG) {
+            if (active) accumulate_pair(acc, m[0], &m[1], 2, k.rho_bar);
+        }
+    }
+    if (active) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            float wm[V];
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                wm[2 * q] = out_m[f][q].x;
+                wm[2 * q + 1] = out_m[f][q].y;
+            }
+            vstore<float, V>(fout.rest(f) + row + x0, wm);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                W w;
+                memcpy(&w, &out_n[f][l][0], sizeof(W));
+                *reinterpret_cast<W*>(fout.mov(f, l + 1) + row + x0) = w;
             }
         }
     }
@@ -282,21 +433,25 @@ __device__ __forceinline__ void warp_split_step_2d(const Layout<S, true, 5>& fin
 template <class S, int V, bool DIAG>
 __global__ void __launch_bounds__(kThreads, 2)
 k_split_step_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
-                    int warps_per_row, Coef<typename Storage<S>::C> k, DiagSink sink,
+                    FastDiv wdiv, Coef<typename Storage<S>::C> k, DiagSink sink,
                     uint32_t* __restrict__ step_ctr, int par) {
-    using C = typename Storage<S>::C;
     using L = Layout<S, true, 5>;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const int lane = threadIdx.x & 31;
-    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     take_step_key(step_ctr, par);   // keeps the step counter in step (the split forms round to nearest)
-    Acc<C> acc;
+    AccPair acc;
     if (DIAG) acc.zero();
-    for (long long item = gwarp, items = (long long)ny * warps_per_row; item < items; item += (DIAG ? nwarps : items))   // warp-uniform
-        warp_split_step_2d<S, V, DIAG>(fin, fout, nx, ny, (int)(item / warps_per_row), (int)(item % warps_per_row),
-                                       lane, k, acc);
-    if (DIAG) block_reduce_finish(acc, sink);
+    const uint32_t items = (uint32_t)ny * wdiv.d;
+    for (uint32_t item = gwarp; item < items; item += (DIAG ? nwarps : items)) {   // warp-uniform
+        const uint32_t y = wdiv.div(item);
+        warp_split_step_2d<S, V, DIAG>(fin, fout, nx, ny, (int)y, (int)(item - y * wdiv.d), lane, k, acc);
+    }
+    if (DIAG) {
+        Acc<float> a = acc.fold();
+        block_reduce_finish(a, sink);
+    }
 }
 
 // One thread per node, any size (2D split form).
@@ -395,126 +550,173 @@ __device__ __forceinline__ void pulled_d3q7_l(const Coef<C>& k, int l, const C (
     }
 }
 
-// Vectorised along x with V = kSplitV3 nodes per lane: sources x -+ 1 by warp
-// shuffle (memory at the warp edge), y -+ 1 rows, z -+ 1 slabs.
-template <class S, bool DIAG>
-__global__ void __launch_bounds__(kThreads, 3)
-k_split_step_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
-                    long long plane, int warps_per_row, Coef<typename Storage<S>::C> k,
-                    DiagSink sink, uint32_t* __restrict__ step_ctr, int par) {
-    using C = typename Storage<S>::C;
-    using L = Layout<S, true, 7>;
-    constexpr int V = kSplitV3;
-    const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
-    const int lane = threadIdx.x & 31;
-    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    take_step_key(step_ctr, par);   // keeps the step counter in step (the split forms round to nearest)
-    Acc<C> acc;
-    if (DIAG) acc.zero();
-    for (long long item = gwarp, items = (long long)ny * nz * warps_per_row; item < items; item += (DIAG ? nwarps : items)) {   // warp-uniform
-        const long long r = item / warps_per_row;
-        const int y = (int)(r % ny), z = (int)(r / ny);
-        const int x0 = ((int)(item % warps_per_row) * 32 + lane) * V;
-        const bool active = x0 < nx;
-        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-        const long long row = r * nx;
-        const long long src_row[7] = {row, row, row, ((long long)z * ny + ym) * nx, ((long long)z * ny + yp) * nx,
-                                      ((long long)zm * ny + y) * nx, ((long long)zp * ny + y) * nx};
-        const int xm = x0 == 0 ? nx - 1 : x0 - 1;
-        const int xp = x0 + V >= nx ? 0 : x0 + V;
-        const bool left_edge = lane == 0 && active;
-        const bool right_edge = active && (lane == 31 || x0 + V >= nx);
+// One row segment of the 3D split step: two nodes per lane (one pair) along x; sources x -+ 1
+// by warp shuffle of the lane's outgoing x populations (the edge lanes evaluate the halo
+// node's population themselves), y -+ 1 rows and z -+ 1 planes.
+template <class S, bool DIAG, class In, class Out, class A>
+__device__ __forceinline__ void warp_split_step_3d(const In& fin, const Out& fout, int nx, int ny, int nz, int y, int z,
+                                                   int seg, int lane, const Coef<float>& k, A& acc) {
+    static_assert(kSplitV3 == 2, "one node pair per lane");
+    using SW = Storage<S>;
+    const int x0 = (seg * 32 + lane) * 2;
+    const bool active = x0 < nx;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    const uint32_t unx = nx, uny = ny;
+    const uint32_t row = ((uint32_t)z * uny + y) * unx;
+    const uint32_t src_row[4] = {((uint32_t)z * uny + ym) * unx, ((uint32_t)z * uny + yp) * unx,
+                                 ((uint32_t)zm * uny + y) * unx, ((uint32_t)zp * uny + y) * unx};
+    const uint32_t xm = x0 == 0 ? nx - 1 : x0 - 1;
+    const uint32_t xp = x0 + 2 >= nx ? 0 : x0 + 2;
+    const uint32_t ux0 = (uint32_t)x0;
+    const bool left_edge = lane == 0 && active;
+    const bool right_edge = active && (lane == 31 || x0 + 2 >= nx);
+    auto ldm = [&](const float* p) {
+        return active ? __ldg(reinterpret_cast<const float2*>(p)) : make_float2(0.0f, 0.0f);
+    };
+    auto ldn = [&](const S* p) { return active ? __ldg(reinterpret_cast<const unsigned int*>(p)) : 0u; };
 
-        C m[4][V], nown[4][V], B[4][6][V];
+    // ---- load phase: every load of the lane is issued before the arithmetic (the node pair's
+    // moments and six own non-equilibrium parts, the y / z neighbours' moments and pulled parts,
+    // the warp-edge halo values)
+    float2 m[4], ms[4][4];
+    uint32_t wn[4][6], wpull[4][4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        m[f] = ldm(fin.rest(f) + row + ux0);
+#pragma unroll
+        for (int l = 1; l < 7; ++l) wn[f][l - 1] = ldn(fin.mov(f, l) + row + ux0);
+    }
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            load_vec_c<float, V>(m[f], fin.rest(f) + row + x0, active, C(1));
+            ms[d][f] = ldm(fin.rest(f) + src_row[d] + ux0);
+            wpull[d][f] = ldn(fin.mov(f, 3 + d) + src_row[d] + ux0);
+        }
+    float hmom_l[4], hn_l[4], hmom_r[4], hn_r[4];
 #pragma unroll
-            for (int i = 0; i < V; ++i) nown[f][i] = C(0);
+    for (int f = 0; f < 4; ++f) hmom_l[f] = hn_l[f] = hmom_r[f] = hn_r[f] = 0.0f;
+    if (left_edge) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            hmom_l[f] = fin.rest(f)[row + xm];
+            hn_l[f] = SW::to_c(fin.mov(f, 1)[row + xm]);
+        }
+    }
+    if (right_edge) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            hmom_r[f] = fin.rest(f)[row + xp];
+            hn_r[f] = SW::to_c(fin.mov(f, 2)[row + xp]);
+        }
+    }
+
+    // ---- outgoing +x / -x populations of the lane's own nodes, shifted by one node
+    float2 nown[4], B[4][6];
+    {
+        float2 a[4], b[4], fl[4], op[4], om[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            a[f] = SW::unpack2(wn[f][0]);
+            b[f] = SW::unpack2(wn[f][1]);
+            nown[f] = p_add(p_add(a[f], b[f]), p_add(p_add(SW::unpack2(wn[f][2]), SW::unpack2(wn[f][3])),
+                                                     p_add(SW::unpack2(wn[f][4]), SW::unpack2(wn[f][5]))));
+        }
+        fluxes_d3q7<float2, 0>(k, m, fl);
+        outgoing<float2, 4, +1>(k, m, fl, a, op);
+        outgoing<float2, 4, -1>(k, m, fl, b, om);
+        float hp[4] = {0.0f, 0.0f, 0.0f, 0.0f}, hm[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (left_edge) {
+            float hfl[4];
+            fluxes_d3q7<float, 0>(k, hmom_l, hfl);
+            outgoing<float, 4, +1>(k, hmom_l, hfl, hn_l, hp);
+        }
+        if (right_edge) {
+            float hfl[4];
+            fluxes_d3q7<float, 0>(k, hmom_r, hfl);
+            outgoing<float, 4, -1>(k, hmom_r, hfl, hn_r, hm);
         }
 #pragma unroll
-        for (int l = 1; l < 7; ++l) {
-            C ms[4][V], np[4][V];
-#pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                const float* mp = fin.rest(f);
-                const S* npl = fin.mov(f, l);
-                C own[V];
-                load_vec_c<S, V>(own, npl + row + x0, active, C(1));   // stored units
-#pragma unroll
-                for (int i = 0; i < V; ++i) nown[f][i] += own[i];
-                if (l == 1) {
-                    C em = C(0), en = C(0);
-                    if (left_edge) {
-                        em = (C)mp[row + xm];
-                        en = Storage<S>::to_c(npl[row + xm]);
-                    }
-                    shift_from_left<C, V>(ms[f], m[f], left_edge, em);
-                    shift_from_left<C, V>(np[f], own, left_edge, en);
-                } else if (l == 2) {
-                    C em = C(0), en = C(0);
-                    if (right_edge) {
-                        em = (C)mp[row + xp];
-                        en = Storage<S>::to_c(npl[row + xp]);
-                    }
-                    shift_from_right<C, V>(ms[f], m[f], right_edge, em);
-                    shift_from_right<C, V>(np[f], own, right_edge, en);
-                } else {
-                    load_vec_c<float, V>(ms[f], mp + src_row[l] + x0, active, C(1));
-                    load_vec_c<S, V>(np[f], npl + src_row[l] + x0, active, C(1));
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < V; ++i) {
-                const C msi[4] = {ms[0][i], ms[1][i], ms[2][i], ms[3][i]};
-                const C npi[4] = {np[0][i], np[1][i], np[2][i], np[3][i]};
-                C Bi[4][6];
-                pulled_d3q7_l(k, l, msi, npi, Bi);
-#pragma unroll
-                for (int f = 0; f < 4; ++f) B[f][l - 1][i] = Bi[f][l - 1];
-            }
+        for (int f = 0; f < 4; ++f) {
+            const float from_left = __shfl_up_sync(0xffffffffu, op[f].y, 1);
+            const float from_right = __shfl_down_sync(0xffffffffu, om[f].x, 1);
+            B[f][0] = make_float2(left_edge ? hp[f] : from_left, op[f].x);
+            B[f][1] = make_float2(om[f].y, right_edge ? hm[f] : from_right);
         }
+    }
+    // +y, -y, +z, -z from rows y -+ 1 and planes z -+ 1
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            C mi[4] = {m[0][i], m[1][i], m[2][i], m[3][i]};
-            const C ni[4] = {nown[0][i], nown[1][i], nown[2][i], nown[3][i]};
-            C Bi[4][6];
+    for (int d = 0; d < 4; ++d) {
+        const int l = 3 + d;
+        float2 n[4], fl[4], o[4];
 #pragma unroll
-            for (int f = 0; f < 4; ++f)
+        for (int f = 0; f < 4; ++f) n[f] = SW::unpack2(wpull[d][f]);
+        if (d < 2) fluxes_d3q7<float2, 1>(k, ms[d], fl);
+        else fluxes_d3q7<float2, 2>(k, ms[d], fl);
+        if (d % 2 == 0) outgoing<float2, 4, +1>(k, ms[d], fl, n, o);
+        else outgoing<float2, 4, -1>(k, ms[d], fl, n, o);
 #pragma unroll
-                for (int l = 0; l < 6; ++l) Bi[f][l] = B[f][l][i];
-            split_update_d3q7(k, mi, Bi, ni);
-            if (DIAG && active) {
-                const C Q[3] = {mi[1], mi[2], mi[3]};
-                accumulate_node(acc, moments_finite(mi[0], Q, 3), mi[0], Q, 3, k.rho_bar);
-            }
+        for (int f = 0; f < 4; ++f) B[f][l - 1] = o[f];
+    }
+
+    // new moments m' = m + (sum_l B_l - 6 alpha_s m - sum_l n_l) / s (6 alpha_s m as 6 (alpha_s m),
+    // the moving equilibria's exact sum), their fluxes, relaxed parts (1 - omega)(B_l - e_l(m'))
+    const float2 six = make_float2(-6.0f, -6.0f);
 #pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                m[f][i] = mi[f];
+    for (int f = 0; f < 4; ++f) {
+        const float2 pulled = p_add(p_add(p_add(B[f][0], B[f][1]), p_add(B[f][2], B[f][3])), p_add(B[f][4], B[f][5]));
+        const float2 d = p_sub(p_fma(six, p_mul(k.p_al[f], m[f]), pulled), nown[f]);
+        m[f] = p_fma(k.p_inv_s, d, m[f]);
+    }
+    float2 fl[3][4];
+    fluxes_d3q7_all<float2>(k, m, fl);
+    if constexpr (DIAG) {
+        if (active) accumulate_pair(acc, m[0], &m[1], 3, k.rho_bar);
+    }
+    if (active) {
 #pragma unroll
-                for (int l = 0; l < 6; ++l) B[f][l][i] = Bi[f][l];
-            }
-        }
-        if (active) {
+        for (int f = 0; f < 4; ++f) {
+            *reinterpret_cast<float2*>(fout.rest(f) + row + ux0) = m[f];
+            const float2 base = p_mul(k.p_nwal[f], m[f]);     // -(1 - omega) alpha_s m'
+            const float2 w = k.p_w[f];
 #pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                float wm[V];
-#pragma unroll
-                for (int i = 0; i < V; ++i) wm[i] = (float)m[f][i];
-                vstore<float, V>(fout.rest(f) + row + x0, wm);
-#pragma unroll
-                for (int l = 0; l < 6; ++l) {
-                    S w[V];
-#pragma unroll
-                    for (int i = 0; i < V; ++i) w[i] = Storage<S>::from_c(B[f][l][i]);
-                    vstore<S, V>(fout.mov(f, l + 1) + row + x0, w);
-                }
+            for (int a = 0; a < 3; ++a) {
+                const uint32_t up = SW::pack2(p_fma(w, p_sub(B[f][2 * a], fl[a][f]), base));
+                const uint32_t dn = SW::pack2(p_fma(w, p_add(B[f][2 * a + 1], fl[a][f]), base));
+                *reinterpret_cast<unsigned int*>(fout.mov(f, 2 * a + 1) + row + ux0) = up;
+                *reinterpret_cast<unsigned int*>(fout.mov(f, 2 * a + 2) + row + ux0) = dn;
             }
         }
     }
-    if (DIAG) block_reduce_finish(acc, sink);
+}
+
+// Two resident blocks per SM (at most 128 registers): the 24 pulled populations of a node
+// pair stay live until the new moments are known, and below 128 registers the compiler
+// spills them and recomputes plane addresses.
+template <class S, bool DIAG>
+__global__ void __launch_bounds__(kThreads, 2)
+k_split_step_3d_vec(const SplitPlanes<S, 7> P, int nx, int ny, int nz, FastDiv wdiv, FastDiv ydiv,
+                    Coef<typename Storage<S>::C> k, DiagSink sink, uint32_t* __restrict__ step_ctr, int par) {
+    const PlanesIn<S, 7> fin{P};
+    const PlanesOut<S, 7> fout{P};
+    const int lane = threadIdx.x & 31;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    take_step_key(step_ctr, par);   // keeps the step counter in step (the split forms round to nearest)
+    AccPair acc;
+    if (DIAG) acc.zero();
+    const uint32_t items = (uint32_t)ny * (uint32_t)nz * wdiv.d;
+    for (uint32_t item = gwarp; item < items; item += (DIAG ? nwarps : items)) {   // warp-uniform
+        const uint32_t r = wdiv.div(item);
+        const uint32_t z = ydiv.div(r);
+        warp_split_step_3d<S, DIAG>(fin, fout, nx, ny, nz, (int)(r - z * (uint32_t)ny), (int)z,
+                                    (int)(item - r * wdiv.d), lane, k, acc);
+    }
+    if (DIAG) {
+        Acc<float> a = acc.fold();
+        block_reduce_finish(a, sink);
+    }
 }
 
 template <class S, bool DIAG>

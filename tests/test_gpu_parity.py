@@ -120,29 +120,27 @@ def test_vector_and_generic_kernels_agree(n, precision):
     op = resolved(n, 0.05, nu=0.02)
     a = gpu_run(op, precision, u, phi, 77, variant=1)
     b = gpu_run(op, precision, u, phi, 77, variant=2)
-    if precision.endswith("split"):
-        # the split kernels inline the same arithmetic into different code, where
-        # the compiler may contract a different multiply-add pair into an FMA:
-        # FP32 rounding differences that occasionally flip the rounding of a 16-bit
-        # non-equilibrium part by one quantum (2^-11 FP16, 2^-8 BF16).  The velocity
-        # sees that quantum times n/m (the part against the moment it feeds); the
-        # density deviation rho - rho_bar (phi's signal, O(dx^2)) sees the rho-field
-        # parts, which carry differences of the mass flux q/(2 mu) and can be 0.1 of
-        # rho - rho_bar: one flip then moves it by ~2^-11 / 10.  u, rho - rho_bar and phi
-        # are each compared against their own maximum.
-        rel_u = 1e-5 if precision.startswith("fp16") else 1e-3
-        rel_rho = 1e-3 if precision.startswith("fp16") else 1e-2
-        (rho_a, u_a, phi_a), (rho_b, u_b, phi_b) = a, b
-        for x, y, rel in ((rho_a - 1.0, rho_b - 1.0, rel_rho), (u_a, u_b, rel_u), (phi_a, phi_b, rel_rho)):
-            assert np.max(np.abs(x - y)) <= rel * np.max(np.abs(y))
-    elif precision == "fp64":
+    if precision == "fp64":
         # same arithmetic; the compiler may fuse a multiply and an add into one FMA in one
         # kernel and not in the other: about one FP64 rounding per step, 77 steps
         for x, y in zip(a, b):
             assert np.max(np.abs(x - y)) <= 1e-13 * max(np.max(np.abs(y)), 1e-300)
-    else:
-        for x, y in zip(a, b):
-            assert np.array_equal(x, y)
+        return
+    # The kernels inline the same arithmetic into different code (the vectorised split kernels
+    # also evaluate it two nodes per instruction), where the compiler may contract a different
+    # multiply-add pair into an FMA: FP32 rounding differences of an ulp, which for 16-bit
+    # storage occasionally flip a stored value by one quantum (2^-11 FP16, 2^-8 BF16).  The
+    # velocity sees that quantum against the moment it feeds; the density deviation
+    # rho - rho_bar (phi's signal, O(dx^2)) sees the rho-field values, which carry the mass flux
+    # q/(2 mu) and can be ten times rho - rho_bar.  An indexing or arithmetic mistake moves
+    # either by O(1) of its own maximum; u, rho - rho_bar and phi are each compared against it.
+    rel_u, rel_rho = {"fp32": (1e-5, 1e-4), "fp16": (2e-3, 2e-2), "bf16": (2e-2, 1e-1),
+                      "fp16split": (1e-5, 1e-3), "bf16split": (1e-3, 1e-2)}[precision]
+    (rho_a, u_a, phi_a), (rho_b, u_b, phi_b) = a, b
+    for name, x, y, rel in (("rho", rho_a - 1.0, rho_b - 1.0, rel_rho), ("u", u_a, u_b, rel_u),
+                            ("phi", phi_a, phi_b, rel_rho)):
+        err, scale = np.max(np.abs(x - y)), np.max(np.abs(y))
+        assert err <= rel * scale, (name, err / scale)
 
 
 def test_graph_replay_is_bitwise_equal_to_launches():
@@ -252,7 +250,16 @@ def test_fused_records_match_invariants(precision):
     lat.step_record(2, 1, dev)
     ref = lat.invariants()
     assert_invariants_close(dev[1].cpu().numpy(), ref, tol, lat)
-    assert lat.time()[0] == 1 + 7 + 140 + 2
+    # page-locked host destination (written by the step kernel itself when mapped), one call per
+    # step as an application polling every step would; records valid after a stream sync
+    pinned = torch.zeros((3, 8), dtype=torch.float64).pin_memory()
+    for s in range(3):
+        lat.step_record(1, 1, pinned[s])
+    torch.cuda.synchronize()
+    ref = lat.invariants()
+    assert_invariants_close(pinned[2].numpy(), ref, tol, lat)
+    assert np.all(pinned[:, 0].numpy() != 0)
+    assert lat.time()[0] == 1 + 7 + 140 + 2 + 3
     lat.close()
 
 
