@@ -480,8 +480,9 @@ def run_vlbm(args):
                      "source_digest": digest},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (ubytes + pbytes) / args.steps,
                 "d2h_bytes_per_step": 64 + ubytes / args.steps,
-                "how": "vlbm_init from pinned host u and phi, per step vlbm_step_record (fused invariants, 64 B "
-                       "D2H), vlbm_macros to pinned host u"},
+                "how": "vlbm_init from pinned host u and phi, per step vlbm_step_record (fused invariants: 64 B "
+                       "D2H per step, written by the step kernel into the mapped pinned record buffer), vlbm_macros "
+                       "to pinned host u; untimed warm-up of the same calls first"},
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }

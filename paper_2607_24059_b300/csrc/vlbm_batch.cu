@@ -39,6 +39,7 @@ struct BatchProblem {
     long long item0;         // first work item of this problem
     int nx, ny, wpr;         // sizes, warps (row segments) per row
     int pad;
+    FastDiv wdiv;            // division by wpr
     Coef<C> k;
 };
 
@@ -49,8 +50,10 @@ struct BatchProblem {
 // 64 c) and at most a few forward steps.
 constexpr int kChunkShift = 6;
 
+// At most 128 registers (two 256-thread blocks per SM): the split body of the single lattice fits
+// them without spilling; unbounded, the compiler took 146-149 and one block ran per SM.
 template <class S, bool SPLIT, int V>
-__global__ void __launch_bounds__(kMaxBatchThreads)
+__global__ void __launch_bounds__(kMaxBatchThreads, 2)
 k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
                 const BatchProblem<typename Storage<S>::C>* __restrict__ probs, const int* __restrict__ chunk_problem,
                 int count, long long items, uint32_t* __restrict__ step_ctr, int par) {
@@ -67,15 +70,16 @@ k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
         while (p + 1 < count && probs[p + 1].item0 <= item) ++p;
         const BatchProblem<C>& P = probs[p];
         const long long local = item - P.item0;
-        const int y = (int)(local / P.wpr), seg = (int)(local % P.wpr);
+        const uint32_t y = P.wdiv.div((uint32_t)local);
+        const int seg = (int)((uint32_t)local - y * (uint32_t)P.wpr);
         const Layout<S, SPLIT, 5> fin{const_cast<char*>(in_base) + P.offset, P.plane};
         const Layout<S, SPLIT, 5> fout{out_base + P.offset, P.plane};
         const Coef<C>& k = P.k;   // read through L1, not copied into registers
         if constexpr (SPLIT)
-            warp_split_step_2d<S, V, false>(fin, fout, P.nx, P.ny, y, seg, lane, k, unused);
+            warp_split_step_2d<S, V, false>(fin, fout, P.nx, P.ny, (int)y, seg, lane, k, unused);
         else
             warp_stream_collide_2d<S, false, Vec16<S>::V, false>(reinterpret_cast<const S*>(in_base + P.offset),
-                                             reinterpret_cast<S*>(out_base + P.offset), P.plane, P.nx, P.ny, y, seg,
+                                             reinterpret_cast<S*>(out_base + P.offset), P.plane, P.nx, P.ny, (int)y, seg,
                                              lane, k, unused, key);
     }
 }
@@ -215,6 +219,7 @@ int upload_table(vlbm_batch* b) {
         t[i].ny = (int)b->p[i].n[1];
         t[i].wpr = (int)((b->p[i].n[0] / V + 31) / 32);
         t[i].pad = 0;
+        t[i].wdiv = FastDiv::make((uint32_t)t[i].wpr);
         t[i].item0 = item;
         t[i].k = make_coef<C>(b->p[i], b->d[i], scale);
         item += (long long)t[i].ny * t[i].wpr;

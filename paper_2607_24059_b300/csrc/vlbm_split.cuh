@@ -240,8 +240,8 @@ __device__ __forceinline__ void outgoing(const Coef<float>& k, const T (&m)[F], 
 // All loads of a lane are issued first (its moments, the moment rows y -+ 1, the six own-row
 // and six pulled rows of non-equilibrium parts, and the warp-edge halo values), then:
 //   outgoing +x / -x populations of the lane's own nodes, shifted by one node (warp shuffle
-//   across lanes; the edge lanes evaluate the halo node's population themselves);
-//   pulled +y / -y populations from the equilibria of rows y -+ 1;
+//   across lanes; the edge lanes evaluate the halo node's population themselves), and
+//   pulled +y / -y populations from the equilibria of rows y -+ 1, in either order;
 //   the new moments, their equilibrium and the relaxed non-equilibrium parts (Section 2's
 //   collision in the split variables).
 template <class S, int V, bool DIAG, class In, class Out, class A>
@@ -307,8 +307,40 @@ __device__ __forceinline__ void warp_split_step_2d(const In& fin, const Out& fou
         }
     }
 
+    // The x part (own outgoing populations, shuffles, halos) and the y part (pulled rows) are
+    // independent; their order only changes the compiler's schedule, and the faster order was
+    // measured per storage format (FP16: y first, 78.4 against 76.3 GLUPS on the 4096^2 shear
+    // layer; BF16: x first, 77.6 against 66.8).  The y part is written out at both places:
+    // moved into a function or a lambda, the FP16 order lost its gain (76.2).
+    constexpr bool kYFirst = std::is_same<S, __half>::value;
+    float2 nown[3][P], B[3][4][P];
+    if constexpr (kYFirst) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) {   // +y from row y - 1, -y from row y + 1
+            {
+                const float2 ms[3] = {mym[0][q], mym[1][q], mym[2][q]};
+                const float2 n[3] = {SW::unpack2(n_py_pull[0][q]), SW::unpack2(n_py_pull[1][q]),
+                                     SW::unpack2(n_py_pull[2][q])};
+                float2 fl[3], o[3];
+                fluxes_d2q5<float2, 1>(k, ms[0], ms[1], ms[2], fl);
+                outgoing<float2, 3, +1>(k, ms, fl, n, o);
+#pragma unroll
+                for (int f = 0; f < 3; ++f) B[f][2][q] = o[f];
+            }
+            {
+                const float2 ms[3] = {myp[0][q], myp[1][q], myp[2][q]};
+                const float2 n[3] = {SW::unpack2(n_my_pull[0][q]), SW::unpack2(n_my_pull[1][q]),
+                                     SW::unpack2(n_my_pull[2][q])};
+                float2 fl[3], o[3];
+                fluxes_d2q5<float2, 1>(k, ms[0], ms[1], ms[2], fl);
+                outgoing<float2, 3, -1>(k, ms, fl, n, o);
+#pragma unroll
+                for (int f = 0; f < 3; ++f) B[f][3][q] = o[f];
+            }
+        }
+    }
     // ---- own non-equilibrium sum and the outgoing x populations of the lane's own nodes
-    float2 nown[3][P], ox_p[3][P], ox_m[3][P];
+    float2 ox_p[3][P], ox_m[3][P];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
         float2 a[3], b[3];
@@ -342,7 +374,6 @@ __device__ __forceinline__ void warp_split_step_2d(const In& fin, const Out& fou
         outgoing<float, 3, -1>(k, hm_r, fl, hn_r, halo_m);
     }
     // pulled populations B[f][l][q] (l = 0..3 for velocities 1..4): +x from x - 1, -x from x + 1
-    float2 B[3][4][P];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         const float from_left = __shfl_up_sync(0xffffffffu, ox_p[f][P - 1].y, 1);
@@ -353,28 +384,29 @@ __device__ __forceinline__ void warp_split_step_2d(const In& fin, const Out& fou
             B[f][1][q] = make_float2(ox_m[f][q].y, q == P - 1 ? (right_edge ? halo_m[f] : from_right) : ox_m[f][q + 1].x);
         }
     }
-    // +y from row y - 1, -y from row y + 1
+    if constexpr (!kYFirst) {
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-        {
-            const float2 ms[3] = {mym[0][q], mym[1][q], mym[2][q]};
-            const float2 n[3] = {SW::unpack2(n_py_pull[0][q]), SW::unpack2(n_py_pull[1][q]),
-                                 SW::unpack2(n_py_pull[2][q])};
-            float2 fl[3], o[3];
-            fluxes_d2q5<float2, 1>(k, ms[0], ms[1], ms[2], fl);
-            outgoing<float2, 3, +1>(k, ms, fl, n, o);
+        for (int q = 0; q < P; ++q) {   // +y from row y - 1, -y from row y + 1
+            {
+                const float2 ms[3] = {mym[0][q], mym[1][q], mym[2][q]};
+                const float2 n[3] = {SW::unpack2(n_py_pull[0][q]), SW::unpack2(n_py_pull[1][q]),
+                                     SW::unpack2(n_py_pull[2][q])};
+                float2 fl[3], o[3];
+                fluxes_d2q5<float2, 1>(k, ms[0], ms[1], ms[2], fl);
+                outgoing<float2, 3, +1>(k, ms, fl, n, o);
 #pragma unroll
-            for (int f = 0; f < 3; ++f) B[f][2][q] = o[f];
-        }
-        {
-            const float2 ms[3] = {myp[0][q], myp[1][q], myp[2][q]};
-            const float2 n[3] = {SW::unpack2(n_my_pull[0][q]), SW::unpack2(n_my_pull[1][q]),
-                                 SW::unpack2(n_my_pull[2][q])};
-            float2 fl[3], o[3];
-            fluxes_d2q5<float2, 1>(k, ms[0], ms[1], ms[2], fl);
-            outgoing<float2, 3, -1>(k, ms, fl, n, o);
+                for (int f = 0; f < 3; ++f) B[f][2][q] = o[f];
+            }
+            {
+                const float2 ms[3] = {myp[0][q], myp[1][q], myp[2][q]};
+                const float2 n[3] = {SW::unpack2(n_my_pull[0][q]), SW::unpack2(n_my_pull[1][q]),
+                                     SW::unpack2(n_my_pull[2][q])};
+                float2 fl[3], o[3];
+                fluxes_d2q5<float2, 1>(k, ms[0], ms[1], ms[2], fl);
+                outgoing<float2, 3, -1>(k, ms, fl, n, o);
 #pragma unroll
-            for (int f = 0; f < 3; ++f) B[f][3][q] = o[f];
+                for (int f = 0; f < 3; ++f) B[f][3][q] = o[f];
+            }
         }
     }
 
@@ -429,9 +461,10 @@ __device__ __forceinline__ void warp_split_step_2d(const In& fin, const Out& fou
 }
 
 // At least two resident blocks per SM (at most 128 registers): the BF16 instantiation with
-// fused diagnostics needs 131 and would otherwise run one block per SM.
+// fused diagnostics needs 131 and would otherwise run one block per SM.  The two-node-per-lane
+// plain step fits 80 registers and runs three blocks per SM (71.2 against 59.0 GLUPS at two).
 template <class S, int V, bool DIAG>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, (V == 2 && !DIAG) ? 3 : 2)
 k_split_step_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
                     FastDiv wdiv, Coef<typename Storage<S>::C> k, DiagSink sink,
                     uint32_t* __restrict__ step_ctr, int par) {
