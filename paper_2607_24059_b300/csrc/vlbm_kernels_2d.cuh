@@ -237,14 +237,15 @@ __device__ __forceinline__ uint32_t take_step_key(uint32_t* __restrict__ step_ct
 }
 
 // 16-bit storage moves half the bytes per node, so it needs more warps in flight to
-// cover the memory latency: three resident blocks per SM (at most 85 registers).  The
-// FP32 step with fused diagnostics does about 1.7 times the instructions of the plain
-// one; it takes V = 2 nodes per lane (DiagVec), also at three blocks per SM.
+// cover the memory latency: three resident blocks per SM (at most 85 registers); its step
+// with fused diagnostics keeps eight nodes per lane at two blocks per SM (at 85 registers it
+// spilled).  The FP32 step with fused diagnostics takes V = 2 nodes per lane (DiagVec), at
+// three blocks per SM.
 template <class S, bool DIAG> struct DiagVec { static constexpr int V = Vec16<S>::V; };
 template <> struct DiagVec<float, true> { static constexpr int V = 2; };
 
 template <class S, bool SPLIT, bool DIAG>
-__global__ void __launch_bounds__(kThreads, (sizeof(S) == 2 || (sizeof(S) == 4 && DIAG)) ? 3 : 1)
+__global__ void __launch_bounds__(kThreads, (sizeof(S) == 2 && DIAG) ? 2 : ((sizeof(S) == 2 || (sizeof(S) == 4 && DIAG)) ? 3 : 1))
 k_stream_collide_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, long long plane,
                         FastDiv wdiv, Coef<typename Storage<S>::C> k, DiagSink sink,
                         uint32_t* __restrict__ step_ctr, int par) {
@@ -256,9 +257,7 @@ k_stream_collide_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t key = take_step_key(step_ctr, par);
-    // FP32 storage accumulates node pairs; the 16-bit shifted kernels (eight nodes per lane,
-    // bounded to 80 registers) keep the smaller single-node accumulators
-    typename std::conditional<std::is_same<S, float>::value, AccPair, Acc<C>>::type acc;
+    typename AccOf<C>::T acc;   // node pairs for FP32 compute
     if (DIAG) acc.zero();
     // one row segment per warp; a smaller (persistent) grid loops, accumulating the
     // diagnostics of all its segments before one block reduction

@@ -15,11 +15,18 @@ template <class S> struct Vec8 {
     static constexpr int V = (8 / sizeof(S)) < 2 ? (8 / sizeof(S)) : 2;
 };
 
+// Resident blocks per SM the register budget is bounded for: the FP32 plain step fits 80
+// registers (three blocks); the steps with fused diagnostics 128 (two; unbounded, they took
+// 184-203 registers and ran one block per SM).  The 16-bit plain steps (96 registers, two
+// blocks) and FP64 keep the compiler's choice.
+template <class S, bool DIAG>
+constexpr int blocks_3d() { return sizeof(S) == 8 ? 1 : (DIAG ? 2 : (sizeof(S) == 4 ? 3 : 1)); }
+
 // Fused stream-collide, vectorised along x (n_x % V == 0).  Warp w handles
 // 32 V consecutive nodes of one (y, z) row.  x-shifts by warp shuffle as in
 // 2D; +-y are rows y -+ 1 of the same z slab, +-z the same row of slab z -+ 1.
 template <class S, bool SPLIT, bool DIAG>
-__global__ void __launch_bounds__(kThreads, (sizeof(S) == 4 && !DIAG) ? 3 : 1)
+__global__ void __launch_bounds__(kThreads, blocks_3d<S, DIAG>())
 k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, int nx, int ny, int nz,
                         long long plane, int warps_per_row, Coef<typename Storage<S>::C> k,
                         DiagSink sink, uint32_t* __restrict__ step_ctr, int par) {
@@ -34,8 +41,10 @@ k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const uint32_t key = take_step_key(step_ctr, par);
-    Acc<C> acc;
+    typename AccOf<C>::T acc;   // node pairs for FP32 compute (V = 2)
     if (DIAG) acc.zero();
+    // (64-bit division here: the multiply-high split of the 2D kernels cost this kernel
+    // registers, a larger spill and 16 % of its FP32 throughput)
     for (long long item = gwarp, items = (long long)ny * nz * warps_per_row; item < items; item += (DIAG ? nwarps : items)) {   // warp-uniform
         const long long r = item / warps_per_row;         // row index (z * ny + y)
         const int y = (int)(r % ny), z = (int)(r / ny);
@@ -85,6 +94,7 @@ k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
             }
         }
 
+        C mom[4][V];   // moments of the transported populations, for the diagnostics
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             C gn[28];
@@ -92,10 +102,25 @@ k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
             for (int p = 0; p < 28; ++p) gn[p] = g[p][i];
             C dr, Q[3];
             moments_d3q7(gn, dr, Q);
-            if (DIAG && active) accumulate_node(acc, moments_finite(dr, Q, 3), dr, Q, 3, k.rho_bar);
+            if constexpr (DIAG) {
+                mom[0][i] = dr;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) mom[1 + d][i] = Q[d];
+                if constexpr (!std::is_same<decltype(acc), AccPair>::value) {
+                    if (active) accumulate_node(acc, moments_finite(dr, Q, 3), dr, Q, 3, k.rho_bar);
+                }
+            }
             relax_d3q7<C, sizeof(S) == 2, SR>(k, gn, dr, Q, SR ? sr_node_word(key, row + x0 + i) : 0u);
 #pragma unroll
             for (int p = 0; p < 28; ++p) g[p][i] = gn[p];
+        }
+        if constexpr (DIAG && std::is_same<decltype(acc), AccPair>::value) {
+            static_assert(V == 2, "one node pair per lane");
+            if (active) {
+                const float2 Q[3] = {make_float2(mom[1][0], mom[1][1]), make_float2(mom[2][0], mom[2][1]),
+                                     make_float2(mom[3][0], mom[3][1])};
+                accumulate_pair(acc, make_float2(mom[0][0], mom[0][1]), Q, 3, k.rho_bar);
+            }
         }
 
         if (active) {
@@ -135,7 +160,10 @@ k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
             }
         }
     }
-    if (DIAG) block_reduce_finish(acc, sink);
+    if (DIAG) {
+        Acc<C> a = acc.fold();
+        block_reduce_finish(a, sink);
+    }
 }
 
 // One thread per node, any size.
