@@ -17,6 +17,7 @@
 #include "vlbm_kernels_2d.cuh"
 #include "vlbm_kernels_3d.cuh"
 #include "vlbm_split.cuh"
+#include "vlbm_fields.cuh"
 #include "vlbm_host.hpp"
 
 using namespace vlbm;

@@ -23,6 +23,7 @@
 #include "vlbm.h"
 #include "vlbm_host.hpp"
 #include "vlbm_split.cuh"
+#include "vlbm_fields.cuh"
 
 using namespace vlbm;
 

@@ -1,5 +1,5 @@
-// D2Q5 vectorial kernels: fused transport + relaxation, initialisation,
-// macroscopic fields, FP64 invariant reduction and population export.
+// D2Q5 vectorial step kernels: fused transport + relaxation (initialisation, macroscopic
+// fields, invariant reductions and export are in vlbm_fields.cuh).
 //
 // Lattice layout in HBM (one lattice per time level, two levels ping-pong):
 //   15 planes (field k = rho, q_x, q_y; velocity l = rest, +x, -x, +y, -y),
@@ -339,221 +339,6 @@ k_stream_collide_2d_generic(const char* __restrict__ fin_b, char* __restrict__ f
         }
     }
     if (DIAG) block_reduce_finish(acc, sink);
-}
-
-// ------------------------------------------------------------------------------
-// Initialisation at equilibrium: P(rho) = P(rho_bar) + dx^2 rho_bar phi,
-// q = rho u, g = f^eq(rho, q) - F.  The density deviation is formed in FP64:
-// gamma = 1 gives dr = dx^2 rho_bar phi exactly; otherwise
-// dr = rho_bar expm1(log1p(dx^2 rho_bar phi / P(rho_bar)) / gamma).
-// Equilibrium state of one node from u (planes x, y) and phi (may be NULL).
-template <class S, bool SPLIT, class T>
-__device__ __forceinline__ void init_node_2d(const Layout<S, SPLIT, 5>& f, long long plane, long long node,
-                                             const T* __restrict__ u, const T* __restrict__ phi,
-                                             const Coef<typename Storage<S>::C>& k, double dx, double gamma,
-                                             double rho_bar, double p_bar) {
-    using C = typename Storage<S>::C;
-    const double ph = phi ? (double)phi[node] : 0.0;
-    const double lift = dx * dx * rho_bar * ph;
-    const double dr = (gamma == 1.0) ? lift : rho_bar * expm1(log1p(lift / p_bar) / gamma);
-    const double rho = rho_bar + dr;
-    const double Qx = dx * rho * (double)u[node];
-    const double Qy = dx * rho * (double)u[plane + node];
-    if constexpr (SPLIT) {   // moments, and no departure from equilibrium
-        f.rest(0)[node] = (float)dr;
-        f.rest(1)[node] = (float)Qx;
-        f.rest(2)[node] = (float)Qy;
-#pragma unroll
-        for (int p = 0; p < 15; ++p)
-            if (p % 5) f.mov(p / 5, p % 5)[node] = Storage<S>::from_c(C(0));
-    } else {
-        C e[15];
-        equilibrium_d2q5(k, (C)dr, (C)Qx, (C)Qy, e);
-#pragma unroll
-        for (int p = 0; p < 15; ++p) store_pop(f, p / 5, p % 5, node, e[p], k);
-    }
-}
-
-template <class S, bool SPLIT, class T>
-__global__ void __launch_bounds__(kThreads)
-k_init_2d(char* __restrict__ f_b, long long plane, const T* __restrict__ u, const T* __restrict__ phi,
-          Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
-    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= plane) return;
-    init_node_2d<S, SPLIT, T>(Layout<S, SPLIT, 5>{f_b, plane}, plane, node, u, phi, k, dx, gamma, rho_bar, p_bar);
-}
-
-// Macroscopic fields of the state (moments of g*(t) = moments of g(t)), in FP64.
-// rho, u (planes x, y) and phi of one node; any output may be NULL.
-template <class S, bool SPLIT, class T>
-__device__ __forceinline__ void macros_node_2d(const Layout<S, SPLIT, 5>& f, long long plane, long long node,
-                                               T* __restrict__ rho, T* __restrict__ u, T* __restrict__ phi,
-                                               const Coef<typename Storage<S>::C>& k, double dx, double gamma,
-                                               double rho_bar, double p_bar) {
-    double m[3];
-#pragma unroll
-    for (int fld = 0; fld < 3; ++fld) {
-        if constexpr (SPLIT) {
-            m[fld] = (double)f.rest(fld)[node];
-        } else {
-            double mv = 0.0;
-#pragma unroll
-            for (int l = 1; l < 5; ++l) mv += (double)load_pop(f, fld, l, node, k);
-            m[fld] = (double)load_pop(f, fld, 0, node, k) + mv;
-        }
-    }
-    const double r = rho_bar + m[0];
-    if (rho) rho[node] = (T)r;
-    if (u) {
-        u[node] = (T)(m[1] / (dx * r));
-        u[plane + node] = (T)(m[2] / (dx * r));
-    }
-    if (phi) {
-        const double dP = (gamma == 1.0) ? m[0] : p_bar * expm1(gamma * log1p(m[0] / rho_bar));
-        phi[node] = (T)(dP / (dx * dx * rho_bar));
-    }
-}
-
-template <class S, bool SPLIT, class T>
-__global__ void __launch_bounds__(kThreads)
-k_macros_2d(const char* __restrict__ f_b, long long plane, T* __restrict__ rho, T* __restrict__ u, T* __restrict__ phi,
-            Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
-    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= plane) return;
-    macros_node_2d<S, SPLIT, T>(Layout<S, SPLIT, 5>{const_cast<char*>(f_b), plane}, plane, node, rho, u, phi, k, dx,
-                                gamma, rho_bar, p_bar);
-}
-
-// Invariant partials over the stored lattice (no transport), grid-stride.
-template <class S, bool SPLIT>
-__global__ void __launch_bounds__(kThreads)
-k_invariants_2d(const char* __restrict__ f_b, long long plane, Coef<typename Storage<S>::C> k,
-                double* __restrict__ partials) {
-    using C = typename Storage<S>::C;
-    const Layout<S, SPLIT, 5> f{const_cast<char*>(f_b), plane};
-    Acc<C> acc;
-    acc.zero();
-    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < plane;
-         node += (long long)gridDim.x * blockDim.x) {
-        C dr, Qx, Qy;
-        if constexpr (SPLIT) {
-            dr = (C)f.rest(0)[node];
-            Qx = (C)f.rest(1)[node];
-            Qy = (C)f.rest(2)[node];
-        } else {
-            C g[15];
-#pragma unroll
-            for (int p = 0; p < 15; ++p) g[p] = load_pop(f, p / 5, p % 5, node, k);
-            moments_d2q5(g, dr, Qx, Qy);
-        }
-        const C Q[2] = {Qx, Qy};
-        accumulate_node(acc, moments_finite(dr, Q, 2), dr, Q, 2, k.rho_bar);
-    }
-    block_reduce_store(acc, partials);
-}
-
-// First stage of the reduction of many partial rows: block b folds rows
-// b, b + gridDim.x, ... (fixed order) into stage[b * 8 + slot].  Spreads the
-// FP64 additions over many SMs (B300's FP64 rate per SM is low); the final
-// kernel then folds gridDim.x rows.  Thread t owns slot t % 8.
-static __global__ void __launch_bounds__(256)
-k_invariants_stage(const double* __restrict__ partials, int nblocks, double* __restrict__ stage) {
-    __shared__ double sh[256];
-    const int t = threadIdx.x, slot = t & 7;
-    const bool is_max = slot == 5;
-    double a = 0.0;
-    for (int b = blockIdx.x + (t >> 3) * gridDim.x; b < nblocks; b += 32 * gridDim.x) {
-        const double v = partials[(size_t)b * 8 + slot];
-        a = is_max ? fmax(a, v) : a + v;
-    }
-    sh[t] = a;
-    __syncthreads();
-    for (int stride = 16; stride > 0; stride >>= 1) {
-        if ((t >> 3) < stride) {
-            const double o = sh[t + stride * 8];
-            sh[t] = is_max ? fmax(sh[t], o) : sh[t] + o;
-        }
-        __syncthreads();
-    }
-    if (t < 8) stage[(size_t)blockIdx.x * 8 + t] = sh[t];
-}
-
-// Final reduction of nblocks partials (one block of 1024 threads, fixed order)
-// into the invariants { N rho_bar + sum dr, sum Q_d / dx (3), E_kin, max|u|,
-// non-finite nodes, sum dr }.  Thread t owns slot t % 8 of blocks t / 8,
-// t / 8 + 128, ...: consecutive threads read consecutive doubles.
-// scale_e = dx^(d-2) turns sum |Q|^2/(2 rho) into 1/2 sum |q|^2/rho dx^d.
-// Shared by 2D and 3D.
-static __global__ void __launch_bounds__(1024)
-k_invariants_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out, double nodes,
-                   double rho_bar, double inv_dx, double scale_e) {
-    __shared__ double sh[1024];
-    const int t = threadIdx.x, slot = t & 7;
-    const bool is_max = slot == 5;
-    double a = 0.0;
-#pragma unroll 16
-    for (int b = t >> 3; b < nblocks; b += 128) {
-        const double v = partials[(size_t)b * 8 + slot];
-        a = is_max ? fmax(a, v) : a + v;
-    }
-    sh[t] = a;
-    __syncthreads();
-    for (int stride = 64; stride > 0; stride >>= 1) {
-        if ((t >> 3) < stride) {
-            const double o = sh[t + stride * 8];
-            sh[t] = is_max ? fmax(sh[t], o) : sh[t] + o;
-        }
-        __syncthreads();
-    }
-    if (t == 0) write_invariants(out, sh, nodes, rho_bar, inv_dx, scale_e);
-}
-
-// Export populations in [p][node] order (p = q k + l): the stored deviation
-// g_p, or g_p + F_p with the rest equilibrium F = f^eq(rho_bar, 0):
-// rho field F = (f_rest, f_move, ..., f_move); momentum field j:
-// +p_half on the population along +e_j, -p_half along -e_j, 0 elsewhere.
-// Shared by 2D (Q = 5) and 3D (Q = 7).
-template <class S, bool SPLIT, int Q, class T>
-__global__ void __launch_bounds__(kThreads)
-k_export(const char* __restrict__ f_b, long long total, long long plane, T* __restrict__ dst,
-         Coef<typename Storage<S>::C> k, double f_rest, double f_move, double p_half, int deviation) {
-    const Layout<S, SPLIT, Q> f{const_cast<char*>(f_b), plane};
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= total) return;
-    const int p = (int)(i / plane);
-    const long long node = i - (long long)p * plane;
-    const int fld = p / Q, l = p % Q;
-    double v;
-    if constexpr (SPLIT) {   // g* = e(m) + n, rest: e_0(m) - sum of n
-        using C = typename Storage<S>::C;
-        C e[4 * 7];
-        if constexpr (Q == 5) {
-            C ev[15];
-            equilibrium_d2q5(k, (C)f.rest(0)[node], (C)f.rest(1)[node], (C)f.rest(2)[node], ev);
-            for (int i = 0; i < 15; ++i) e[i] = ev[i];
-        } else {
-            C ev[28];
-            const C qv[3] = {(C)f.rest(1)[node], (C)f.rest(2)[node], (C)f.rest(3)[node]};
-            equilibrium_d3q7(k, (C)f.rest(0)[node], qv, ev);
-            for (int i = 0; i < 28; ++i) e[i] = ev[i];
-        }
-        const C isc = mov_load_scale<S>(k, fld);
-        if (l == 0) {
-            double sn = 0.0;
-            for (int j = 1; j < Q; ++j) sn += (double)(Storage<S>::to_c(f.mov(fld, j)[node]) * isc);
-            v = (double)e[fld * Q] - sn;
-        } else {
-            v = (double)e[fld * Q + l] + (double)(Storage<S>::to_c(f.mov(fld, l)[node]) * isc);
-        }
-    } else {
-        v = (double)load_pop(f, fld, l, node, k);
-    }
-    if (!deviation) {
-        if (fld == 0) v += (l == 0) ? f_rest : f_move;
-        else if (l == 2 * (fld - 1) + 1) v += p_half;
-        else if (l == 2 * (fld - 1) + 2) v -= p_half;
-    }
-    dst[i] = (T)v;
 }
 
 }  // namespace vlbm

@@ -1,6 +1,5 @@
-// D3Q7 vectorial kernels (4 fields x 7 velocities = 28 populations per node):
-// fused transport + relaxation, initialisation, macroscopic fields and the
-// FP64 invariant partials.  Layout: 28 planes addressed through
+// D3Q7 vectorial step kernels (4 fields x 7 velocities = 28 populations per node):
+// fused transport + relaxation (the field kernels are in vlbm_fields.cuh).  Layout: 28 planes addressed through
 // Layout<S, SPLIT, 7>, each plane n_z x n_y x n_x, x fastest; velocities rest,
 // +x, -x, +y, -y, +z, -z.
 #pragma once
@@ -215,146 +214,6 @@ k_stream_collide_3d_generic(const char* __restrict__ fin_b, char* __restrict__ f
         }
     }
     if (DIAG) block_reduce_finish(acc, sink);
-}
-
-template <class S, bool SPLIT, class T>
-__global__ void __launch_bounds__(kThreads)
-k_init_3d(char* __restrict__ f_b, long long plane, const T* __restrict__ u, const T* __restrict__ phi,
-          Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
-    using C = typename Storage<S>::C;
-    const Layout<S, SPLIT, 7> f{f_b, plane};
-    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= plane) return;
-    const double ph = phi ? (double)phi[node] : 0.0;
-    const double lift = dx * dx * rho_bar * ph;
-    const double dr = (gamma == 1.0) ? lift : rho_bar * expm1(log1p(lift / p_bar) / gamma);
-    const double rho = rho_bar + dr;
-    C Q[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) Q[d] = (C)(dx * rho * (double)u[d * plane + node]);
-    if constexpr (SPLIT) {   // moments, and no departure from equilibrium
-        f.rest(0)[node] = (float)dr;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) f.rest(d + 1)[node] = (float)Q[d];
-#pragma unroll
-        for (int p = 0; p < 28; ++p)
-            if (p % 7) f.mov(p / 7, p % 7)[node] = Storage<S>::from_c(C(0));
-    } else {
-        C e[28];
-        equilibrium_d3q7(k, (C)dr, Q, e);
-#pragma unroll
-        for (int p = 0; p < 28; ++p) store_pop(f, p / 7, p % 7, node, e[p], k);
-    }
-}
-
-template <class S, bool SPLIT, class T>
-__global__ void __launch_bounds__(kThreads)
-k_macros_3d(const char* __restrict__ f_b, long long plane, T* __restrict__ rho, T* __restrict__ u, T* __restrict__ phi,
-            Coef<typename Storage<S>::C> k, double dx, double gamma, double rho_bar, double p_bar) {
-    const Layout<S, SPLIT, 7> f{const_cast<char*>(f_b), plane};
-    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= plane) return;
-    double m[4];
-#pragma unroll
-    for (int fld = 0; fld < 4; ++fld) {
-        if constexpr (SPLIT) {
-            m[fld] = (double)f.rest(fld)[node];
-        } else {
-            double mv = 0.0;
-#pragma unroll
-            for (int l = 1; l < 7; ++l) mv += (double)load_pop(f, fld, l, node, k);
-            m[fld] = (double)load_pop(f, fld, 0, node, k) + mv;
-        }
-    }
-    const double r = rho_bar + m[0];
-    if (rho) rho[node] = (T)r;
-    if (u)
-        for (int d = 0; d < 3; ++d) u[d * plane + node] = (T)(m[1 + d] / (dx * r));
-    if (phi) {
-        const double dP = (gamma == 1.0) ? m[0] : p_bar * expm1(gamma * log1p(m[0] / rho_bar));
-        phi[node] = (T)(dP / (dx * dx * rho_bar));
-    }
-}
-
-template <class S, bool SPLIT>
-__global__ void __launch_bounds__(kThreads)
-k_invariants_3d(const char* __restrict__ f_b, long long plane, Coef<typename Storage<S>::C> k,
-                double* __restrict__ partials) {
-    using C = typename Storage<S>::C;
-    const Layout<S, SPLIT, 7> f{const_cast<char*>(f_b), plane};
-    Acc<C> acc;
-    acc.zero();
-    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < plane;
-         node += (long long)gridDim.x * blockDim.x) {
-        C dr, Q[3];
-        if constexpr (SPLIT) {
-            dr = (C)f.rest(0)[node];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) Q[d] = (C)f.rest(d + 1)[node];
-        } else {
-            C g[28];
-#pragma unroll
-            for (int p = 0; p < 28; ++p) g[p] = load_pop(f, p / 7, p % 7, node, k);
-            moments_d3q7(g, dr, Q);
-        }
-        accumulate_node(acc, moments_finite(dr, Q, 3), dr, Q, 3, k.rho_bar);
-    }
-    block_reduce_store(acc, partials);
-}
-
-// ------------------------------------------------------------------------------
-// Vorticity diagnostic: per-block FP64 sums of |curl u|^2 with centred differences
-// (periodic), u [dim][nz][ny][nx] FP32 (2D: nz = 1, the scalar d_x u_y - d_y u_x).
-// The differences are taken in FP64 from the FP32 velocities; the caller scales by
-// 1 / (2 dx)^2 and dx^d.  Used every few hundred steps, not on the step path.
-static __global__ void __launch_bounds__(kThreads)
-k_vorticity_sq(const float* __restrict__ u, int nx, int ny, int nz, int dim, double* __restrict__ partials) {
-    __shared__ double sh[kThreads];
-    const long long N = (long long)nx * ny * nz;
-    double acc = 0.0;
-    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < N;
-         node += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(node % nx);
-        const long long r = node / nx;
-        const int y = (int)(r % ny), z = (int)(r / ny);
-        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-        auto U = [&](int c, int xx, int yy, int zz) {
-            return (double)__ldg(u + (long long)c * N + ((long long)zz * ny + yy) * nx + xx);
-        };
-        if (dim == 2) {
-            const double w = (U(1, xp, y, z) - U(1, xm, y, z)) - (U(0, x, yp, z) - U(0, x, ym, z));
-            acc += w * w;
-        } else {
-            const double wx = (U(2, x, yp, z) - U(2, x, ym, z)) - (U(1, x, y, zp) - U(1, x, y, zm));
-            const double wy = (U(0, x, y, zp) - U(0, x, y, zm)) - (U(2, xp, y, z) - U(2, xm, y, z));
-            const double wz = (U(1, xp, y, z) - U(1, xm, y, z)) - (U(0, x, yp, z) - U(0, x, ym, z));
-            acc += wx * wx + wy * wy + wz * wz;
-        }
-    }
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int stride = kThreads / 2; stride > 0; stride >>= 1) {
-        if ((int)threadIdx.x < stride) sh[threadIdx.x] += sh[threadIdx.x + stride];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
-}
-
-// One block: out[0] = scale * (sum of rows[0 .. n)), in a fixed order.
-static __global__ void __launch_bounds__(kThreads)
-k_sum_rows(const double* __restrict__ rows, int n, double scale, double* __restrict__ out) {
-    __shared__ double sh[kThreads];
-    double a = 0.0;
-    for (int i = threadIdx.x; i < n; i += kThreads) a += rows[i];
-    sh[threadIdx.x] = a;
-    __syncthreads();
-    for (int stride = kThreads / 2; stride > 0; stride >>= 1) {
-        if ((int)threadIdx.x < stride) sh[threadIdx.x] += sh[threadIdx.x + stride];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[0] = sh[0] * scale;
 }
 
 }  // namespace vlbm

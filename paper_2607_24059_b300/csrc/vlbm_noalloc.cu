@@ -32,7 +32,7 @@
 #include "vlbm.h"
 #include "vlbm_kernels_2d.cuh"
 #include "vlbm_host.hpp"
-#include "vlbm_kernels_3d.cuh"
+#include "vlbm_fields.cuh"
 
 using namespace vlbm;
 
