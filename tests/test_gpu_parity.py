@@ -515,7 +515,9 @@ def test_reduced_precision_benchmark_lattice_1000_steps(precision):
 
 # ------------------------------------------------------------ D3Q7
 
-@pytest.mark.parametrize("n", [(16, 12, 8), (15, 6, 5), (2, 3, 4), (1, 1, 6)])
+# (136, 6, 5): three row segments per row and six rows per plane, so the vectorised kernels'
+# work-item split (segment, row, plane) divides by numbers that are not powers of two
+@pytest.mark.parametrize("n", [(16, 12, 8), (15, 6, 5), (2, 3, 4), (1, 1, 6), (136, 6, 5)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("fp16split", 2e-3)])
 def test_d3q7_matches_oracle(orc, n, precision, tol):
     rng = np.random.default_rng(sum(n))
