@@ -63,6 +63,8 @@ extern "C" {
 /* ---- vlbm_step flags ---------------------------------------------------- */
 #define VLBM_STEP_CHECK_FINITE 1  /* after stepping, scan the lattice; VLBM_EDIVERGED if non-finite */
 #define VLBM_STEP_NO_GRAPH     2  /* launch kernel by kernel instead of replaying a captured CUDA graph */
+#define VLBM_STEP_PERSISTENT   4  /* vlbm_batch_step only: all steps in one cooperative launch (below) */
+#define VLBM_STEP_TEST_TIMEOUT 8  /* with VLBM_STEP_PERSISTENT: test of the timeout path (below) */
 
 /* Number of doubles written by vlbm_invariants. */
 #define VLBM_NUM_INVARIANTS 8
@@ -248,8 +250,9 @@ int vlbm_invariants_noalloc(const vlbm_params* p, const void* lattice, double* o
  * all share one precision, and n[0] of each must be a multiple of 4.  A
  * vlbm_batch_step advances every problem by one of its own time steps with
  * one persistent kernel launch over a work list of (problem, row, segment)
- * items; runs of steps replay a captured CUDA graph.  The arithmetic is that
- * of a single handle.  Not an operation of the paper: a way to run many of
+ * items; runs of steps replay a captured CUDA graph, or run in one
+ * cooperative launch (VLBM_STEP_PERSISTENT).  The arithmetic is that of a
+ * single handle.  Not an operation of the paper: a way to run many of
  * its problems at once. */
 typedef struct vlbm_batch vlbm_batch;
 
@@ -263,7 +266,18 @@ void vlbm_batch_destroy(vlbm_batch* b);
  * ([ny][nx] or NULL), as vlbm_init; host or device pointers. */
 int vlbm_batch_init(vlbm_batch* b, int32_t problem, const void* u, const void* phi, int32_t dtype);
 
-/* Advance every problem by nsteps of its own time step (asynchronous). */
+/* Advance every problem by nsteps of its own time step (asynchronous).
+ * flags & VLBM_STEP_PERSISTENT: one cooperative launch runs all nsteps (its
+ * grid is the configured launch shape capped at the blocks that can be
+ * resident together); its blocks wait for one another at every step
+ * boundary, each wait bounded to about one second.  The call synchronises
+ * and returns VLBM_ETIMEOUT if a wait gave up (the state is then partly
+ * advanced).  The arithmetic, and so the state, is that of per-step
+ * launches.  VLBM_STEP_TEST_TIMEOUT (with nsteps >= 2) makes the first
+ * step boundary wait for one block more than the launch has, so every
+ * block gives up after its bounded wait: the call returns VLBM_ETIMEOUT and
+ * the handle stays usable.  Otherwise one launch per step (flags &
+ * VLBM_STEP_NO_GRAPH) or replays of a captured graph of 32 launches. */
 int vlbm_batch_step(vlbm_batch* b, int64_t nsteps, int32_t flags);
 
 /* Macroscopic fields / invariants of one problem, as vlbm_macros / vlbm_invariants. */

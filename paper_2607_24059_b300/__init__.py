@@ -157,8 +157,10 @@ class Batch:
     def init(self, problem, u, phi=None):
         _binding.vlbm_batch_init(self.handle, problem, u, phi)
 
-    def step(self, nsteps=1, graph=True):
-        _binding.vlbm_batch_step(self.handle, nsteps, 0 if graph else _binding.VLBM_STEP_NO_GRAPH)
+    def step(self, nsteps=1, graph=True, persistent=False):
+        """persistent: all nsteps in one cooperative launch (synchronises; VlbmError on a barrier timeout)."""
+        flags = (0 if graph else _binding.VLBM_STEP_NO_GRAPH) | (_binding.VLBM_STEP_PERSISTENT if persistent else 0)
+        _binding.vlbm_batch_step(self.handle, nsteps, flags)
 
     def velocity(self, problem, dtype=None, device="cuda"):
         import torch

@@ -47,6 +47,8 @@ VLBM_DTYPE_F64 = 1
 
 VLBM_STEP_CHECK_FINITE = 1
 VLBM_STEP_NO_GRAPH = 2
+VLBM_STEP_PERSISTENT = 4
+VLBM_STEP_TEST_TIMEOUT = 8
 
 VLBM_NUM_INVARIANTS = 8
 VLBM_OPT_KERNEL = 0

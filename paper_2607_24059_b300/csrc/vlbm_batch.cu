@@ -85,6 +85,87 @@ k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
     }
 }
 
+// Grid-wide barrier of a cooperative launch (every block resident): block counts arrive on
+// *count, which the host zeroes before the launch; barrier k completes when it reaches
+// (k + 1) * gridDim.x.  The wait is bounded (about one second of globaltimer), and a block
+// that gives up, or sees another block's failure in *status, records it and returns false.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int target, int* status) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        const unsigned long long t0 = global_ns();
+        int ok = 1;
+        while (ld_acquire_gpu(count) < target) {
+            if (*(volatile int*)status != 0 || global_ns() - t0 > 1000000000ull) {
+                ok = 0;
+                atomicExch(status, 1);
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// nsteps time steps of every problem in one cooperative launch (VLBM_STEP_PERSISTENT): the
+// body of k_batch_step_2d per step, levels alternating from par0, a grid barrier between steps.
+// A step reads what the previous step of other blocks wrote, so its lattice loads are the
+// coherent L2 loads (COH) instead of the read-only path.  The step counter of the stochastic
+// rounding advances in registers; block 0 leaves step0 + nsteps in the slot the next launch reads.
+template <class S, bool SPLIT, int V>
+__global__ void __launch_bounds__(kMaxBatchThreads, 2)
+k_batch_steps_2d(char* level0, char* level1, const BatchProblem<typename Storage<S>::C>* __restrict__ probs,
+                 const int* __restrict__ chunk_problem, int count, long long items, uint32_t* step_ctr, int par0,
+                 int nsteps, unsigned int* bar_count, int* status, unsigned int phantom) {
+    using C = typename Storage<S>::C;
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const uint32_t step0 = __ldcg(step_ctr + par0);
+    Acc<C> unused;
+    for (int s = 0; s < nsteps; ++s) {
+        const int par = (par0 + s) & 1;
+        const char* in_base = par ? level1 : level0;
+        char* out_base = par ? level0 : level1;
+        const uint32_t key = sr_step_key(step0 + (uint32_t)s);
+        for (long long item = warp; item < items; item += nwarps) {   // warp-uniform
+            int p = __ldg(chunk_problem + (item >> kChunkShift));
+            while (p + 1 < count && probs[p + 1].item0 <= item) ++p;
+            const BatchProblem<C>& P = probs[p];
+            const long long local = item - P.item0;
+            const uint32_t y = P.wdiv.div((uint32_t)local);
+            const int seg = (int)((uint32_t)local - y * (uint32_t)P.wpr);
+            const Layout<S, SPLIT, 5> fin{const_cast<char*>(in_base) + P.offset, P.plane};
+            const Layout<S, SPLIT, 5> fout{out_base + P.offset, P.plane};
+            const Coef<C>& k = P.k;
+            if constexpr (SPLIT)
+                warp_split_step_2d<S, V, false, true>(fin, fout, P.nx, P.ny, (int)y, seg, lane, k, unused);
+            else
+                warp_stream_collide_2d<S, false, Vec16<S>::V, false, true>(
+                    reinterpret_cast<const S*>(in_base + P.offset), reinterpret_cast<S*>(out_base + P.offset), P.plane,
+                    P.nx, P.ny, (int)y, seg, lane, k, unused, key);
+        }
+        // (phantom = 1 only in the test of the timeout path: a block that never arrives)
+        if (s + 1 < nsteps && !grid_barrier(bar_count, (unsigned int)(s + 1) * gridDim.x + phantom, status)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) step_ctr[(par0 + nsteps) & 1] = step0 + (uint32_t)nsteps;
+}
+
 // Masked initialisation / read-out of equally sized problems against one state
 // array states [count][channels][ny][nx] FP32: channels 0, 1 = u, channel 2 =
 // phi when channels >= 3.  blockIdx.y = problem; problems with mask 0 are skipped.
@@ -166,7 +247,9 @@ struct vlbm_batch {
     size_t level_bytes = 0;
     int cur = 0;
     void* table = nullptr;          // BatchProblem<C>[count] on the device
-    uint32_t* ctr = nullptr;        // step counter of the stochastic rounding (2 slots, see take_step_key)
+    uint32_t* ctr = nullptr;        // step counter of the stochastic rounding (2 slots, see take_step_key),
+                                    // then the persistent launch's barrier count and status word
+    int* status_host = nullptr;     // pinned copy of the status word
     int* chunks = nullptr;          // problem of item 64 c, c = 0 .. items / 64
     long long items = 0;
     int threads = 256, blocks_per_sm = 4, lanes = 4;
@@ -284,6 +367,47 @@ void launch_batch_step(vlbm_batch* b, cudaStream_t s, int src) {
     }
 }
 
+// One cooperative launch of k_batch_steps_2d for nsteps steps: the launch shape of the per-step
+// kernel, its grid capped at the blocks that can be resident together.
+template <class S, bool SPLIT, int V>
+int launch_batch_steps(vlbm_batch* b, int nsteps, unsigned int phantom) {
+    using C = typename Storage<S>::C;
+    auto kernel = k_batch_steps_2d<S, SPLIT, V>;
+    int per_sm = 0;
+    VLBM_BCUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, b->threads, 0));
+    if (per_sm < 1) return VLBM_EINVAL;
+    const int grid = b->sm_count * std::min(per_sm, b->blocks_per_sm);
+    char* l0 = b->level[0];
+    char* l1 = b->level[1];
+    const BatchProblem<C>* probs = (const BatchProblem<C>*)b->table;
+    const int* chunks = b->chunks;
+    int count = b->count;
+    long long items = b->items;
+    uint32_t* ctr = b->ctr;
+    int par0 = b->cur;
+    unsigned int* bar = reinterpret_cast<unsigned int*>(b->ctr + 2);
+    int* status = reinterpret_cast<int*>(b->ctr + 3);
+    void* args[] = {&l0, &l1, &probs, &chunks, &count, &items, &ctr, &par0, &nsteps, &bar, &status, &phantom};
+    VLBM_BCUDA(b, cudaMemsetAsync(b->ctr + 2, 0, 2 * sizeof(uint32_t), b->stream));
+    VLBM_BCUDA(b, cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(b->threads), args, 0, b->stream));
+    return VLBM_OK;
+}
+
+int launch_batch_steps_any(vlbm_batch* b, int nsteps, unsigned int phantom) {
+    switch (b->precision) {
+        case VLBM_FP64: return launch_batch_steps<double, false, Vec16<double>::V>(b, nsteps, phantom);
+        case VLBM_FP32: return launch_batch_steps<float, false, Vec16<float>::V>(b, nsteps, phantom);
+        case VLBM_FP16_SHIFTED: return launch_batch_steps<__half, false, Vec16<__half>::V>(b, nsteps, phantom);
+        case VLBM_BF16_SHIFTED: return launch_batch_steps<__nv_bfloat16, false, Vec16<__nv_bfloat16>::V>(b, nsteps, phantom);
+        case VLBM_FP16_SPLIT:
+            return b->lanes == 2 ? launch_batch_steps<__half, true, 2>(b, nsteps, phantom)
+                                 : launch_batch_steps<__half, true, 4>(b, nsteps, phantom);
+        default:
+            return b->lanes == 2 ? launch_batch_steps<__nv_bfloat16, true, 2>(b, nsteps, phantom)
+                                 : launch_batch_steps<__nv_bfloat16, true, 4>(b, nsteps, phantom);
+    }
+}
+
 bool device_pointer(const void* ptr) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
@@ -317,6 +441,7 @@ void free_batch(vlbm_batch* b) {
     if (b->partials) cudaFree(b->partials);
     if (b->inv_dev) cudaFree(b->inv_dev);
     if (b->inv_host) cudaFreeHost(b->inv_host);
+    if (b->status_host) cudaFreeHost(b->status_host);
     if (b->staging) cudaFree(b->staging);
 }
 
@@ -437,11 +562,12 @@ extern "C" int vlbm_batch_create(const vlbm_params* problems, int32_t count, voi
     if (st == VLBM_OK &&
         (cudaMalloc(&b->partials, (size_t)b->partial_blocks * 8 * sizeof(double)) != cudaSuccess ||
          cudaMalloc(&b->inv_dev, 8 * sizeof(double)) != cudaSuccess ||
-         cudaMalloc(&b->ctr, 2 * sizeof(uint32_t)) != cudaSuccess ||
-         cudaMallocHost(&b->inv_host, 8 * sizeof(double)) != cudaSuccess))
+         cudaMalloc(&b->ctr, 4 * sizeof(uint32_t)) != cudaSuccess ||
+         cudaMallocHost(&b->inv_host, 8 * sizeof(double)) != cudaSuccess ||
+         cudaMallocHost(&b->status_host, sizeof(int)) != cudaSuccess))
         st = VLBM_ENOMEM;
     if (st == VLBM_OK && (cudaMemsetAsync(b->level[0], 0, off, b->stream) != cudaSuccess ||
-                          cudaMemsetAsync(b->ctr, 0, 2 * sizeof(uint32_t), b->stream) != cudaSuccess))
+                          cudaMemsetAsync(b->ctr, 0, 4 * sizeof(uint32_t), b->stream) != cudaSuccess))
         st = VLBM_ECUDA;
     if (st == VLBM_OK) st = rebuild_table(b);
     if (st != VLBM_OK) {
@@ -489,6 +615,26 @@ extern "C" int vlbm_batch_init(vlbm_batch* b, int32_t problem, const void* u, co
 
 extern "C" int vlbm_batch_step(vlbm_batch* b, int64_t nsteps, int32_t flags) {
     if (!b || nsteps < 0) return VLBM_EINVAL;
+    if (flags & VLBM_STEP_PERSISTENT) {
+        // all steps in cooperative launches of at most 2^30 steps, then the status word
+        for (int64_t left = nsteps; left > 0;) {
+            const int n = (int)std::min<int64_t>(left, 1 << 30);
+            int rc = launch_batch_steps_any(b, n, (flags & VLBM_STEP_TEST_TIMEOUT) ? 1u : 0u);
+            if (rc) return rc;
+            b->launches++;
+            b->step += n;
+            if (n & 1) b->cur ^= 1;
+            left -= n;
+        }
+        if (nsteps == 0) return VLBM_OK;
+        VLBM_BCUDA(b, cudaMemcpyAsync(b->status_host, b->ctr + 3, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+        VLBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+        if (*b->status_host != 0) {
+            b->err = "a grid barrier of the persistent batched step gave up waiting";
+            return VLBM_ETIMEOUT;
+        }
+        return VLBM_OK;
+    }
     const bool graphs = !(flags & VLBM_STEP_NO_GRAPH);
     int64_t left = nsteps;
     while (left > 0) {

@@ -438,10 +438,37 @@ template <> struct RawVec<8> { using T = uint2; };
 template <> struct RawVec<4> { using T = unsigned int; };
 template <> struct RawVec<2> { using T = unsigned short; };
 
-template <class S, int V>
+// Loads of lattice data.  A step kernel reads the level it does not write, so its loads take the
+// read-only (non-coherent) path; a kernel that runs several steps writes in one step what it
+// reads in the next (COH): those loads bypass L1 and read L2 (ld.global.cg), which is coherent
+// within the kernel once the step boundary's barrier has ordered the writes before them.
+template <bool COH, class T>
+__device__ __forceinline__ T ld_lattice(const T* p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ __half ld_lattice(const __half* p) {
+    const unsigned short b = ld_lattice<COH>(reinterpret_cast<const unsigned short*>(p));
+    return __ushort_as_half(b);
+}
+template <bool COH>
+__device__ __forceinline__ __nv_bfloat16 ld_lattice(const __nv_bfloat16* p) {
+    const unsigned short b = ld_lattice<COH>(reinterpret_cast<const unsigned short*>(p));
+    return __ushort_as_bfloat16(b);
+}
+
+// A plain load, or the coherent one of a multi-step kernel.
+template <bool COH, class T>
+__device__ __forceinline__ T ld_plain(const T* p) {
+    if constexpr (COH) return ld_lattice<true>(p);
+    else return *p;
+}
+
+template <class S, int V, bool COH = false>
 __device__ __forceinline__ void vload(S (&e)[V], const S* p) {
     using R = typename RawVec<V * sizeof(S)>::T;
-    *reinterpret_cast<R*>(&e[0]) = __ldg(reinterpret_cast<const R*>(p));
+    *reinterpret_cast<R*>(&e[0]) = ld_lattice<COH>(reinterpret_cast<const R*>(p));
 }
 
 template <class S, int V>

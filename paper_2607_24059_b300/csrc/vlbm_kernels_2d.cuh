@@ -27,10 +27,10 @@ template <class S> struct Vec16 {
     static constexpr int V = (16 / sizeof(S)) < 4 ? (16 / sizeof(S)) : 4;
 };
 
-template <class T, int V>
+template <class T, int V, bool COH = false>
 __device__ __forceinline__ void load_or_zero(T (&w)[V], const T* p, bool active) {
     if (active) {
-        vload<T, V>(w, p);
+        vload<T, V, COH>(w, p);
     } else {
 #pragma unroll
         for (int i = 0; i < V; ++i) w[i] = Storage<T>::from_c(typename Storage<T>::C(0));
@@ -57,7 +57,7 @@ __device__ __forceinline__ void load_or_zero(T (&w)[V], const T* p, bool active)
 // (FP32 0.2948 against 0.3162 ms), the interleaved order inside the persistent
 // loops of the recorded step and the batch kernel (recorded step 324 against
 // ~360 us).
-template <class S, bool DIAG, int V = Vec16<S>::V, bool LOAD_FIRST = !DIAG, class A>
+template <class S, bool DIAG, int V = Vec16<S>::V, bool LOAD_FIRST = !DIAG, bool COH = false, class A>
 __device__ __forceinline__ void warp_stream_collide_2d(const S* __restrict__ fin, S* __restrict__ fout, long long N,
                                                        int nx, int ny, int y, int seg, int lane,
                                                        const Coef<typename Storage<S>::C>& k, A& acc, uint32_t key) {
@@ -84,31 +84,31 @@ __device__ __forceinline__ void warp_stream_collide_2d(const S* __restrict__ fin
                 const C risc = rest_load_scale<S, false>(k, f);
                 const C isc = mov_load_scale<S>(k, f);
                 S w[V];
-                load_or_zero<S, V>(w, in_plane(f, 0) + row + x0, active);
+                load_or_zero<S, V, COH>(w, in_plane(f, 0) + row + x0, active);
 #pragma unroll
                 for (int i = 0; i < V; ++i) g[5 * f + 0][i] = Storage<S>::to_c(w[i]) * risc;
                 const S* px = in_plane(f, 1);
-                load_or_zero<S, V>(w, px + row + x0, active);
+                load_or_zero<S, V, COH>(w, px + row + x0, active);
                 {
                     S prev = __shfl_up_sync(0xffffffffu, w[V - 1], 1);
-                    if (lane == 0 && active) prev = __ldg(px + row + xm);
+                    if (lane == 0 && active) prev = ld_lattice<COH>(px + row + xm);
                     g[5 * f + 1][0] = Storage<S>::to_c(prev) * isc;
 #pragma unroll
                     for (int i = 1; i < V; ++i) g[5 * f + 1][i] = Storage<S>::to_c(w[i - 1]) * isc;
                 }
                 const S* mx = in_plane(f, 2);
-                load_or_zero<S, V>(w, mx + row + x0, active);
+                load_or_zero<S, V, COH>(w, mx + row + x0, active);
                 {
                     S next = __shfl_down_sync(0xffffffffu, w[0], 1);
-                    if (fetch_next) next = __ldg(mx + row + xp);
+                    if (fetch_next) next = ld_lattice<COH>(mx + row + xp);
 #pragma unroll
                     for (int i = 0; i < V - 1; ++i) g[5 * f + 2][i] = Storage<S>::to_c(w[i + 1]) * isc;
                     g[5 * f + 2][V - 1] = Storage<S>::to_c(next) * isc;
                 }
-                load_or_zero<S, V>(w, in_plane(f, 3) + row_m + x0, active);
+                load_or_zero<S, V, COH>(w, in_plane(f, 3) + row_m + x0, active);
 #pragma unroll
                 for (int i = 0; i < V; ++i) g[5 * f + 3][i] = Storage<S>::to_c(w[i]) * isc;
-                load_or_zero<S, V>(w, in_plane(f, 4) + row_p + x0, active);
+                load_or_zero<S, V, COH>(w, in_plane(f, 4) + row_p + x0, active);
 #pragma unroll
                 for (int i = 0; i < V; ++i) g[5 * f + 4][i] = Storage<S>::to_c(w[i]) * isc;
             }
@@ -119,17 +119,17 @@ __device__ __forceinline__ void warp_stream_collide_2d(const S* __restrict__ fin
             S edge_l[3], edge_r[3];
     #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                load_or_zero<S, V>(raw[f][0], in_plane(f, 0) + row + x0, active);
-                load_or_zero<S, V>(raw[f][1], in_plane(f, 1) + row + x0, active);
-                load_or_zero<S, V>(raw[f][2], in_plane(f, 2) + row + x0, active);
-                load_or_zero<S, V>(raw[f][3], in_plane(f, 3) + row_m + x0, active);
-                load_or_zero<S, V>(raw[f][4], in_plane(f, 4) + row_p + x0, active);
+                load_or_zero<S, V, COH>(raw[f][0], in_plane(f, 0) + row + x0, active);
+                load_or_zero<S, V, COH>(raw[f][1], in_plane(f, 1) + row + x0, active);
+                load_or_zero<S, V, COH>(raw[f][2], in_plane(f, 2) + row + x0, active);
+                load_or_zero<S, V, COH>(raw[f][3], in_plane(f, 3) + row_m + x0, active);
+                load_or_zero<S, V, COH>(raw[f][4], in_plane(f, 4) + row_p + x0, active);
             }
     #pragma unroll
             for (int f = 0; f < 3; ++f) {
                 edge_l[f] = edge_r[f] = Storage<S>::from_c(C(0));
-                if (lane == 0 && active) edge_l[f] = __ldg(in_plane(f, 1) + row + xm);
-                if (fetch_next) edge_r[f] = __ldg(in_plane(f, 2) + row + xp);
+                if (lane == 0 && active) edge_l[f] = ld_lattice<COH>(in_plane(f, 1) + row + xm);
+                if (fetch_next) edge_r[f] = ld_lattice<COH>(in_plane(f, 2) + row + xp);
             }
             // ---- shifts and conversion to deviations
     #pragma unroll

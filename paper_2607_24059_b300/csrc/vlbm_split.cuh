@@ -244,7 +244,7 @@ __device__ __forceinline__ void outgoing(const Coef<float>& k, const T (&m)[F], 
 //   pulled +y / -y populations from the equilibria of rows y -+ 1, in either order;
 //   the new moments, their equilibrium and the relaxed non-equilibrium parts (Section 2's
 //   collision in the split variables).
-template <class S, int V, bool DIAG, class In, class Out, class A>
+template <class S, int V, bool DIAG, bool COH = false, class In, class Out, class A>
 __device__ __forceinline__ void warp_split_step_2d(const In& fin, const Out& fout, int nx, int ny, int y, int seg,
                                                    int lane, const Coef<float>& k, A& acc) {
     static_assert(V % 2 == 0, "node pairs");
@@ -268,7 +268,7 @@ __device__ __forceinline__ void warp_split_step_2d(const In& fin, const Out& fou
     auto ldm = [&](float2 (&d)[P], const float* p) {
         if (active) {
             float t[V];
-            vload<float, V>(t, p);
+            vload<float, V, COH>(t, p);
 #pragma unroll
             for (int q = 0; q < P; ++q) d[q] = make_float2(t[2 * q], t[2 * q + 1]);
         } else {
@@ -278,7 +278,7 @@ __device__ __forceinline__ void warp_split_step_2d(const In& fin, const Out& fou
     };
     auto ldn = [&](uint32_t (&d)[P], const S* p) {
         if (active) {
-            const W w = __ldg(reinterpret_cast<const W*>(p));
+            const W w = ld_lattice<COH>(reinterpret_cast<const W*>(p));
             memcpy(&d[0], &w, sizeof(W));
         } else {
 #pragma unroll
@@ -298,12 +298,12 @@ __device__ __forceinline__ void warp_split_step_2d(const In& fin, const Out& fou
         ldn(n_my_own[f], fin.mov(f, 4) + row + x0);
         hm_l[f] = hm_r[f] = hn_l[f] = hn_r[f] = 0.0f;
         if (left_edge) {
-            hm_l[f] = fin.rest(f)[row + xm];
-            hn_l[f] = SW::to_c(fin.mov(f, 1)[row + xm]);
+            hm_l[f] = ld_plain<COH>(fin.rest(f) + row + xm);
+            hn_l[f] = SW::to_c(ld_plain<COH>(fin.mov(f, 1) + row + xm));
         }
         if (right_edge) {
-            hm_r[f] = fin.rest(f)[row + xp];
-            hn_r[f] = SW::to_c(fin.mov(f, 2)[row + xp]);
+            hm_r[f] = ld_plain<COH>(fin.rest(f) + row + xp);
+            hn_r[f] = SW::to_c(ld_plain<COH>(fin.mov(f, 2) + row + xp));
         }
     }
 

@@ -184,3 +184,49 @@ def test_batched_problem_set_members_match_oracle(orc):
         print(f"problem {q.index}: side {q.side}, nu {q.nu:.2e}: L2 {err:.2e}")
         assert err <= 1e-3, (q, err)
     b.close()
+
+
+def batch_of_problems(precision):
+    qs = [dict(n=q["n"], dx=problem_inputs(q)[2], nu=q["nu"]) for q in PROBLEMS]
+    b = v.Batch(qs, precision=precision)
+    for i, q in enumerate(PROBLEMS):
+        u, phi, _ = problem_inputs(q)
+        b.init(i, torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+    return b
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16", "bf16", "fp16split", "bf16split"])
+def test_persistent_launch_matches_per_step_launches(precision):
+    """VLBM_STEP_PERSISTENT runs the steps in one cooperative launch whose blocks wait for each
+    other at step boundaries; it advances every problem as per-step launches do (odd and even
+    step counts, so the levels end on either parity, and a per-step launch after it)."""
+    out = []
+    for persistent in (False, True):
+        b = batch_of_problems(precision)
+        b.set_config(128, 4, 4)
+        b.step(7, graph=False, persistent=persistent)
+        b.step(10, graph=False, persistent=persistent)
+        b.step(1, graph=False)
+        out.append([b.velocity(i).cpu().numpy() for i in range(len(PROBLEMS))])
+        assert b.info()[1] == 18
+        b.close()
+    # the two launch forms instantiate the same per-node arithmetic with different loads; the
+    # compiler may still contract a multiply-add pair differently in the two kernels
+    rel = {"fp64": 1e-13, "fp32": 1e-6}.get(precision, 2e-3 if "fp16" in precision else 1.6e-2)
+    for a, c in zip(*out):
+        assert np.max(np.abs(a - c)) <= rel * np.max(np.abs(c)), np.max(np.abs(a - c)) / np.max(np.abs(c))
+
+
+def test_persistent_launch_timeout_path_reports_and_recovers():
+    """The test flag makes the first step boundary wait for a block that does not exist: every
+    block gives up after its bounded wait (about one second), the call reports VLBM_ETIMEOUT,
+    and the batch steps normally afterwards."""
+    b = batch_of_problems("fp32")
+    with pytest.raises(v.VlbmError) as e:
+        v.vlbm_batch_step(b.handle, 2, v.VLBM_STEP_PERSISTENT | v.VLBM_STEP_TEST_TIMEOUT)
+    assert e.value.code == v.VLBM_ETIMEOUT
+    b.step(3, graph=False)
+    b.step(2, graph=False, persistent=True)
+    for i in range(len(PROBLEMS)):
+        assert np.all(np.isfinite(b.velocity(i).cpu().numpy()))
+    b.close()
