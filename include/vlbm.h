@@ -247,7 +247,8 @@ int vlbm_invariants_noalloc(const vlbm_params* p, const void* lattice, double* o
 /* ---- batched problems ----------------------------------------------------
  * Many independent periodic 2D problems advanced together: each has its own
  * vlbm_params (size, dx, viscosity, relaxation; dt = dx^2 / mu of its own),
- * all share one precision, and n[0] of each must be a multiple of 4.  A
+ * all share one precision; any n[0] (a problem whose n[0] is not a multiple
+ * of the format's vector width runs the per-node body, one node per lane).  A
  * vlbm_batch_step advances every problem by one of its own time steps with
  * one persistent kernel launch over a work list of (problem, row, segment)
  * items; runs of steps replay a captured CUDA graph, or run in one

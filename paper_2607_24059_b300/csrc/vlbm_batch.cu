@@ -39,7 +39,8 @@ struct BatchProblem {
     long long plane;         // nodes
     long long item0;         // first work item of this problem
     int nx, ny, wpr;         // sizes, warps (row segments) per row
-    int pad;
+    int vec;                 // 1: n_x is a multiple of the vector width (the vectorised warp body);
+                             // 0: one node per lane, 32 per row segment (the per-node body)
     FastDiv wdiv;            // division by wpr
     Coef<C> k;
 };
@@ -76,12 +77,20 @@ k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
         const Layout<S, SPLIT, 5> fin{const_cast<char*>(in_base) + P.offset, P.plane};
         const Layout<S, SPLIT, 5> fout{out_base + P.offset, P.plane};
         const Coef<C>& k = P.k;   // read through L1, not copied into registers
-        if constexpr (SPLIT)
+        if (!P.vec) {             // warp-uniform: one node per lane
+            const int x = seg * 32 + lane;
+            const long long node = (long long)y * P.nx + x;
+            if (x < P.nx) {
+                if constexpr (SPLIT) node_split_step_2d<S, false>(fin, fout, P.nx, P.ny, node, k, unused);
+                else node_stream_collide_2d<S, SPLIT, false>(fin, fout, P.nx, P.ny, node, k, unused, key);
+            }
+        } else if constexpr (SPLIT) {
             warp_split_step_2d<S, V, false>(fin, fout, P.nx, P.ny, (int)y, seg, lane, k, unused);
-        else
+        } else {
             warp_stream_collide_2d<S, false, Vec16<S>::V, false>(reinterpret_cast<const S*>(in_base + P.offset),
                                              reinterpret_cast<S*>(out_base + P.offset), P.plane, P.nx, P.ny, (int)y, seg,
                                              lane, k, unused, key);
+        }
     }
 }
 
@@ -153,12 +162,20 @@ k_batch_steps_2d(char* level0, char* level1, const BatchProblem<typename Storage
             const Layout<S, SPLIT, 5> fin{const_cast<char*>(in_base) + P.offset, P.plane};
             const Layout<S, SPLIT, 5> fout{out_base + P.offset, P.plane};
             const Coef<C>& k = P.k;
-            if constexpr (SPLIT)
+            if (!P.vec) {
+                const int x = seg * 32 + lane;
+                const long long node = (long long)y * P.nx + x;
+                if (x < P.nx) {
+                    if constexpr (SPLIT) node_split_step_2d<S, false, true>(fin, fout, P.nx, P.ny, node, k, unused);
+                    else node_stream_collide_2d<S, SPLIT, false, true>(fin, fout, P.nx, P.ny, node, k, unused, key);
+                }
+            } else if constexpr (SPLIT) {
                 warp_split_step_2d<S, V, false, true>(fin, fout, P.nx, P.ny, (int)y, seg, lane, k, unused);
-            else
+            } else {
                 warp_stream_collide_2d<S, false, Vec16<S>::V, false, true>(
                     reinterpret_cast<const S*>(in_base + P.offset), reinterpret_cast<S*>(out_base + P.offset), P.plane,
                     P.nx, P.ny, (int)y, seg, lane, k, unused, key);
+            }
         }
         // (phantom = 1 only in the test of the timeout path: a block that never arrives)
         if (s + 1 < nsteps && !grid_barrier(bar_count, (unsigned int)(s + 1) * gridDim.x + phantom, status)) return;
@@ -301,8 +318,8 @@ int upload_table(vlbm_batch* b) {
         t[i].plane = b->d[i].nodes;
         t[i].nx = (int)b->p[i].n[0];
         t[i].ny = (int)b->p[i].n[1];
-        t[i].wpr = (int)((b->p[i].n[0] / V + 31) / 32);
-        t[i].pad = 0;
+        t[i].vec = b->p[i].n[0] % V == 0;
+        t[i].wpr = (int)(t[i].vec ? (b->p[i].n[0] / V + 31) / 32 : (b->p[i].n[0] + 31) / 32);
         t[i].wdiv = FastDiv::make((uint32_t)t[i].wpr);
         t[i].item0 = item;
         t[i].k = make_coef<C>(b->p[i], b->d[i], scale);
@@ -533,7 +550,7 @@ extern "C" int vlbm_batch_create(const vlbm_params* problems, int32_t count, voi
     std::vector<vlbm_derived> d(count);
     for (int i = 0; i < count; ++i) {
         const vlbm_params& q = problems[i];
-        if (q.dim != 2 || q.precision != prec || q.n[0] % 4 != 0) return VLBM_EINVAL;
+        if (q.dim != 2 || q.precision != prec) return VLBM_EINVAL;
         if (q.n[0] > (1 << 24) || q.n[1] > (1 << 24)) return VLBM_EINVAL;
         if (vlbm_params_check(&q, &d[i]) < 0) return VLBM_EINVAL;
     }

@@ -274,12 +274,12 @@ k_stream_collide_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
 }
 
 // Load / store one population of one node through the layout (scaled to deviations).
-template <class S, bool SPLIT, int Q>
+template <bool COH = false, class S, bool SPLIT, int Q>
 __device__ __forceinline__ typename Storage<S>::C load_pop(const Layout<S, SPLIT, Q>& L, int f, int l, long long node,
                                                            const Coef<typename Storage<S>::C>& k) {
     using R = typename Layout<S, SPLIT, Q>::R;
-    if (l == 0) return Storage<R>::to_c(L.rest(f)[node]) * rest_load_scale<S, SPLIT>(k, f);
-    return Storage<S>::to_c(L.mov(f, l)[node]) * mov_load_scale<S>(k, f);
+    if (l == 0) return Storage<R>::to_c(ld_plain<COH>(L.rest(f) + node)) * rest_load_scale<S, SPLIT>(k, f);
+    return Storage<S>::to_c(ld_plain<COH>(L.mov(f, l) + node)) * mov_load_scale<S>(k, f);
 }
 
 template <class S, bool SPLIT, int Q>
@@ -288,6 +288,49 @@ __device__ __forceinline__ void store_pop(const Layout<S, SPLIT, Q>& L, int f, i
     using R = typename Layout<S, SPLIT, Q>::R;
     if (l == 0) L.rest(f)[node] = Storage<R>::from_c(v * rest_store_scale<S, SPLIT>(k, f));
     else L.mov(f, l)[node] = Storage<S>::from_c(v * mov_store_scale<S>(k, f));
+}
+
+// One node of the fused stream-collide (the per-node kernel's body; also the batched step's
+// path for problems whose n_x is not a multiple of its vector width).  COH: coherent loads
+// (the multi-step batched launch).
+template <class S, bool SPLIT, bool DIAG, bool COH = false>
+__device__ __forceinline__ void node_stream_collide_2d(const Layout<S, SPLIT, 5>& fin, const Layout<S, SPLIT, 5>& fout,
+                                                       int nx, int ny, long long node,
+                                                       const Coef<typename Storage<S>::C>& k,
+                                                       Acc<typename Storage<S>::C>& acc, uint32_t key) {
+    using C = typename Storage<S>::C;
+    constexpr bool SR = StochasticMoments<S>::value && !SPLIT;
+    constexpr bool SR16 = StochasticStore16<S>::value && !SPLIT;
+    const int x = (int)(node % nx), y = (int)(node / nx);
+    const long long row = (long long)y * nx;
+    const long long src[5] = {
+        node,
+        row + (x == 0 ? nx - 1 : x - 1),
+        row + (x == nx - 1 ? 0 : x + 1),
+        (long long)(y == 0 ? ny - 1 : y - 1) * nx + x,
+        (long long)(y == ny - 1 ? 0 : y + 1) * nx + x,
+    };
+    C g[15];
+#pragma unroll
+    for (int p = 0; p < 15; ++p) g[p] = load_pop<COH>(fin, p / 5, p % 5, src[p % 5], k);
+    C dr, Qx, Qy;
+    moments_d2q5(g, dr, Qx, Qy);
+    if constexpr (DIAG) {
+        const C Q[2] = {Qx, Qy};
+        accumulate_node(acc, moments_finite(dr, Q, 2), dr, Q, 2, k.rho_bar);
+    }
+    relax_d2q5<C, sizeof(S) == 2, SR>(k, g, dr, Qx, Qy, SR ? sr_node_word(key, node) : 0u);
+#pragma unroll
+    for (int p = 0; p < 15; ++p) {
+        if constexpr (SR16) {
+            if (p % 5 == 0 && k.sr16) {
+                fout.rest(p / 5)[node] =
+                    sr16_store_one<S>(g[p] * rest_store_scale<S, SPLIT>(k, p / 5), node, key, p / 5);
+                continue;
+            }
+        }
+        store_pop(fout, p / 5, p % 5, node, g[p], k);
+    }
 }
 
 // ------------------------------------------------------------------------------
@@ -299,44 +342,13 @@ k_stream_collide_2d_generic(const char* __restrict__ fin_b, char* __restrict__ f
                             uint32_t* __restrict__ step_ctr, int par) {
     using C = typename Storage<S>::C;
     using L = Layout<S, SPLIT, 5>;
-    constexpr bool SR = StochasticMoments<S>::value && !SPLIT;
-    constexpr bool SR16 = StochasticStore16<S>::value && !SPLIT;
     const L fin{const_cast<char*>(fin_b), plane}, fout{fout_b, plane};
     const uint32_t key = take_step_key(step_ctr, par);
     Acc<C> acc;
     if (DIAG) acc.zero();
     for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < plane;
          node += (DIAG ? (long long)gridDim.x * blockDim.x : plane)) {
-        const int x = (int)(node % nx), y = (int)(node / nx);
-        const long long row = (long long)y * nx;
-        const long long src[5] = {
-            node,
-            row + (x == 0 ? nx - 1 : x - 1),
-            row + (x == nx - 1 ? 0 : x + 1),
-            (long long)(y == 0 ? ny - 1 : y - 1) * nx + x,
-            (long long)(y == ny - 1 ? 0 : y + 1) * nx + x,
-        };
-        C g[15];
-#pragma unroll
-        for (int p = 0; p < 15; ++p) g[p] = load_pop(fin, p / 5, p % 5, src[p % 5], k);
-        C dr, Qx, Qy;
-        moments_d2q5(g, dr, Qx, Qy);
-        if (DIAG) {
-            const C Q[2] = {Qx, Qy};
-            accumulate_node(acc, moments_finite(dr, Q, 2), dr, Q, 2, k.rho_bar);
-        }
-        relax_d2q5<C, sizeof(S) == 2, SR>(k, g, dr, Qx, Qy, SR ? sr_node_word(key, node) : 0u);
-#pragma unroll
-        for (int p = 0; p < 15; ++p) {
-            if constexpr (SR16) {
-                if (p % 5 == 0 && k.sr16) {
-                    fout.rest(p / 5)[node] =
-                        sr16_store_one<S>(g[p] * rest_store_scale<S, SPLIT>(k, p / 5), node, key, p / 5);
-                    continue;
-                }
-            }
-            store_pop(fout, p / 5, p % 5, node, g[p], k);
-        }
+        node_stream_collide_2d<S, SPLIT, DIAG>(fin, fout, nx, ny, node, k, acc, key);
     }
     if (DIAG) block_reduce_finish(acc, sink);
 }

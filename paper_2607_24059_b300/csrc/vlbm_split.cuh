@@ -487,6 +487,52 @@ k_split_step_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_b, i
     }
 }
 
+// One node of the 2D split step (the per-node kernel's body; also the batched step's path for
+// problems whose n_x is not a multiple of its vector width).  COH: coherent loads.
+template <class S, bool DIAG, bool COH = false>
+__device__ __forceinline__ void node_split_step_2d(const Layout<S, true, 5>& fin, const Layout<S, true, 5>& fout,
+                                                   int nx, int ny, long long node, const Coef<float>& k,
+                                                   Acc<float>& acc) {
+    using C = float;
+    const int x = (int)(node % nx), y = (int)(node / nx);
+    const long long row = (long long)y * nx;
+    const long long src[5] = {
+        node,
+        row + (x == 0 ? nx - 1 : x - 1),
+        row + (x == nx - 1 ? 0 : x + 1),
+        (long long)(y == 0 ? ny - 1 : y - 1) * nx + x,
+        (long long)(y == ny - 1 ? 0 : y + 1) * nx + x,
+    };
+    C m[3], nown[3] = {C(0), C(0), C(0)}, B[3][4];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) m[f] = ld_plain<COH>(fin.rest(f) + node);
+#pragma unroll
+    for (int l = 1; l < 5; ++l) {
+        C ms[3], np[3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            ms[f] = ld_plain<COH>(fin.rest(f) + src[l]);
+            np[f] = Storage<S>::to_c(ld_plain<COH>(fin.mov(f, l) + src[l]));      // stored units
+            nown[f] += Storage<S>::to_c(ld_plain<COH>(fin.mov(f, l) + node));
+        }
+        if (l == 1) pulled_d2q5<C, 1>(k, ms, np, B);
+        else if (l == 2) pulled_d2q5<C, 2>(k, ms, np, B);
+        else if (l == 3) pulled_d2q5<C, 3>(k, ms, np, B);
+        else pulled_d2q5<C, 4>(k, ms, np, B);
+    }
+    split_update_d2q5(k, m, B, nown);
+    if constexpr (DIAG) {
+        const C Q[2] = {m[1], m[2]};
+        accumulate_node(acc, moments_finite(m[0], Q, 2), m[0], Q, 2, k.rho_bar);
+    }
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        fout.rest(f)[node] = (float)m[f];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) fout.mov(f, l + 1)[node] = Storage<S>::from_c(B[f][l]);
+    }
+}
+
 // One thread per node, any size (2D split form).
 template <class S, bool DIAG>
 __global__ void __launch_bounds__(kThreads)
@@ -500,45 +546,8 @@ k_split_step_2d_generic(const char* __restrict__ fin_b, char* __restrict__ fout_
     Acc<C> acc;
     if (DIAG) acc.zero();
     for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < plane;
-         node += (DIAG ? (long long)gridDim.x * blockDim.x : plane)) {
-        const int x = (int)(node % nx), y = (int)(node / nx);
-        const long long row = (long long)y * nx;
-        const long long src[5] = {
-            node,
-            row + (x == 0 ? nx - 1 : x - 1),
-            row + (x == nx - 1 ? 0 : x + 1),
-            (long long)(y == 0 ? ny - 1 : y - 1) * nx + x,
-            (long long)(y == ny - 1 ? 0 : y + 1) * nx + x,
-        };
-        C m[3], nown[3] = {C(0), C(0), C(0)}, B[3][4];
-#pragma unroll
-        for (int f = 0; f < 3; ++f) m[f] = (C)fin.rest(f)[node];
-#pragma unroll
-        for (int l = 1; l < 5; ++l) {
-            C ms[3], np[3];
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                ms[f] = (C)fin.rest(f)[src[l]];
-                np[f] = Storage<S>::to_c(fin.mov(f, l)[src[l]]);      // stored units
-                nown[f] += Storage<S>::to_c(fin.mov(f, l)[node]);
-            }
-            if (l == 1) pulled_d2q5<C, 1>(k, ms, np, B);
-            else if (l == 2) pulled_d2q5<C, 2>(k, ms, np, B);
-            else if (l == 3) pulled_d2q5<C, 3>(k, ms, np, B);
-            else pulled_d2q5<C, 4>(k, ms, np, B);
-        }
-        split_update_d2q5(k, m, B, nown);
-        if (DIAG) {
-            const C Q[2] = {m[1], m[2]};
-            accumulate_node(acc, moments_finite(m[0], Q, 2), m[0], Q, 2, k.rho_bar);
-        }
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            fout.rest(f)[node] = (float)m[f];
-#pragma unroll
-            for (int l = 0; l < 4; ++l) fout.mov(f, l + 1)[node] = Storage<S>::from_c(B[f][l]);
-        }
-    }
+         node += (DIAG ? (long long)gridDim.x * blockDim.x : plane))
+        node_split_step_2d<S, DIAG>(fin, fout, nx, ny, node, k, acc);
     if (DIAG) block_reduce_finish(acc, sink);
 }
 

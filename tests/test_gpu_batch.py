@@ -156,7 +156,9 @@ def test_batch_invariants_match_oracle():
 
 def test_batch_rejects_bad_problems():
     with pytest.raises(v.VlbmError):
-        v.Batch([dict(n=(30, 16), dx=0.1, nu=0.01)])          # n_x not a multiple of 4
+        v.Batch([dict(n=(32, 16), dx=0.1, nu=0.01), dict(n=(0, 16), dx=0.1, nu=0.01)])   # empty lattice
+    with pytest.raises(v.VlbmError):
+        v.Batch([dict(n=(32, 16), dx=0.1, nu=0.01, omega_q=2.5)])                         # omega outside (0, 2)
 
 
 def test_batched_problem_set_members_match_oracle(orc):
@@ -230,3 +232,57 @@ def test_persistent_launch_timeout_path_reports_and_recovers():
     for i in range(len(PROBLEMS)):
         assert np.all(np.isfinite(b.velocity(i).cpu().numpy()))
     b.close()
+
+
+# widths that are not multiples of the vector width (4 for FP32 and split, 8 for the 16-bit
+# shifted formats, 2 for FP64): those problems run the per-node body, one node per lane
+RAGGED = [
+    dict(n=(37, 23), nu=0.01, seed=11),
+    dict(n=(50, 30), nu=0.004, seed=12),
+    dict(n=(36, 20), nu=0.002, seed=13),
+    dict(n=(64, 16), nu=0.006, seed=14),
+    dict(n=(13, 11), nu=0.01, seed=15),
+]
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16split", "bf16split"])
+def test_ragged_widths_match_oracle_per_problem(precision, persistent):
+    qs = [dict(n=q["n"], dx=problem_inputs(q)[2], nu=q["nu"]) for q in RAGGED]
+    b = v.Batch(qs, precision=precision)
+    orc = oracle.default()
+    steps = 37
+    refs = []
+    for i, q in enumerate(RAGGED):
+        u, phi, dx = problem_inputs(q)
+        b.init(i, torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+        op = oracle.make_params(q["n"], dx, nu=q["nu"])
+        refs.append(orc.macros(op, orc.run(op, orc.init(op, u, phi), steps))[1])
+    b.step(steps, graph=False, persistent=persistent)
+    for i, uo in enumerate(refs):
+        ug = b.velocity(i).cpu().numpy()
+        err = np.max(np.abs(ug - uo)) / np.max(np.abs(uo)) if precision in ("fp64", "fp32") else l2_rel(ug, uo)
+        assert err <= TOL[precision], (RAGGED[i]["n"], err)
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_ragged_widths_shifted_equal_single_handles(precision):
+    qs = [dict(n=q["n"], dx=problem_inputs(q)[2], nu=q["nu"]) for q in RAGGED]
+    b = v.Batch(qs, precision=precision)
+    singles = []
+    for i, q in enumerate(RAGGED):
+        u, phi, dx = problem_inputs(q)
+        b.init(i, torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+        lat = v.Lattice(q["n"], dx, nu=q["nu"], precision=precision)
+        lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+        lat.step(25)
+        singles.append(lat.macros()[1].cpu().numpy())
+        lat.close()
+    b.step(25)
+    tol = {"fp16": 2e-3, "bf16": 1.6e-2}[precision]
+    for i, us in enumerate(singles):
+        ub = b.velocity(i).cpu().numpy()
+        assert np.max(np.abs(ub - us)) <= tol * np.max(np.abs(us)), RAGGED[i]["n"]
+    b.close()
+
