@@ -14,12 +14,12 @@ template <class S> struct Vec8 {
     static constexpr int V = (8 / sizeof(S)) < 2 ? (8 / sizeof(S)) : 2;
 };
 
-// Resident blocks per SM the register budget is bounded for: the FP32 plain step fits 80
-// registers (three blocks); the steps with fused diagnostics 128 (two; unbounded, they took
-// 184-203 registers and ran one block per SM).  The 16-bit plain steps (96 registers, two
-// blocks) and FP64 keep the compiler's choice.
+// Resident blocks per SM the register budget is bounded for: the FP32 and 16-bit plain steps
+// fit 80 registers (three blocks; the 16-bit ones with every load first, 40.2 -> 49.8 GLUPS
+// for FP16 at 256^3); the steps with fused diagnostics 128 (two; unbounded, they took
+// 184-203 registers and ran one block per SM).  FP64 keeps the compiler's choice.
 template <class S, bool DIAG>
-constexpr int blocks_3d() { return sizeof(S) == 8 ? 1 : (DIAG ? 2 : (sizeof(S) == 4 ? 3 : 1)); }
+constexpr int blocks_3d() { return sizeof(S) == 8 ? 1 : (DIAG ? 2 : 3); }
 
 // Fused stream-collide, vectorised along x (n_x % V == 0).  Warp w handles
 // 32 V consecutive nodes of one (y, z) row.  x-shifts by warp shuffle as in
@@ -59,6 +59,52 @@ k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
         const bool fetch_next = active && (lane == 31 || x0 + V >= nx);
 
         C g[28][V];
+        // 16-bit storage: every vector of the lane and the warp-edge elements requested before the
+        // first shuffle (half the bytes per warp of FP32 need more of them in flight); FP32, at the
+        // HBM roofline with either order, keeps the interleaved one
+        constexpr bool LOAD_FIRST = !DIAG && sizeof(S) == 2;
+        if constexpr (LOAD_FIRST) {
+            R raw0[4][V];
+            S raw[4][6][V];
+            S edge_l[4], edge_r[4];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                load_or_zero<R, V>(raw0[f], fin.rest(f) + row + x0, active);
+#pragma unroll
+                for (int l = 1; l < 7; ++l) load_or_zero<S, V>(raw[f][l - 1], fin.mov(f, l) + src_row[l] + x0, active);
+            }
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                edge_l[f] = edge_r[f] = Storage<S>::from_c(C(0));
+                if (lane == 0 && active) edge_l[f] = __ldg(fin.mov(f, 1) + row + xm);
+                if (fetch_next) edge_r[f] = __ldg(fin.mov(f, 2) + row + xp);
+            }
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const C risc = rest_load_scale<S, SPLIT>(k, f);
+                const C isc = mov_load_scale<S>(k, f);
+#pragma unroll
+                for (int i = 0; i < V; ++i) g[7 * f][i] = Storage<R>::to_c(raw0[f][i]) * risc;
+                {
+                    S prev = __shfl_up_sync(0xffffffffu, raw[f][0][V - 1], 1);
+                    if (lane == 0) prev = edge_l[f];
+                    g[7 * f + 1][0] = Storage<S>::to_c(prev) * isc;
+#pragma unroll
+                    for (int i = 1; i < V; ++i) g[7 * f + 1][i] = Storage<S>::to_c(raw[f][0][i - 1]) * isc;
+                }
+                {
+                    S next = __shfl_down_sync(0xffffffffu, raw[f][1][0], 1);
+                    if (fetch_next) next = edge_r[f];
+#pragma unroll
+                    for (int i = 0; i < V - 1; ++i) g[7 * f + 2][i] = Storage<S>::to_c(raw[f][1][i + 1]) * isc;
+                    g[7 * f + 2][V - 1] = Storage<S>::to_c(next) * isc;
+                }
+#pragma unroll
+                for (int l = 3; l < 7; ++l)
+#pragma unroll
+                    for (int i = 0; i < V; ++i) g[7 * f + l][i] = Storage<S>::to_c(raw[f][l - 1][i]) * isc;
+            }
+        } else
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             const C risc = rest_load_scale<S, SPLIT>(k, f);
