@@ -53,7 +53,16 @@ struct BatchProblem {
 constexpr int kChunkShift = 6;
 
 // At most 128 registers (two 256-thread blocks per SM): the split body of the single lattice fits
-// them without spilling; unbounded, the compiler took 146-149 and one block ran per SM.
+// them without spilling; unbounded, the compiler took 146-149 and one block ran per SM.  The
+// shifted 16-bit storage moves half the bytes of FP32 per node, so a warp has few bytes in
+// flight unless it requests every load of its lane before the first shuffle (kLoadFirst, as the
+// single-lattice kernel does).  Measured at 512 problems, FP16 shifted: interleaved 78 GLUPS,
+// load-first at 128 registers 90 GLUPS, load-first bounded to 80 registers (three blocks per SM,
+// ~130 bytes of spills) 86 GLUPS.  FP32 keeps the interleaved order (load-first: 50.5 against 53.0).
+template <class S, bool SPLIT> struct BatchShape {
+    static constexpr bool kLoadFirst = sizeof(S) == 2 && !SPLIT;
+};
+
 template <class S, bool SPLIT, int V>
 __global__ void __launch_bounds__(kMaxBatchThreads, 2)
 k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
@@ -87,7 +96,8 @@ k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
         } else if constexpr (SPLIT) {
             warp_split_step_2d<S, V, false>(fin, fout, P.nx, P.ny, (int)y, seg, lane, k, unused);
         } else {
-            warp_stream_collide_2d<S, false, Vec16<S>::V, false>(reinterpret_cast<const S*>(in_base + P.offset),
+            warp_stream_collide_2d<S, false, Vec16<S>::V, BatchShape<S, SPLIT>::kLoadFirst>(
+                                             reinterpret_cast<const S*>(in_base + P.offset),
                                              reinterpret_cast<S*>(out_base + P.offset), P.plane, P.nx, P.ny, (int)y, seg,
                                              lane, k, unused, key);
         }
@@ -172,7 +182,7 @@ k_batch_steps_2d(char* level0, char* level1, const BatchProblem<typename Storage
             } else if constexpr (SPLIT) {
                 warp_split_step_2d<S, V, false, true>(fin, fout, P.nx, P.ny, (int)y, seg, lane, k, unused);
             } else {
-                warp_stream_collide_2d<S, false, Vec16<S>::V, false, true>(
+                warp_stream_collide_2d<S, false, Vec16<S>::V, BatchShape<S, SPLIT>::kLoadFirst, true>(
                     reinterpret_cast<const S*>(in_base + P.offset), reinterpret_cast<S*>(out_base + P.offset), P.plane,
                     P.nx, P.ny, (int)y, seg, lane, k, unused, key);
             }

@@ -161,10 +161,15 @@ def test_batch_rejects_bad_problems():
         v.Batch([dict(n=(32, 16), dx=0.1, nu=0.01, omega_q=2.5)])                         # omega outside (0, 2)
 
 
-def test_batched_problem_set_members_match_oracle(orc):
+_MEMBER_REFS = {}
+
+
+@pytest.mark.parametrize("precision", ["fp16split", "bf16split", "fp32"])
+def test_batched_problem_set_members_match_oracle(orc, precision):
     """Problems drawn from the batched workload's own set (sides 512 and 1024, seeded random
-    Fourier fields, their own viscosities), advanced together 200 steps in the batched FP16
-    split storage the benchmark uses, each against the oracle at the L2 gate of 1e-3."""
+    Fourier fields, their own viscosities), advanced together 200 steps in the batched 16-bit
+    split storage the benchmark uses (and FP32), each against the oracle at the L2 gate of 1e-3.
+    (The shifted 16-bit forms miss that gate on these flows: 4e-3 to 1.3e-2 after 200 steps.)"""
     chosen = [q for q in synthetic.batched_problem_set(512) if q.side >= 512][:8]
     assert len(chosen) == 8
     specs, inputs = [], []
@@ -172,19 +177,24 @@ def test_batched_problem_set_members_match_oracle(orc):
         u, phi, dx = synthetic.random_fourier_field(q.side, q.seed)
         specs.append(dict(n=(q.side, q.side), dx=dx, nu=q.nu))
         inputs.append((u, phi, dx))
-    b = v.Batch(specs, precision="fp16split")
+    b = v.Batch(specs, precision=precision)
     for i, (u, phi, _) in enumerate(inputs):
         b.init(i, torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
     steps = 200
     b.step(steps)
     for i, (q, (u, phi, dx)) in enumerate(zip(chosen, inputs)):
-        op = oracle.make_params((q.side, q.side), dx, nu=q.nu)
-        _, uo, _ = orc.macros(op, orc.run(op, orc.init(op, u, phi), steps))
+        key = (q.index, steps)
+        if key not in _MEMBER_REFS:     # the oracle's velocity, shared by the storage forms
+            op = oracle.make_params((q.side, q.side), dx, nu=q.nu)
+            _MEMBER_REFS[key] = orc.macros(op, orc.run(op, orc.init(op, u, phi), steps))[1]
+        uo = _MEMBER_REFS[key]
         assert np.isfinite(uo).all(), q
         ug = b.velocity(i).cpu().numpy()
         err = l2_rel(ug, uo)
-        print(f"problem {q.index}: side {q.side}, nu {q.nu:.2e}: L2 {err:.2e}")
+        print(f"{precision} problem {q.index}: side {q.side}, nu {q.nu:.2e}: L2 {err:.2e}")
         assert err <= 1e-3, (q, err)
+        if precision == "fp32":     # the FP32 gate: max-abs error <= 1e-5 of max|u|
+            assert np.max(np.abs(ug - uo)) <= 1e-5 * np.max(np.abs(uo)), q
     b.close()
 
 
