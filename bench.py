@@ -566,6 +566,11 @@ def run_batch(args):
     bpn = bytes_per_node(args)
     achieved = bpn * nodes / (elapsed / args.steps) / 1e9
     peak, peak_kind = measured_peaks()
+    kname = "{}<{}, {}>".format("k_batch_steps_2d" if persistent else "k_batch_step_2d", CTYPE[args.precision],
+                                "split" if split(args) else "uniform")
+    digest = source_digest("batch")
+    # DRAM bytes of one step of the whole batch (a persistent launch runs several steps)
+    traffic = profiled_traffic(kname, count, digest)
     line = {
         "metric": METRIC, "value": nodes * args.steps / elapsed / 1e9, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
@@ -583,9 +588,9 @@ def run_batch(args):
                                              "note": "under-resolved problems diverge in the scheme itself "
                                                      "(the FP64 oracle as well); the work per node is the same"}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": peak_kind, "traffic": None, "bytes_per_node": bpn,
-                     "kernel": "k_batch_steps_2d" if persistent else "k_batch_step_2d",
-                     "avg_launch_ms": elapsed / args.steps * 1e3},
+                     "peak_kind": peak_kind, "traffic": traffic, "bytes_per_node": bpn, "kernel": kname,
+                     "avg_launch_ms": elapsed / args.steps * 1e3, "per": "one step of every problem",
+                     "source_digest": digest},
         "e2e": {"value": nodes * args.steps / e2e_el / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": in_bytes / args.steps, "d2h_bytes_per_step": out_bytes / args.steps},
         "gpu_launches": launches,

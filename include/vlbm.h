@@ -286,7 +286,8 @@ int vlbm_batch_macros(vlbm_batch* b, int32_t problem, void* rho, void* u, void* 
 int vlbm_batch_invariants(vlbm_batch* b, int32_t problem, double* out);
 
 /* Launch shape of the step kernel: threads per block (128 or 256), blocks per
- * SM (1..16) and, for the split formats, nodes per lane (2 or 4). */
+ * SM (1..16) and, for the split and shifted 16-bit formats, nodes per lane
+ * (2 or 4; ignored for FP32 and FP64, which take 16-byte vectors). */
 int vlbm_batch_set_config(vlbm_batch* b, int32_t threads, int32_t blocks_per_sm, int32_t lanes);
 
 /* Time every candidate launch shape on `repeats` dry-run steps (they read the

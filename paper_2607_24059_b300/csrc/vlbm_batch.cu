@@ -59,12 +59,14 @@ constexpr int kChunkShift = 6;
 // single-lattice kernel does).  Measured at 512 problems, FP16 shifted: interleaved 78 GLUPS,
 // load-first at 128 registers 90 GLUPS, load-first bounded to 80 registers (three blocks per SM,
 // ~130 bytes of spills) 86 GLUPS.  FP32 keeps the interleaved order (load-first: 50.5 against 53.0).
-template <class S, bool SPLIT> struct BatchShape {
+template <class S, bool SPLIT, int V = 4> struct BatchShape {
     static constexpr bool kLoadFirst = sizeof(S) == 2 && !SPLIT;
+    // two nodes per lane halve the registers of the load-first body: three 256-thread blocks per SM
+    static constexpr int kMinBlocks = (kLoadFirst && V == 2) ? 3 : 2;
 };
 
 template <class S, bool SPLIT, int V>
-__global__ void __launch_bounds__(kMaxBatchThreads, 2)
+__global__ void __launch_bounds__(kMaxBatchThreads, (BatchShape<S, SPLIT, V>::kMinBlocks))
 k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
                 const BatchProblem<typename Storage<S>::C>* __restrict__ probs, const int* __restrict__ chunk_problem,
                 int count, long long items, uint32_t* __restrict__ step_ctr, int par) {
@@ -96,7 +98,7 @@ k_batch_step_2d(const char* __restrict__ in_base, char* __restrict__ out_base,
         } else if constexpr (SPLIT) {
             warp_split_step_2d<S, V, false>(fin, fout, P.nx, P.ny, (int)y, seg, lane, k, unused);
         } else {
-            warp_stream_collide_2d<S, false, Vec16<S>::V, BatchShape<S, SPLIT>::kLoadFirst>(
+            warp_stream_collide_2d<S, false, V, BatchShape<S, SPLIT>::kLoadFirst>(
                                              reinterpret_cast<const S*>(in_base + P.offset),
                                              reinterpret_cast<S*>(out_base + P.offset), P.plane, P.nx, P.ny, (int)y, seg,
                                              lane, k, unused, key);
@@ -147,7 +149,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int t
 // coherent L2 loads (COH) instead of the read-only path.  The step counter of the stochastic
 // rounding advances in registers; block 0 leaves step0 + nsteps in the slot the next launch reads.
 template <class S, bool SPLIT, int V>
-__global__ void __launch_bounds__(kMaxBatchThreads, 2)
+__global__ void __launch_bounds__(kMaxBatchThreads, (BatchShape<S, SPLIT, V>::kMinBlocks))
 k_batch_steps_2d(char* level0, char* level1, const BatchProblem<typename Storage<S>::C>* __restrict__ probs,
                  const int* __restrict__ chunk_problem, int count, long long items, uint32_t* step_ctr, int par0,
                  int nsteps, unsigned int* bar_count, int* status, unsigned int phantom) {
@@ -182,7 +184,7 @@ k_batch_steps_2d(char* level0, char* level1, const BatchProblem<typename Storage
             } else if constexpr (SPLIT) {
                 warp_split_step_2d<S, V, false, true>(fin, fout, P.nx, P.ny, (int)y, seg, lane, k, unused);
             } else {
-                warp_stream_collide_2d<S, false, Vec16<S>::V, BatchShape<S, SPLIT>::kLoadFirst, true>(
+                warp_stream_collide_2d<S, false, V, BatchShape<S, SPLIT>::kLoadFirst, true>(
                     reinterpret_cast<const S*>(in_base + P.offset), reinterpret_cast<S*>(out_base + P.offset), P.plane,
                     P.nx, P.ny, (int)y, seg, lane, k, unused, key);
             }
@@ -306,9 +308,15 @@ int bfail(vlbm_batch* b, int code, const char* what, cudaError_t e) {
                                             #call, e_);                                                  \
     } while (0)
 
+// Formats whose nodes per lane are a launch-shape choice (2 or 4, vlbm_batch_set_config): the
+// split layouts and the shifted 16-bit storage.
+bool lanes_tunable(int precision) {
+    return is_split(precision) || precision == VLBM_FP16_SHIFTED || precision == VLBM_BF16_SHIFTED;
+}
+
 // Nodes per lane of the step kernel for the batch's precision and config.
 int batch_lanes(const vlbm_batch* b) {
-    if (is_split(b->precision)) return b->lanes;
+    if (lanes_tunable(b->precision)) return b->lanes;
     switch (b->precision) {
         case VLBM_FP64: return Vec16<double>::V;
         case VLBM_FP32: return Vec16<float>::V;
@@ -381,8 +389,14 @@ void launch_batch_step(vlbm_batch* b, cudaStream_t s, int src) {
     switch (b->precision) {
         case VLBM_FP64: launch_batch<double, false, Vec16<double>::V>(b, s, src); break;
         case VLBM_FP32: launch_batch<float, false, Vec16<float>::V>(b, s, src); break;
-        case VLBM_FP16_SHIFTED: launch_batch<__half, false, Vec16<__half>::V>(b, s, src); break;
-        case VLBM_BF16_SHIFTED: launch_batch<__nv_bfloat16, false, Vec16<__nv_bfloat16>::V>(b, s, src); break;
+        case VLBM_FP16_SHIFTED:
+            if (b->lanes == 2) launch_batch<__half, false, 2>(b, s, src);
+            else launch_batch<__half, false, 4>(b, s, src);
+            break;
+        case VLBM_BF16_SHIFTED:
+            if (b->lanes == 2) launch_batch<__nv_bfloat16, false, 2>(b, s, src);
+            else launch_batch<__nv_bfloat16, false, 4>(b, s, src);
+            break;
         case VLBM_FP16_SPLIT:
             if (b->lanes == 2) launch_batch<__half, true, 2>(b, s, src);
             else launch_batch<__half, true, 4>(b, s, src);
@@ -424,8 +438,12 @@ int launch_batch_steps_any(vlbm_batch* b, int nsteps, unsigned int phantom) {
     switch (b->precision) {
         case VLBM_FP64: return launch_batch_steps<double, false, Vec16<double>::V>(b, nsteps, phantom);
         case VLBM_FP32: return launch_batch_steps<float, false, Vec16<float>::V>(b, nsteps, phantom);
-        case VLBM_FP16_SHIFTED: return launch_batch_steps<__half, false, Vec16<__half>::V>(b, nsteps, phantom);
-        case VLBM_BF16_SHIFTED: return launch_batch_steps<__nv_bfloat16, false, Vec16<__nv_bfloat16>::V>(b, nsteps, phantom);
+        case VLBM_FP16_SHIFTED:
+            return b->lanes == 2 ? launch_batch_steps<__half, false, 2>(b, nsteps, phantom)
+                                 : launch_batch_steps<__half, false, 4>(b, nsteps, phantom);
+        case VLBM_BF16_SHIFTED:
+            return b->lanes == 2 ? launch_batch_steps<__nv_bfloat16, false, 2>(b, nsteps, phantom)
+                                 : launch_batch_steps<__nv_bfloat16, false, 4>(b, nsteps, phantom);
         case VLBM_FP16_SPLIT:
             return b->lanes == 2 ? launch_batch_steps<__half, true, 2>(b, nsteps, phantom)
                                  : launch_batch_steps<__half, true, 4>(b, nsteps, phantom);
@@ -789,11 +807,11 @@ extern "C" int vlbm_batch_invariants(vlbm_batch* b, int32_t problem, double* out
 
 extern "C" int vlbm_batch_set_config(vlbm_batch* b, int32_t threads, int32_t blocks_per_sm, int32_t lanes) {
     if (!b || (threads != 128 && threads != 256) || blocks_per_sm < 1 || blocks_per_sm > 16) return VLBM_EINVAL;
-    if (is_split(b->precision) && lanes != 2 && lanes != 4) return VLBM_EINVAL;
-    const bool relayout = is_split(b->precision) && lanes != b->lanes;
+    if (lanes_tunable(b->precision) && lanes != 2 && lanes != 4) return VLBM_EINVAL;
+    const bool relayout = lanes_tunable(b->precision) && lanes != b->lanes;   // the work list depends on it
     b->threads = threads;
     b->blocks_per_sm = blocks_per_sm;
-    if (is_split(b->precision)) b->lanes = lanes;
+    if (lanes_tunable(b->precision)) b->lanes = lanes;
     drop_graphs(b);
     return relayout ? rebuild_table(b) : VLBM_OK;
 }
@@ -803,7 +821,7 @@ extern "C" int vlbm_batch_autotune(vlbm_batch* b, int32_t repeats, int32_t* conf
     const int thread_opts[2] = {128, 256};
     const int bps_opts[5] = {1, 2, 4, 8, 16};
     const int lane_opts[2] = {2, 4};
-    const int nl = is_split(b->precision) ? 2 : 1;
+    const int nl = lanes_tunable(b->precision) ? 2 : 1;
     cudaEvent_t e0, e1;
     VLBM_BCUDA(b, cudaEventCreate(&e0));
     VLBM_BCUDA(b, cudaEventCreate(&e1));

@@ -79,10 +79,13 @@ def test_batch_matches_oracle_per_problem(precision):
     b.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16split", "fp16", "bf16"])
-def test_batch_equals_single_handles(precision):
+@pytest.mark.parametrize("precision,lanes", [("fp32", 4), ("fp16split", 4), ("fp16", 4), ("bf16", 4),
+                                           ("fp16", 2), ("bf16", 2)])
+def test_batch_equals_single_handles(precision, lanes):
+    """lanes: nodes per lane of the batched kernel (the single-lattice 16-bit kernels take 4)."""
     qs = [dict(n=q["n"], dx=problem_inputs(q)[2], nu=q["nu"]) for q in PROBLEMS]
     b = v.Batch(qs, precision=precision)
+    b.set_config(256, 2, lanes)
     singles = []
     for i, q in enumerate(PROBLEMS):
         u, phi, dx = problem_inputs(q)
@@ -244,8 +247,8 @@ def test_persistent_launch_timeout_path_reports_and_recovers():
     b.close()
 
 
-# widths that are not multiples of the vector width (4 for FP32 and split, 8 for the 16-bit
-# shifted formats, 2 for FP64): those problems run the per-node body, one node per lane
+# widths that are not multiples of the nodes per lane (4 for FP32, 2 for FP64, 4 or 2 for the
+# split and shifted 16-bit formats): those problems run the per-node body, one node per lane
 RAGGED = [
     dict(n=(37, 23), nu=0.01, seed=11),
     dict(n=(50, 30), nu=0.004, seed=12),
@@ -276,10 +279,12 @@ def test_ragged_widths_match_oracle_per_problem(precision, persistent):
     b.close()
 
 
+@pytest.mark.parametrize("lanes", [4, 2])
 @pytest.mark.parametrize("precision", ["fp16", "bf16"])
-def test_ragged_widths_shifted_equal_single_handles(precision):
+def test_ragged_widths_shifted_equal_single_handles(precision, lanes):
     qs = [dict(n=q["n"], dx=problem_inputs(q)[2], nu=q["nu"]) for q in RAGGED]
     b = v.Batch(qs, precision=precision)
+    b.set_config(256, 2, lanes)
     singles = []
     for i, q in enumerate(RAGGED):
         u, phi, dx = problem_inputs(q)
