@@ -54,9 +54,10 @@ __device__ __forceinline__ void load_or_zero(T (&w)[V], const T* p, bool active)
 // (sr_step_key).  LOAD_FIRST: request all fifteen vectors (and the warp-edge
 // elements) before the first shuffle; otherwise each plane is shifted right after
 // its load.  Measured at 4096^2: load-first is faster for one segment per warp
-// (FP32 0.2948 against 0.3162 ms), the interleaved order inside the persistent
-// loops of the recorded step and the batch kernel (recorded step 324 against
-// ~360 us).
+// (FP32 0.2948 against 0.3162 ms); inside the persistent loops of the recorded
+// step and the batch kernel it is faster for the 16-bit formats, which move
+// half the bytes per lane (FP16 recorded step 225 -> 187 us; batched FP16 78 ->
+// 90 GLUPS), and slower for FP32 (recorded step ~360 against 324 us).
 template <class S, bool DIAG, int V = Vec16<S>::V, bool LOAD_FIRST = !DIAG, bool COH = false, class A>
 __device__ __forceinline__ void warp_stream_collide_2d(const S* __restrict__ fin, S* __restrict__ fout, long long N,
                                                        int nx, int ny, int y, int seg, int lane,
@@ -264,7 +265,7 @@ k_stream_collide_2d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
     const uint32_t items = (uint32_t)ny * wdiv.d;
     for (uint32_t item = gwarp; item < items; item += (DIAG ? nwarps : items)) {   // warp-uniform
         const uint32_t y = wdiv.div(item);
-        warp_stream_collide_2d<S, DIAG, DiagVec<S, DIAG>::V>(fin, fout, plane, nx, ny, (int)y,
+        warp_stream_collide_2d<S, DIAG, DiagVec<S, DIAG>::V, !DIAG || sizeof(S) == 2>(fin, fout, plane, nx, ny, (int)y,
                                                              (int)(item - y * wdiv.d), lane, k, acc, key);
     }
     if (DIAG) {

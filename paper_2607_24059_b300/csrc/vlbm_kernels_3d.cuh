@@ -60,9 +60,10 @@ k_stream_collide_3d_vec(const char* __restrict__ fin_b, char* __restrict__ fout_
 
         C g[28][V];
         // 16-bit storage: every vector of the lane and the warp-edge elements requested before the
-        // first shuffle (half the bytes per warp of FP32 need more of them in flight); FP32, at the
-        // HBM roofline with either order, keeps the interleaved one
-        constexpr bool LOAD_FIRST = !DIAG && sizeof(S) == 2;
+        // first shuffle (half the bytes per warp of FP32 need more of them in flight), also in the
+        // persistent loop of the recorded step (FP16 at 256^3: 823 -> 412 us per recorded step,
+        // 120 registers); FP32, at the HBM roofline with either order, keeps the interleaved one
+        constexpr bool LOAD_FIRST = sizeof(S) == 2;
         if constexpr (LOAD_FIRST) {
             R raw0[4][V];
             S raw[4][6][V];
