@@ -271,8 +271,6 @@ def test_recorded_steps_advance_the_same_state(n, precision):
     against 9 plain ones (same arithmetic; only FMA contraction may differ between the two
     instantiations, which for 16-bit storage can flip a stored quantum)."""
     if len(n) == 3:
-        if precision in ("fp16", "bf16", "bf16split"):
-            pytest.skip("3D: fp64, fp32 and fp16split cover the recorded 3D kernels")
         rng = np.random.default_rng(5)
         u = 0.2 * rng.standard_normal((3,) + tuple(reversed(n)))
         phi = 0.1 * rng.standard_normal(tuple(reversed(n)))
