@@ -13,7 +13,10 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
       pinned by the exact shear-wave recurrence, the one-step closed form,
       per-step conservation, the fixed point, agreement of the two collision
       forms, Fourier-mode decay against the pinned spectrum, and the
-      Taylor-Green closed-form decay with second-order convergence (Table 1).
+      Taylor-Green closed-form decay with second-order convergence (Table 1),
+      and by Table 2: with the ghost-cell boundaries of Section 6.2.1
+      (poiseuille.py) the scheme reproduces the printed Poiseuille errors to
+      their four digits.
   invariants: pinned by direct sums on hand-built states.
   3D (D3Q7, reading R4 in vlbm_oracle.c): pinned by the shear-wave
       recurrence for every carrier-field / axis pair, conservation, Fourier
