@@ -209,6 +209,40 @@ int vlbm_launch_count(const vlbm_handle* h, int64_t* count);
 #define VLBM_OPT_ROUNDING_16 2
 int vlbm_set_option(vlbm_handle* h, int32_t key, int64_t value);
 
+/* Boundary conditions of a 2D lattice (Section 6.2.1, the Poiseuille test of
+ * Section 6.2).  VLBM_BC_PERIODIC (the default): periodic wrap on every side.
+ * VLBM_BC_CHANNEL: the ghost-cell conditions of the paper on the domain
+ * [0, n_x dx] x [0, n_y dx]: ghost cells at distance dx/2 outside each side get
+ * conserved moments from the two nearest interior cells of the current time
+ * level -- left side: prescribed velocity (u_in(y), 0) (momentum
+ * 2 rho_bar u_in - q of the adjacent cell) and linearly extrapolated density;
+ * right side: prescribed pressure potential Phi_out (density
+ * 2 rho_bar (1 + dx^2 Phi_out) - rho of the adjacent cell) and linearly
+ * extrapolated momentum; lower and upper walls: zero velocity (momentum -q of
+ * the adjacent cell) and extrapolated density -- and the population that
+ * streams from a ghost cell into the domain is that cell's equilibrium (Eqs.
+ * BCPoiseuilleLeftEquilibrium, BCPoiseuilleRightEquilibrium,
+ * BCPoiseuilleLowerEquilibrium).  wall_correction = 1 adds at the walls the
+ * non-equilibrium part of the same population at the adjacent interior cell
+ * (Eq. BCPoiseuilleLowerEquilibriumPlusCorrection), which the paper shows is
+ * needed for second order when omega_q != 1.
+ * u_in: host array of n_y velocities u_x at the cell centres y = (j + 1/2) dx,
+ * copied by the call (which synchronises the handle's stream).  Only 2D
+ * lattices with VLBM_FP64 or VLBM_FP32 storage and at least 2 x 2 nodes
+ * (VLBM_EINVAL otherwise).  A channel step is two kernel launches (ghost
+ * populations, then the per-node stream-collide); vlbm_step_record is not
+ * available with a channel (VLBM_EINVAL: step with vlbm_step and reduce with
+ * vlbm_invariants).  Setting VLBM_BC_PERIODIC returns to the periodic step. */
+#define VLBM_BC_PERIODIC 0
+#define VLBM_BC_CHANNEL 1
+typedef struct {
+    int32_t kind;             /* VLBM_BC_PERIODIC or VLBM_BC_CHANNEL */
+    int32_t wall_correction;  /* 1: non-equilibrium correction at the walls */
+    double phi_out;           /* pressure potential Phi at the outlet x = n_x dx */
+    const double* u_in;       /* host, n_y inflow velocities u_x(y) (VLBM_BC_CHANNEL) */
+} vlbm_boundary;
+int vlbm_set_boundary(vlbm_handle* h, const vlbm_boundary* bc);
+
 /* Vorticity diagnostic of the current state: out[0] = sum over nodes of
  * |curl u|^2 dx^d, u = q / rho, with centred differences (periodic) of spacing
  * dx; in 2D the scalar vorticity d_x u_y - d_y u_x.  With the kinetic energy E of

@@ -45,34 +45,39 @@ import numpy as np
 from . import Oracle, Params, alpha_from_nu
 
 
-def exact(n: int, L: float = 1.0, U: float = 1.0, re: float = 100.0):
-    """(u (2, n, n), phi (n, n), dx, nu) of the steady Poiseuille profile at the cell centres."""
+def exact(n: int, L: float = 1.0, U: float = 1.0, re: float = 100.0, nx: int | None = None):
+    """(u (2, n, nx), phi (n, nx), dx, nu) of the steady Poiseuille profile at the cell centres of
+    n cells across the channel (height L) and nx (default n) along it (length nx dx)."""
+    nx = n if nx is None else nx
     dx = L / n
     nu = U * L / re
-    c = (np.arange(n) + 0.5) * dx
-    X, Y = np.meshgrid(c, c, indexing="xy")
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(n) + 0.5) * dx, indexing="xy")
     u = np.stack([4.0 * U * Y * (L - Y) / L ** 2, np.zeros_like(Y)])
-    phi = 8.0 * nu * U * (L - X) / L ** 2
+    phi = 8.0 * nu * U * (nx * dx - X) / L ** 2
     return u, phi, dx, nu
 
 
 def params(n: int, omega_q: float, mu: float = 8.0, omega_rho: float = 1.2, alpha_rho: float = 0.075,
-           L: float = 1.0, U: float = 1.0, re: float = 100.0) -> Params:
+           L: float = 1.0, U: float = 1.0, re: float = 100.0, nx: int | None = None) -> Params:
     dx = L / n
     nu = U * L / re
     aq = alpha_from_nu(nu, mu, omega_q)
-    return Params(n=(n, n), dx=dx, mu=mu, omega=(omega_rho, omega_q, omega_q), alpha=(alpha_rho, aq, aq))
+    return Params(n=(n if nx is None else nx, n), dx=dx, mu=mu, omega=(omega_rho, omega_q, omega_q),
+                  alpha=(alpha_rho, aq, aq))
 
 
 class Poiseuille:
-    """Poiseuille flow on n x n cells of [0, L]^2 (L = 1, U = 1, Re = 100)."""
+    """Poiseuille flow on n cells across (height L = 1) and nx (default n) along the channel
+    (U = 1, Re = 100)."""
 
-    def __init__(self, orc: Oracle, n: int, omega_q: float, corrected: bool = False, mu: float = 8.0):
+    def __init__(self, orc: Oracle, n: int, omega_q: float, corrected: bool = False, mu: float = 8.0,
+                 nx: int | None = None):
         self.orc = orc
         self.n = n
-        self.p = params(n, omega_q, mu=mu)
+        self.nx = n if nx is None else nx
+        self.p = params(n, omega_q, mu=mu, nx=nx)
         self.corrected = corrected
-        u, phi, dx, nu = exact(n)
+        u, phi, dx, nu = exact(n, nx=nx)
         self.u_ex, self.dx, self.nu = u, dx, nu
         self.rho_bar = self.p.rho_bar
         self.uex_y = u[0][:, 0]                 # u_x^ex at the cell centres' y (the left side's profile)
@@ -93,11 +98,11 @@ class Poiseuille:
         return self.orc.init(g, u, phi)[:, :, 0, :]
 
     def step(self, count: int = 1) -> None:
-        n, rb, dx = self.n, self.rho_bar, self.dx
+        ny, nx, rb, dx = self.n, self.nx, self.rho_bar, self.dx
         for _ in range(count):
             f = self.f
-            rho, qx, qy = self._moments(f)                       # (n, n): [y, x]
-            F = np.zeros((3, 5, n + 2, n + 2))
+            rho, qx, qy = self._moments(f)                       # (ny, nx): [y, x]
+            F = np.zeros((3, 5, ny + 2, nx + 2))
             F[:, :, 1:-1, 1:-1] = f
             # left side (x = -dx/2): the +x populations enter
             e = self._equilibria(2 * rho[:, 0] - rho[:, 1], 2 * rb * self.uex_y - qx[:, 0], -qy[:, 0])

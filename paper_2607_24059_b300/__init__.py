@@ -113,6 +113,14 @@ class Lattice:
     def set_option(self, key, value):
         _binding.vlbm_set_option(self.handle, key, value)
 
+    def set_channel(self, u_in, phi_out=0.0, wall_correction=False):
+        """Ghost-cell channel boundaries of Section 6.2.1 (2D, FP64/FP32): inflow velocity u_in(y)
+        on the left, pressure potential phi_out on the right, no-slip walls below and above."""
+        _binding.vlbm_set_boundary(self.handle, _binding.VLBM_BC_CHANNEL, u_in, phi_out, wall_correction)
+
+    def set_periodic(self):
+        _binding.vlbm_set_boundary(self.handle, _binding.VLBM_BC_PERIODIC)
+
     def launch_count(self):
         return _binding.vlbm_launch_count(self.handle)
 

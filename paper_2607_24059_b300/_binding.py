@@ -55,6 +55,9 @@ VLBM_OPT_KERNEL = 0
 VLBM_OPT_SPLIT_LANES = 1
 VLBM_OPT_ROUNDING_16 = 2
 
+VLBM_BC_PERIODIC = 0
+VLBM_BC_CHANNEL = 1
+
 PRECISIONS = {"fp64": VLBM_FP64, "fp32": VLBM_FP32, "fp16": VLBM_FP16_SHIFTED, "bf16": VLBM_BF16_SHIFTED,
               "fp16split": VLBM_FP16_SPLIT, "bf16split": VLBM_BF16_SPLIT}
 
@@ -62,7 +65,7 @@ EXPORTED = [
     "vlbm_params_default", "vlbm_params_check", "vlbm_create", "vlbm_destroy", "vlbm_set_stream",
     "vlbm_init", "vlbm_step", "vlbm_step_record", "vlbm_macros", "vlbm_invariants", "vlbm_time", "vlbm_state_bytes",
     "vlbm_get_state", "vlbm_set_state", "vlbm_get_populations", "vlbm_launch_count", "vlbm_set_option",
-    "vlbm_strerror", "vlbm_last_error", "vlbm_invariants_noalloc", "vlbm_vorticity_sq",
+    "vlbm_strerror", "vlbm_last_error", "vlbm_invariants_noalloc", "vlbm_vorticity_sq", "vlbm_set_boundary",
     "vlbm_batch_create", "vlbm_batch_destroy", "vlbm_batch_init", "vlbm_batch_step", "vlbm_batch_macros",
     "vlbm_batch_invariants", "vlbm_batch_set_config", "vlbm_batch_autotune", "vlbm_batch_info",
     "vlbm_batch_last_error", "vlbm_batch_init_states", "vlbm_batch_macros_states", "vlbm_tc_gemm_bf16", "vlbm_sur_conv3x3", "vlbm_sur_conv3x3_wgrad",
@@ -88,6 +91,13 @@ class vlbm_derived(ctypes.Structure):
         ("dt", ctypes.c_double), ("alpha", ctypes.c_double * 4), ("viscosity", ctypes.c_double * 4),
         ("mu_min", ctypes.c_double), ("nodes", ctypes.c_int64), ("populations_per_node", ctypes.c_int32),
         ("bytes_per_population", ctypes.c_int32), ("lattice_bytes", ctypes.c_size_t),
+    ]
+
+
+class vlbm_boundary(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("wall_correction", ctypes.c_int32), ("phi_out", ctypes.c_double),
+        ("u_in", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -117,6 +127,7 @@ lib.vlbm_set_state.argtypes = [_H, _V, ctypes.c_size_t]
 lib.vlbm_get_populations.argtypes = [_H, _V, ctypes.c_int32, ctypes.c_int32]
 lib.vlbm_launch_count.argtypes = [_H, ctypes.POINTER(ctypes.c_int64)]
 lib.vlbm_set_option.argtypes = [_H, ctypes.c_int32, ctypes.c_int64]
+lib.vlbm_set_boundary.argtypes = [_H, ctypes.POINTER(vlbm_boundary)]
 lib.vlbm_invariants_noalloc.argtypes = [_P, _V, _V, _V]
 lib.vlbm_batch_create.argtypes = [_P, ctypes.c_int32, _V, ctypes.POINTER(_H)]
 lib.vlbm_batch_destroy.argtypes = [_H]
@@ -350,6 +361,19 @@ def vlbm_launch_count(h) -> int:
 
 def vlbm_set_option(h, key: int, value: int) -> None:
     _check(lib.vlbm_set_option(h, int(key), int(value)), "vlbm_set_option", h)
+
+
+def vlbm_set_boundary(h, kind: int, u_in=None, phi_out: float = 0.0, wall_correction: bool = False) -> None:
+    """kind VLBM_BC_PERIODIC or VLBM_BC_CHANNEL; u_in: the n_y inflow velocities (host, FP64)."""
+    b = vlbm_boundary()
+    b.kind = int(kind)
+    b.wall_correction = 1 if wall_correction else 0
+    b.phi_out = float(phi_out)
+    keep = None
+    if u_in is not None:
+        keep = np.ascontiguousarray(u_in, dtype=np.float64)
+        b.u_in = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(lib.vlbm_set_boundary(h, ctypes.byref(b)), "vlbm_set_boundary", h)
 
 
 def vlbm_invariants_noalloc(p: vlbm_params, lattice, out, stream=None) -> None:

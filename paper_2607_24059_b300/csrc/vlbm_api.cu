@@ -18,6 +18,7 @@
 #include "vlbm_kernels_3d.cuh"
 #include "vlbm_split.cuh"
 #include "vlbm_fields.cuh"
+#include "vlbm_boundary.cuh"
 #include "vlbm_host.hpp"
 
 using namespace vlbm;
@@ -68,6 +69,13 @@ struct vlbm_handle {
     std::string err;
     Coef<double> kd{};
     Coef<float> kf{};
+    // boundary conditions (vlbm_set_boundary): periodic, or the channel of Section 6.2.1
+    int bc_kind = VLBM_BC_PERIODIC;
+    int bc_correction = 0;
+    double bc_phi_out = 0.0;
+    double* bc_u_in = nullptr;        // n_y inflow velocities
+    void* bc_ghost = nullptr;         // 4 sides x 3 fields x n_ghost entering populations
+    int bc_n_ghost = 0;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -225,6 +233,8 @@ static void free_all(vlbm_handle* h) {
     if (h->inv_host) cudaFreeHost(h->inv_host);
     if (h->staging) cudaFree(h->staging);
     if (h->hist) cudaFree(h->hist);
+    if (h->bc_u_in) cudaFree(h->bc_u_in);
+    if (h->bc_ghost) cudaFree(h->bc_ghost);
 }
 
 static void storage_scales(const vlbm_params& p, const vlbm_derived& d, double* scale) {
@@ -519,8 +529,40 @@ static DiagSink diag_sink(vlbm_handle* h, double* out, int nblocks) {
     return k;
 }
 
-static int launch_one_step(vlbm_handle* h, cudaStream_t s, int src) {
+// One step of a channel (vlbm_set_boundary): the ghost populations of the four sides from the
+// current level, then the per-node step that reads them where a pull crosses a side.
+template <class S>
+static void step_channel(vlbm_handle* h, cudaStream_t s, int src) {
+    using C = typename Storage<S>::C;
+    const int nx = (int)h->p.n[0], ny = (int)h->p.n[1];
+    ChannelBC<C> bc;
+    bc.u_in = h->bc_u_in;
+    bc.ghost = (C*)h->bc_ghost;
+    bc.n_ghost = h->bc_n_ghost;
+    bc.phi_term = (C)(2.0 * h->p.rho_bar * h->p.dx * h->p.dx * h->bc_phi_out);
+    bc.u_scale = (C)(2.0 * h->p.rho_bar * h->p.dx);
+    bc.correction = h->bc_correction;
+    const char* fin = (const char*)h->buf[src];
+    k_channel_ghosts<S><<<dim3((unsigned)((h->bc_n_ghost + kThreads - 1) / kThreads), 4), kThreads, 0, s>>>(
+        fin, nx, ny, h->d.nodes, coef<C>(h), bc);
+    k_stream_collide_2d_channel<S><<<(unsigned)((h->d.nodes + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        fin, (char*)h->buf[src ^ 1], nx, ny, h->d.nodes, coef<C>(h), bc, h->ctr, src);
+}
+
+// Kernel launches of one step.
+static int launches_per_step(const vlbm_handle* h) { return h->bc_kind == VLBM_BC_CHANNEL ? 2 : 1; }
+
+static void dispatch_step(vlbm_handle* h, cudaStream_t s, int src) {
+    if (h->bc_kind == VLBM_BC_CHANNEL) {
+        if (h->p.precision == VLBM_FP64) step_channel<double>(h, s, src);
+        else step_channel<float>(h, s, src);
+        return;
+    }
     VLBM_DISPATCH_STORAGE(h, step_plain, h, s, src);
+}
+
+static int launch_one_step(vlbm_handle* h, cudaStream_t s, int src) {
+    dispatch_step(h, s, src);
     return check_launch(h, "stream-collide");
 }
 
@@ -531,7 +573,7 @@ static int build_graph(vlbm_handle* h, int src) {
     int b = src;
     int rc = VLBM_OK;
     for (int i = 0; i < kGraphSteps; ++i) {
-        VLBM_DISPATCH_STORAGE(h, step_plain, h, h->capture_stream, b);
+        dispatch_step(h, h->capture_stream, b);
         b ^= 1;
     }
     cudaGraph_t g = nullptr;
@@ -559,13 +601,13 @@ extern "C" int vlbm_step(vlbm_handle* h, int64_t nsteps, int32_t flags) {
                 if (rc) return rc;
             }
             VLBM_CUDA(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
-            h->launches += kGraphSteps;
+            h->launches += (int64_t)kGraphSteps * launches_per_step(h);
             h->step += kGraphSteps;
             left -= kGraphSteps;   // kGraphSteps is even: parity unchanged
         } else {
             int rc = launch_one_step(h, h->stream, h->cur);
             if (rc) return rc;
-            h->launches++;
+            h->launches += launches_per_step(h);
             h->cur ^= 1;
             h->step++;
             left--;
@@ -579,6 +621,45 @@ extern "C" int vlbm_step(vlbm_handle* h, int64_t nsteps, int32_t flags) {
         if (h->inv_host[6] != 0.0) return fail(h, VLBM_EDIVERGED, "%.0f non-finite nodes at step %lld", h->inv_host[6],
                                                (long long)h->step);
     }
+    return VLBM_OK;
+}
+
+extern "C" int vlbm_set_boundary(vlbm_handle* h, const vlbm_boundary* bc) {
+    if (!h || !bc) return VLBM_EINVAL;
+    if (bc->kind == VLBM_BC_PERIODIC) {
+        if (h->bc_kind != VLBM_BC_PERIODIC) {
+            for (int i = 0; i < 2; ++i)
+                if (h->graph[i]) {
+                    cudaGraphExecDestroy(h->graph[i]);
+                    h->graph[i] = nullptr;
+                }
+        }
+        h->bc_kind = VLBM_BC_PERIODIC;
+        return VLBM_OK;
+    }
+    if (bc->kind != VLBM_BC_CHANNEL) return fail(h, VLBM_EINVAL, "unknown boundary kind %d", bc->kind);
+    if (h->p.dim != 2 || (h->p.precision != VLBM_FP64 && h->p.precision != VLBM_FP32))
+        return fail(h, VLBM_EINVAL, "channel boundaries: 2D lattices with FP64 or FP32 storage only");
+    if (h->p.n[0] < 2 || h->p.n[1] < 2) return fail(h, VLBM_EINVAL, "channel boundaries need at least 2 x 2 nodes");
+    if (!bc->u_in || !std::isfinite(bc->phi_out)) return fail(h, VLBM_EINVAL, "channel boundaries: u_in and a finite phi_out");
+    const int ny = (int)h->p.n[1];
+    for (int j = 0; j < ny; ++j)
+        if (!std::isfinite(bc->u_in[j])) return fail(h, VLBM_EINVAL, "channel boundaries: u_in[%d] is not finite", j);
+    const int n_ghost = (int)std::max(h->p.n[0], h->p.n[1]);
+    const size_t es = h->p.precision == VLBM_FP64 ? sizeof(double) : sizeof(float);
+    if (!h->bc_u_in) VLBM_CUDA(h, cudaMalloc(&h->bc_u_in, (size_t)ny * sizeof(double)));
+    if (!h->bc_ghost) VLBM_CUDA(h, cudaMalloc(&h->bc_ghost, (size_t)4 * 3 * n_ghost * es));
+    VLBM_CUDA(h, cudaMemcpyAsync(h->bc_u_in, bc->u_in, (size_t)ny * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    VLBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < 2; ++i)
+        if (h->graph[i]) {
+            cudaGraphExecDestroy(h->graph[i]);
+            h->graph[i] = nullptr;
+        }
+    h->bc_kind = VLBM_BC_CHANNEL;
+    h->bc_correction = bc->wall_correction ? 1 : 0;
+    h->bc_phi_out = bc->phi_out;
+    h->bc_n_ghost = n_ghost;
     return VLBM_OK;
 }
 
@@ -604,6 +685,8 @@ static PtrKind pointer_kind(const void* ptr, void** device_view = nullptr) {
 
 extern "C" int vlbm_step_record(vlbm_handle* h, int64_t nsteps, int64_t every, double* history) {
     if (!h || nsteps < 0 || every < 1 || (nsteps > 0 && !history)) return VLBM_EINVAL;
+    if (h->bc_kind != VLBM_BC_PERIODIC)
+        return fail(h, VLBM_EINVAL, "fused records need periodic boundaries (use vlbm_step and vlbm_invariants)");
     if (nsteps == 0) return VLBM_OK;
     const int64_t records = (nsteps + every - 1) / every;
     void* mapped = nullptr;
