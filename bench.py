@@ -45,6 +45,16 @@ WORKLOADS = {
     "tgv3d": (3, 28, 256, 1.0 / 1600.0),
     "batch512": (2, 15, 0, None),      # 512 problems: sides and nu drawn per problem
     "sur256": (2, 15, 1024, 1e-3),     # learned surrogate on 256^2, pooled from 1024^2 runs
+    "poiseuille": (2, 15, 253, 1e-2),  # channel of Section 6.2 (Table 2), 75..253 cells per direction
+}
+
+# Table 2 of the paper (Section 6.2.2): L2 error on u_x at t = 0.05, omega_rho = 6/5, alpha_rho = 3/40;
+# (cells, omega_q, wall correction) -> printed value
+TABLE2 = {
+    (75, 1.0, False): 2.938e-05, (112, 1.0, False): 1.333e-05, (168, 1.0, False): 5.994e-06, (253, 1.0, False): 2.668e-06,
+    (75, 1.15, False): 5.661e-04, (112, 1.15, False): 3.812e-04, (168, 1.15, False): 2.563e-04, (253, 1.15, False): 1.707e-04,
+    (75, 1.0, True): 2.943e-05, (112, 1.0, True): 1.335e-05, (168, 1.0, True): 5.997e-06, (253, 1.0, True): 2.670e-06,
+    (75, 1.15, True): 1.485e-05, (112, 1.15, True): 6.672e-06, (168, 1.15, True): 3.043e-06, (253, 1.15, True): 1.368e-06,
 }
 
 
@@ -789,10 +799,84 @@ def run_surrogate(args):
     return 0
 
 
+def run_poiseuille(args):
+    """The channel test of Section 6.2 on the GPU: every row of Table 2 (75, 112, 168, 253 cells,
+    omega_q = 1 and 1.15, walls with and without the correction) run to t = 0.05 with the ghost-cell
+    boundaries of vlbm_set_boundary, the L2 error on u_x beside the printed one, and the time to t.
+    value: GLUPS of the 253-cell runs (small lattices of per-node steps: latency-bound)."""
+    import torch
+    import paper_2607_24059_b300 as vlbm
+    import synthetic
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    prec = args.precision if "--precision" in sys.argv else "fp64"
+    mu, t_final = 8.0, 0.05
+    rows, nodes_253, secs_253 = [], 0, 0.0
+    stream = torch.cuda.current_stream()
+    launches = 0
+    with ClockSampler(local) as clk:
+        for n in (75, 112, 168, 253):
+            u, phi, dx, nu, u_in = synthetic.poiseuille_channel(n)
+            steps = int(math.floor(t_final * mu / dx ** 2 + 1e-6))    # whole steps up to t
+            for omega_q in (1.0, 1.15):
+                alpha_q = nu / (2.0 * mu * (1.0 / omega_q - 0.5))      # Prop. 1
+                for corrected in (False, True):
+                    lat = vlbm.Lattice((n, n), dx, nu=0.0, precision=prec, mu=mu, omega_rho=1.2, alpha_rho=0.075,
+                                       omega_q=omega_q, alpha_q=alpha_q)
+                    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+                    lat.set_channel(u_in, phi_out=0.0, wall_correction=corrected)
+                    lat.step(64)                                           # first launches, graph capture
+                    lat.init(torch.from_numpy(u).cuda(), torch.from_numpy(phi).cuda())
+                    c0 = lat.launch_count()
+                    torch.cuda.synchronize()
+                    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    start.record(stream)
+                    lat.step(steps)
+                    end.record(stream)
+                    torch.cuda.synchronize()
+                    ms = start.elapsed_time(end)
+                    launches += lat.launch_count() - c0
+                    ux = lat.macros()[1][0].cpu().numpy()
+                    lat.close()
+                    err = math.sqrt(dx * dx * float(np.sum((ux - u[0]) ** 2)))
+                    printed = TABLE2[(n, omega_q, corrected)]
+                    rows.append({"cells": n, "omega_q": omega_q, "wall_correction": corrected, "steps": steps,
+                                 "l2_error_ux": err, "table2": printed, "ms_to_t": ms})
+                    if n == 253:
+                        nodes_253 += n * n * steps
+                        secs_253 += ms / 1e3
+    value = nodes_253 / secs_253 / 1e9
+    per_step = secs_253 / (4 * rows[-1]["steps"])
+    bpn = 2 * 15 * ELEM_BYTES[prec]
+    peak, peak_kind = measured_peaks()
+    achieved = bpn * 253 * 253 / per_step / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": rows[-1]["steps"],
+        "warmup": 64, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64"}[prec], "data": "synthetic",
+        "config": {"workload": "Poiseuille channel of Section 6.2 (Table 2): [0,1]^2, U = 1, Re = 100, mu = 8, "
+                               "omega_rho = 6/5, alpha_rho = 3/40, to t = 0.05, ghost-cell boundaries",
+                   "storage": prec, "l2": "small lattices (75..253 cells per direction) fit in L2"},
+        "table2": rows,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": None, "bytes_per_node": bpn,
+                     "kernel": "k_channel_ghosts + k_stream_collide_2d_channel",
+                     "note": "253^2 nodes per step: two short launches per step, latency-bound, far from the "
+                             "bandwidth roofline by construction"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "poiseuille":
+        return run_poiseuille(args)
     if args.workload == "batch512":
         return run_batch(args)
     if args.workload == "sur256":

@@ -33,8 +33,7 @@ Readings where Section 6.2 is silent (listed with the other readings of the pape
   last time level not after t: at 112 cells, t mu / dx^2 = 5017.6, and 5017 steps reproduce
   all four printed errors of that row while 5018 miss two by more than a printed unit); the
   error is (dx^2 sum (u_x - u_x^ex)^2)^(1/2) over the cell centres.  With these, the oracle
-  reproduces every error of Table 2 that was run (75, 112 and 168 cells) to the four printed
-  digits.
+  reproduces all 16 errors of Table 2 (75, 112, 168 and 253 cells) to the four printed digits.
 """
 from __future__ import annotations
 

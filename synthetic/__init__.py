@@ -168,3 +168,20 @@ def taylor_green_3d(n: int):
     u[2] = 0.0
     phi = (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0) / 16.0
     return u, phi, dx
+
+
+def poiseuille_channel(n: int, nx: int | None = None, height: float = 1.0, u_max: float = 1.0,
+                       reynolds: float = 100.0):
+    """Steady Poiseuille profile of the channel test (Section 6.2) at the cell centres.
+
+    n cells across the channel (height L), nx (default n) along it (length nx dx), dx = L / n:
+    u_x = 4 U y (L - y) / L^2, u_y = 0, phi = 8 nu U (nx dx - x) / L^2, nu = U L / Re.
+    Returns (u (2, n, nx), phi (n, nx), dx, nu, u_in) with u_in = u_x at the left side's cells.
+    """
+    nx = n if nx is None else nx
+    dx = height / n
+    nu = u_max * height / reynolds
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(n) + 0.5) * dx, indexing="xy")
+    u = np.stack([4.0 * u_max * Y * (height - Y) / height ** 2, np.zeros_like(Y)])
+    phi = 8.0 * nu * u_max * (nx * dx - X) / height ** 2
+    return u, phi, dx, nu, u[0][:, 0].copy()
