@@ -364,9 +364,45 @@ def tgv3d_history(lat, u, phi, nu, steps, every, torch):
 
 
 # ---------------------------------------------------------------- the two arms
+def run_reference_poiseuille(args):
+    """Reference arm of the channel workload: the oracle's Poiseuille simulation (ghost-cell
+    boundaries of Section 6.2.1) on the host cores, the 75-cell row of Table 2 (four runs)."""
+    import oracle
+    from oracle.poiseuille import Poiseuille
+    orc = oracle.default()
+    rows, nodes, t0 = [], 0, time.perf_counter()
+    for omega_q in (1.0, 1.15):
+        for corrected in (False, True):
+            sim = Poiseuille(orc, 75, omega_q, corrected=corrected)
+            steps = sim.run_to(0.05)
+            nodes += 75 * 75 * steps
+            rows.append({"cells": 75, "omega_q": omega_q, "wall_correction": corrected, "steps": steps,
+                         "l2_error_ux": sim.l2_error_ux(), "table2": TABLE2[(75, omega_q, corrected)]})
+    el = time.perf_counter() - t0
+    value = nodes / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": rows[0]["steps"],
+        "warmup": 0, "ms_per_step": el / (4 * rows[0]["steps"]) * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "Poiseuille channel of Section 6.2 (Table 2), 75-cell row", "storage": "fp64 (oracle)"},
+        "table2": rows,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+                         "sample": "the four 75-cell runs of Table 2 to t = 0.05 (2250 steps each)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
+        return 0
+    if args.workload == "poiseuille":
+        return run_reference_poiseuille(args)
+    if args.workload not in ("dsl2d", "tgv3d"):
+        print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm times the single-lattice workloads "
+                          f"(dsl2d, tgv3d) and the channel; {args.workload} has no oracle arm"}), flush=True)
         return 0
     import oracle
     import synthetic
