@@ -25,7 +25,11 @@ using namespace vlbm;
 
 namespace {
 
-constexpr int kGraphSteps = 64;               // steps captured per CUDA graph (even: parity is kept)
+// Steps captured per CUDA graph, largest first (even: a replay keeps the parity of the levels).
+// Replays run each step about 6 us faster than single launches at 4096^2, so runs shorter than
+// the largest graph replay the smaller ones too.
+constexpr int kGraphSizes = 3;
+constexpr int kGraphSteps[kGraphSizes] = {64, 16, 4};
 constexpr int kStageBlocks = 128;             // first-stage blocks when many partial rows are reduced
 constexpr uint64_t kStateMagic = 0x315F4D424C56ull;  // "VLBM_1"
 
@@ -65,7 +69,7 @@ struct vlbm_handle {
     int kernel_variant = 0;           // 0 auto, 1 generic, 2 vectorised
     int split_lanes = kSplitV2;       // nodes per lane of the 2D split kernel (2 or 4)
     cudaStream_t capture_stream = nullptr;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph[kGraphSizes][2] = {};   // [size][parity of the starting level]
     std::string err;
     Coef<double> kd{};
     Coef<float> kf{};
@@ -219,9 +223,18 @@ static int64_t inv_blocks(const vlbm_handle* h) {
     return std::min<int64_t>(blocks_for(h->d.nodes), (int64_t)h->sm_count * 8);
 }
 
+// Destroy every captured step graph (their kernel parameters changed, or the handle is closed).
+static void drop_graphs(vlbm_handle* h) {
+    for (auto& per_size : h->graph)
+        for (auto& g : per_size)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+}
+
 static void free_all(vlbm_handle* h) {
-    for (int i = 0; i < 2; ++i)
-        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+    drop_graphs(h);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (int i = 0; i < 2; ++i)
         if (h->buf[i]) cudaFree(h->buf[i]);
@@ -566,23 +579,23 @@ static int launch_one_step(vlbm_handle* h, cudaStream_t s, int src) {
     return check_launch(h, "stream-collide");
 }
 
-// Capture kGraphSteps steps starting from buffer `src` on a private stream.
-static int build_graph(vlbm_handle* h, int src) {
+// Capture kGraphSteps[size] steps starting from buffer `src` on a private stream.
+static int build_graph(vlbm_handle* h, int size, int src) {
     if (!h->capture_stream) VLBM_CUDA(h, cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     VLBM_CUDA(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
     int b = src;
     int rc = VLBM_OK;
-    for (int i = 0; i < kGraphSteps; ++i) {
+    for (int i = 0; i < kGraphSteps[size]; ++i) {
         dispatch_step(h, h->capture_stream, b);
         b ^= 1;
     }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->capture_stream, &g);
     if (e != cudaSuccess) return fail(h, VLBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&h->graph[src], g, 0);
+    e = cudaGraphInstantiate(&h->graph[size][src], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        h->graph[src] = nullptr;
+        h->graph[size][src] = nullptr;
         rc = fail(h, VLBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     }
     return rc;
@@ -595,15 +608,17 @@ extern "C" int vlbm_step(vlbm_handle* h, int64_t nsteps, int32_t flags) {
     int64_t left = nsteps;
     const bool graphs = !(flags & VLBM_STEP_NO_GRAPH);
     while (left > 0) {
-        if (graphs && left >= kGraphSteps) {
-            if (!h->graph[h->cur]) {
-                int rc = build_graph(h, h->cur);
+        int size = 0;
+        while (size < kGraphSizes && left < kGraphSteps[size]) ++size;
+        if (graphs && size < kGraphSizes) {
+            if (!h->graph[size][h->cur]) {
+                int rc = build_graph(h, size, h->cur);
                 if (rc) return rc;
             }
-            VLBM_CUDA(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
-            h->launches += (int64_t)kGraphSteps * launches_per_step(h);
-            h->step += kGraphSteps;
-            left -= kGraphSteps;   // kGraphSteps is even: parity unchanged
+            VLBM_CUDA(h, cudaGraphLaunch(h->graph[size][h->cur], h->stream));
+            h->launches += (int64_t)kGraphSteps[size] * launches_per_step(h);
+            h->step += kGraphSteps[size];
+            left -= kGraphSteps[size];   // an even count: parity unchanged
         } else {
             int rc = launch_one_step(h, h->stream, h->cur);
             if (rc) return rc;
@@ -628,11 +643,7 @@ extern "C" int vlbm_set_boundary(vlbm_handle* h, const vlbm_boundary* bc) {
     if (!h || !bc) return VLBM_EINVAL;
     if (bc->kind == VLBM_BC_PERIODIC) {
         if (h->bc_kind != VLBM_BC_PERIODIC) {
-            for (int i = 0; i < 2; ++i)
-                if (h->graph[i]) {
-                    cudaGraphExecDestroy(h->graph[i]);
-                    h->graph[i] = nullptr;
-                }
+            drop_graphs(h);
         }
         h->bc_kind = VLBM_BC_PERIODIC;
         return VLBM_OK;
@@ -651,11 +662,7 @@ extern "C" int vlbm_set_boundary(vlbm_handle* h, const vlbm_boundary* bc) {
     if (!h->bc_ghost) VLBM_CUDA(h, cudaMalloc(&h->bc_ghost, (size_t)4 * 3 * n_ghost * es));
     VLBM_CUDA(h, cudaMemcpyAsync(h->bc_u_in, bc->u_in, (size_t)ny * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     VLBM_CUDA(h, cudaStreamSynchronize(h->stream));
-    for (int i = 0; i < 2; ++i)
-        if (h->graph[i]) {
-            cudaGraphExecDestroy(h->graph[i]);
-            h->graph[i] = nullptr;
-        }
+    drop_graphs(h);
     h->bc_kind = VLBM_BC_CHANNEL;
     h->bc_correction = bc->wall_correction ? 1 : 0;
     h->bc_phi_out = bc->phi_out;
@@ -930,31 +937,19 @@ extern "C" int vlbm_set_option(vlbm_handle* h, int32_t key, int64_t value) {
             if (value < 0 || value > 2) return VLBM_EINVAL;
             if (value == 2 && h->p.n[0] % vec_width(h) != 0) return VLBM_EINVAL;
             h->kernel_variant = (int)value;
-            for (int i = 0; i < 2; ++i)
-                if (h->graph[i]) {
-                    cudaGraphExecDestroy(h->graph[i]);
-                    h->graph[i] = nullptr;
-                }
+            drop_graphs(h);
             return VLBM_OK;
         case VLBM_OPT_ROUNDING_16:
             if (value != 0 && value != 1) return VLBM_EINVAL;
             if (h->p.precision != VLBM_FP16_SHIFTED && h->p.precision != VLBM_BF16_SHIFTED) return VLBM_EINVAL;
             h->kf.sr16 = (int)value;   // a kernel parameter: captured graphs are rebuilt
-            for (int i = 0; i < 2; ++i)
-                if (h->graph[i]) {
-                    cudaGraphExecDestroy(h->graph[i]);
-                    h->graph[i] = nullptr;
-                }
+            drop_graphs(h);
             return VLBM_OK;
         case VLBM_OPT_SPLIT_LANES:
             if (value != 2 && value != 4) return VLBM_EINVAL;
             if (h->p.dim == 2 && h->p.n[0] % value != 0 && h->kernel_variant == 2) return VLBM_EINVAL;
             h->split_lanes = (int)value;
-            for (int i = 0; i < 2; ++i)
-                if (h->graph[i]) {
-                    cudaGraphExecDestroy(h->graph[i]);
-                    h->graph[i] = nullptr;
-                }
+            drop_graphs(h);
             return VLBM_OK;
         default: return VLBM_EINVAL;
     }
